@@ -1,0 +1,205 @@
+/*
+ * c2.h -- C ABI of the GB300 (sm_103a) Cluster-and-Conquer KNN-graph library.
+ *
+ * Cluster-and-Conquer (C^2), Giakkoupis, Kermarrec, Ruas & Taiani,
+ * arXiv 2010.11497.  The library builds an approximate k-nearest-neighbour
+ * graph of users described by binary item profiles, under the Jaccard
+ * similarity J(u,v) = |P_u n P_v| / |P_u u P_v| (Section II-A), in three steps:
+ *
+ *   1. clustering with t FastRandomHash functions, H_i(u) = min h_i(x) over
+ *      the user's items (Eq. 3, Algorithm 1), with recursive splitting of
+ *      clusters larger than N (Section II-D);
+ *   2. a KNN graph inside every cluster, by brute force for clusters with
+ *      fewer than `greedy_threshold` users and by greedy neighbours-of-
+ *      neighbours refinement otherwise (Algorithm 2, Section II-F);
+ *   3. a merge of each user's t cluster-local lists into one top-k list
+ *      (Algorithm 3).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Pointers named d_* are DEVICE pointers (CUDA global memory of the current
+ *   device); pointers named h_* are HOST pointers.  All are owned by the
+ *   caller and only borrowed until the work queued on `stream` completes.
+ * - Profiles are CSR: d_csr_ptr[n_users+1] (int32, d_csr_ptr[0] == 0,
+ *   non-decreasing) and d_csr_items[nnz] (int32 item ids in [0, n_items),
+ *   strictly increasing within a row: profiles are sets).
+ * - Every function is asynchronous on `stream` unless stated otherwise.  The
+ *   library allocates no device memory: scratch space comes from the caller's
+ *   workspace `d_ws` of at least c2_workspace_size() bytes (256-byte aligned).
+ * - Host-detected argument errors are returned at once.  Errors detected on
+ *   the device (an invalid CSR, a bounded wait that ran out) are recorded in
+ *   a status word inside the workspace; read it with c2_get_status().  Once a
+ *   device error is recorded, later kernels of the same workspace return
+ *   without touching memory.
+ * - Neighbour lists are rows of k slots: id, |P_u n P_v| (inter) and
+ *   |P_u u P_v| (union), sorted best first.  "Better" compares Jaccard values
+ *   exactly by integer cross-multiplication, equal values going to the lower
+ *   user id.  Users with no common item are never listed; unused slots hold
+ *   id -1 and counts 0.  Users, items and buckets are 0-based.
+ * - Limits: 1 <= k <= 32, 1 <= t <= 64, 1 <= b <= 65536, N >= 2,
+ *   nnz < 2^31, t * n_users < 2^31, every profile shorter than 65536 items.
+ *   Anything else returns C2_ERR_UNSUPPORTED (profile lengths: on the device).
+ */
+#ifndef C2_H
+#define C2_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* c2_stream_t; /* a cudaStream_t; NULL = legacy default stream */
+
+typedef enum {
+  C2_OK = 0,
+  C2_ERR_INVALID_ARG = 1,  /* a NULL pointer, a negative size, k/t/b/N out of range      */
+  C2_ERR_INVALID_CSR = 2,  /* profiles are not sorted sets of valid item ids            */
+  C2_ERR_UNSUPPORTED = 3,  /* a size beyond the documented limits                        */
+  C2_ERR_WORKSPACE = 4,    /* d_ws NULL, misaligned or smaller than c2_workspace_size()  */
+  C2_ERR_CUDA = 5,         /* a CUDA runtime call failed                                 */
+  C2_ERR_TIMEOUT = 6,      /* a bounded device-side wait gave up                         */
+  C2_ERR_QUALITY_FALLBACK = 7 /* informational: the learned proposer fell back to FRH    */
+} c2_status;
+
+/* Strategy used to count common items inside clusters (Step 2). */
+enum {
+  C2_STRATEGY_AUTO = -1,   /* autotuned table, per (cluster size, density) bucket         */
+  C2_STRATEGY_MERGE = 0,   /* sorted-list merge, one warp per query user                  */
+  C2_STRATEGY_TABLE32 = 1, /* shared-memory item table, 32 query users per block          */
+  C2_STRATEGY_TABLE64 = 2  /* shared-memory item table, 64 query users per block          */
+};
+
+typedef struct {
+  int32_t greedy_threshold; /* brute force iff |C| < greedy_threshold (Algorithm 2);
+                               <= 0 selects the paper's rho*k^2 with rho = 5 (Section II-F) */
+  int32_t greedy_rounds;    /* synchronous refinement rounds; < 0 selects 10               */
+  int32_t greedy_random;    /* extra random candidates per user and round; default 0       */
+  int32_t strategy;         /* C2_STRATEGY_*                                               */
+  const int32_t* d_hash_table; /* optional explicit generative hashes h_i(x), device int32
+                               [t][n_items] with values in [0, b); NULL = the library's
+                               seeded hash (a test hook for hand-worked examples)          */
+  int64_t gram_budget_bytes;/* cap on the intersection-count matrices of greedy clusters
+                               held at once; <= 0 selects 2 GiB                            */
+  int32_t reserved[8];      /* must be zero                                                */
+} c2_options;
+
+/* Run statistics, filled by c2_get_stats(). */
+typedef struct {
+  int64_t pairs;            /* similarity evaluations of the method: M(M-1)/2 per
+                               brute-force cluster plus the greedy candidate evaluations   */
+  int64_t gram_pairs;       /* intersection counts computed for greedy clusters            */
+  int32_t n_clusters;       /* clusters after splitting, all t functions                   */
+  int32_t split_levels;     /* recursive-split levels that found an oversized cluster      */
+  int32_t n_greedy_clusters;
+  int32_t max_cluster;      /* largest cluster                                             */
+  int32_t max_profile;      /* longest profile                                             */
+  int32_t reserved[7];
+} c2_stats;
+
+/* Fills *opt with the defaults described above.  Never fails. */
+void c2_default_options(c2_options* opt);
+
+/* Human-readable name of a status code (static storage). */
+const char* c2_status_string(c2_status s);
+
+/* Bytes of workspace the entry points below need for these sizes (the
+ * maximum over all of them).  Returns 0 on invalid sizes.  Host only. */
+size_t c2_workspace_size(int32_t n_users, int64_t nnz, int32_t n_items, int32_t k, int32_t t,
+                         int32_t b, int32_t N, const c2_options* opt);
+
+/* Step 1 (Algorithm 1 + recursive split of Section II-D).  For each hash
+ * function i < t and user u, cluster_of[i*n_users+u] is the number of u's
+ * final cluster.  Clusters are numbered by function, then by their path of
+ * hash keys (key, then each split key) with a split cluster's residual --
+ * the users left in it -- before its sub-clusters; members are listed in
+ * increasing user id.  The residual of a split is never split again.
+ * Outputs (device, caller-allocated):
+ *   d_cluster_of[t*n_users], d_cptr[t*n_users+1] (cluster offsets into
+ *   d_cusers; entries past *d_n_clusters are left undefined),
+ *   d_cusers[t*n_users], d_n_clusters (one int32),
+ *   d_cmeta (optional, [t*n_users][4]: function, split depth, residual flag,
+ *   last hash key of the cluster's path).
+ * This call synchronises `stream` once per split level to read the number of
+ * oversized clusters. */
+c2_status c2_frh_cluster(const int32_t* d_csr_ptr, const int32_t* d_csr_items, int32_t n_users,
+                         int32_t n_items, int32_t t, int32_t b, int32_t N, uint64_t seed,
+                         const c2_options* opt, int32_t* d_cluster_of, int32_t* d_cptr,
+                         int32_t* d_cusers, int32_t* d_n_clusters, int32_t* d_cmeta, void* d_ws,
+                         size_t ws_bytes, c2_stream_t stream);
+
+/* Step 2 (Algorithm 2): the KNN graph inside every cluster given by
+ * (d_cptr, d_cusers, d_n_clusters) as produced by c2_frh_cluster.  Outputs
+ * one row of k per cluster slot s (a position in d_cusers):
+ * d_loc_id/d_loc_inter/d_loc_union[t*n_users][k].
+ * Greedy clusters start from a random k-graph drawn with Philox4x32-10
+ * (key = seed, counter = (cluster number, member index, round, draw)) and
+ * refine every member's list with its neighbours' neighbours for
+ * greedy_rounds synchronous rounds.  Synchronises `stream` once to size the
+ * greedy phase. */
+c2_status c2_cluster_knn(const int32_t* d_csr_ptr, const int32_t* d_csr_items, int32_t n_users,
+                         int32_t n_items, int32_t t, const int32_t* d_cptr,
+                         const int32_t* d_cusers, const int32_t* d_n_clusters, int32_t k,
+                         uint64_t seed, const c2_options* opt, int32_t* d_loc_id,
+                         int32_t* d_loc_inter, int32_t* d_loc_union, void* d_ws,
+                         size_t ws_bytes, c2_stream_t stream);
+
+/* Step 3 (Algorithm 3): per user, the k best distinct neighbours found in its
+ * t cluster-local rows.  d_cusers[t*n_users] maps slots to users (each
+ * function's slots are one permutation of the users).  Outputs
+ * d_nbr_id/d_nbr_inter/d_nbr_union[n_users][k]. */
+c2_status c2_merge_topk(const int32_t* d_cusers, int32_t n_users, int32_t t, int32_t k,
+                        const int32_t* d_loc_id, const int32_t* d_loc_inter,
+                        const int32_t* d_loc_union, int32_t* d_nbr_id, int32_t* d_nbr_inter,
+                        int32_t* d_nbr_union, void* d_ws, size_t ws_bytes, c2_stream_t stream);
+
+/* The whole method: Steps 1-3.  Outputs d_nbr_*[n_users][k]. */
+c2_status c2_build_knn_graph(const int32_t* d_csr_ptr, const int32_t* d_csr_items,
+                             int32_t n_users, int32_t n_items, int32_t k, int32_t t, int32_t b,
+                             int32_t N, uint64_t seed, const c2_options* opt, int32_t* d_nbr_id,
+                             int32_t* d_nbr_inter, int32_t* d_nbr_union, void* d_ws,
+                             size_t ws_bytes, c2_stream_t stream);
+
+/* The whole method from HOST buffers: copies the profiles to the device
+ * workspace, builds the graph and copies the three [n_users][k] result arrays
+ * back.  h_* buffers should be pinned for full copy speed.  Synchronous: it
+ * returns after the results are in host memory.  The workspace must hold
+ * c2_workspace_size_host() bytes. */
+size_t c2_workspace_size_host(int32_t n_users, int64_t nnz, int32_t n_items, int32_t k,
+                              int32_t t, int32_t b, int32_t N, const c2_options* opt);
+c2_status c2_build_knn_graph_host(const int32_t* h_csr_ptr, const int32_t* h_csr_items,
+                                  int32_t n_users, int32_t n_items, int32_t k, int32_t t,
+                                  int32_t b, int32_t N, uint64_t seed, const c2_options* opt,
+                                  int32_t* h_nbr_id, int32_t* h_nbr_inter, int32_t* h_nbr_union,
+                                  void* d_ws, size_t ws_bytes, c2_stream_t stream);
+
+/* Exact KNN by brute force (the judge of Section IV-B): for each query user
+ * (d_queries[n_queries], or every user when d_queries is NULL) the k best of
+ * all other users.  Outputs d_nbr_*[rows][k]. */
+c2_status c2_bruteforce_knn(const int32_t* d_csr_ptr, const int32_t* d_csr_items,
+                            int32_t n_users, int32_t n_items, int32_t k,
+                            const int32_t* d_queries, int32_t n_queries, int32_t* d_nbr_id,
+                            int32_t* d_nbr_inter, int32_t* d_nbr_union, void* d_ws,
+                            size_t ws_bytes, c2_stream_t stream);
+
+/* Eq. 1: average similarity of the rows d_nbr_inter/d_nbr_union[rows][k],
+ * sum of J over filled slots divided by k*rows, accumulated in FP64 in row
+ * order.  Writes one double to d_out. */
+c2_status c2_avg_sim(const int32_t* d_nbr_inter, const int32_t* d_nbr_union, int32_t rows,
+                     int32_t k, double* d_out, void* d_ws, size_t ws_bytes, c2_stream_t stream);
+
+/* Synchronises `stream` and returns the device status word of d_ws. */
+c2_status c2_get_status(const void* d_ws, c2_stream_t stream);
+
+/* Synchronises `stream` and copies the run statistics of d_ws to *out. */
+c2_status c2_get_stats(const void* d_ws, c2_stream_t stream, c2_stats* out);
+
+/* Clears the device status word and statistics of d_ws (asynchronous). */
+c2_status c2_reset_status(void* d_ws, c2_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* C2_H */

@@ -52,8 +52,8 @@ def lib():
                                          C.c_int32, C.c_uint64, C.c_void_p, I32P, I32P, I32P, I32P,
                                          C.c_void_p]
         L.oracle_cluster_knn.argtypes = [I32P, I32P, C.c_int32, I32P, I32P, C.c_int32, C.c_int32,
-                                         C.c_uint64, C.c_int32, C.c_int32, C.c_int32, I32P, I32P,
-                                         I32P, I64P]
+                                         C.c_uint64, C.c_int32, C.c_int32, C.c_int32, C.c_void_p,
+                                         I32P, I32P, I32P, I64P]
         L.oracle_merge_topk.argtypes = [I32P, I32P, C.c_int32, C.c_int32, C.c_int32, I32P, I32P,
                                         I32P, I32P, I32P, I32P]
         L.oracle_build.argtypes = [I32P, I32P, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
@@ -124,17 +124,21 @@ def frh_cluster(ptr, items, m, t, b, N, seed, htab=None):
 
 
 def cluster_knn(ptr, items, cptr, cusers, k, seed, greedy_threshold, greedy_rounds=10,
-                greedy_random=0):
+                greedy_random=0, only=None):
+    """Local KNN rows [t*n, k] per slot; `only` = bool mask of clusters to compute."""
     ptr, items, cptr, cusers = _i32(ptr), _i32(items), _i32(cptr), _i32(cusers)
     n = ptr.size - 1
     nc = cptr.size - 1
     S = cusers.size
-    li = np.zeros((S, k), np.int32)
+    li = np.full((S, k), -1, np.int32)
     lc = np.zeros((S, k), np.int32)
     lu = np.zeros((S, k), np.int32)
     pairs = np.zeros(1, np.int64)
+    mask = None if only is None else np.ascontiguousarray(only, dtype=np.uint8)
     lib().oracle_cluster_knn(ptr, items, n, cptr, cusers, nc, k, seed, greedy_threshold,
-                             greedy_rounds, greedy_random, li, lc, lu, pairs)
+                             greedy_rounds, greedy_random,
+                             None if mask is None else mask.ctypes.data_as(C.c_void_p),
+                             li, lc, lu, pairs)
     return li, lc, lu, int(pairs[0])
 
 

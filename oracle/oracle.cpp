@@ -373,14 +373,18 @@ int oracle_frh_cluster(const int32_t* ptr, const int32_t* items, int32_t n, int3
 
 // Step 2: local KNN of every cluster (Algorithm 2).  Brute force iff
 // |C| < greedy_threshold.  Output rows are per cluster slot (position in
-// cusers), [t*n][k], sorted by R8 and padded with id -1.
+// cusers), [t*n][k], sorted by R8 and padded with id -1.  `only` (optional,
+// one byte per cluster) restricts the work to the marked clusters; rows of
+// the others are left untouched.
 int oracle_cluster_knn(const int32_t* ptr, const int32_t* items, int32_t n, const int32_t* cptr,
                        const int32_t* cusers, int32_t n_clusters, int32_t k, uint64_t seed,
                        int32_t greedy_threshold, int32_t greedy_rounds, int32_t greedy_random,
-                       int32_t* loc_id, int32_t* loc_inter, int32_t* loc_union, int64_t* pairs_out) {
+                       const uint8_t* only, int32_t* loc_id, int32_t* loc_inter,
+                       int32_t* loc_union, int64_t* pairs_out) {
   Csr P{ptr, items, n};
   int64_t pairs = 0;
   for (int32_t c = 0; c < n_clusters; ++c) {
+    if (only && !only[c]) continue;
     std::vector<int32_t> mem(cusers + cptr[c], cusers + cptr[c + 1]);
     std::vector<std::vector<Nbr>> lists;
     if ((int32_t)mem.size() < greedy_threshold || mem.size() < 2)
@@ -430,7 +434,8 @@ int oracle_build(const int32_t* ptr, const int32_t* items, int32_t n, int32_t m,
   if (rc) return rc;
   std::vector<int32_t> li((size_t)t * n * k), lc((size_t)t * n * k), lu((size_t)t * n * k);
   oracle_cluster_knn(ptr, items, n, cptr.data(), cusers.data(), nc, k, seed, greedy_threshold,
-                     greedy_rounds, greedy_random, li.data(), lc.data(), lu.data(), pairs_out);
+                     greedy_rounds, greedy_random, nullptr, li.data(), lc.data(), lu.data(),
+                     pairs_out);
   return oracle_merge_topk(cptr.data(), cusers.data(), nc, n, k, li.data(), lc.data(), lu.data(),
                            nbr_id, nbr_inter, nbr_union);
 }

@@ -1,0 +1,282 @@
+"""ctypes binding of libc2 (include/c2.h): argument marshalling only.
+
+Every step of the method runs in libc2's CUDA kernels.  PyTorch provides the
+device memory (tensors) and the stream; this module passes their raw pointers
+through the C ABI with the same function names.  There is no fallback: if
+libc2.so is missing or a call fails, an exception is raised.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+LIB_PATH = os.path.join(HERE, "libc2.so")
+HEADER = os.path.join(ROOT, "include", "c2.h")
+
+STRATEGY_AUTO, STRATEGY_MERGE, STRATEGY_TABLE32, STRATEGY_TABLE64 = -1, 0, 1, 2
+STATUS = {0: "C2_OK", 1: "C2_ERR_INVALID_ARG", 2: "C2_ERR_INVALID_CSR", 3: "C2_ERR_UNSUPPORTED",
+          4: "C2_ERR_WORKSPACE", 5: "C2_ERR_CUDA", 6: "C2_ERR_TIMEOUT",
+          7: "C2_ERR_QUALITY_FALLBACK"}
+
+
+class C2Error(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {STATUS.get(code, code)}")
+
+
+class Options(C.Structure):
+    _fields_ = [("greedy_threshold", C.c_int32), ("greedy_rounds", C.c_int32),
+                ("greedy_random", C.c_int32), ("strategy", C.c_int32),
+                ("d_hash_table", C.c_void_p), ("gram_budget_bytes", C.c_int64),
+                ("reserved", C.c_int32 * 8)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("pairs", C.c_int64), ("gram_pairs", C.c_int64), ("n_clusters", C.c_int32),
+                ("split_levels", C.c_int32), ("n_greedy_clusters", C.c_int32),
+                ("max_cluster", C.c_int32), ("max_profile", C.c_int32),
+                ("reserved", C.c_int32 * 7)]
+
+
+_lib = None
+P = C.c_void_p
+I32, I64, U64, SZ = C.c_int32, C.c_int64, C.c_uint64, C.c_size_t
+
+_SIGS = {
+    "c2_default_options": (None, [C.POINTER(Options)]),
+    "c2_status_string": (C.c_char_p, [C.c_int]),
+    "c2_workspace_size": (SZ, [I32, I64, I32, I32, I32, I32, I32, C.POINTER(Options)]),
+    "c2_workspace_size_host": (SZ, [I32, I64, I32, I32, I32, I32, I32, C.POINTER(Options)]),
+    "c2_frh_cluster": (C.c_int, [P, P, I32, I32, I32, I32, I32, U64, C.POINTER(Options), P, P, P,
+                                 P, P, P, SZ, P]),
+    "c2_cluster_knn": (C.c_int, [P, P, I32, I32, I32, P, P, P, I32, U64, C.POINTER(Options), P, P,
+                                 P, P, SZ, P]),
+    "c2_merge_topk": (C.c_int, [P, I32, I32, I32, P, P, P, P, P, P, P, SZ, P]),
+    "c2_build_knn_graph": (C.c_int, [P, P, I32, I32, I32, I32, I32, I32, U64,
+                                     C.POINTER(Options), P, P, P, P, SZ, P]),
+    "c2_build_knn_graph_host": (C.c_int, [P, P, I32, I32, I32, I32, I32, I32, U64,
+                                          C.POINTER(Options), P, P, P, P, SZ, P]),
+    "c2_bruteforce_knn": (C.c_int, [P, P, I32, I32, I32, P, I32, P, P, P, P, SZ, P]),
+    "c2_avg_sim": (C.c_int, [P, P, I32, I32, P, P, SZ, P]),
+    "c2_get_status": (C.c_int, [P, P]),
+    "c2_get_stats": (C.c_int, [P, P, C.POINTER(Stats)]),
+    "c2_reset_status": (C.c_int, [P, P]),
+}
+
+
+def header_functions() -> list[str]:
+    """Names of the functions include/c2.h declares."""
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(c2_[a-z0-9_]+)\s*\(", txt)))
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def options(greedy_threshold=0, greedy_rounds=-1, greedy_random=0, strategy=STRATEGY_AUTO,
+            hash_table: torch.Tensor | None = None, gram_budget_bytes=0) -> Options:
+    o = Options()
+    lib().c2_default_options(C.byref(o))
+    o.greedy_threshold = greedy_threshold
+    o.greedy_rounds = greedy_rounds
+    o.greedy_random = greedy_random
+    o.strategy = strategy
+    o.d_hash_table = None if hash_table is None else hash_table.data_ptr()
+    o.gram_budget_bytes = gram_budget_bytes
+    o._keep = hash_table      # keep the table alive with the options
+    return o
+
+
+def _ptr(t):
+    return None if t is None else t.data_ptr()
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _check(rc, where):
+    if rc != 0:
+        raise C2Error(rc, where)
+
+
+def _dev_i32(x, device):
+    if isinstance(x, np.ndarray):
+        x = torch.from_numpy(np.ascontiguousarray(x, dtype=np.int32))
+    return x.to(device=device, dtype=torch.int32).contiguous()
+
+
+def workspace_size(n_users, nnz, n_items, k, t, b, N, opts=None) -> int:
+    o = opts if opts is not None else options()
+    sz = lib().c2_workspace_size(n_users, nnz, n_items, k, t, b, N, C.byref(o))
+    if sz == 0:
+        raise C2Error(1, "c2_workspace_size")
+    return int(sz)
+
+
+def workspace(nbytes: int, device="cuda") -> torch.Tensor:
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+# ------------------------------------------------------------------ entry points
+def c2_frh_cluster(ptr, items, n_items, t, b, N, seed, opts=None, ws=None, stream=None):
+    """Step 1.  Returns dict(cluster_of[t,n], cptr[nc+1], cusers[t*n], n_clusters, cmeta[nc,4])."""
+    dev = ptr.device
+    n = ptr.numel() - 1
+    o = opts if opts is not None else options()
+    if ws is None:
+        ws = workspace(workspace_size(n, items.numel(), n_items, 1, t, b, N, o), dev)
+    S = t * n
+    cluster_of = torch.empty((t, n), dtype=torch.int32, device=dev)
+    cptr = torch.empty(S + 1, dtype=torch.int32, device=dev)
+    cusers = torch.empty(max(S, 1), dtype=torch.int32, device=dev)
+    ncl = torch.zeros(1, dtype=torch.int32, device=dev)
+    cmeta = torch.empty((max(S, 1), 4), dtype=torch.int32, device=dev)
+    rc = lib().c2_frh_cluster(_ptr(ptr), _ptr(items), n, n_items, t, b, N, seed, C.byref(o),
+                              _ptr(cluster_of), _ptr(cptr), _ptr(cusers), _ptr(ncl), _ptr(cmeta),
+                              _ptr(ws), ws.numel(), _stream(stream))
+    _check(rc, "c2_frh_cluster")
+    _check(c2_get_status(ws, stream), "c2_frh_cluster (device)")
+    nc = int(ncl.item())
+    return dict(cluster_of=cluster_of, cptr=cptr[:nc + 1], cusers=cusers[:S], n_clusters=nc,
+                cmeta=cmeta[:nc], n_clusters_dev=ncl, cptr_full=cptr)
+
+
+def c2_cluster_knn(ptr, items, n_items, t, cptr, cusers, n_clusters_dev, k, seed, opts=None,
+                   ws=None, stream=None):
+    """Step 2.  Returns (loc_id, loc_inter, loc_union) of shape [t*n, k]."""
+    dev = ptr.device
+    n = ptr.numel() - 1
+    o = opts if opts is not None else options()
+    if ws is None:
+        ws = workspace(workspace_size(n, items.numel(), n_items, k, t, 2, 2, o), dev)
+    S = t * n
+    out = [torch.empty((max(S, 1), k), dtype=torch.int32, device=dev) for _ in range(3)]
+    rc = lib().c2_cluster_knn(_ptr(ptr), _ptr(items), n, n_items, t, _ptr(cptr), _ptr(cusers),
+                              _ptr(n_clusters_dev), k, seed, C.byref(o), *[_ptr(x) for x in out],
+                              _ptr(ws), ws.numel(), _stream(stream))
+    _check(rc, "c2_cluster_knn")
+    return tuple(x[:S] for x in out)
+
+
+def c2_merge_topk(cusers, n_users, t, k, loc_id, loc_inter, loc_union, ws=None, stream=None):
+    dev = cusers.device
+    if ws is None:
+        ws = workspace(workspace_size(n_users, 0, 0, k, t, 2, 2), dev)
+    out = [torch.empty((n_users, k), dtype=torch.int32, device=dev) for _ in range(3)]
+    rc = lib().c2_merge_topk(_ptr(cusers), n_users, t, k, _ptr(loc_id), _ptr(loc_inter),
+                             _ptr(loc_union), *[_ptr(x) for x in out], _ptr(ws), ws.numel(),
+                             _stream(stream))
+    _check(rc, "c2_merge_topk")
+    return tuple(out)
+
+
+def c2_build_knn_graph(ptr, items, n_items, k, t, b, N, seed, opts=None, ws=None, out=None,
+                       stream=None, check=True):
+    """The whole method.  Returns (nbr_id, nbr_inter, nbr_union) of shape [n, k]."""
+    dev = ptr.device
+    n = ptr.numel() - 1
+    o = opts if opts is not None else options()
+    if ws is None:
+        ws = workspace(workspace_size(n, items.numel(), n_items, k, t, b, N, o), dev)
+    if out is None:
+        out = [torch.empty((n, k), dtype=torch.int32, device=dev) for _ in range(3)]
+    rc = lib().c2_build_knn_graph(_ptr(ptr), _ptr(items), n, n_items, k, t, b, N, seed,
+                                  C.byref(o), *[_ptr(x) for x in out], _ptr(ws), ws.numel(),
+                                  _stream(stream))
+    _check(rc, "c2_build_knn_graph")
+    if check:
+        _check(c2_get_status(ws, stream), "c2_build_knn_graph (device)")
+    return tuple(out)
+
+
+def workspace_size_host(n_users, nnz, n_items, k, t, b, N, opts=None) -> int:
+    o = opts if opts is not None else options()
+    sz = lib().c2_workspace_size_host(n_users, nnz, n_items, k, t, b, N, C.byref(o))
+    if sz == 0:
+        raise C2Error(1, "c2_workspace_size_host")
+    return int(sz)
+
+
+def c2_build_knn_graph_host(h_ptr, h_items, n_items, k, t, b, N, seed, opts=None, ws=None,
+                            out=None, stream=None):
+    """Whole method from host (ideally pinned) CPU tensors; results land in host tensors."""
+    n = h_ptr.numel() - 1
+    o = opts if opts is not None else options()
+    if ws is None:
+        ws = workspace(workspace_size_host(n, h_items.numel(), n_items, k, t, b, N, o))
+    if out is None:
+        out = [torch.empty((n, k), dtype=torch.int32).pin_memory() for _ in range(3)]
+    rc = lib().c2_build_knn_graph_host(_ptr(h_ptr), _ptr(h_items), n, n_items, k, t, b, N, seed,
+                                       C.byref(o), *[_ptr(x) for x in out], _ptr(ws), ws.numel(),
+                                       _stream(stream))
+    _check(rc, "c2_build_knn_graph_host")
+    return tuple(out)
+
+
+def c2_bruteforce_knn(ptr, items, n_items, k, queries=None, ws=None, stream=None):
+    dev = ptr.device
+    n = ptr.numel() - 1
+    rows = n if queries is None else queries.numel()
+    if ws is None:
+        ws = workspace(workspace_size(n, items.numel(), n_items, k, 1, 1, 2), dev)
+    out = [torch.empty((rows, k), dtype=torch.int32, device=dev) for _ in range(3)]
+    rc = lib().c2_bruteforce_knn(_ptr(ptr), _ptr(items), n, n_items, k, _ptr(queries),
+                                 rows if queries is not None else 0, *[_ptr(x) for x in out],
+                                 _ptr(ws), ws.numel(), _stream(stream))
+    _check(rc, "c2_bruteforce_knn")
+    _check(c2_get_status(ws, stream), "c2_bruteforce_knn (device)")
+    return tuple(out)
+
+
+def c2_avg_sim(nbr_inter, nbr_union, ws=None, stream=None) -> float:
+    dev = nbr_inter.device
+    rows, k = nbr_inter.shape
+    if ws is None:
+        ws = workspace(workspace_size(1, 0, 0, k, 1, 1, 2), dev)
+    out = torch.zeros(1, dtype=torch.float64, device=dev)
+    rc = lib().c2_avg_sim(_ptr(nbr_inter), _ptr(nbr_union), rows, k, _ptr(out), _ptr(ws),
+                          ws.numel(), _stream(stream))
+    _check(rc, "c2_avg_sim")
+    return float(out.item())
+
+
+def c2_get_status(ws, stream=None) -> int:
+    return int(lib().c2_get_status(_ptr(ws), _stream(stream)))
+
+
+def c2_get_stats(ws, stream=None) -> dict:
+    s = Stats()
+    _check(lib().c2_get_stats(_ptr(ws), _stream(stream), C.byref(s)), "c2_get_stats")
+    return dict(pairs=s.pairs, gram_pairs=s.gram_pairs, n_clusters=s.n_clusters,
+                split_levels=s.split_levels, n_greedy_clusters=s.n_greedy_clusters,
+                max_cluster=s.max_cluster, max_profile=s.max_profile)
+
+
+def c2_reset_status(ws, stream=None):
+    _check(lib().c2_reset_status(_ptr(ws), _stream(stream)), "c2_reset_status")
+
+
+def c2_status_string(code: int) -> str:
+    return lib().c2_status_string(code).decode()

@@ -1,0 +1,232 @@
+// Internal declarations of the sm_103a Cluster-and-Conquer library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/c2.h"
+
+namespace c2 {
+
+constexpr int kMaxK = 32;
+constexpr int kMaxT = 64;
+constexpr int kMaxB = 65536;
+constexpr int kMaxProfile = 65535;
+
+// ---------------------------------------------------------------- device header
+// First 256 bytes of every workspace: the device status word and run counters.
+struct DevHeader {
+  int32_t status;              // first device-detected c2_status (0 = OK)
+  int32_t n_labels;            // labels (clusters) of the current split level
+  int32_t n_oversized;         // oversized labels found at the current level
+  int32_t split_levels;
+  int32_t max_profile;
+  int32_t max_cluster;
+  int32_t n_greedy;            // greedy clusters
+  int32_t n_work;              // table work items
+  unsigned long long pairs;    // method pair evaluations
+  unsigned long long gram_pairs;
+  unsigned long long greedy_gram_elems;  // sum of M*M over greedy clusters
+  unsigned int work_counter[8];  // persistent-kernel work counters
+  int32_t pad[26];
+};
+static_assert(sizeof(DevHeader) <= 256, "header must fit 256 bytes");
+
+__device__ __forceinline__ bool dev_failed(const DevHeader* h) {
+  return *(volatile const int32_t*)&h->status != 0;
+}
+__device__ __forceinline__ void dev_fail(DevHeader* h, int code) { atomicCAS(&h->status, 0, code); }
+
+// ---------------------------------------------------------------- label flags
+// Per-cluster metadata during splitting: terminal | residual | fn | depth.
+__host__ __device__ __forceinline__ int32_t lf_pack(int terminal, int residual, int fn, int depth) {
+  return (terminal & 1) | ((residual & 1) << 1) | ((fn & 63) << 2) | (depth << 8);
+}
+__host__ __device__ __forceinline__ int lf_terminal(int32_t f) { return f & 1; }
+__host__ __device__ __forceinline__ int lf_residual(int32_t f) { return (f >> 1) & 1; }
+__host__ __device__ __forceinline__ int lf_fn(int32_t f) { return (f >> 2) & 63; }
+__host__ __device__ __forceinline__ int lf_depth(int32_t f) { return f >> 8; }
+
+// ---------------------------------------------------------------- workspace
+// Offsets (bytes) of every scratch array inside the caller's workspace.  The
+// same function sizes the workspace (base 0) and binds it (real base).
+struct Ws {
+  char* base = nullptr;
+  size_t top = 0;
+  template <class T>
+  T* take(size_t count) {
+    size_t off = (top + 255) & ~size_t(255);
+    top = off + count * sizeof(T);
+    return reinterpret_cast<T*>(base + off);
+  }
+};
+
+struct Sizes {
+  int32_t n, m, k, t, b, N;
+  int64_t nnz;
+  int64_t S;           // t * n slots
+  int32_t tp;          // t rounded up to a multiple of 8 (hash-table row)
+  int64_t omax;        // max oversized clusters in one split level
+  int64_t gram_budget; // bytes
+};
+
+struct ClusterWs {
+  DevHeader* hdr;
+  uint16_t* htab;          // [m][tp]
+  int32_t* key;            // [S] level-0 keys, then next keys
+  int32_t *lab, *lab2;     // [S] per-slot labels
+  int32_t* hist;           // [t*(b+1)+1]
+  int32_t* binlab;         // [t*(b+1)+1]
+  int32_t* ovlist;         // [S]
+  int32_t *lsize, *lsize2; // [S+1] per-label sizes
+  int32_t *leta, *leta2;   // [S]
+  int32_t *lflag, *lflag2; // [S]
+  int32_t* ovidx;          // [S+1]
+  int32_t* nchild;         // [S+1]
+  int32_t* subcnt;         // [omax][b+1]
+  int32_t* subrank;        // [omax][b+1]
+  int32_t* sub_resid;      // [omax]
+  uint32_t *skey, *skey2;  // [S] radix sort keys
+  int32_t *sval, *sval2;   // [S] radix sort values
+  uint32_t* shist;         // radix histograms
+  int32_t* scan_tmp;       // scan scratch
+};
+
+struct KnnWs {
+  DevHeader* hdr;
+  int32_t* slot2c;         // [S] slot -> cluster
+  int32_t* slen;           // [S] profile length of the slot's user
+  int32_t* ntiles;         // [S+1] brute-force tiles per cluster
+  int32_t* toff;           // [S+1]
+  int32_t* gflag;          // [S+1] greedy cluster flag
+  int32_t* gidx;           // [S+1]
+  int32_t* work_c;         // [S+1] work item -> cluster
+  int32_t* work_t;         // [S+1] work item -> query tile
+  int32_t* gcl;            // [S] greedy cluster list
+  int32_t* gsz;            // [S] greedy cluster sizes
+  int64_t* gsq;            // [S+1] squared sizes
+  int64_t* goff;           // [S+1] their prefix sums
+  int64_t* gofs;           // [S] per-cluster offset into gram, -1 = none
+  int32_t *bt_cnt, *bt_off, *bu_cnt, *bu_off;  // [S+1] greedy batch tiles / users
+  int32_t *gu_slot, *gu_g; // [S] greedy users of a batch
+  int32_t *wl0, *wl1;      // [S*k] greedy working lists (local indices)
+  uint16_t* gram;          // gram_budget bytes
+  int32_t* pos_of;         // [S] (function, user) -> slot
+  double* partial;         // [1024] reduction partials
+  int32_t* scan_tmp;
+  int64_t* scan_tmp64;
+};
+
+Sizes make_sizes(int32_t n, int64_t nnz, int32_t m, int32_t k, int32_t t, int32_t b, int32_t N,
+                 const c2_options* opt);
+void bind_cluster_ws(Ws& w, const Sizes& s, ClusterWs& c);
+void bind_knn_ws(Ws& w, const Sizes& s, KnnWs& c);
+size_t scan_tmp_elems(int64_t n);
+size_t sort_hist_elems(int64_t n);
+
+// ---------------------------------------------------------------- primitives
+// Exclusive prefix sum of d_in[n] into d_out[n+1] (d_out[n] = total).
+// In-place allowed.  tmp needs scan_tmp_elems(n) ints.
+cudaError_t scan_exclusive(const int32_t* d_in, int32_t* d_out, int64_t n, int32_t* tmp,
+                           cudaStream_t st);
+// Stable LSD radix sort of (key, value) pairs by the low `bits` bits of key.
+// Result ends in (k0, v0); k1/v1 are scratch of the same size.
+cudaError_t radix_sort_pairs(uint32_t* k0, int32_t* v0, uint32_t* k1, int32_t* v1, int64_t n,
+                             int bits, uint32_t* hist, int32_t* scan_tmp, cudaStream_t st);
+
+// ---------------------------------------------------------------- device math
+// SplitMix64 output function (Steele, Lea & Flood, OOPSLA 2014), GPU side.
+__host__ __device__ __forceinline__ uint64_t sm64_mix(uint64_t z) {
+  z ^= z >> 30;
+  z *= 0xBF58476D1CE4E5B9ull;
+  z ^= z >> 27;
+  z *= 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return z;
+}
+
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11), GPU side.
+__device__ __forceinline__ uint4 philox10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    k.x += 0x9E3779B9u;
+    k.y += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// Exact neighbour order: (c1/u1, id1) before (c2/u2, id2) iff the Jaccard
+// value is larger, or equal with the smaller id.  Cross-multiplied in 64 bits.
+__device__ __forceinline__ bool nbr_better(uint32_t c1, uint32_t u1, int32_t id1, uint32_t c2,
+                                           uint32_t u2, int32_t id2) {
+  uint64_t l = (uint64_t)c1 * u2, r = (uint64_t)c2 * u1;
+  return l > r || (l == r && (uint32_t)id1 < (uint32_t)id2);
+}
+
+// Warp-held sorted list: lane j < k holds entry j (id -1 = empty, worst).
+struct WarpList {
+  int32_t id;
+  uint32_t c, u;
+};
+
+// True iff the candidate beats entry `e` (an empty entry is beaten by all).
+__device__ __forceinline__ bool beats(const WarpList& e, int32_t id, uint32_t c, uint32_t u) {
+  return e.id < 0 || nbr_better(c, u, id, e.c, e.u, e.id);
+}
+
+// Inserts a candidate known to all lanes into the warp list of length k when
+// it ranks among the first k.  Returns true if inserted.
+__device__ __forceinline__ bool warp_list_insert(WarpList& e, int k, int32_t id, uint32_t c,
+                                                 uint32_t u) {
+  const int lane = threadIdx.x & 31;
+  bool mine_better = lane < k && !beats(e, id, c, u);
+  int pos = __popc(__ballot_sync(0xffffffffu, mine_better));
+  if (pos >= k) return false;
+  int32_t pid = __shfl_up_sync(0xffffffffu, e.id, 1);
+  uint32_t pc = __shfl_up_sync(0xffffffffu, e.c, 1);
+  uint32_t pu = __shfl_up_sync(0xffffffffu, e.u, 1);
+  if (lane > pos) { e.id = pid; e.c = pc; e.u = pu; }
+  if (lane == pos) { e.id = id; e.c = c; e.u = u; }
+  return true;
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+#define C2_CUDA_TRY(expr)                         \
+  do {                                            \
+    cudaError_t e_ = (expr);                      \
+    if (e_ != cudaSuccess) return C2_ERR_CUDA;    \
+  } while (0)
+
+// ---------------------------------------------------------------- phases
+c2_status run_frh_cluster(const int32_t* ptr, const int32_t* items, const Sizes& s, uint64_t seed,
+                          const c2_options& opt, int32_t* cluster_of, int32_t* cptr,
+                          int32_t* cusers, int32_t* n_clusters, int32_t* cmeta, ClusterWs& w,
+                          cudaStream_t st);
+c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes& s,
+                          const int32_t* cptr, const int32_t* cusers, const int32_t* n_clusters,
+                          uint64_t seed, const c2_options& opt, int32_t* lid, int32_t* lin,
+                          int32_t* lun, KnnWs& w, cudaStream_t st);
+c2_status run_merge(const int32_t* cusers, const Sizes& s, const int32_t* lid, const int32_t* lin,
+                    const int32_t* lun, int32_t* nid, int32_t* nin, int32_t* nun, KnnWs& w,
+                    cudaStream_t st);
+c2_status run_bruteforce(const int32_t* ptr, const int32_t* items, const Sizes& s,
+                         const int32_t* queries, int32_t nq, int32_t* nid, int32_t* nin,
+                         int32_t* nun, KnnWs& w, cudaStream_t st);
+c2_status run_avg_sim(const int32_t* nin, const int32_t* nun, int32_t rows, int32_t k, double* out,
+                      DevHeader* hdr, double* partial, cudaStream_t st);
+c2_status run_validate(const int32_t* ptr, const int32_t* items, const Sizes& s, DevHeader* hdr,
+                       cudaStream_t st);
+
+int num_sms();
+
+}  // namespace c2

@@ -1,0 +1,118 @@
+// Step 3 of Cluster-and-Conquer on sm_103a (Algorithm 3): every user's t
+// cluster-local lists are folded into one list of the k best distinct
+// neighbours, reusing the carried counts.  Also Eq. 1 (average similarity).
+#include "c2_internal.cuh"
+
+namespace c2 {
+
+namespace {
+
+// pos_of[i*n + u] = the slot of user u under function i.
+__global__ void k_pos_of(const int32_t* __restrict__ cusers, int64_t S, int32_t n,
+                         int32_t* __restrict__ pos_of) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= S) return;
+  const int64_t i = s / n;
+  pos_of[i * n + cusers[s]] = (int32_t)s;
+}
+
+// One warp per user.  Rows are sorted, so a row is abandoned at its first
+// entry that no longer beats the current k-th; an id already held is skipped.
+__global__ void k_merge(const int32_t* __restrict__ pos_of, int32_t n, int32_t t, int32_t k,
+                        const int32_t* __restrict__ lid, const int32_t* __restrict__ lin,
+                        const int32_t* __restrict__ lun, int32_t* __restrict__ nid,
+                        int32_t* __restrict__ nin, int32_t* __restrict__ nun,
+                        const DevHeader* hdr) {
+  const int lane = threadIdx.x & 31;
+  const int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (u >= n || dev_failed(hdr)) return;
+  WarpList L;
+  L.id = -1; L.c = 0; L.u = 0;
+  for (int i = 0; i < t; ++i) {
+    const int64_t s = pos_of[(int64_t)i * n + u];
+    int32_t eid = -1;
+    uint32_t ec = 0, eu = 0;
+    if (lane < k) {
+      eid = lid[s * k + lane];
+      ec = (uint32_t)lin[s * k + lane];
+      eu = (uint32_t)lun[s * k + lane];
+    }
+    for (int j = 0; j < k; ++j) {
+      const int32_t id = __shfl_sync(0xffffffffu, eid, j);
+      const uint32_t c = __shfl_sync(0xffffffffu, ec, j);
+      const uint32_t uu = __shfl_sync(0xffffffffu, eu, j);
+      if (id < 0) break;
+      if (__any_sync(0xffffffffu, L.id == id)) continue;
+      if (!warp_list_insert(L, k, id, c, uu)) break;
+    }
+  }
+  if (lane < k) {
+    const int64_t o = u * k + lane;
+    nid[o] = L.id;
+    nin[o] = L.id >= 0 ? (int32_t)L.c : 0;
+    nun[o] = L.id >= 0 ? (int32_t)L.u : 0;
+  }
+}
+
+// Eq. 1 in FP64: per-block partial sums over rows (fixed order), then one
+// block adds the partials in block order.
+constexpr int kAvgBlocks = 1024;
+
+__global__ void k_avg_partial(const int32_t* __restrict__ nin, const int32_t* __restrict__ nun,
+                              int64_t rows, int32_t k, double* __restrict__ partial) {
+  __shared__ double red[256];
+  const int64_t per = (rows + gridDim.x - 1) / gridDim.x;
+  const int64_t r0 = (int64_t)blockIdx.x * per, r1 = min(rows, r0 + per);
+  double acc = 0.0;
+  for (int64_t e = r0 * k + threadIdx.x; e < r1 * k; e += blockDim.x) {
+    const int32_t U = nun[e];
+    if (U > 0) acc += (double)nin[e] / (double)U;
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+__global__ void k_avg_final(const double* __restrict__ partial, int nb, double denom,
+                            double* __restrict__ out) {
+  __shared__ double red[256];
+  double acc = 0.0;
+  for (int j = threadIdx.x; j < nb; j += blockDim.x) acc += partial[j];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = red[0] / denom;
+}
+
+}  // namespace
+
+c2_status run_merge(const int32_t* cusers, const Sizes& s, const int32_t* lid, const int32_t* lin,
+                    const int32_t* lun, int32_t* nid, int32_t* nin, int32_t* nun, KnnWs& w,
+                    cudaStream_t st) {
+  if (s.n == 0) return C2_OK;
+  k_pos_of<<<div_up(s.S, 256), 256, 0, st>>>(cusers, s.S, s.n, w.pos_of);
+  k_merge<<<div_up((int64_t)s.n * 32, 256), 256, 0, st>>>(w.pos_of, s.n, s.t, s.k, lid, lin, lun,
+                                                          nid, nin, nun, w.hdr);
+  C2_CUDA_TRY(cudaGetLastError());
+  return C2_OK;
+}
+
+c2_status run_avg_sim(const int32_t* nin, const int32_t* nun, int32_t rows, int32_t k, double* out,
+                      DevHeader* hdr, double* partial, cudaStream_t st) {
+  (void)hdr;
+  if (rows <= 0) return C2_ERR_INVALID_ARG;
+  const int nb = (int)std::min<int64_t>(kAvgBlocks, rows);
+  k_avg_partial<<<nb, 256, 0, st>>>(nin, nun, rows, k, partial);
+  k_avg_final<<<1, 256, 0, st>>>(partial, nb, (double)k * (double)rows, out);
+  C2_CUDA_TRY(cudaGetLastError());
+  return C2_OK;
+}
+
+}  // namespace c2

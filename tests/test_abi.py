@@ -1,0 +1,73 @@
+"""CPU checks of the C ABI: the library builds, loads and exports every
+function include/c2.h declares; host-side argument checks need no GPU."""
+import ctypes as C
+
+import pytest
+
+import paper_2010_11497_gb300 as c2
+from paper_2010_11497_gb300 import build as c2build
+
+
+@pytest.fixture(scope="module")
+def lib():
+    c2build.build()
+    return c2.lib()
+
+
+def test_header_symbols_exported(lib):
+    names = c2.header_functions()
+    assert "c2_build_knn_graph" in names and "c2_frh_cluster" in names
+    assert {"c2_cluster_knn", "c2_merge_topk", "c2_bruteforce_knn", "c2_avg_sim"} <= set(names)
+    for name in names:
+        assert hasattr(lib, name), f"{name} declared in include/c2.h but not exported"
+
+
+def test_status_strings(lib):
+    for code in range(8):
+        assert c2.c2_status_string(code)
+    assert c2.c2_status_string(0) == "ok"
+
+
+def test_default_options(lib):
+    o = c2.options()
+    assert o.greedy_threshold == 0 and o.greedy_rounds == -1 and o.strategy == -1
+    assert list(o.reserved) == [0] * 8
+
+
+def test_workspace_size_validates(lib):
+    ws = c2.workspace_size(1000, 20000, 500, 30, 8, 4096, 2000)
+    assert ws > 0
+    # larger problems need more
+    assert c2.workspace_size(2000, 40000, 500, 30, 8, 4096, 2000) > ws
+    bad = [(1000, 0, 500, 0, 8, 64, 10), (1000, 0, 500, 33, 8, 64, 10),
+           (1000, 0, 500, 10, 65, 64, 10), (1000, 0, 500, 10, 8, 65537, 10),
+           (1000, 0, 500, 10, 8, 64, 1), (-1, 0, 500, 10, 8, 64, 10)]
+    for args in bad:
+        o = c2.options()
+        assert lib.c2_workspace_size(*args, C.byref(o)) == 0
+
+
+def test_host_argument_errors_need_no_gpu(lib):
+    o = c2.options()
+    # NULL pointers are rejected before any CUDA call
+    rc = lib.c2_build_knn_graph(None, None, 10, 10, 5, 2, 8, 4, 1, C.byref(o), None, None, None,
+                                None, 0, None)
+    assert rc == 1
+    # k out of range
+    rc = lib.c2_build_knn_graph(None, None, 10, 10, 40, 2, 8, 4, 1, C.byref(o), None, None, None,
+                                None, 0, None)
+    assert rc == 3
+    # missing workspace
+    fake = C.c_void_p(256)
+    rc = lib.c2_build_knn_graph(fake, fake, 10, 10, 5, 2, 8, 4, 1, C.byref(o), fake, fake, fake,
+                                None, 0, None)
+    assert rc == 4
+    # misaligned workspace
+    rc = lib.c2_build_knn_graph(fake, fake, 10, 10, 5, 2, 8, 4, 1, C.byref(o), fake, fake, fake,
+                                C.c_void_p(4096 + 8), 1 << 30, None)
+    assert rc == 4
+    # non-zero reserved option fields
+    o.reserved[3] = 1
+    rc = lib.c2_build_knn_graph(fake, fake, 10, 10, 5, 2, 8, 4, 1, C.byref(o), fake, fake, fake,
+                                C.c_void_p(4096), 1 << 30, None)
+    assert rc == 1
