@@ -1,0 +1,444 @@
+"""Benchmark: Cluster-and-Conquer KNN-graph build on one GB300 per rank.
+
+One step = one whole build (FastRandomHash clustering with recursive split,
+local KNN in every cluster, merge) of the ml10m-like synthetic workload:
+69,878 users x 10,677 items, ~10M profile entries, k=30, t=8, b=4096,
+N=2000, greedy refinement (10 rounds) in clusters of more than 500 users.
+
+`value` is exact-Jaccard pair evaluations per second of the whole job,
+device-timed with CUDA events around each step, inputs resident in HBM and
+L2 flushed (a 512 MiB write) before every step.  `e2e` repeats the build
+through the host-buffer C entry point (pinned host CSR in, pinned host graph
+out, copies inside the timed region).  With --impl reference the CPU oracle
+is timed instead, on a bounded sample of the same workload.
+
+Multi-GPU: every rank builds the graph of its own independent problem (the
+same workload shape with seed + rank): weak scaling, no collective on the
+data path; only the timing uses a barrier and a max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2010_11497_gb300 import synth  # noqa: E402
+
+METRIC = "KNN-graph build s & exact-Jaccard pairs/s at k=30, quality≥0.95 vs brute force"
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                  "sm_max_mhz": 2070.0}
+N_SM = 152
+LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="c2", choices=["c2", "reference"])
+    ap.add_argument("--workload", default="ml10m_like")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-quality", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0,
+                    help="target CPU seconds of the oracle sample")
+    return ap.parse_args()
+
+
+def peaks():
+    p = dict(FALLBACK_PEAKS)
+    src = "fallback"
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            p.update(json.load(open(path)))
+            src = "measured"
+        except Exception:
+            pass
+    return p, src
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        try:
+            rows = [r.split(",") for r in open(self.path).read().strip().splitlines()]
+            os.unlink(self.path)
+        except Exception:
+            return out
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if sm:
+            busy = [x for x in sm if x > 0.5 * max(sm)] or sm
+            out.update(sm_mhz=statistics.median(busy), sm_max_mhz=max(mx), samples=len(sm))
+        out["reasons"] = sorted(reasons)
+        return out
+
+
+# ------------------------------------------------------------------ distributed
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend=backend)
+        return dist, rank, local, ws
+    return None, rank, local, ws
+
+
+def barrier(dist, dev=None):
+    if dist is not None:
+        import torch
+        if dev is not None and dist.get_backend() == "nccl":
+            dist.barrier(device_ids=[dev.index])
+        else:
+            dist.barrier()
+
+
+def max_over_ranks(dist, x: float, dev=None) -> float:
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64,
+                     device=dev if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(dist, x: float, dev=None) -> float:
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64,
+                     device=dev if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ CPU oracle
+def oracle_sample(ptr, items, w, seed, budget_s, rng_seed=2010, clustering=None, t_cluster=None):
+    """Times the oracle on a seeded sample of the workload's clusters.
+
+    Step 1 (clustering) runs on the whole workload and is charged pro rata;
+    Step 2 runs on clusters drawn in a seeded random order, each kept only if
+    its estimated oracle time still fits the budget.
+    Returns (pairs/s, description, clustering)."""
+    import oracle
+    t0 = time.perf_counter()
+    cl = clustering or oracle.frh_cluster(ptr, items, w.n_items, w.t, w.b, w.N, seed)
+    if t_cluster is None:
+        t_cluster = time.perf_counter() - t0
+    sizes = np.diff(cl["cptr"]).astype(np.int64)
+    greedy = sizes >= w.greedy_threshold
+    est_pairs = np.where(greedy, sizes * (w.k + w.greedy_rounds * w.k * w.k),
+                         sizes * (sizes - 1) // 2).astype(np.float64)
+    steps_per_pair = 2.0 * float(np.diff(ptr).mean()) + 20.0
+    est_s = est_pairs * steps_per_pair / 1.5e8
+    order = np.random.default_rng(rng_seed).permutation(sizes.size)
+    only = np.zeros(sizes.size, np.uint8)
+    left = budget_s
+    for c in order:
+        if sizes[c] >= 2 and est_s[c] <= left:
+            only[c] = 1
+            left -= est_s[c]
+        if left <= 0.02 * budget_s:
+            break
+    t1 = time.perf_counter()
+    _, _, _, pairs = oracle.cluster_knn(ptr, items, cl["cptr"], cl["cusers"], w.k, seed,
+                                        w.greedy_threshold, w.greedy_rounds, 0, only=only)
+    t_knn = time.perf_counter() - t1
+    sel = only.astype(bool)
+    frac = float(est_pairs[sel].sum()) / max(float(est_pairs.sum()), 1.0)
+    t_total = t_knn + t_cluster * frac
+    desc = (f"oracle Step 1 on all {w.n_users} users ({t_cluster:.1f} s, charged pro rata "
+            f"{frac:.3f}), Step 2 on {int(sel.sum())} of {sizes.size} clusters in seeded random "
+            f"order ({int((sel & greedy).sum())} greedy): {pairs} pair evaluations in "
+            f"{t_knn:.1f} s; single thread")
+    return pairs / t_total, desc, cl
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args):
+    dist, rank, local, world = dist_setup(args)
+    if rank != 0:
+        return 0
+    w = synth.WORKLOADS[args.workload]
+    ptr, items, _ = synth.load(args.workload, w.seed)
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    cl = oracle.frh_cluster(ptr, items, w.n_items, w.t, w.b, w.N, w.seed)
+    t_cluster = time.perf_counter() - t0
+    budget = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    vals = []
+    desc = ""
+    for i in range(args.warmup + args.steps):
+        v, desc, _ = oracle_sample(ptr, items, w, w.seed, budget, rng_seed=2010 + i,
+                                   clustering=cl, t_cluster=t_cluster)
+        if i >= args.warmup:
+            vals.append(v)
+    value = float(np.mean(vals))
+    line = {"metric": METRIC, "value": value, "unit": "pairs/s", "impl": "reference",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic", "config": {"workload": w.name, **w.params()},
+            "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": 1, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------ roofline
+def roofline(phase_ms, phase_calls, stats, w, nnz, pk, pk_src, W):
+    """Roofline of the dominant kernel phase (the largest share of device time)."""
+    n, t, k = w.n_users, w.t, w.k
+    S = t * n
+    candidates = {k_: v for k_, v in phase_ms.items() if v > 0}
+    if not candidates:
+        return None
+    dom = max(candidates, key=candidates.get)
+    calls = max(1, phase_calls.get(dom, 1))
+    ms = phase_ms[dom] / calls
+    alu_peak = N_SM * LANES_PER_SM * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12   # Tlane-op/s
+    if dom in ("brute_table", "greedy_gram"):
+        visits = stats["item_visits_brute" if dom == "brute_table" else "item_visits_greedy"]
+        ops_per_visit = 1 + W + 12 * W + 48 * W / 15.0
+        achieved = visits / calls * ops_per_visit / (ms * 1e-3) / 1e12
+        return {"kernel": "k_table<%d>" % W, "phase": dom, "bound": "alu", "achieved": achieved,
+                "peak": alu_peak, "unit": "Tlane-op/s", "frac": achieved / alu_peak,
+                "traffic": None, "ms_per_launch": ms,
+                "model": f"{ops_per_visit:.1f} integer lane-ops per candidate item visit "
+                         f"({visits / calls:.3e} visits/launch); peak = 152 SMs x 128 lanes x "
+                         f"{pk.get('sm_max_mhz', 2070.0):.0f} MHz"}
+    if dom == "greedy_rounds":
+        # per user and round: own row (k ids), k neighbour rows (k*k ids), one 2-byte count
+        # and one 4-byte length per candidate, k ids written
+        users = stats.get("greedy_users", 0)
+        per = 4 * k + 4 * k * k + (2 + 4) * k * k + 4 * k
+        bytes_ = users * per
+        achieved = bytes_ / (ms * 1e-3) / 1e9
+        return {"kernel": "k_greedy_round", "phase": dom, "bound": "hbm", "achieved": achieved,
+                "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": achieved / pk["hbm_gbs"],
+                "traffic": None, "ms_per_launch": ms,
+                "model": f"{per} B per greedy user per round, {users} users"}
+    if dom == "merge":
+        bytes_ = 4 * S + 12 * S * k + 12 * n * k
+        achieved = bytes_ / (ms * 1e-3) / 1e9
+        return {"kernel": "k_merge", "phase": dom, "bound": "hbm", "achieved": achieved,
+                "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": achieved / pk["hbm_gbs"],
+                "traffic": None, "ms_per_launch": ms}
+    bytes_ = 4 * (n + 1) + 4 * nnz + 4 * S
+    achieved = bytes_ / (ms * 1e-3) / 1e9
+    return {"kernel": dom, "phase": dom, "bound": "hbm", "achieved": achieved,
+            "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": achieved / pk["hbm_gbs"],
+            "traffic": None, "ms_per_launch": ms}
+
+
+# ------------------------------------------------------------------ main arm
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import paper_2010_11497_gb300 as c2
+    dist, rank, local, world = dist_setup(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = synth.WORKLOADS[args.workload]
+    seed = w.seed + rank
+    ptr_np, items_np, man = synth.load(args.workload, seed)
+    nnz = int(items_np.size)
+    ptr = torch.from_numpy(ptr_np).to(dev)
+    items = torch.from_numpy(items_np).to(dev)
+    opts = c2.options(greedy_threshold=w.greedy_threshold, greedy_rounds=w.greedy_rounds)
+    ws = c2.workspace(c2.workspace_size(w.n_users, nnz, w.n_items, w.k, w.t, w.b, w.N, opts), dev)
+    out = [torch.empty((w.n_users, w.k), dtype=torch.int32, device=dev) for _ in range(3)]
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        c2.c2_build_knn_graph(ptr, items, w.n_items, w.k, w.t, w.b, w.N, seed, opts=opts, ws=ws,
+                              out=out, check=False)
+
+    for _ in range(max(3, args.warmup)):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    assert c2.c2_get_status(ws) == 0, "build reported a device error"
+    stats = c2.c2_get_stats(ws)
+
+    # timed region
+    c2.c2_profile_enable(True)
+    c2.c2_profile_report()                       # clear
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    launches0 = c2.c2_kernel_launches()
+    with ClockSampler(local) as clk:
+        barrier(dist, dev)
+        torch.cuda.synchronize()
+        wall0 = time.perf_counter()
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            step()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+        barrier(dist, dev)
+    launches = c2.c2_kernel_launches() - launches0
+    prof = c2.c2_profile_report()
+    c2.c2_profile_enable(False)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    dev_s = sum(step_ms) / 1e3
+    dev_s_max = max_over_ranks(dist, dev_s, dev)
+    pairs = stats["pairs"]
+    total_pairs = sum_over_ranks(dist, float(pairs) * args.steps, dev)
+    value = total_pairs / dev_s_max
+    clocks = clk.summary()
+
+    # end to end through the host-buffer entry point
+    e2e = None
+    if not args.no_e2e:
+        hptr = torch.from_numpy(ptr_np).pin_memory()
+        hitems = torch.from_numpy(items_np).pin_memory()
+        hws = c2.workspace(c2.workspace_size_host(w.n_users, nnz, w.n_items, w.k, w.t, w.b, w.N,
+                                                  opts), dev)
+        hout = [torch.empty((w.n_users, w.k), dtype=torch.int32).pin_memory() for _ in range(3)]
+        for _ in range(max(3, args.warmup)):
+            c2.c2_build_knn_graph_host(hptr, hitems, w.n_items, w.k, w.t, w.b, w.N, seed,
+                                       opts=opts, ws=hws, out=hout)
+        barrier(dist, dev)
+        torch.cuda.synchronize()
+        e2e_s = 0.0
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            a = time.perf_counter()
+            c2.c2_build_knn_graph_host(hptr, hitems, w.n_items, w.k, w.t, w.b, w.N, seed,
+                                       opts=opts, ws=hws, out=hout)
+            e2e_s += time.perf_counter() - a
+        e2e = e2e_s
+        e2e_max = max_over_ranks(dist, e2e, dev)
+        assert np.array_equal(hout[0].numpy(), out[0].cpu().numpy()), "host entry differs"
+        e2e = {"value": total_pairs / e2e_max, "unit": "pairs/s",
+               "h2d_bytes_per_step": int(ptr_np.nbytes + items_np.nbytes),
+               "d2h_bytes_per_step": int(3 * w.n_users * w.k * 4),
+               "ms_per_step": e2e_max / args.steps * 1e3}
+        del hws
+
+    # quality (Eq. 2) against the exact graph from the GPU judge
+    quality = None
+    if not args.no_quality and rank == 0:
+        bid, bin_, bun = c2.c2_bruteforce_knn(ptr, items, w.n_items, w.k)
+        a_c2 = c2.c2_avg_sim(out[1], out[2])
+        a_bf = c2.c2_avg_sim(bin_, bun)
+        quality = {"avg_sim": a_c2, "avg_sim_bruteforce": a_bf, "quality": a_c2 / a_bf}
+        del bid, bin_, bun
+
+    pk, pk_src = peaks()
+    phase_ms = {k_: v["ms"] / args.steps for k_, v in prof.items()}
+    phase_calls = {k_: v["calls"] / args.steps for k_, v in prof.items()}
+    W = 2 if w.n_items * 8 + 40000 <= 227 * 1024 else 1
+    stats2 = dict(stats)
+    rf = None
+    try:
+        rf = roofline({k_: v["ms"] for k_, v in prof.items()},
+                      {k_: v["calls"] for k_, v in prof.items()}, stats2, w, nnz, pk, pk_src, W)
+        if rf:
+            rf["peak_source"] = pk_src
+    except Exception as e:   # the measurement stands without the model
+        rf = {"error": str(e)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        v, desc, _ = oracle_sample(ptr_np, items_np, w, seed, args.cpu_seconds)
+        cpu = {"value": v, "unit": "pairs/s", "cores": 1, "kind": "oracle", "sample": desc}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": dev_s_max / args.steps * 1e3,
+                "build_s": dev_s_max / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "int32", "data": "synthetic",
+                "config": {"workload": w.name, "n_users": w.n_users, "n_items": w.n_items,
+                           "nnz": nnz, **w.params(), "l2": "flushed (512 MiB write) before each step",
+                           "parallelism": f"replicas{world}" if world > 1 else "single"},
+                "pairs_per_step": pairs, "gram_pairs_per_step": stats["gram_pairs"],
+                "quality": quality, "e2e": e2e, "gpu_launches": launches,
+                "gpu_launches_per_step": launches / args.steps,
+                "wall_s_timed": wall, "step_ms": step_ms,
+                "phases_ms_per_step": phase_ms, "roofline": rf, "cpu_baseline": cpu,
+                "clocks": clocks, "stats": stats}
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -95,7 +95,10 @@ typedef struct {
   int32_t n_greedy_clusters;
   int32_t max_cluster;      /* largest cluster                                             */
   int32_t max_profile;      /* longest profile                                             */
-  int32_t reserved[7];
+  int32_t greedy_users;     /* users (slots) in greedy clusters                            */
+  int64_t item_visits_brute;/* profile items walked by the shared-memory table kernel:     */
+  int64_t item_visits_greedy; /* brute-force clusters / greedy intersection matrices       */
+  int32_t reserved[4];
 } c2_stats;
 
 /* Fills *opt with the defaults described above.  Never fails. */
@@ -197,6 +200,19 @@ c2_status c2_get_stats(const void* d_ws, c2_stream_t stream, c2_stats* out);
 
 /* Clears the device status word and statistics of d_ws (asynchronous). */
 c2_status c2_reset_status(void* d_ws, c2_stream_t stream);
+
+/* Instrumentation (no counterpart in the paper; the paper reports wall-clock
+ * time only, Section IV-E).  c2_kernel_launches() returns how many CUDA
+ * kernels this library has launched in the process.  With profiling enabled
+ * the library records a CUDA event pair on the caller's stream around every
+ * phase of the build; c2_profile_report() synchronises on those events,
+ * writes a JSON object {"phase": {"ms": total, "calls": n, "launches": n}}
+ * into buf (NUL-terminated, truncated to len) and clears the records.  It
+ * returns the number of bytes the full report needs.  Host only; the
+ * profiler state is process-wide and guarded by a mutex. */
+int64_t c2_kernel_launches(void);
+void c2_profile_enable(int on);
+size_t c2_profile_report(char* buf, size_t len);
 
 #ifdef __cplusplus
 }

@@ -42,7 +42,8 @@ class Stats(C.Structure):
     _fields_ = [("pairs", C.c_int64), ("gram_pairs", C.c_int64), ("n_clusters", C.c_int32),
                 ("split_levels", C.c_int32), ("n_greedy_clusters", C.c_int32),
                 ("max_cluster", C.c_int32), ("max_profile", C.c_int32),
-                ("reserved", C.c_int32 * 7)]
+                ("greedy_users", C.c_int32), ("item_visits_brute", C.c_int64),
+                ("item_visits_greedy", C.c_int64), ("reserved", C.c_int32 * 4)]
 
 
 _lib = None
@@ -68,6 +69,9 @@ _SIGS = {
     "c2_get_status": (C.c_int, [P, P]),
     "c2_get_stats": (C.c_int, [P, P, C.POINTER(Stats)]),
     "c2_reset_status": (C.c_int, [P, P]),
+    "c2_kernel_launches": (C.c_int64, []),
+    "c2_profile_enable": (None, [C.c_int]),
+    "c2_profile_report": (C.c_size_t, [C.c_char_p, C.c_size_t]),
 }
 
 
@@ -271,7 +275,8 @@ def c2_get_stats(ws, stream=None) -> dict:
     _check(lib().c2_get_stats(_ptr(ws), _stream(stream), C.byref(s)), "c2_get_stats")
     return dict(pairs=s.pairs, gram_pairs=s.gram_pairs, n_clusters=s.n_clusters,
                 split_levels=s.split_levels, n_greedy_clusters=s.n_greedy_clusters,
-                max_cluster=s.max_cluster, max_profile=s.max_profile)
+                max_cluster=s.max_cluster, max_profile=s.max_profile,
+                greedy_users=s.greedy_users, item_visits_brute=s.item_visits_brute, item_visits_greedy=s.item_visits_greedy)
 
 
 def c2_reset_status(ws, stream=None):
@@ -280,3 +285,19 @@ def c2_reset_status(ws, stream=None):
 
 def c2_status_string(code: int) -> str:
     return lib().c2_status_string(code).decode()
+
+
+def c2_kernel_launches() -> int:
+    return int(lib().c2_kernel_launches())
+
+
+def c2_profile_enable(on: bool = True):
+    lib().c2_profile_enable(1 if on else 0)
+
+
+def c2_profile_report() -> dict:
+    import json
+    need = lib().c2_profile_report(None, 0)
+    buf = C.create_string_buffer(int(need) + 4096)
+    lib().c2_profile_report(buf, len(buf))
+    return json.loads(buf.value.decode() or "{}")

@@ -214,6 +214,9 @@ c2_status c2_get_stats(const void* d_ws, c2_stream_t stream, c2_stats* out) {
   out->n_greedy_clusters = h.n_greedy;
   out->max_cluster = h.max_cluster;
   out->max_profile = h.max_profile;
+  out->greedy_users = h.greedy_users;
+  out->item_visits_brute = (int64_t)h.item_visits[0];
+  out->item_visits_greedy = (int64_t)h.item_visits[1];
   return C2_OK;
 }
 

@@ -374,7 +374,7 @@ int bits_for(int64_t v) {
 
 c2_status run_validate(const int32_t* ptr, const int32_t* items, const Sizes& s, DevHeader* hdr,
                        cudaStream_t st) {
-  if (s.n > 0) k_validate<<<div_up((int64_t)s.n * 32, 256), 256, 0, st>>>(ptr, items, s.n, s.m, hdr);
+  if (s.n > 0) C2_LAUNCH(k_validate, div_up((int64_t)s.n * 32, 256), 256, 0, st, ptr, items, s.n, s.m, hdr);
   C2_CUDA_TRY(cudaGetLastError());
   return C2_OK;
 }
@@ -386,30 +386,37 @@ c2_status run_frh_cluster(const int32_t* ptr, const int32_t* items, const Sizes&
   const int64_t S = s.S;
   const int64_t nbins = (int64_t)s.t * (s.b + 1);
   const int T = 256;
-  c2_status rc = run_validate(ptr, items, s, w.hdr, st);
+  c2_status rc;
+  {
+    Prof p(st, "validate");
+    rc = run_validate(ptr, items, s, w.hdr, st);
+  }
   if (rc) return rc;
+  Prof p_hash(st, "hash_minhash_level0");
   if (s.m > 0)
-    k_build_htab<<<div_up((int64_t)s.m * s.tp, T), T, 0, st>>>(w.htab, s.m, s.t, s.tp, s.b, seed,
+    C2_LAUNCH(k_build_htab, div_up((int64_t)s.m * s.tp, T), T, 0, st, w.htab, s.m, s.t, s.tp, s.b, seed,
                                                                  opt.d_hash_table, w.hdr);
   C2_CUDA_TRY(cudaMemsetAsync(w.hist, 0, (nbins + 1) * sizeof(int32_t), st));
   if (s.n > 0)
-    k_minhash<<<div_up((int64_t)s.n * 32, T), T, 0, st>>>(ptr, items, w.htab, s.n, s.t, s.tp, s.b,
+    C2_LAUNCH(k_minhash, div_up((int64_t)s.n * 32, T), T, 0, st, ptr, items, w.htab, s.n, s.t, s.tp, s.b,
                                                            w.key, w.hist, w.hdr);
-  k_flag_nonzero<<<div_up(nbins, T), T, 0, st>>>(w.hist, w.binlab, nbins);
+  C2_LAUNCH(k_flag_nonzero, div_up(nbins, T), T, 0, st, w.hist, w.binlab, nbins);
   C2_CUDA_TRY(scan_exclusive(w.binlab, w.binlab, nbins, w.scan_tmp, st));
   C2_CUDA_TRY(cudaMemsetAsync(w.lsize, 0, (S + 1) * sizeof(int32_t), st));
-  k_level0_meta<<<div_up(nbins, T), T, 0, st>>>(w.hist, w.binlab, nbins, s.b, w.lsize, w.leta,
+  C2_LAUNCH(k_level0_meta, div_up(nbins, T), T, 0, st, w.hist, w.binlab, nbins, s.b, w.lsize, w.leta,
                                                  w.lflag, w.hdr);
-  if (S > 0) k_level0_labels<<<div_up(S, T), T, 0, st>>>(w.key, w.binlab, s.n, S, s.b, w.lab, w.hdr);
+  if (S > 0) C2_LAUNCH(k_level0_labels, div_up(S, T), T, 0, st, w.key, w.binlab, s.n, S, s.b, w.lab, w.hdr);
   C2_CUDA_TRY(cudaGetLastError());
 
+  p_hash.end();
   // Recursive split, one level per iteration (at most b levels: keys grow).
+  Prof p_split(st, "split");
   int32_t h_over = 0;
   c2_status out = C2_OK;
   for (int level = 0; level <= s.b + 1 && S > 0; ++level) {
-    k_mark_oversized<<<div_up(S, T), T, 0, st>>>(w.lsize, w.lflag, S, s.N, w.ovidx, w.nchild, w.hdr);
+    C2_LAUNCH(k_mark_oversized, div_up(S, T), T, 0, st, w.lsize, w.lflag, S, s.N, w.ovidx, w.nchild, w.hdr);
     if (scan_exclusive(w.ovidx, w.ovidx, S, w.scan_tmp, st) != cudaSuccess) { out = C2_ERR_CUDA; break; }
-    k_copy_oversized<<<1, 1, 0, st>>>(w.hdr, w.ovidx + S);
+    C2_LAUNCH(k_copy_oversized, 1, 1, 0, st, w.hdr, w.ovidx + S);
     if (cudaMemcpyAsync(&h_over, &w.hdr->n_oversized, sizeof(int32_t), cudaMemcpyDeviceToHost, st) !=
             cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess) {
@@ -419,40 +426,42 @@ c2_status run_frh_cluster(const int32_t* ptr, const int32_t* items, const Sizes&
     const int64_t O = h_over;
     if (O == 0) break;
     if (O > s.omax) { out = C2_ERR_UNSUPPORTED; break; }
-    k_ovlist<<<div_up(S, T), T, 0, st>>>(w.ovidx, S, w.ovlist);
+    C2_LAUNCH(k_ovlist, div_up(S, T), T, 0, st, w.ovidx, S, w.ovlist);
     cudaMemsetAsync(w.subcnt, 0, O * (s.b + 1) * sizeof(int32_t), st);
-    k_split_keys<<<div_up(S, T), T, 0, st>>>(ptr, items, w.htab, s.n, S, s.tp, s.b, w.lab, w.ovidx,
+    C2_LAUNCH(k_split_keys, div_up(S, T), T, 0, st, ptr, items, w.htab, s.n, S, s.tp, s.b, w.lab, w.ovidx,
                                              w.leta, w.key, w.subcnt, w.hdr);
-    k_split_plan<<<(unsigned)O, 256, 0, st>>>(w.ovlist, s.b, w.subcnt, w.subrank, w.sub_resid,
+    C2_LAUNCH(k_split_plan, (unsigned)O, 256, 0, st, w.ovlist, s.b, w.subcnt, w.subrank, w.sub_resid,
                                                w.nchild, w.hdr);
     if (scan_exclusive(w.nchild, w.nchild, S, w.scan_tmp, st) != cudaSuccess) { out = C2_ERR_CUDA; break; }
-    k_relabel<<<div_up(S, T), T, 0, st>>>(w.lab, w.ovidx, w.nchild, w.key, w.subcnt, w.subrank,
+    C2_LAUNCH(k_relabel, div_up(S, T), T, 0, st, w.lab, w.ovidx, w.nchild, w.key, w.subcnt, w.subrank,
                                           w.sub_resid, S, s.b, w.lab2);
     cudaMemsetAsync(w.lsize2, 0, (S + 1) * sizeof(int32_t), st);
-    k_newmeta_copy<<<div_up(S, T), T, 0, st>>>(w.ovidx, w.nchild, w.lsize, w.leta, w.lflag, S,
+    C2_LAUNCH(k_newmeta_copy, div_up(S, T), T, 0, st, w.ovidx, w.nchild, w.lsize, w.leta, w.lflag, S,
                                                w.lsize2, w.leta2, w.lflag2, w.hdr);
-    k_newmeta_split<<<(unsigned)O, 256, 0, st>>>(w.ovlist, w.nchild, w.lflag, w.leta, s.b,
+    C2_LAUNCH(k_newmeta_split, (unsigned)O, 256, 0, st, w.ovlist, w.nchild, w.lflag, w.leta, s.b,
                                                   w.subcnt, w.subrank, w.sub_resid, w.lsize2,
                                                   w.leta2, w.lflag2);
-    k_set_nlabels<<<1, 1, 0, st>>>(w.hdr, w.nchild + S);
+    C2_LAUNCH(k_set_nlabels, 1, 1, 0, st, w.hdr, w.nchild + S);
     std::swap(w.lab, w.lab2);
     std::swap(w.lsize, w.lsize2);
     std::swap(w.leta, w.leta2);
     std::swap(w.lflag, w.lflag2);
     if (cudaGetLastError() != cudaSuccess) { out = C2_ERR_CUDA; break; }
   }
+  p_split.end();
   if (out) return out;
 
   // Canonical CSR: stable sort of slots (function-major, user-minor) by label.
+  Prof p_csr(st, "cluster_csr");
   if (S > 0) {
-    k_zero_tail<<<div_up(S, T), T, 0, st>>>(w.lsize, S, w.hdr);
+    C2_LAUNCH(k_zero_tail, div_up(S, T), T, 0, st, w.lsize, S, w.hdr);
     C2_CUDA_TRY(scan_exclusive(w.lsize, cptr, S, w.scan_tmp, st));
-    k_sort_input<<<div_up(S, T), T, 0, st>>>(w.lab, S, s.n, w.skey, w.sval);
+    C2_LAUNCH(k_sort_input, div_up(S, T), T, 0, st, w.lab, S, s.n, w.skey, w.sval);
     C2_CUDA_TRY(radix_sort_pairs(w.skey, w.sval, w.skey2, w.sval2, S, bits_for(S), w.shist,
                                  w.scan_tmp, st));
     C2_CUDA_TRY(cudaMemcpyAsync(cusers, w.sval, S * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
     C2_CUDA_TRY(cudaMemcpyAsync(cluster_of, w.lab, S * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
-    k_final_meta<<<div_up(S, T), T, 0, st>>>(w.lsize, w.leta, w.lflag, S, cmeta, n_clusters, w.hdr);
+    C2_LAUNCH(k_final_meta, div_up(S, T), T, 0, st, w.lsize, w.leta, w.lflag, S, cmeta, n_clusters, w.hdr);
   } else {
     C2_CUDA_TRY(cudaMemsetAsync(cptr, 0, sizeof(int32_t), st));
     C2_CUDA_TRY(cudaMemsetAsync(n_clusters, 0, sizeof(int32_t), st));

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "../../include/c2.h"
 
 namespace c2 {
@@ -28,7 +30,9 @@ struct DevHeader {
   unsigned long long gram_pairs;
   unsigned long long greedy_gram_elems;  // sum of M*M over greedy clusters
   unsigned int work_counter[8];  // persistent-kernel work counters
-  int32_t pad[26];
+  unsigned long long item_visits[2];  // table kernel: candidate items walked (brute, greedy)
+  int32_t greedy_users;
+  int32_t pad[21];
 };
 static_assert(sizeof(DevHeader) <= 256, "header must fit 256 bytes");
 
@@ -200,6 +204,29 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 }
 
 inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+// ---------------------------------------------------------------- launches
+// Every kernel launch of the library goes through C2_LAUNCH, which counts it.
+extern std::atomic<long long> g_launches;
+#define C2_LAUNCH(kern, grid, block, smem, st, ...)            \
+  do {                                                         \
+    kern<<<(grid), (block), (smem), (st)>>>(__VA_ARGS__);      \
+    ::c2::g_launches.fetch_add(1, std::memory_order_relaxed);  \
+  } while (0)
+
+// Optional per-phase CUDA-event timing (off unless c2_profile_enable(1)):
+// a Prof object records an event pair around its scope on `st`.
+class Prof {
+ public:
+  Prof(cudaStream_t st, const char* name);
+  ~Prof() { end(); }
+  void end();   // records the closing event (once)
+ private:
+  cudaStream_t st_;
+  const char* name_;
+  int idx_;
+  long long launches0_;
+};
 
 #define C2_CUDA_TRY(expr)                         \
   do {                                            \

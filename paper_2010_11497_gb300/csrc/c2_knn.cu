@@ -113,6 +113,7 @@ __global__ void __launch_bounds__(kNT) k_table(TableArgs a) {
   const int k = a.k;
   for (int i = tid; i < a.n_items * W; i += kNT) T[i] = 0;
   const int nwork = *a.n_work;
+  unsigned long long visits = 0;
   __syncthreads();
   for (;;) {
     if (tid == 0) s_work = dev_failed(a.hdr) ? nwork : (int)atomicAdd(a.counter, 1u);
@@ -171,6 +172,7 @@ __global__ void __launch_bounds__(kNT) k_table(TableArgs a) {
 #pragma unroll
       for (int r = 0; r < 16 * W; ++r) C[r] = 0;
       if (act) count_profile<W>(a.items + a.ptr[v], len, T, C);
+      visits += (unsigned)len;
       if (gofs >= 0) {
         // greedy cluster: keep every count (row = query, column = candidate)
         uint16_t* G = a.gram + gofs + (int64_t)(tq * Q) * M + vl;
@@ -244,6 +246,9 @@ __global__ void __launch_bounds__(kNT) k_table(TableArgs a) {
     }
     __syncthreads();
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) visits += __shfl_xor_sync(0xffffffffu, visits, o);
+  if (lane == 0 && visits) atomicAdd(&a.hdr->item_visits[a.gofs ? 1 : 0], visits);
 }
 
 // ------------------------------------------------------------------ merge kernel
@@ -412,6 +417,7 @@ __global__ void k_greedy_list(const int32_t* __restrict__ gflag, const int32_t* 
   gsq[g] = (int64_t)M * M;
   gsz[g] = M;
   atomicMax(&hdr->max_cluster, M);
+  atomicAdd(&hdr->greedy_users, M);
 }
 
 __global__ void k_batch_setup(const int32_t* __restrict__ gcl, const int64_t* __restrict__ goff,
@@ -664,7 +670,7 @@ c2_status launch_table(const TableArgs& a, cudaStream_t st) {
   C2_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_table<W>, kNT, smem));
   if (per_sm < 1) return C2_ERR_UNSUPPORTED;
   C2_CUDA_TRY(cudaMemsetAsync(a.counter, 0, sizeof(unsigned), st));
-  k_table<W><<<num_sms() * per_sm, kNT, smem, st>>>(a);
+  C2_LAUNCH(k_table<W>, num_sms() * per_sm, kNT, smem, st, a);
   C2_CUDA_TRY(cudaGetLastError());
   return C2_OK;
 }
@@ -698,15 +704,18 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
   const int W = pick_w(opt.strategy, s.m);
   const int Q = W ? 32 * W : 32;
 
-  k_prep<<<div_up(S, T), T, 0, st>>>(cptr, n_clusters, S, thr, Q, k, w.ntiles, w.gflag, lid, lin,
+  Prof p_prep(st, "knn_prep");
+  C2_LAUNCH(k_prep, div_up(S, T), T, 0, st, cptr, n_clusters, S, thr, Q, k, w.ntiles, w.gflag, lid, lin,
                                       lun, w.hdr);
-  k_slot_info<<<div_up(S, T), T, 0, st>>>(cptr, n_clusters, cusers, ptr, S, w.slot2c, w.slen);
+  C2_LAUNCH(k_slot_info, div_up(S, T), T, 0, st, cptr, n_clusters, cusers, ptr, S, w.slot2c, w.slen);
   C2_CUDA_TRY(cudaGetLastError());
 
+  p_prep.end();
   // ---- brute-force clusters
+  Prof p_brute(st, W ? "brute_table" : "brute_merge");
   if (W) {
     C2_CUDA_TRY(scan_exclusive(w.ntiles, w.toff, S, w.scan_tmp, st));
-    k_fill_work<<<div_up(S, T), T, 0, st>>>(w.ntiles, w.toff, nullptr, S, w.work_c, w.work_t,
+    C2_LAUNCH(k_fill_work, div_up(S, T), T, 0, st, w.ntiles, w.toff, nullptr, S, w.work_c, w.work_t,
                                             &w.hdr->n_work);
     TableArgs a{};
     a.ptr = ptr; a.items = items; a.n_items = s.m; a.k = k;
@@ -721,20 +730,22 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
     MergeArgs a{};
     a.ptr = ptr; a.items = items; a.k = k; a.cptr = cptr; a.cusers = cusers; a.slot2c = w.slot2c;
     a.n_rows = S; a.thr = thr; a.out_id = lid; a.out_in = lin; a.out_un = lun; a.hdr = w.hdr;
-    k_merge_knn<<<div_up(S * 32, kNT), kNT, 0, st>>>(a);
+    C2_LAUNCH(k_merge_knn, div_up(S * 32, kNT), kNT, 0, st, a);
     C2_CUDA_TRY(cudaGetLastError());
   }
 
+  p_brute.end();
   // ---- greedy clusters
+  Prof p_gsetup(st, "greedy_setup");
   C2_CUDA_TRY(scan_exclusive(w.gflag, w.gidx, S, w.scan_tmp, st));
-  k_greedy_list<<<div_up(S, T), T, 0, st>>>(w.gflag, w.gidx, cptr, S, w.gcl, w.gsq, w.gsz, w.hdr);
+  C2_LAUNCH(k_greedy_list, div_up(S, T), T, 0, st, w.gflag, w.gidx, cptr, S, w.gcl, w.gsq, w.gsz, w.hdr);
   int32_t ng = 0;
   C2_CUDA_TRY(cudaMemcpyAsync(&ng, &w.hdr->n_greedy, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   C2_CUDA_TRY(cudaStreamSynchronize(st));
   if (ng == 0) return C2_OK;
   if (W == 0) return C2_ERR_UNSUPPORTED;   // greedy needs the table kernel for its counts
   C2_CUDA_TRY(scan_exclusive64(w.gsq, w.goff, ng, w.scan_tmp64, st));
-  k_gram_stats<<<1, 1, 0, st>>>(w.goff, ng, w.hdr);
+  C2_LAUNCH(k_gram_stats, 1, 1, 0, st, w.goff, ng, w.hdr);
   std::vector<int64_t> goff(ng + 1);
   std::vector<int32_t> gsz(ng);
   C2_CUDA_TRY(cudaMemcpyAsync(goff.data(), w.goff, (ng + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
@@ -744,7 +755,7 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
   for (int g = 0; g < ng; ++g) {
     if (gsz[g] > kMaxGreedyM || goff[g + 1] - goff[g] > cap) return C2_ERR_UNSUPPORTED;
   }
-  k_fill_i64<<<div_up(S, T), T, 0, st>>>(w.gofs, S, -1);
+  C2_LAUNCH(k_fill_i64, div_up(S, T), T, 0, st, w.gofs, S, -1);
   const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
   int g0 = 0;
   while (g0 < ng) {
@@ -752,12 +763,14 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
     int64_t nu = 0;
     while (g1 < ng && goff[g1 + 1] - goff[g0] <= cap) nu += gsz[g1++];
     const int nb = g1 - g0;
+    p_gsetup.end();
+    Prof p_gram(st, "greedy_gram");
     // counts of the batch's greedy clusters into their intersection matrices
-    k_batch_setup<<<div_up(nb, T), T, 0, st>>>(w.gcl, w.goff, w.gsz, g0, g1, Q, w.gofs, w.bt_cnt,
+    C2_LAUNCH(k_batch_setup, div_up(nb, T), T, 0, st, w.gcl, w.goff, w.gsz, g0, g1, Q, w.gofs, w.bt_cnt,
                                                w.bu_cnt);
     C2_CUDA_TRY(scan_exclusive(w.bt_cnt, w.bt_off, nb, w.scan_tmp, st));
     C2_CUDA_TRY(scan_exclusive(w.bu_cnt, w.bu_off, nb, w.scan_tmp, st));
-    k_fill_work<<<div_up(nb, T), T, 0, st>>>(w.bt_cnt, w.bt_off, w.gcl + g0, nb, w.work_c,
+    C2_LAUNCH(k_fill_work, div_up(nb, T), T, 0, st, w.bt_cnt, w.bt_off, w.gcl + g0, nb, w.work_c,
                                              w.work_t, &w.hdr->n_work);
     TableArgs a{};
     a.ptr = ptr; a.items = items; a.n_items = s.m; a.k = k;
@@ -768,8 +781,10 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
     a.hdr = w.hdr; a.counter = &w.hdr->work_counter[1];
     c2_status rc = launch_table_w(W, a, st);
     if (rc) return rc;
+    p_gram.end();
+    Prof p_init(st, "greedy_init");
     // greedy rounds over the batch's users
-    k_fill_users<<<nb, 256, 0, st>>>(w.gcl, cptr, w.bu_off, g0, nb, w.gu_slot, w.gu_g);
+    C2_LAUNCH(k_fill_users, nb, 256, 0, st, w.gcl, cptr, w.bu_off, g0, nb, w.gu_slot, w.gu_g);
     GreedyArgs ga{};
     ga.cptr = cptr; ga.cusers = cusers; ga.slen = w.slen; ga.gcl = w.gcl; ga.gofs = w.gofs;
     ga.gram = w.gram; ga.gu_slot = w.gu_slot; ga.gu_g = w.gu_g; ga.n_users_dev = w.bu_off + nb;
@@ -779,18 +794,22 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
     ga.round = 0;
     ga.wl_in = nullptr;
     ga.wl_out = w.wl0;
-    k_greedy_init<<<grid, kNT, 0, st>>>(ga);
+    C2_LAUNCH(k_greedy_init, grid, kNT, 0, st, ga);
+    p_init.end();
+    Prof p_rounds(st, "greedy_rounds");
     int32_t* cur = w.wl0;
     int32_t* nxt = w.wl1;
     for (int r = 1; r <= rounds; ++r) {
       ga.round = r;
       ga.wl_in = cur;
       ga.wl_out = nxt;
-      k_greedy_round<<<grid, kNT, 0, st>>>(ga);
+      C2_LAUNCH(k_greedy_round, grid, kNT, 0, st, ga);
       std::swap(cur, nxt);
     }
+    p_rounds.end();
+    Prof p_emit(st, "greedy_emit");
     ga.wl_in = cur;
-    k_greedy_emit<<<div_up(nu * 32, kNT), kNT, 0, st>>>(ga);
+    C2_LAUNCH(k_greedy_emit, div_up(nu * 32, kNT), kNT, 0, st, ga);
     C2_CUDA_TRY(cudaGetLastError());
     g0 = g1;
   }
@@ -821,7 +840,7 @@ c2_status run_bruteforce(const int32_t* ptr, const int32_t* items, const Sizes& 
   a.ptr = ptr; a.items = items; a.k = s.k; a.cptr = nullptr; a.n_rows = rows;
   a.queries = queries; a.n_users = s.n; a.out_id = nid; a.out_in = nin; a.out_un = nun;
   a.hdr = w.hdr;
-  k_merge_knn<<<div_up((int64_t)rows * 32, kNT), kNT, 0, st>>>(a);
+  C2_LAUNCH(k_merge_knn, div_up((int64_t)rows * 32, kNT), kNT, 0, st, a);
   C2_CUDA_TRY(cudaGetLastError());
   return C2_OK;
 }

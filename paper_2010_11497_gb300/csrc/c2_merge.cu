@@ -97,8 +97,9 @@ c2_status run_merge(const int32_t* cusers, const Sizes& s, const int32_t* lid, c
                     const int32_t* lun, int32_t* nid, int32_t* nin, int32_t* nun, KnnWs& w,
                     cudaStream_t st) {
   if (s.n == 0) return C2_OK;
-  k_pos_of<<<div_up(s.S, 256), 256, 0, st>>>(cusers, s.S, s.n, w.pos_of);
-  k_merge<<<div_up((int64_t)s.n * 32, 256), 256, 0, st>>>(w.pos_of, s.n, s.t, s.k, lid, lin, lun,
+  Prof p(st, "merge");
+  C2_LAUNCH(k_pos_of, div_up(s.S, 256), 256, 0, st, cusers, s.S, s.n, w.pos_of);
+  C2_LAUNCH(k_merge, div_up((int64_t)s.n * 32, 256), 256, 0, st, w.pos_of, s.n, s.t, s.k, lid, lin, lun,
                                                           nid, nin, nun, w.hdr);
   C2_CUDA_TRY(cudaGetLastError());
   return C2_OK;
@@ -109,8 +110,8 @@ c2_status run_avg_sim(const int32_t* nin, const int32_t* nun, int32_t rows, int3
   (void)hdr;
   if (rows <= 0) return C2_ERR_INVALID_ARG;
   const int nb = (int)std::min<int64_t>(kAvgBlocks, rows);
-  k_avg_partial<<<nb, 256, 0, st>>>(nin, nun, rows, k, partial);
-  k_avg_final<<<1, 256, 0, st>>>(partial, nb, (double)k * (double)rows, out);
+  C2_LAUNCH(k_avg_partial, nb, 256, 0, st, nin, nun, rows, k, partial);
+  C2_LAUNCH(k_avg_final, 1, 256, 0, st, partial, nb, (double)k * (double)rows, out);
   C2_CUDA_TRY(cudaGetLastError());
   return C2_OK;
 }

@@ -65,15 +65,15 @@ cudaError_t scan_impl(const T* in, T* out, int64_t n, T* tmp, cudaStream_t st) {
   if (n <= 0) return cudaMemsetAsync(out, 0, sizeof(T), st);
   const int64_t nb = (n + kScanTile - 1) / kScanTile;
   T* bsum = tmp;
-  k_scan_tile<T><<<(unsigned)nb, kScanNT, 0, st>>>(in, out, n, bsum);
+  C2_LAUNCH(k_scan_tile<T>, (unsigned)nb, kScanNT, 0, st, in, out, n, bsum);
   if (nb > 1) {
     const int64_t used = ((nb + 1 + 63) / 64) * 64;
     cudaError_t e = scan_impl<T>(bsum, bsum, nb, tmp + used, st);
     if (e != cudaSuccess) return e;
-    k_scan_add<T><<<(unsigned)nb, 256, 0, st>>>(out, n, bsum);
-    k_store_total<T><<<1, 1, 0, st>>>(out + n, bsum + nb);
+    C2_LAUNCH(k_scan_add<T>, (unsigned)nb, 256, 0, st, out, n, bsum);
+    C2_LAUNCH(k_store_total<T>, 1, 1, 0, st, out + n, bsum + nb);
   } else {
-    k_store_total<T><<<1, 1, 0, st>>>(out + n, bsum);
+    C2_LAUNCH(k_store_total<T>, 1, 1, 0, st, out + n, bsum);
   }
   return cudaGetLastError();
 }
@@ -187,10 +187,10 @@ cudaError_t radix_sort_pairs(uint32_t* k0, int32_t* v0, uint32_t* k1, int32_t* v
     int32_t* vi = flipped ? v1 : v0;
     uint32_t* ko = flipped ? k0 : k1;
     int32_t* vo = flipped ? v0 : v1;
-    k_rs_upsweep<<<ntiles, kRsNT, 0, st>>>(ki, n, shift, h, ntiles);
+    C2_LAUNCH(k_rs_upsweep, ntiles, kRsNT, 0, st, ki, n, shift, h, ntiles);
     cudaError_t e = scan_exclusive(h, h, (int64_t)256 * ntiles, scan_tmp, st);
     if (e != cudaSuccess) return e;
-    k_rs_downsweep<<<ntiles, kRsNT, 0, st>>>(ki, vi, ko, vo, n, shift, h, ntiles);
+    C2_LAUNCH(k_rs_downsweep, ntiles, kRsNT, 0, st, ki, vi, ko, vo, n, shift, h, ntiles);
     flipped = !flipped;
   }
   if (flipped) {
