@@ -193,7 +193,7 @@ def oracle_sample(ptr, items, w, seed, budget_s, rng_seed=2010, clustering=None,
     est_pairs = np.where(greedy, sizes * (w.k + w.greedy_rounds * w.k * w.k),
                          sizes * (sizes - 1) // 2).astype(np.float64)
     steps_per_pair = 2.0 * float(np.diff(ptr).mean()) + 20.0
-    est_s = est_pairs * steps_per_pair / 1.5e8
+    est_s = est_pairs * steps_per_pair / 2.5e8
     order = np.random.default_rng(rng_seed).permutation(sizes.size)
     only = np.zeros(sizes.size, np.uint8)
     left = budget_s

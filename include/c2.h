@@ -207,8 +207,9 @@ c2_status c2_reset_status(void* d_ws, c2_stream_t stream);
  * the library records a CUDA event pair on the caller's stream around every
  * phase of the build; c2_profile_report() synchronises on those events,
  * writes a JSON object {"phase": {"ms": total, "calls": n, "launches": n}}
- * into buf (NUL-terminated, truncated to len) and clears the records.  It
- * returns the number of bytes the full report needs.  Host only; the
+ * into buf (NUL-terminated, truncated to len) and clears the records; with
+ * buf == NULL it only returns the size.  It returns the number of bytes the
+ * full report needs.  Host only; the
  * profiler state is process-wide and guarded by a mutex. */
 int64_t c2_kernel_launches(void);
 void c2_profile_enable(int on);

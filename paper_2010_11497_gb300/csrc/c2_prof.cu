@@ -72,6 +72,7 @@ void c2_profile_enable(int on) {
 
 size_t c2_profile_report(char* buf, size_t len) {
   std::lock_guard<std::mutex> g(g_mu);
+  const bool consume = buf != nullptr;
   struct Agg {
     double ms = 0;
     long long calls = 0, launches = 0;
@@ -87,10 +88,12 @@ size_t c2_profile_report(char* buf, size_t len) {
     x.ms += ms;
     x.calls += 1;
     x.launches += r.launches;
-    g_pool.push_back(r.a);
-    g_pool.push_back(r.b);
+    if (consume) {
+      g_pool.push_back(r.a);
+      g_pool.push_back(r.b);
+    }
   }
-  g_recs.clear();
+  if (consume) g_recs.clear();
   std::string out = "{";
   for (size_t i = 0; i < order.size(); ++i) {
     const Agg& x = agg[order[i]];
