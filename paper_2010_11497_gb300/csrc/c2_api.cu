@@ -70,6 +70,12 @@ void bind_knn_ws(Ws& w, const Sizes& s, KnnWs& c) {
   c.bu_off = w.take<int32_t>(S + 1);
   c.gu_slot = w.take<int32_t>(S + 1);
   c.gu_g = w.take<int32_t>(S + 1);
+  c.gw_g = w.take<int32_t>(S + 1);
+  c.gw_t = w.take<int32_t>(S + 1);
+  c.bw_cnt = w.take<int32_t>(S + 1);
+  c.bw_off = w.take<int32_t>(S + 1);
+  c.gseq = w.take<int32_t>(S + 1);
+  c.pptr = w.take<int32_t>((int64_t)s.n + 1);
   c.wl0 = w.take<int32_t>((S + 1) * s.k);
   c.wl1 = w.take<int32_t>((S + 1) * s.k);
   c.gram = w.take<uint16_t>(s.gram_budget / 2);
@@ -86,8 +92,8 @@ struct BuildBufs {
 
 // Whole workspace: header, build intermediates, then the larger of the two
 // phase scratch areas (they never live at the same time).
-size_t layout(char* base, const Sizes& s, DevHeader** hdr, BuildBufs* bb, ClusterWs* cw,
-              KnnWs* kw) {
+size_t layout(char* base, size_t ws_bytes, const Sizes& s, DevHeader** hdr, BuildBufs* bb,
+              ClusterWs* cw, KnnWs* kw) {
   Ws w;
   w.base = base;
   DevHeader* h = w.take<DevHeader>(1);
@@ -110,12 +116,20 @@ size_t layout(char* base, const Sizes& s, DevHeader** hdr, BuildBufs* bb, Cluste
   bind_knn_ws(k2, s, kk);
   c.hdr = h;
   kk.hdr = h;
+  // the padded profiles take the rest of the workspace (sized by the caller
+  // through c2_workspace_size, which knows nnz)
+  const size_t fixed = (std::max(a.top, k2.top) + 255) & ~size_t(255);
+  kk.pitems = reinterpret_cast<int32_t*>(base + fixed);
+  kk.pitems_cap = ws_bytes > fixed ? (int64_t)((ws_bytes - fixed) / 4) : 0;
   if (hdr) *hdr = h;
   if (bb) *bb = b;
   if (cw) *cw = c;
   if (kw) *kw = kk;
-  return std::max(a.top, k2.top) + 256;
+  return fixed;
 }
+
+// Bytes of the padded-profile tail for nnz entries over n rows.
+size_t tail_bytes(int64_t nnz, int32_t n) { return (size_t)(nnz + 3 * (int64_t)n + 64) * 4; }
 
 bool sizes_ok(int32_t n, int32_t m, int32_t k, int32_t t, int32_t b, int32_t N) {
   return n >= 0 && m >= 0 && k >= 1 && k <= kMaxK && t >= 1 && t <= kMaxT && b >= 1 &&
@@ -184,7 +198,7 @@ size_t c2_workspace_size(int32_t n_users, int64_t nnz, int32_t n_items, int32_t 
                          int32_t b, int32_t N, const c2_options* opt) {
   if (check_common(n_users, n_items, k, t, b, N, opt) != C2_OK || nnz < 0) return 0;
   Sizes s = make_sizes(n_users, nnz, n_items, k, t, b, N, opt);
-  return layout(nullptr, s, nullptr, nullptr, nullptr, nullptr);
+  return layout(nullptr, 0, s, nullptr, nullptr, nullptr, nullptr) + tail_bytes(nnz, n_users);
 }
 
 c2_status c2_reset_status(void* d_ws, c2_stream_t stream) {
@@ -233,7 +247,7 @@ c2_status c2_frh_cluster(const int32_t* d_csr_ptr, const int32_t* d_csr_items, i
   Sizes s = make_sizes(n_users, 0, n_items, 1, t, b, N, opt);
   DevHeader* hdr;
   ClusterWs cw;
-  size_t need = layout((char*)d_ws, s, &hdr, nullptr, &cw, nullptr);
+  size_t need = layout((char*)d_ws, ws_bytes, s, &hdr, nullptr, &cw, nullptr);
   rc = check_ws(d_ws, ws_bytes, need);
   if (rc) return rc;
   cudaStream_t st = (cudaStream_t)stream;
@@ -257,7 +271,7 @@ c2_status c2_cluster_knn(const int32_t* d_csr_ptr, const int32_t* d_csr_items, i
   Sizes s = make_sizes(n_users, 0, n_items, k, t, 1, 2, opt);
   DevHeader* hdr;
   KnnWs kw;
-  size_t need = layout((char*)d_ws, s, &hdr, nullptr, nullptr, &kw);
+  size_t need = layout((char*)d_ws, ws_bytes, s, &hdr, nullptr, nullptr, &kw);
   rc = check_ws(d_ws, ws_bytes, need);
   if (rc) return rc;
   c2_options o = resolve(opt);
@@ -277,7 +291,7 @@ c2_status c2_merge_topk(const int32_t* d_cusers, int32_t n_users, int32_t t, int
   Sizes s = make_sizes(n_users, 0, 0, k, t, 1, 2, nullptr);
   DevHeader* hdr;
   KnnWs kw;
-  size_t need = layout((char*)d_ws, s, &hdr, nullptr, nullptr, &kw);
+  size_t need = layout((char*)d_ws, ws_bytes, s, &hdr, nullptr, nullptr, &kw);
   rc = check_ws(d_ws, ws_bytes, need);
   if (rc) return rc;
   return run_merge(d_cusers, s, d_loc_id, d_loc_inter, d_loc_union, d_nbr_id, d_nbr_inter,
@@ -298,7 +312,7 @@ c2_status c2_build_knn_graph(const int32_t* d_csr_ptr, const int32_t* d_csr_item
   BuildBufs bb;
   ClusterWs cw;
   KnnWs kw;
-  size_t need = layout((char*)d_ws, s, &hdr, &bb, &cw, &kw);
+  size_t need = layout((char*)d_ws, ws_bytes, s, &hdr, &bb, &cw, &kw);
   rc = check_ws(d_ws, ws_bytes, need);
   if (rc) return rc;
   cudaStream_t st = (cudaStream_t)stream;
@@ -376,7 +390,7 @@ c2_status c2_bruteforce_knn(const int32_t* d_csr_ptr, const int32_t* d_csr_items
   Sizes s = make_sizes(n_users, 0, n_items, k, 1, 1, 2, nullptr);
   DevHeader* hdr;
   KnnWs kw;
-  size_t need = layout((char*)d_ws, s, &hdr, nullptr, nullptr, &kw);
+  size_t need = layout((char*)d_ws, ws_bytes, s, &hdr, nullptr, nullptr, &kw);
   rc = check_ws(d_ws, ws_bytes, need);
   if (rc) return rc;
   cudaStream_t st = (cudaStream_t)stream;
@@ -394,7 +408,7 @@ c2_status c2_avg_sim(const int32_t* d_nbr_inter, const int32_t* d_nbr_union, int
   Sizes s = make_sizes(1, 0, 0, k, 1, 1, 2, nullptr);
   DevHeader* hdr;
   KnnWs kw;
-  size_t need = layout((char*)d_ws, s, &hdr, nullptr, nullptr, &kw);
+  size_t need = layout((char*)d_ws, ws_bytes, s, &hdr, nullptr, nullptr, &kw);
   c2_status rc = check_ws(d_ws, ws_bytes, need);
   if (rc) return rc;
   return run_avg_sim(d_nbr_inter, d_nbr_union, rows, k, d_out, hdr, kw.partial,

@@ -41,6 +41,9 @@ __global__ void k_validate(const int32_t* __restrict__ ptr, const int32_t* __res
   }
   if (__any_sync(0xffffffffu, bad) && lane == 0) dev_fail(hdr, C2_ERR_INVALID_CSR);
   if (lane == 0) atomicMax(&hdr->max_profile, e - s);
+  // padded rows (multiples of 4 items) must still be addressable with int32
+  if (row == n - 1 && lane == 0 && (int64_t)e + 3 * (int64_t)n + 64 >= (int64_t(1) << 31))
+    dev_fail(hdr, C2_ERR_UNSUPPORTED);
 }
 
 // ------------------------------------------------------------------ A1: item hashes

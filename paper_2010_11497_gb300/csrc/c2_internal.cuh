@@ -32,7 +32,8 @@ struct DevHeader {
   unsigned int work_counter[8];  // persistent-kernel work counters
   unsigned long long item_visits[2];  // table kernel: candidate items walked (brute, greedy)
   int32_t greedy_users;
-  int32_t pad[21];
+  int32_t n_gwork;             // greedy round work items of the current batch
+  int32_t pad[20];
 };
 static_assert(sizeof(DevHeader) <= 256, "header must fit 256 bytes");
 
@@ -113,6 +114,12 @@ struct KnnWs {
   int64_t* gofs;           // [S] per-cluster offset into gram, -1 = none
   int32_t *bt_cnt, *bt_off, *bu_cnt, *bu_off;  // [S+1] greedy batch tiles / users
   int32_t *gu_slot, *gu_g; // [S] greedy users of a batch
+  int32_t *gw_g, *gw_t;    // [S+1] greedy round work items: greedy index, user chunk
+  int32_t *bw_cnt, *bw_off;// [S+1] chunks per greedy cluster of a batch
+  int32_t* gseq;           // [S+1] 0, 1, 2, ...
+  int32_t* pptr;           // [n+1] padded CSR offsets
+  int32_t* pitems;         // padded CSR items: the workspace tail
+  int64_t pitems_cap;      // capacity of pitems (elements)
   int32_t *wl0, *wl1;      // [S*k] greedy working lists (local indices)
   uint16_t* gram;          // gram_budget bytes
   int32_t* pos_of;         // [S] (function, user) -> slot
@@ -208,6 +215,7 @@ inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 // ---------------------------------------------------------------- launches
 // Every kernel launch of the library goes through C2_LAUNCH, which counts it.
 extern std::atomic<long long> g_launches;
+#define COMMA ,
 #define C2_LAUNCH(kern, grid, block, smem, st, ...)            \
   do {                                                         \
     kern<<<(grid), (block), (smem), (st)>>>(__VA_ARGS__);      \

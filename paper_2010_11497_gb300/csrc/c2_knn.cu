@@ -25,13 +25,17 @@ cudaError_t scan_exclusive64(const int64_t* d_in, int64_t* d_out, int64_t n, int
 namespace {
 
 constexpr int kNT = 256;
-constexpr int kMaxGreedyM = 32768;            // greedy cluster size limit (shared bitmap)
+constexpr int kMaxGreedyM = 10240;            // greedy cluster size limit (shared staging)
 constexpr int kBitmapWords = kMaxGreedyM / 32;
+constexpr int kGreedyUsersPerWarp = 4;
+constexpr int kGreedyChunk = 8 * kGreedyUsersPerWarp;   // users per block work item
 
 // ------------------------------------------------------------------ table kernel
 struct TableArgs {
-  const int32_t* ptr;
+  const int32_t* ptr;      // CSR (query items, profile lengths)
   const int32_t* items;
+  const int32_t* pptr;     // padded CSR: rows start on 16-byte boundaries,
+  const int32_t* pitems;   //   padded with the sentinel item n_items
   int32_t n_items, k;
   const int32_t* work_c;   // cluster of each work item (cluster mode)
   const int32_t* work_t;   // query tile of each work item
@@ -42,7 +46,7 @@ struct TableArgs {
   int32_t n_queries, n_users;
   int32_t *out_id, *out_in, *out_un;
   const int64_t* gofs;     // per-cluster offset into gram (elements), -1 = brute force
-  uint16_t* gram;
+  uint16_t* gram;          // rows of stride round_up(M, 8)
   DevHeader* hdr;
   unsigned* counter;
 };
@@ -79,39 +83,66 @@ __device__ __forceinline__ void flush(uint32_t* acc, uint32_t* C) {
 }
 
 template <int W>
-__device__ __forceinline__ void count_profile(const int32_t* __restrict__ row, int len,
-                                              const uint32_t* __restrict__ T, uint32_t* C) {
-  uint32_t acc[4 * W];
+__device__ __forceinline__ void look4(const uint32_t* __restrict__ T, const int4 q, uint32_t* acc) {
+  const int xs[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
-  for (int i = 0; i < 4 * W; ++i) acc[i] = 0;
-  for (int e0 = 0; e0 < len; e0 += 15) {
-    const int e1 = min(len, e0 + 15);
-    for (int e = e0; e < e1; ++e) {
-      const int x = __ldg(row + e);
-      if (W == 1) {
-        add_mask(acc, T[x]);
-      } else {
-        const uint2 m = reinterpret_cast<const uint2*>(T)[x];
-        add_mask(acc, m.x);
-        add_mask(acc + 4, m.y);
-      }
+  for (int i = 0; i < 4; ++i) {
+    if (W == 1) {
+      add_mask(acc, T[xs[i]]);
+    } else {
+      const uint2 m = reinterpret_cast<const uint2*>(T)[xs[i]];
+      add_mask(acc, m.x);
+      add_mask(acc + 4, m.y);
     }
-#pragma unroll
-    for (int w = 0; w < W; ++w) flush(acc + 4 * w, C + 16 * w);
   }
 }
 
+// Walks one padded profile (n4 int4 words) in groups of 12 items (3 loads),
+// the next group's loads issued before the current group is counted.
 template <int W>
-__global__ void __launch_bounds__(kNT) k_table(TableArgs a) {
-  constexpr int Q = 32 * W, QPW = Q / 8;
-  extern __shared__ __align__(16) uint32_t T[];
-  __shared__ uint32_t cntw[16 * W][kNT];
-  __shared__ int32_t cand_id[kNT], cand_len[kNT];
+__device__ __forceinline__ void count_row4(const int4* __restrict__ r4, int n4,
+                                           const uint32_t* __restrict__ T, int sentinel,
+                                           uint32_t* C) {
+  const int4 pad = make_int4(sentinel, sentinel, sentinel, sentinel);
+  int4 cur[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) cur[j] = j < n4 ? __ldg(r4 + j) : pad;
+  uint32_t acc[4 * W];
+#pragma unroll
+  for (int i = 0; i < 4 * W; ++i) acc[i] = 0;
+  for (int i = 0; i < n4; i += 3) {
+    int4 nxt[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) nxt[j] = (i + 3 + j < n4) ? __ldg(r4 + i + 3 + j) : pad;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) look4<W>(T, cur[j], acc);
+#pragma unroll
+    for (int w = 0; w < W; ++w) flush(acc + 4 * w, C + 16 * w);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) cur[j] = nxt[j];
+  }
+}
+
+template <int W, int NT>
+__host__ __device__ constexpr int table_static_words() {
+  return 16 * W * NT + 2 * NT;
+}
+
+__host__ __device__ inline int table_T_words(int W, int m) { return (((m + 1) * W) + 3) & ~3; }
+
+template <int W, int NT>
+__global__ void __launch_bounds__(NT) k_table(TableArgs a) {
+  constexpr int Q = 32 * W, NWARP = NT / 32, QPW = (Q + NWARP - 1) / NWARP;
+  extern __shared__ __align__(16) uint32_t smem[];
+  uint32_t* T = smem;
+  uint32_t* cntw = smem + table_T_words(W, a.n_items);      // [16W][NT]
+  int32_t* cand_id = reinterpret_cast<int32_t*>(cntw + 16 * W * NT);
+  int32_t* cand_len = cand_id + NT;
   __shared__ int32_t q_id[Q], q_len[Q];
   __shared__ int s_work;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int k = a.k;
-  for (int i = tid; i < a.n_items * W; i += kNT) T[i] = 0;
+  for (int i = tid; i < (a.n_items + 1) * W; i += NT) T[i] = 0;
   const int nwork = *a.n_work;
   unsigned long long visits = 0;
   __syncthreads();
@@ -154,7 +185,7 @@ __global__ void __launch_bounds__(kNT) k_table(TableArgs a) {
       q_len[tid] = len;
     }
     __syncthreads();
-    for (int j = warp; j < nq; j += 8) {
+    for (int j = warp; j < nq; j += NWARP) {
       const int u = q_id[j];
       for (int e = a.ptr[u] + lane; e < a.ptr[u + 1]; e += 32)
         atomicOr(&T[a.items[e] * W + (j >> 5)], 1u << (j & 31));
@@ -163,7 +194,8 @@ __global__ void __launch_bounds__(kNT) k_table(TableArgs a) {
     WarpList L[QPW];
 #pragma unroll
     for (int s = 0; s < QPW; ++s) { L[s].id = -1; L[s].c = 0; L[s].u = 0; }
-    for (int cb = 0; cb < M; cb += kNT) {
+    const int Mp = (M + 7) & ~7;
+    for (int cb = 0; cb < M; cb += NT) {
       const int vl = cb + tid;
       const bool act = vl < M;
       const int v = act ? (clist ? clist[cbase + vl] : vl) : -1;
@@ -171,27 +203,30 @@ __global__ void __launch_bounds__(kNT) k_table(TableArgs a) {
       uint32_t C[16 * W];
 #pragma unroll
       for (int r = 0; r < 16 * W; ++r) C[r] = 0;
-      if (act) count_profile<W>(a.items + a.ptr[v], len, T, C);
-      visits += (unsigned)len;
+      if (act) {
+        count_row4<W>(reinterpret_cast<const int4*>(a.pitems + a.pptr[v]), (len + 3) >> 2, T,
+                      a.n_items, C);
+        visits += (unsigned)len;
+      }
       if (gofs >= 0) {
         // greedy cluster: keep every count (row = query, column = candidate)
-        uint16_t* G = a.gram + gofs + (int64_t)(tq * Q) * M + vl;
+        uint16_t* G = a.gram + gofs + (int64_t)(tq * Q) * Mp + vl;
         if (act) {
 #pragma unroll
           for (int j = 0; j < Q; ++j)
-            if (j < nq) G[(int64_t)j * M] = (uint16_t)((C[creg(j)] >> (16 * chalf(j))) & 0xFFFFu);
+            if (j < nq) G[(int64_t)j * Mp] = (uint16_t)((C[creg(j)] >> (16 * chalf(j))) & 0xFFFFu);
         }
         continue;
       }
 #pragma unroll
-      for (int r = 0; r < 16 * W; ++r) cntw[r][tid] = C[r];
+      for (int r = 0; r < 16 * W; ++r) cntw[r * NT + tid] = C[r];
       cand_id[tid] = v;
       cand_len[tid] = len;
       __syncthreads();
-      const int nc = min(kNT, M - cb);
+      const int nc = min(NT, M - cb);
 #pragma unroll
       for (int s = 0; s < QPW; ++s) {
-        const int j = warp + 8 * s;
+        const int j = warp + NWARP * s;
         if (j < nq) {
           const int qid = q_id[j], qlen = q_len[j];
           const int r = creg(j), h = chalf(j);
@@ -205,7 +240,7 @@ __global__ void __launch_bounds__(kNT) k_table(TableArgs a) {
             uint32_t cc = 0, uu = 0;
             int32_t vid = -1;
             if (i < nc) {
-              cc = (cntw[r][i] >> (16 * h)) & 0xFFFFu;
+              cc = (cntw[r * NT + i] >> (16 * h)) & 0xFFFFu;
               vid = cand_id[i];
               if (vid != qid && cc > 0) {
                 uu = (uint32_t)(qlen + cand_len[i]) - cc;
@@ -229,7 +264,7 @@ __global__ void __launch_bounds__(kNT) k_table(TableArgs a) {
     if (gofs < 0) {
 #pragma unroll
       for (int s = 0; s < QPW; ++s) {
-        const int j = warp + 8 * s;
+        const int j = warp + NWARP * s;
         if (j < nq && lane < k) {
           const int64_t row = (int64_t)(qbase + j) * k + lane;
           const bool ok = L[s].id >= 0;
@@ -240,7 +275,7 @@ __global__ void __launch_bounds__(kNT) k_table(TableArgs a) {
       }
     }
     __syncthreads();
-    for (int j = warp; j < nq; j += 8) {
+    for (int j = warp; j < nq; j += NWARP) {
       const int u = q_id[j];
       for (int e = a.ptr[u] + lane; e < a.ptr[u + 1]; e += 32) T[a.items[e] * W + (j >> 5)] = 0;
     }
@@ -249,6 +284,28 @@ __global__ void __launch_bounds__(kNT) k_table(TableArgs a) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) visits += __shfl_xor_sync(0xffffffffu, visits, o);
   if (lane == 0 && visits) atomicAdd(&a.hdr->item_visits[a.gofs ? 1 : 0], visits);
+}
+
+// ------------------------------------------------------------------ padded CSR
+// Rows padded to a multiple of 4 items with the sentinel item m, so that each
+// row starts on a 16-byte boundary and is read with int4 loads.
+__global__ void k_pad_len(const int32_t* __restrict__ ptr, int32_t n, int32_t* __restrict__ plen) {
+  const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (u < n) plen[u] = ((ptr[u + 1] - ptr[u]) + 3) & ~3;
+}
+
+__global__ void k_pad_copy(const int32_t* __restrict__ ptr, const int32_t* __restrict__ items,
+                           const int32_t* __restrict__ pptr, int32_t n, int32_t m,
+                           int64_t capacity, int32_t* __restrict__ pitems, DevHeader* hdr) {
+  const int lane = threadIdx.x & 31;
+  const int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (u >= n || dev_failed(hdr)) return;
+  if ((int64_t)pptr[n] > capacity || pptr[n] < 0) {
+    if (lane == 0) dev_fail(hdr, C2_ERR_WORKSPACE);
+    return;
+  }
+  const int32_t s = ptr[u], len = ptr[u + 1] - s, ps = pptr[u], plen = pptr[u + 1] - ps;
+  for (int j = lane; j < plen; j += 32) pitems[ps + j] = j < len ? items[s + j] : m;
 }
 
 // ------------------------------------------------------------------ merge kernel
@@ -414,7 +471,7 @@ __global__ void k_greedy_list(const int32_t* __restrict__ gflag, const int32_t* 
   const int g = gidx[c];
   const int32_t M = cptr[c + 1] - cptr[c];
   gcl[g] = (int32_t)c;
-  gsq[g] = (int64_t)M * M;
+  gsq[g] = (int64_t)M * ((M + 7) & ~7);   // rows padded to 16 bytes
   gsz[g] = M;
   atomicMax(&hdr->max_cluster, M);
   atomicAdd(&hdr->greedy_users, M);
@@ -445,6 +502,19 @@ __global__ void k_fill_users(const int32_t* __restrict__ gcl, const int32_t* __r
   }
 }
 
+__global__ void k_chunk_count(const int32_t* __restrict__ gsz, int32_t g0, int32_t nb,
+                              int32_t* __restrict__ cnt) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < nb) cnt[j] = (gsz[g0 + j] + kGreedyChunk - 1) / kGreedyChunk;
+}
+
+__global__ void k_set_count(int32_t* p, int32_t v) { *p = v; }
+
+__global__ void k_iota(int32_t* p, int64_t n) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n) p[j] = (int32_t)j;
+}
+
 __global__ void k_fill_i64(int64_t* p, int64_t n, int64_t v) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j < n) p[j] = v;
@@ -457,11 +527,15 @@ struct GreedyArgs {
   const int32_t* slen;     // profile length per slot
   const int32_t* gcl;
   const int64_t* gofs;     // per cluster
-  const uint16_t* gram;
-  const int32_t* gu_slot;
+  const uint16_t* gram;    // count rows of stride round_up(M, 8)
+  const int32_t* gu_slot;  // per-user launches: slot and greedy index
   const int32_t* gu_g;
   const int32_t* n_users_dev;
-  int32_t k, round, n_random;
+  const int32_t* gw_g;     // per-block launches: greedy index and user chunk
+  const int32_t* gw_t;
+  const int32_t* n_gwork;
+  unsigned* counter;
+  int32_t k, round, n_random, mcap;
   uint2 key;               // Philox key = run seed
   const int32_t* wl_in;    // [S][k] local indices
   int32_t* wl_out;
@@ -492,7 +566,7 @@ __global__ void __launch_bounds__(kNT) k_greedy_init(GreedyArgs a) {
     const int slot = a.gu_slot[w];
     const int c = a.gcl[a.gu_g[w]];
     const int cs = a.cptr[c], M = a.cptr[c + 1] - cs, l = slot - cs;
-    const uint16_t* G = a.gram + a.gofs[c] + (int64_t)l * M;
+    const uint16_t* G = a.gram + a.gofs[c] + (int64_t)l * ((M + 7) & ~7);
     const int k = a.k, k0 = min(k, M - 1);
     int cnt = 0;
     // rejection sampling of distinct members; bounded so that no warp can
@@ -534,87 +608,111 @@ __global__ void __launch_bounds__(kNT) k_greedy_init(GreedyArgs a) {
       atomicAnd(&bm[v >> 5], ~(1u << (v & 31)));
     }
     __syncwarp();
-    evals += (unsigned long long)k0;
+    evals += (unsigned long long)cnt;
   }
   if (lane == 0 && evals) atomicAdd(&a.hdr->pairs, evals);
 }
 
-// One synchronous round: candidates = own list + neighbours' lists (+ random
-// draws), deduplicated with a per-warp bitmap of the cluster.
+// One synchronous round.  A block takes a chunk of users of one cluster: the
+// cluster's profile lengths are staged in shared memory once, and every warp
+// stages its user's row of intersection counts before walking the
+// candidates (own list, neighbours' lists, optional random draws),
+// deduplicated with a per-warp bitmap of the cluster.
 __global__ void __launch_bounds__(kNT) k_greedy_round(GreedyArgs a) {
-  __shared__ uint32_t bm_all[8][kBitmapWords];
+  extern __shared__ __align__(16) uint32_t gsm[];
+  const int mcap = a.mcap;                               // multiple of 32
+  int32_t* s_len = reinterpret_cast<int32_t*>(gsm);      // [mcap]
+  uint16_t* s_rows = reinterpret_cast<uint16_t*>(gsm + mcap);   // [8][mcap]
+  uint32_t* s_bm = gsm + mcap + 4 * mcap;                // [8][mcap/32]
+  __shared__ int s_work;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint32_t* bm = bm_all[warp];
-  for (int i = lane; i < kBitmapWords; i += 32) bm[i] = 0;
-  __syncwarp();
-  const int nu = *a.n_users_dev;
-  const int nwarps = gridDim.x * 8;
+  uint16_t* row = s_rows + warp * mcap;
+  uint32_t* bm = s_bm + warp * (mcap >> 5);
+  const int nwork = *a.n_gwork;
+  const int k = a.k;
   unsigned long long evals = 0;
-  for (int w = blockIdx.x * 8 + warp; w < nu; w += nwarps) {
-    if (dev_failed(a.hdr)) break;
-    const int slot = a.gu_slot[w];
-    const int c = a.gcl[a.gu_g[w]];
-    const int cs = a.cptr[c], M = a.cptr[c + 1] - cs, l = slot - cs;
-    const uint16_t* G = a.gram + a.gofs[c] + (int64_t)l * M;
-    const int k = a.k;
-    const uint32_t my = (uint32_t)a.slen[slot];
-    const int e = lane < k ? a.wl_in[(int64_t)slot * k + lane] : -1;
-    WarpList Lst;
-    Lst.id = e;
-    Lst.c = 0;
-    Lst.u = 0;
-    if (e >= 0) {
-      Lst.c = G[e];
-      Lst.u = my + (uint32_t)a.slen[cs + e] - Lst.c;
-      atomicOr(&bm[e >> 5], 1u << (e & 31));
-    }
-    if (lane == 0) atomicOr(&bm[l >> 5], 1u << (l & 31));
-    __syncwarp();
-    unsigned fresh = 0;
-    const int nlist = __popc(__ballot_sync(0xffffffffu, e >= 0));
-    const int nsrc = nlist + ((a.n_random + 31) / 32);
-    for (int j = 0; j < nsrc; ++j) {
-      int v = -1;
-      if (j < nlist) {
+  for (;;) {
+    if (threadIdx.x == 0) s_work = dev_failed(a.hdr) ? nwork : (int)atomicAdd(a.counter, 1u);
+    __syncthreads();
+    const int wi = s_work;
+    if (wi >= nwork) break;
+    const int g = a.gw_g[wi], chunk = a.gw_t[wi];
+    const int c = a.gcl[g];
+    const int cs = a.cptr[c], M = a.cptr[c + 1] - cs, Mp = (M + 7) & ~7;
+    for (int v = threadIdx.x; v < M; v += kNT) s_len[v] = a.slen[cs + v];
+    __syncthreads();
+    const uint16_t* Gc = a.gram + a.gofs[c];
+    for (int uu = 0; uu < kGreedyUsersPerWarp; ++uu) {
+      const int l = chunk * kGreedyChunk + uu * 8 + warp;
+      if (l >= M) break;
+      const int slot = cs + l;
+      // stage my row of counts (16-byte aligned rows) and clear my bitmap
+      const uint4* g4 = reinterpret_cast<const uint4*>(Gc + (int64_t)l * Mp);
+      uint4* r4 = reinterpret_cast<uint4*>(row);
+      for (int i = lane; i < (Mp >> 3); i += 32) r4[i] = g4[i];
+      for (int i = lane; i < ((M + 31) >> 5); i += 32) bm[i] = 0;
+      __syncwarp();
+      const uint32_t my = (uint32_t)s_len[l];
+      const int e = lane < k ? a.wl_in[(int64_t)slot * k + lane] : -1;
+      WarpList Lst;
+      Lst.id = e;
+      Lst.c = e >= 0 ? row[e] : 0u;
+      Lst.u = e >= 0 ? my + (uint32_t)s_len[e] - Lst.c : 0u;
+      if (e >= 0) atomicOr(&bm[e >> 5], 1u << (e & 31));
+      if (lane == 0) atomicOr(&bm[l >> 5], 1u << (l & 31));
+      const int nlist = __popc(__ballot_sync(0xffffffffu, e >= 0));
+      // all neighbour rows at once (independent loads)
+      int cand[kMaxK];
+#pragma unroll
+      for (int j = 0; j < kMaxK; ++j) {
         const int nb = __shfl_sync(0xffffffffu, e, j);
-        if (lane < k) v = a.wl_in[(int64_t)(cs + nb) * k + lane];
-      } else {
-        const int d = (j - nlist) * 32 + lane;
-        if (d < a.n_random) {
-          const uint4 r = philox10(make_uint4((uint32_t)c, (uint32_t)l, (uint32_t)a.round, (uint32_t)d), a.key);
+        cand[j] = (j < nlist && lane < k) ? a.wl_in[(int64_t)(cs + nb) * k + lane] : -1;
+      }
+      __syncwarp();
+      unsigned fresh = 0;
+      // one candidate per lane: dedupe, count lookup, exact filter, insert
+      auto consider = [&](int v) {
+        bool isnew = false;
+        if (v >= 0) {
+          const uint32_t bit = 1u << (v & 31);
+          isnew = (atomicOr(&bm[v >> 5], bit) & bit) == 0;
+        }
+        uint32_t cc = 0, uu2 = 0;
+        if (isnew) {
+          ++fresh;
+          cc = row[v];
+          uu2 = my + (uint32_t)s_len[v] - cc;
+        }
+        WarpList kth;
+        kth.id = __shfl_sync(0xffffffffu, Lst.id, k - 1);
+        kth.c = __shfl_sync(0xffffffffu, Lst.c, k - 1);
+        kth.u = __shfl_sync(0xffffffffu, Lst.u, k - 1);
+        const bool pass = isnew && beats(kth, v, cc, uu2);
+        unsigned mask = __ballot_sync(0xffffffffu, pass);
+        while (mask) {
+          const int src = __ffs(mask) - 1;
+          mask &= mask - 1;
+          warp_list_insert(Lst, k, __shfl_sync(0xffffffffu, v, src),
+                           __shfl_sync(0xffffffffu, cc, src), __shfl_sync(0xffffffffu, uu2, src));
+        }
+      };
+#pragma unroll
+      for (int j = 0; j < kMaxK; ++j)
+        if (j < nlist) consider(cand[j]);
+      for (int d0 = 0; d0 < a.n_random; d0 += 32) {
+        int v = -1;
+        if (d0 + lane < a.n_random) {
+          const uint4 r = philox10(make_uint4((uint32_t)c, (uint32_t)l, (uint32_t)a.round,
+                                              (uint32_t)(d0 + lane)), a.key);
           v = draw_other(r.x, l, M);
         }
+        consider(v);
       }
-      bool isnew = false;
-      if (v >= 0) {
-        const uint32_t bit = 1u << (v & 31);
-        isnew = (atomicOr(&bm[v >> 5], bit) & bit) == 0;
-      }
-      uint32_t cc = 0, uu = 0;
-      bool pass = false;
-      if (isnew) {
-        ++fresh;
-        cc = G[v];
-        uu = my + (uint32_t)a.slen[cs + v] - cc;
-      }
-      WarpList kth;
-      kth.id = __shfl_sync(0xffffffffu, Lst.id, k - 1);
-      kth.c = __shfl_sync(0xffffffffu, Lst.c, k - 1);
-      kth.u = __shfl_sync(0xffffffffu, Lst.u, k - 1);
-      if (isnew) pass = beats(kth, v, cc, uu);
-      unsigned mask = __ballot_sync(0xffffffffu, pass);
-      while (mask) {
-        const int src = __ffs(mask) - 1;
-        mask &= mask - 1;
-        warp_list_insert(Lst, k, __shfl_sync(0xffffffffu, v, src), __shfl_sync(0xffffffffu, cc, src),
-                         __shfl_sync(0xffffffffu, uu, src));
-      }
+      if (lane < k) a.wl_out[(int64_t)slot * k + lane] = Lst.id;
+      evals += fresh;
+      __syncwarp();
     }
-    if (lane < k) a.wl_out[(int64_t)slot * k + lane] = Lst.id;
-    __syncwarp();
-    for (int i = lane; i < (M + 31) / 32; i += 32) bm[i] = 0;
-    __syncwarp();
-    evals += fresh;
+    __syncthreads();
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) evals += __shfl_xor_sync(0xffffffffu, evals, o);
@@ -629,7 +727,7 @@ __global__ void __launch_bounds__(kNT) k_greedy_emit(GreedyArgs a) {
   const int slot = a.gu_slot[w];
   const int c = a.gcl[a.gu_g[w]];
   const int cs = a.cptr[c], M = a.cptr[c + 1] - cs, l = slot - cs;
-  const uint16_t* G = a.gram + a.gofs[c] + (int64_t)l * M;
+  const uint16_t* G = a.gram + a.gofs[c] + (int64_t)l * ((M + 7) & ~7);
   const int k = a.k;
   if (lane >= k) return;
   const int e = a.wl_in[(int64_t)slot * k + lane];
@@ -652,41 +750,75 @@ __global__ void k_gram_stats(const int64_t* __restrict__ goff, int32_t ng, DevHe
 }
 
 // ------------------------------------------------------------------ launch helpers
-int table_smem_bytes(int W, int m) { return m * W * 4; }
+struct TableCfg {
+  int W, NT;
+};
 
-bool table_fits(int W, int m) {
-  int dev = 0, optin = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  const int stat = 16 * W * kNT * 4 + 2 * kNT * 4 + 64 * W * 4 * 2 + 64;
-  return table_smem_bytes(W, m) + stat <= optin;
+int smem_optin() {
+  static int v = 0;
+  if (!v) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  }
+  return v;
 }
 
-template <int W>
-c2_status launch_table(const TableArgs& a, cudaStream_t st) {
-  const int smem = table_smem_bytes(W, a.n_items);
-  C2_CUDA_TRY(cudaFuncSetAttribute(k_table<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+int table_smem_bytes(TableCfg c, int m) {
+  return 4 * (table_T_words(c.W, m) + 16 * c.W * c.NT + 2 * c.NT);
+}
+
+bool table_fits(TableCfg c, int m) {
+  const int stat = 4 * (2 * 32 * c.W + 1) + 64;
+  return table_smem_bytes(c, m) + stat <= smem_optin();
+}
+
+template <int W, int NT>
+c2_status launch_table_t(const TableArgs& a, cudaStream_t st) {
+  const int smem = table_smem_bytes(TableCfg{W, NT}, a.n_items);
+  C2_CUDA_TRY(cudaFuncSetAttribute(k_table<W, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   int per_sm = 0;
-  C2_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_table<W>, kNT, smem));
+  C2_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_table<W, NT>, NT, smem));
   if (per_sm < 1) return C2_ERR_UNSUPPORTED;
   C2_CUDA_TRY(cudaMemsetAsync(a.counter, 0, sizeof(unsigned), st));
-  C2_LAUNCH(k_table<W>, num_sms() * per_sm, kNT, smem, st, a);
+  C2_LAUNCH(k_table<W COMMA NT>, num_sms() * per_sm, NT, smem, st, a);
   C2_CUDA_TRY(cudaGetLastError());
   return C2_OK;
 }
 
-int pick_w(int strategy, int m) {
-  if (strategy == C2_STRATEGY_MERGE) return 0;
-  if (strategy == C2_STRATEGY_TABLE32) return table_fits(1, m) ? 1 : 0;
-  if (strategy == C2_STRATEGY_TABLE64) return table_fits(2, m) ? 2 : (table_fits(1, m) ? 1 : 0);
-  // automatic: the widest table that fits
-  if (table_fits(2, m)) return 2;
-  if (table_fits(1, m)) return 1;
-  return 0;
+c2_status launch_table(TableCfg c, const TableArgs& a, cudaStream_t st) {
+  if (c.W == 1 && c.NT == 256) return launch_table_t<1, 256>(a, st);
+  if (c.W == 1 && c.NT == 512) return launch_table_t<1, 512>(a, st);
+  if (c.W == 1 && c.NT == 1024) return launch_table_t<1, 1024>(a, st);
+  if (c.W == 2 && c.NT == 256) return launch_table_t<2, 256>(a, st);
+  if (c.W == 2 && c.NT == 512) return launch_table_t<2, 512>(a, st);
+  return C2_ERR_UNSUPPORTED;
 }
 
-c2_status launch_table_w(int W, const TableArgs& a, cudaStream_t st) {
-  return W == 2 ? launch_table<2>(a, st) : launch_table<1>(a, st);
+// Table shapes in order of preference when nothing is forced; W = 0 means
+// the sorted-merge kernel.
+TableCfg pick_table(int strategy, int m) {
+  static const TableCfg wide[] = {{2, 512}, {2, 256}};
+  static const TableCfg narrow[] = {{1, 1024}, {1, 512}, {1, 256}};
+  if (strategy == C2_STRATEGY_MERGE) return {0, 0};
+  if (strategy != C2_STRATEGY_TABLE32) {
+    for (const TableCfg& c : wide)
+      if (table_fits(c, m)) return c;
+  }
+  for (const TableCfg& c : narrow)
+    if (table_fits(c, m)) return c;
+  return {0, 0};
+}
+
+c2_status build_padded_csr(const int32_t* ptr, const int32_t* items, const Sizes& s, KnnWs& w,
+                           cudaStream_t st) {
+  if (s.n == 0) return C2_OK;
+  C2_LAUNCH(k_pad_len, div_up(s.n, 256), 256, 0, st, ptr, s.n, w.pptr);
+  C2_CUDA_TRY(scan_exclusive(w.pptr, w.pptr, s.n, w.scan_tmp, st));
+  C2_LAUNCH(k_pad_copy, div_up((int64_t)s.n * 32, 256), 256, 0, st, ptr, items, w.pptr, s.n, s.m,
+            w.pitems_cap, w.pitems, w.hdr);
+  C2_CUDA_TRY(cudaGetLastError());
+  return C2_OK;
 }
 
 }  // namespace
@@ -701,49 +833,61 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
   const int k = s.k;
   const int thr = opt.greedy_threshold > 0 ? opt.greedy_threshold : 5 * k * k;
   const int rounds = opt.greedy_rounds >= 0 ? opt.greedy_rounds : 10;
-  const int W = pick_w(opt.strategy, s.m);
-  const int Q = W ? 32 * W : 32;
+  const TableCfg tc = pick_table(opt.strategy, s.m);
+  const int Q = tc.W ? 32 * tc.W : 32;
 
   Prof p_prep(st, "knn_prep");
-  C2_LAUNCH(k_prep, div_up(S, T), T, 0, st, cptr, n_clusters, S, thr, Q, k, w.ntiles, w.gflag, lid, lin,
-                                      lun, w.hdr);
-  C2_LAUNCH(k_slot_info, div_up(S, T), T, 0, st, cptr, n_clusters, cusers, ptr, S, w.slot2c, w.slen);
+  C2_LAUNCH(k_prep, div_up(S, T), T, 0, st, cptr, n_clusters, S, thr, Q, k, w.ntiles, w.gflag,
+            lid, lin, lun, w.hdr);
+  C2_LAUNCH(k_slot_info, div_up(S, T), T, 0, st, cptr, n_clusters, cusers, ptr, S, w.slot2c,
+            w.slen);
   C2_CUDA_TRY(cudaGetLastError());
-
-  p_prep.end();
-  // ---- brute-force clusters
-  Prof p_brute(st, W ? "brute_table" : "brute_merge");
-  if (W) {
-    C2_CUDA_TRY(scan_exclusive(w.ntiles, w.toff, S, w.scan_tmp, st));
-    C2_LAUNCH(k_fill_work, div_up(S, T), T, 0, st, w.ntiles, w.toff, nullptr, S, w.work_c, w.work_t,
-                                            &w.hdr->n_work);
-    TableArgs a{};
-    a.ptr = ptr; a.items = items; a.n_items = s.m; a.k = k;
-    a.work_c = w.work_c; a.work_t = w.work_t; a.n_work = &w.hdr->n_work;
-    a.cptr = cptr; a.cusers = cusers;
-    a.out_id = lid; a.out_in = lin; a.out_un = lun;
-    a.gofs = nullptr; a.gram = nullptr;
-    a.hdr = w.hdr; a.counter = &w.hdr->work_counter[0];
-    c2_status rc = launch_table_w(W, a, st);
+  if (tc.W) {
+    c2_status rc = build_padded_csr(ptr, items, s, w, st);
     if (rc) return rc;
-  } else {
-    MergeArgs a{};
-    a.ptr = ptr; a.items = items; a.k = k; a.cptr = cptr; a.cusers = cusers; a.slot2c = w.slot2c;
-    a.n_rows = S; a.thr = thr; a.out_id = lid; a.out_in = lin; a.out_un = lun; a.hdr = w.hdr;
-    C2_LAUNCH(k_merge_knn, div_up(S * 32, kNT), kNT, 0, st, a);
-    C2_CUDA_TRY(cudaGetLastError());
+  }
+  p_prep.end();
+
+  TableArgs ta{};
+  ta.ptr = ptr; ta.items = items; ta.pptr = w.pptr; ta.pitems = w.pitems;
+  ta.n_items = s.m; ta.k = k;
+  ta.work_c = w.work_c; ta.work_t = w.work_t; ta.n_work = &w.hdr->n_work;
+  ta.cptr = cptr; ta.cusers = cusers;
+  ta.out_id = lid; ta.out_in = lin; ta.out_un = lun;
+  ta.hdr = w.hdr;
+
+  // ---- brute-force clusters
+  {
+    Prof p_brute(st, tc.W ? "brute_table" : "brute_merge");
+    if (tc.W) {
+      C2_CUDA_TRY(scan_exclusive(w.ntiles, w.toff, S, w.scan_tmp, st));
+      C2_LAUNCH(k_fill_work, div_up(S, T), T, 0, st, w.ntiles, w.toff, nullptr, S, w.work_c,
+                w.work_t, &w.hdr->n_work);
+      TableArgs a = ta;
+      a.gofs = nullptr;
+      a.counter = &w.hdr->work_counter[0];
+      c2_status rc = launch_table(tc, a, st);
+      if (rc) return rc;
+    } else {
+      MergeArgs a{};
+      a.ptr = ptr; a.items = items; a.k = k; a.cptr = cptr; a.cusers = cusers;
+      a.slot2c = w.slot2c; a.n_rows = S; a.thr = thr; a.out_id = lid; a.out_in = lin;
+      a.out_un = lun; a.hdr = w.hdr;
+      C2_LAUNCH(k_merge_knn, div_up(S * 32, kNT), kNT, 0, st, a);
+      C2_CUDA_TRY(cudaGetLastError());
+    }
   }
 
-  p_brute.end();
   // ---- greedy clusters
   Prof p_gsetup(st, "greedy_setup");
   C2_CUDA_TRY(scan_exclusive(w.gflag, w.gidx, S, w.scan_tmp, st));
-  C2_LAUNCH(k_greedy_list, div_up(S, T), T, 0, st, w.gflag, w.gidx, cptr, S, w.gcl, w.gsq, w.gsz, w.hdr);
+  C2_LAUNCH(k_greedy_list, div_up(S, T), T, 0, st, w.gflag, w.gidx, cptr, S, w.gcl, w.gsq, w.gsz,
+            w.hdr);
   int32_t ng = 0;
   C2_CUDA_TRY(cudaMemcpyAsync(&ng, &w.hdr->n_greedy, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   C2_CUDA_TRY(cudaStreamSynchronize(st));
   if (ng == 0) return C2_OK;
-  if (W == 0) return C2_ERR_UNSUPPORTED;   // greedy needs the table kernel for its counts
+  if (tc.W == 0) return C2_ERR_UNSUPPORTED;   // greedy needs the table kernel for its counts
   C2_CUDA_TRY(scan_exclusive64(w.gsq, w.goff, ng, w.scan_tmp64, st));
   C2_LAUNCH(k_gram_stats, 1, 1, 0, st, w.goff, ng, w.hdr);
   std::vector<int64_t> goff(ng + 1);
@@ -757,59 +901,78 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
   }
   C2_LAUNCH(k_fill_i64, div_up(S, T), T, 0, st, w.gofs, S, -1);
   const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+  p_gsetup.end();
   int g0 = 0;
   while (g0 < ng) {
     int g1 = g0;
     int64_t nu = 0;
-    while (g1 < ng && goff[g1 + 1] - goff[g0] <= cap) nu += gsz[g1++];
+    int mmax = 0;
+    while (g1 < ng && goff[g1 + 1] - goff[g0] <= cap) {
+      mmax = std::max(mmax, gsz[g1]);
+      nu += gsz[g1++];
+    }
     const int nb = g1 - g0;
-    p_gsetup.end();
-    Prof p_gram(st, "greedy_gram");
-    // counts of the batch's greedy clusters into their intersection matrices
-    C2_LAUNCH(k_batch_setup, div_up(nb, T), T, 0, st, w.gcl, w.goff, w.gsz, g0, g1, Q, w.gofs, w.bt_cnt,
-                                               w.bu_cnt);
-    C2_CUDA_TRY(scan_exclusive(w.bt_cnt, w.bt_off, nb, w.scan_tmp, st));
-    C2_CUDA_TRY(scan_exclusive(w.bu_cnt, w.bu_off, nb, w.scan_tmp, st));
-    C2_LAUNCH(k_fill_work, div_up(nb, T), T, 0, st, w.bt_cnt, w.bt_off, w.gcl + g0, nb, w.work_c,
-                                             w.work_t, &w.hdr->n_work);
-    TableArgs a{};
-    a.ptr = ptr; a.items = items; a.n_items = s.m; a.k = k;
-    a.work_c = w.work_c; a.work_t = w.work_t; a.n_work = &w.hdr->n_work;
-    a.cptr = cptr; a.cusers = cusers;
-    a.out_id = lid; a.out_in = lin; a.out_un = lun;
-    a.gofs = w.gofs; a.gram = w.gram;
-    a.hdr = w.hdr; a.counter = &w.hdr->work_counter[1];
-    c2_status rc = launch_table_w(W, a, st);
-    if (rc) return rc;
-    p_gram.end();
-    Prof p_init(st, "greedy_init");
-    // greedy rounds over the batch's users
-    C2_LAUNCH(k_fill_users, nb, 256, 0, st, w.gcl, cptr, w.bu_off, g0, nb, w.gu_slot, w.gu_g);
+    {
+      // counts of the batch's greedy clusters into their intersection matrices
+      Prof p_gram(st, "greedy_gram");
+      C2_LAUNCH(k_batch_setup, div_up(nb, T), T, 0, st, w.gcl, w.goff, w.gsz, g0, g1, Q, w.gofs,
+                w.bt_cnt, w.bu_cnt);
+      C2_CUDA_TRY(scan_exclusive(w.bt_cnt, w.bt_off, nb, w.scan_tmp, st));
+      C2_CUDA_TRY(scan_exclusive(w.bu_cnt, w.bu_off, nb, w.scan_tmp, st));
+      C2_LAUNCH(k_fill_work, div_up(nb, T), T, 0, st, w.bt_cnt, w.bt_off, w.gcl + g0, nb,
+                w.work_c, w.work_t, &w.hdr->n_work);
+      TableArgs a = ta;
+      a.gofs = w.gofs;
+      a.gram = w.gram;
+      a.counter = &w.hdr->work_counter[1];
+      c2_status rc = launch_table(tc, a, st);
+      if (rc) return rc;
+    }
     GreedyArgs ga{};
     ga.cptr = cptr; ga.cusers = cusers; ga.slen = w.slen; ga.gcl = w.gcl; ga.gofs = w.gofs;
     ga.gram = w.gram; ga.gu_slot = w.gu_slot; ga.gu_g = w.gu_g; ga.n_users_dev = w.bu_off + nb;
+    ga.gw_g = w.gw_g; ga.gw_t = w.gw_t; ga.n_gwork = &w.hdr->n_gwork;
+    ga.counter = &w.hdr->work_counter[2];
     ga.k = k; ga.n_random = opt.greedy_random; ga.key = key;
     ga.out_id = lid; ga.out_in = lin; ga.out_un = lun; ga.hdr = w.hdr;
-    const int grid = (int)std::min<int64_t>(div_up(nu, 8), (int64_t)num_sms() * 8);
-    ga.round = 0;
-    ga.wl_in = nullptr;
-    ga.wl_out = w.wl0;
-    C2_LAUNCH(k_greedy_init, grid, kNT, 0, st, ga);
-    p_init.end();
-    Prof p_rounds(st, "greedy_rounds");
+    ga.mcap = (mmax + 31) & ~31;
+    {
+      Prof p_init(st, "greedy_init");
+      C2_LAUNCH(k_fill_users, nb, 256, 0, st, w.gcl, cptr, w.bu_off, g0, nb, w.gu_slot, w.gu_g);
+      C2_LAUNCH(k_chunk_count, div_up(nb, T), T, 0, st, w.gsz, g0, nb, w.bw_cnt);
+      C2_CUDA_TRY(scan_exclusive(w.bw_cnt, w.bw_off, nb, w.scan_tmp, st));
+      C2_LAUNCH(k_iota, div_up(g1, T), T, 0, st, w.gseq, (int64_t)g1);
+      C2_LAUNCH(k_fill_work, div_up(nb, T), T, 0, st, w.bw_cnt, w.bw_off, w.gseq + g0, nb,
+                w.gw_g, w.gw_t, &w.hdr->n_gwork);
+      const int grid = (int)std::min<int64_t>(div_up(nu, 8), (int64_t)num_sms() * 8);
+      ga.round = 0;
+      ga.wl_in = nullptr;
+      ga.wl_out = w.wl0;
+      C2_LAUNCH(k_greedy_init, grid, kNT, 0, st, ga);
+    }
     int32_t* cur = w.wl0;
     int32_t* nxt = w.wl1;
-    for (int r = 1; r <= rounds; ++r) {
-      ga.round = r;
-      ga.wl_in = cur;
-      ga.wl_out = nxt;
-      C2_LAUNCH(k_greedy_round, grid, kNT, 0, st, ga);
-      std::swap(cur, nxt);
+    {
+      Prof p_rounds(st, "greedy_rounds");
+      const int smem = 21 * ga.mcap;
+      C2_CUDA_TRY(cudaFuncSetAttribute(k_greedy_round, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+      int per_sm = 0;
+      C2_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_greedy_round, kNT, smem));
+      if (per_sm < 1) return C2_ERR_UNSUPPORTED;
+      for (int r = 1; r <= rounds; ++r) {
+        ga.round = r;
+        ga.wl_in = cur;
+        ga.wl_out = nxt;
+        C2_CUDA_TRY(cudaMemsetAsync(ga.counter, 0, sizeof(unsigned), st));
+        C2_LAUNCH(k_greedy_round, num_sms() * per_sm, kNT, smem, st, ga);
+        std::swap(cur, nxt);
+      }
     }
-    p_rounds.end();
-    Prof p_emit(st, "greedy_emit");
-    ga.wl_in = cur;
-    C2_LAUNCH(k_greedy_emit, div_up(nu * 32, kNT), kNT, 0, st, ga);
+    {
+      Prof p_emit(st, "greedy_emit");
+      ga.wl_in = cur;
+      C2_LAUNCH(k_greedy_emit, div_up(nu * 32, kNT), kNT, 0, st, ga);
+    }
     C2_CUDA_TRY(cudaGetLastError());
     g0 = g1;
   }
@@ -821,20 +984,20 @@ c2_status run_bruteforce(const int32_t* ptr, const int32_t* items, const Sizes& 
                          int32_t* nun, KnnWs& w, cudaStream_t st) {
   const int rows = queries ? nq : s.n;
   if (rows == 0) return C2_OK;
-  const int W = pick_w(C2_STRATEGY_AUTO, s.m);
-  if (W) {
-    const int Q = 32 * W;
-    const int nwork = div_up(rows, Q);
-    C2_CUDA_TRY(cudaMemcpyAsync(&w.hdr->n_work, &nwork, sizeof(int32_t), cudaMemcpyHostToDevice, st));
+  const TableCfg tc = pick_table(C2_STRATEGY_AUTO, s.m);
+  if (tc.W) {
+    c2_status rc = build_padded_csr(ptr, items, s, w, st);
+    if (rc) return rc;
+    const int Q = 32 * tc.W;
+    C2_LAUNCH(k_set_count, 1, 1, 0, st, &w.hdr->n_work, div_up(rows, Q));
     TableArgs a{};
-    a.ptr = ptr; a.items = items; a.n_items = s.m; a.k = s.k;
+    a.ptr = ptr; a.items = items; a.pptr = w.pptr; a.pitems = w.pitems;
+    a.n_items = s.m; a.k = s.k;
     a.n_work = &w.hdr->n_work;
     a.cptr = nullptr; a.queries = queries; a.n_queries = rows; a.n_users = s.n;
     a.out_id = nid; a.out_in = nin; a.out_un = nun;
-    a.hdr = w.hdr; a.counter = &w.hdr->work_counter[2];
-    c2_status rc = launch_table_w(W, a, st);
-    C2_CUDA_TRY(cudaStreamSynchronize(st));   // nwork lives on this host stack frame
-    return rc;
+    a.hdr = w.hdr; a.counter = &w.hdr->work_counter[3];
+    return launch_table(tc, a, st);
   }
   MergeArgs a{};
   a.ptr = ptr; a.items = items; a.k = s.k; a.cptr = nullptr; a.n_rows = rows;
