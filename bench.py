@@ -273,6 +273,7 @@ def roofline(phase_ms, phase_calls, stats, w, nnz, pk, pk_src, W):
                          f"({visits / calls:.3e} visits/launch); peak = 152 SMs x 128 lanes x "
                          f"{pk.get('sm_max_mhz', 2070.0):.0f} MHz"}
     if dom == "greedy_rounds":
+        ms = phase_ms[dom] / (calls * max(1, w.greedy_rounds))   # one launch per round
         # per user and round: own row (k ids), k neighbour rows (k*k ids), one 2-byte count
         # and one 4-byte length per candidate, k ids written
         users = stats.get("greedy_users", 0)

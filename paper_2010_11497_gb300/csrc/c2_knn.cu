@@ -28,6 +28,7 @@ constexpr int kNT = 256;
 constexpr int kMaxGreedyM = 10240;            // greedy cluster size limit (shared staging)
 constexpr int kBitmapWords = kMaxGreedyM / 32;
 constexpr int kGreedyUsersPerWarp = 4;
+constexpr int kSmallCut = 32;    // brute clusters below this size use the merge kernel
 constexpr int kGreedyChunk = 8 * kGreedyUsersPerWarp;   // users per block work item
 
 // ------------------------------------------------------------------ table kernel
@@ -333,6 +334,7 @@ struct MergeArgs {
   const int32_t* slot2c;
   int64_t n_rows;          // slots (cluster mode) or queries (judge mode)
   int32_t thr;             // brute force iff |C| < thr
+  int32_t max_m;           // cluster mode: only clusters with |C| < max_m
   const int32_t* queries;  // judge mode when cptr == NULL
   int32_t n_users;
   int32_t *out_id, *out_in, *out_un;
@@ -349,7 +351,7 @@ __global__ void __launch_bounds__(kNT) k_merge_knn(MergeArgs a) {
     const int c = a.slot2c[row];
     cbase = a.cptr[c];
     M = a.cptr[c + 1] - cbase;
-    if (M < 2 || M >= a.thr) return;
+    if (M < 2 || M >= a.thr || M >= a.max_m) return;
     u = a.cusers[row];
     clist = a.cusers;
   } else {
@@ -402,7 +404,8 @@ __global__ void __launch_bounds__(kNT) k_merge_knn(MergeArgs a) {
 // Per cluster: brute-force tiles, greedy flag, pair count; singletons get an
 // empty row (nobody else is in their cluster).
 __global__ void k_prep(const int32_t* __restrict__ cptr, const int32_t* __restrict__ n_clusters,
-                       int64_t S, int32_t thr, int32_t Q, int32_t k, int32_t* __restrict__ ntiles,
+                       int64_t S, int32_t thr, int32_t small_cut, int32_t Q, int32_t k,
+                       int32_t* __restrict__ ntiles,
                        int32_t* __restrict__ gflag, int32_t* __restrict__ lid,
                        int32_t* __restrict__ lin, int32_t* __restrict__ lun, DevHeader* hdr) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -412,7 +415,7 @@ __global__ void k_prep(const int32_t* __restrict__ cptr, const int32_t* __restri
   const bool brute = M >= 2 && M < thr;
   const bool greedy = M >= 2 && M >= thr;
   if (c < S) {
-    ntiles[c] = brute ? (M + Q - 1) / Q : 0;
+    ntiles[c] = (brute && M >= small_cut) ? (M + Q - 1) / Q : 0;
     gflag[c] = greedy ? 1 : 0;
     if (M == 1) {
       const int64_t s = cptr[c];
@@ -618,7 +621,7 @@ __global__ void __launch_bounds__(kNT) k_greedy_init(GreedyArgs a) {
 // stages its user's row of intersection counts before walking the
 // candidates (own list, neighbours' lists, optional random draws),
 // deduplicated with a per-warp bitmap of the cluster.
-__global__ void __launch_bounds__(kNT) k_greedy_round(GreedyArgs a) {
+__global__ void __launch_bounds__(kNT, 4) k_greedy_round(GreedyArgs a) {
   extern __shared__ __align__(16) uint32_t gsm[];
   const int mcap = a.mcap;                               // multiple of 32
   int32_t* s_len = reinterpret_cast<int32_t*>(gsm);      // [mcap]
@@ -661,13 +664,6 @@ __global__ void __launch_bounds__(kNT) k_greedy_round(GreedyArgs a) {
       if (e >= 0) atomicOr(&bm[e >> 5], 1u << (e & 31));
       if (lane == 0) atomicOr(&bm[l >> 5], 1u << (l & 31));
       const int nlist = __popc(__ballot_sync(0xffffffffu, e >= 0));
-      // all neighbour rows at once (independent loads)
-      int cand[kMaxK];
-#pragma unroll
-      for (int j = 0; j < kMaxK; ++j) {
-        const int nb = __shfl_sync(0xffffffffu, e, j);
-        cand[j] = (j < nlist && lane < k) ? a.wl_in[(int64_t)(cs + nb) * k + lane] : -1;
-      }
       __syncwarp();
       unsigned fresh = 0;
       // one candidate per lane: dedupe, count lookup, exact filter, insert
@@ -696,9 +692,18 @@ __global__ void __launch_bounds__(kNT) k_greedy_round(GreedyArgs a) {
                            __shfl_sync(0xffffffffu, cc, src), __shfl_sync(0xffffffffu, uu2, src));
         }
       };
+      // neighbour rows, 16 at a time (independent loads in flight)
+      for (int j0 = 0; j0 < nlist; j0 += 16) {
+        int cand[16];
 #pragma unroll
-      for (int j = 0; j < kMaxK; ++j)
-        if (j < nlist) consider(cand[j]);
+        for (int j = 0; j < 16; ++j) {
+          const int nb = __shfl_sync(0xffffffffu, e, (j0 + j) & 31);
+          cand[j] = (j0 + j < nlist && lane < k) ? a.wl_in[(int64_t)(cs + nb) * k + lane] : -1;
+        }
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          if (j0 + j < nlist) consider(cand[j]);
+      }
       for (int d0 = 0; d0 < a.n_random; d0 += 32) {
         int v = -1;
         if (d0 + lane < a.n_random) {
@@ -837,8 +842,11 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
   const int Q = tc.W ? 32 * tc.W : 32;
 
   Prof p_prep(st, "knn_prep");
-  C2_LAUNCH(k_prep, div_up(S, T), T, 0, st, cptr, n_clusters, S, thr, Q, k, w.ntiles, w.gflag,
-            lid, lin, lun, w.hdr);
+  // brute-force clusters smaller than small_cut go to the warp-per-query
+  // merge kernel, the others to the shared-memory table kernel
+  const int small_cut = tc.W ? kSmallCut : (1 << 30);
+  C2_LAUNCH(k_prep, div_up(S, T), T, 0, st, cptr, n_clusters, S, thr, small_cut, Q, k, w.ntiles,
+            w.gflag, lid, lin, lun, w.hdr);
   C2_LAUNCH(k_slot_info, div_up(S, T), T, 0, st, cptr, n_clusters, cusers, ptr, S, w.slot2c,
             w.slen);
   C2_CUDA_TRY(cudaGetLastError());
@@ -858,7 +866,16 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
 
   // ---- brute-force clusters
   {
-    Prof p_brute(st, tc.W ? "brute_table" : "brute_merge");
+    {
+      Prof p_small(st, "brute_merge");
+      MergeArgs a{};
+      a.ptr = ptr; a.items = items; a.k = k; a.cptr = cptr; a.cusers = cusers;
+      a.slot2c = w.slot2c; a.n_rows = S; a.thr = thr; a.max_m = small_cut; a.out_id = lid;
+      a.out_in = lin; a.out_un = lun; a.hdr = w.hdr;
+      C2_LAUNCH(k_merge_knn, div_up(S * 32, kNT), kNT, 0, st, a);
+      C2_CUDA_TRY(cudaGetLastError());
+    }
+    Prof p_brute(st, "brute_table");
     if (tc.W) {
       C2_CUDA_TRY(scan_exclusive(w.ntiles, w.toff, S, w.scan_tmp, st));
       C2_LAUNCH(k_fill_work, div_up(S, T), T, 0, st, w.ntiles, w.toff, nullptr, S, w.work_c,
@@ -868,13 +885,6 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
       a.counter = &w.hdr->work_counter[0];
       c2_status rc = launch_table(tc, a, st);
       if (rc) return rc;
-    } else {
-      MergeArgs a{};
-      a.ptr = ptr; a.items = items; a.k = k; a.cptr = cptr; a.cusers = cusers;
-      a.slot2c = w.slot2c; a.n_rows = S; a.thr = thr; a.out_id = lid; a.out_in = lin;
-      a.out_un = lun; a.hdr = w.hdr;
-      C2_LAUNCH(k_merge_knn, div_up(S * 32, kNT), kNT, 0, st, a);
-      C2_CUDA_TRY(cudaGetLastError());
     }
   }
 

@@ -154,7 +154,8 @@ def test_local_greedy_small_budget_batches(c2):
     ptr, items = synth.random_profiles(3000, 300, 15, 15, zipf_s=1.2)
     o = oracle.frh_cluster(ptr, items, 300, 2, 8, 500, 4)
     sizes = np.diff(o["cptr"])
-    big = int((sizes.astype(np.int64) ** 2).max()) * 2
+    # count matrices keep rows padded to 8 entries (16 bytes)
+    big = int((sizes.astype(np.int64) * ((sizes + 7) // 8 * 8)).max()) * 2
     k, thr = 8, 100
     li, lc, lu, pairs = oracle.cluster_knn(ptr, items, o["cptr"], o["cusers"], k, 4, thr, 3)
     dptr, ditems = to_dev(ptr), to_dev(items)
