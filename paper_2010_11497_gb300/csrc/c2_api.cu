@@ -75,6 +75,13 @@ void bind_knn_ws(Ws& w, const Sizes& s, KnnWs& c) {
   c.bw_cnt = w.take<int32_t>(S + 1);
   c.bw_off = w.take<int32_t>(S + 1);
   c.gseq = w.take<int32_t>(S + 1);
+  c.gkind_c = w.take<int32_t>(S + 1);
+  c.gkind = w.take<int32_t>(S + 1);
+  c.bb_cnt = w.take<int32_t>(S + 1);
+  c.bb_off = w.take<int32_t>(S + 1);
+  c.ub_slot = w.take<int32_t>(S + 1);
+  c.ub_g = w.take<int32_t>(S + 1);
+  c.ord = w.take<int32_t>(S + 1);
   c.pptr = w.take<int32_t>((int64_t)s.n + 1);
   c.wl0 = w.take<int32_t>((S + 1) * s.k);
   c.wl1 = w.take<int32_t>((S + 1) * s.k);

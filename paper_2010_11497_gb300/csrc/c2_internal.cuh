@@ -117,6 +117,11 @@ struct KnnWs {
   int32_t *gw_g, *gw_t;    // [S+1] greedy round work items: greedy index, user chunk
   int32_t *bw_cnt, *bw_off;// [S+1] chunks per greedy cluster of a batch
   int32_t* gseq;           // [S+1] 0, 1, 2, ...
+  int32_t* gkind_c;        // [S+1] per cluster: greedy (1) or brute force (0)
+  int32_t* gkind;          // [S+1] per count-matrix cluster
+  int32_t *bb_cnt, *bb_off;// [S+1] brute-force users per cluster of a batch
+  int32_t *ub_slot, *ub_g; // [S+1] brute-force users of a batch
+  int32_t* ord;            // [S+1] candidate order inside each cluster
   int32_t* pptr;           // [n+1] padded CSR offsets
   int32_t* pitems;         // padded CSR items: the workspace tail
   int64_t pitems_cap;      // capacity of pitems (elements)

@@ -287,6 +287,204 @@ __global__ void __launch_bounds__(NT) k_table(TableArgs a) {
   if (lane == 0 && visits) atomicAdd(&a.hdr->item_visits[a.gofs ? 1 : 0], visits);
 }
 
+// ------------------------------------------------------------------ gram kernel
+// Count matrix of one cluster, G[v][q] = |P_v n P_q| for members v, q (local
+// indices), stored in rows of stride Mp = round_up(M, 8).  A work item is a
+// tile of Q = 32*W query members marked in the shared table; the cluster's
+// candidates are taken 32 at a time by whichever warp is free, in order of
+// decreasing profile length (so the lanes of a warp walk rows of similar
+// length), and each thread writes its candidate's counts against the tile's
+// queries as one contiguous row segment (the matrix is symmetric).
+struct GramArgs {
+  const int32_t* ptr;
+  const int32_t* items;
+  const int32_t* pptr;
+  const int32_t* pitems;
+  int32_t n_items;
+  const int32_t* work_c;
+  const int32_t* work_t;
+  const int32_t* n_work;
+  const int32_t* cptr;
+  const int32_t* cusers;
+  const int32_t* ord;      // per slot: candidate order (local indices) of its cluster
+  const int64_t* gofs;
+  uint16_t* gram;
+  DevHeader* hdr;
+  unsigned* counter;
+};
+
+template <int W, int NT>
+__global__ void __launch_bounds__(NT) k_gram(GramArgs a) {
+  constexpr int Q = 32 * W, NWARP = NT / 32;
+  extern __shared__ __align__(16) uint32_t T[];
+  __shared__ int32_t q_id[Q];
+  __shared__ int s_work, s_next;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int i = tid; i < (a.n_items + 1) * W; i += NT) T[i] = 0;
+  if (tid == 0) s_next = 0;
+  const int nwork = *a.n_work;
+  unsigned long long visits = 0;
+  __syncthreads();
+  for (;;) {
+    if (tid == 0) s_work = dev_failed(a.hdr) ? nwork : (int)atomicAdd(a.counter, 1u);
+    __syncthreads();
+    const int wi = s_work;
+    if (wi >= nwork) break;
+    const int c = a.work_c[wi], tq = a.work_t[wi];
+    const int cbase = a.cptr[c], M = a.cptr[c + 1] - cbase, Mp = (M + 7) & ~7;
+    const int nq = min(Q, M - tq * Q);
+    if (tid < Q) q_id[tid] = tid < nq ? a.cusers[cbase + tq * Q + tid] : -1;
+    __syncthreads();
+    for (int j = warp; j < nq; j += NWARP) {
+      const int u = q_id[j];
+      for (int e = a.ptr[u] + lane; e < a.ptr[u + 1]; e += 32)
+        atomicOr(&T[a.items[e] * W + (j >> 5)], 1u << (j & 31));
+    }
+    __syncthreads();
+    uint16_t* Gc = a.gram + a.gofs[c] + tq * Q;
+    for (;;) {
+      int p0 = 0;
+      if (lane == 0) p0 = atomicAdd(&s_next, 32);
+      p0 = __shfl_sync(0xffffffffu, p0, 0);
+      if (p0 >= M) break;
+      const int p = p0 + lane;
+      if (p < M) {
+        const int vl = a.ord[cbase + p];
+        const int v = a.cusers[cbase + vl];
+        const int len = a.ptr[v + 1] - a.ptr[v];
+        uint32_t C[16 * W];
+#pragma unroll
+        for (int r = 0; r < 16 * W; ++r) C[r] = 0;
+        count_row4<W>(reinterpret_cast<const int4*>(a.pitems + a.pptr[v]), (len + 3) >> 2, T,
+                      a.n_items, C);
+        visits += (unsigned)len;
+        // row vl, columns tq*Q .. tq*Q + nq (16-byte stores, padding columns allowed)
+        uint4* dst = reinterpret_cast<uint4*>(Gc + (int64_t)vl * Mp);
+#pragma unroll
+        for (int g8 = 0; g8 < Q / 8; ++g8) {
+          if (g8 * 8 < nq) {
+            uint32_t wv[4];
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+              const int j0 = g8 * 8 + 2 * h, j1 = j0 + 1;
+              const uint32_t lo = (C[creg(j0)] >> (16 * chalf(j0))) & 0xFFFFu;
+              const uint32_t hi = (C[creg(j1)] >> (16 * chalf(j1))) & 0xFFFFu;
+              wv[h] = lo | (hi << 16);
+            }
+            dst[g8] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+          }
+        }
+      }
+    }
+    __syncthreads();
+    for (int j = warp; j < nq; j += NWARP) {
+      const int u = q_id[j];
+      for (int e = a.ptr[u] + lane; e < a.ptr[u + 1]; e += 32) T[a.items[e] * W + (j >> 5)] = 0;
+    }
+    if (tid == 0) s_next = 0;
+    __syncthreads();
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) visits += __shfl_xor_sync(0xffffffffu, visits, o);
+  if (lane == 0 && visits) atomicAdd(&a.hdr->item_visits[1], visits);
+}
+
+// Candidate order of a cluster: members by decreasing profile length, in 64
+// buckets (4 per octave); one block per cluster, counting sort in shared memory.
+__device__ __forceinline__ int len_bucket(int len) {
+  if (len < 4) return len;
+  const int oct = 31 - __clz(len);                 // >= 2
+  const int b = oct * 4 + ((len >> (oct - 2)) & 3);
+  return min(b, 63);
+}
+
+__global__ void __launch_bounds__(256) k_order(const int32_t* __restrict__ gcl, int32_t g0,
+                                               const int32_t* __restrict__ cptr,
+                                               const int32_t* __restrict__ slen,
+                                               int32_t* __restrict__ ord) {
+  __shared__ int32_t cnt[64];
+  const int c = gcl[g0 + blockIdx.x];
+  const int cbase = cptr[c], M = cptr[c + 1] - cbase;
+  if (threadIdx.x < 64) cnt[threadIdx.x] = 0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < M; i += blockDim.x) atomicAdd(&cnt[63 - len_bucket(slen[cbase + i])], 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int b = 0; b < 64; ++b) {
+      const int x = cnt[b];
+      cnt[b] = acc;
+      acc += x;
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < M; i += blockDim.x) {
+    const int pos = atomicAdd(&cnt[63 - len_bucket(slen[cbase + i])], 1);
+    ord[cbase + pos] = i;
+  }
+}
+
+// Brute-force top-k of one member from its row of the count matrix: warp per
+// member, exact comparison, candidates with no common item skipped.
+struct RowTopkArgs {
+  const int32_t* cptr;
+  const int32_t* cusers;
+  const int32_t* slen;
+  const int32_t* gcl;
+  const int64_t* gofs;
+  const uint16_t* gram;
+  const int32_t* u_slot;
+  const int32_t* u_g;
+  const int32_t* n_users_dev;
+  int32_t k;
+  int32_t *out_id, *out_in, *out_un;
+  DevHeader* hdr;
+};
+
+__global__ void __launch_bounds__(kNT) k_gram_topk(RowTopkArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (w >= *a.n_users_dev || dev_failed(a.hdr)) return;
+  const int slot = a.u_slot[w];
+  const int c = a.gcl[a.u_g[w]];
+  const int cs = a.cptr[c], M = a.cptr[c + 1] - cs, l = slot - cs, Mp = (M + 7) & ~7;
+  const uint16_t* row = a.gram + a.gofs[c] + (int64_t)l * Mp;
+  const uint32_t my = (uint32_t)a.slen[slot];
+  const int k = a.k;
+  WarpList L;
+  L.id = -1; L.c = 0; L.u = 0;
+  for (int v0 = 0; v0 < M; v0 += 32) {
+    const int v = v0 + lane;
+    WarpList kth;
+    kth.id = __shfl_sync(0xffffffffu, L.id, k - 1);
+    kth.c = __shfl_sync(0xffffffffu, L.c, k - 1);
+    kth.u = __shfl_sync(0xffffffffu, L.u, k - 1);
+    uint32_t cc = 0, uu = 0;
+    bool pass = false;
+    if (v < M && v != l) {
+      cc = row[v];
+      if (cc > 0) {
+        uu = my + (uint32_t)a.slen[cs + v] - cc;
+        pass = beats(kth, v, cc, uu);   // local index order = user id order
+      }
+    }
+    unsigned mask = __ballot_sync(0xffffffffu, pass);
+    while (mask) {
+      const int src = __ffs(mask) - 1;
+      mask &= mask - 1;
+      warp_list_insert(L, k, __shfl_sync(0xffffffffu, v, src), __shfl_sync(0xffffffffu, cc, src),
+                       __shfl_sync(0xffffffffu, uu, src));
+    }
+  }
+  if (lane < k) {
+    const int64_t o = (int64_t)slot * k + lane;
+    const bool ok = L.id >= 0;
+    a.out_id[o] = ok ? a.cusers[cs + L.id] : -1;
+    a.out_in[o] = ok ? (int32_t)L.c : 0;
+    a.out_un[o] = ok ? (int32_t)L.u : 0;
+  }
+}
+
 // ------------------------------------------------------------------ padded CSR
 // Rows padded to a multiple of 4 items with the sentinel item m, so that each
 // row starts on a 16-byte boundary and is read with int4 loads.
@@ -401,13 +599,14 @@ __global__ void __launch_bounds__(kNT) k_merge_knn(MergeArgs a) {
 }
 
 // ------------------------------------------------------------------ preparation
-// Per cluster: brute-force tiles, greedy flag, pair count; singletons get an
-// empty row (nobody else is in their cluster).
+// Per cluster: does it get a count matrix (every greedy cluster, and brute-
+// force clusters of at least small_cut members), is it greedy, pair count;
+// singletons get an empty row (nobody else is in their cluster).
 __global__ void k_prep(const int32_t* __restrict__ cptr, const int32_t* __restrict__ n_clusters,
-                       int64_t S, int32_t thr, int32_t small_cut, int32_t Q, int32_t k,
-                       int32_t* __restrict__ ntiles,
-                       int32_t* __restrict__ gflag, int32_t* __restrict__ lid,
-                       int32_t* __restrict__ lin, int32_t* __restrict__ lun, DevHeader* hdr) {
+                       int64_t S, int32_t thr, int32_t small_cut, int32_t k,
+                       int32_t* __restrict__ gflag, int32_t* __restrict__ gkind,
+                       int32_t* __restrict__ lid, int32_t* __restrict__ lin,
+                       int32_t* __restrict__ lun, DevHeader* hdr) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int32_t L = *n_clusters;
   int32_t M = 0;
@@ -415,8 +614,8 @@ __global__ void k_prep(const int32_t* __restrict__ cptr, const int32_t* __restri
   const bool brute = M >= 2 && M < thr;
   const bool greedy = M >= 2 && M >= thr;
   if (c < S) {
-    ntiles[c] = (brute && M >= small_cut) ? (M + Q - 1) / Q : 0;
-    gflag[c] = greedy ? 1 : 0;
+    gflag[c] = (greedy || (brute && M >= small_cut)) ? 1 : 0;
+    gkind[c] = greedy ? 1 : 0;
     if (M == 1) {
       const int64_t s = cptr[c];
       for (int j = 0; j < k; ++j) {
@@ -466,49 +665,57 @@ __global__ void k_fill_work(const int32_t* __restrict__ ntiles, const int32_t* _
 }
 
 __global__ void k_greedy_list(const int32_t* __restrict__ gflag, const int32_t* __restrict__ gidx,
-                              const int32_t* __restrict__ cptr, int64_t S, int32_t* __restrict__ gcl,
-                              int64_t* __restrict__ gsq, int32_t* __restrict__ gsz, DevHeader* hdr) {
+                              const int32_t* __restrict__ gkind_c, const int32_t* __restrict__ cptr,
+                              int64_t S, int32_t* __restrict__ gcl, int64_t* __restrict__ gsq,
+                              int32_t* __restrict__ gsz, int32_t* __restrict__ gkind,
+                              DevHeader* hdr) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c == 0) hdr->n_greedy = gidx[S];
+  if (c == 0) hdr->n_work = gidx[S];   // count-matrix clusters
   if (c >= S || !gflag[c]) return;
   const int g = gidx[c];
   const int32_t M = cptr[c + 1] - cptr[c];
   gcl[g] = (int32_t)c;
   gsq[g] = (int64_t)M * ((M + 7) & ~7);   // rows padded to 16 bytes
   gsz[g] = M;
-  atomicMax(&hdr->max_cluster, M);
-  atomicAdd(&hdr->greedy_users, M);
+  gkind[g] = gkind_c[c];
+  if (gkind_c[c]) {
+    atomicMax(&hdr->max_cluster, M);
+    atomicAdd(&hdr->greedy_users, M);
+    atomicAdd(&hdr->n_greedy, 1);
+  }
 }
 
+// Per count-matrix cluster of a batch: its matrix offset, query tiles, and
+// its members as greedy users / brute-force users / greedy work chunks.
 __global__ void k_batch_setup(const int32_t* __restrict__ gcl, const int64_t* __restrict__ goff,
-                              const int32_t* __restrict__ gsz, int32_t g0, int32_t g1, int32_t Q,
-                              int64_t* __restrict__ gofs, int32_t* __restrict__ ntiles,
-                              int32_t* __restrict__ nusers) {
+                              const int32_t* __restrict__ gsz, const int32_t* __restrict__ gkind,
+                              int32_t g0, int32_t g1, int32_t Q, int64_t* __restrict__ gofs,
+                              int32_t* __restrict__ ntiles, int32_t* __restrict__ ngu,
+                              int32_t* __restrict__ nbu, int32_t* __restrict__ ngw) {
   const int g = g0 + blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= g1) return;
+  const int M = gsz[g], j = g - g0;
   gofs[gcl[g]] = goff[g] - goff[g0];
-  ntiles[g - g0] = (gsz[g] + Q - 1) / Q;
-  nusers[g - g0] = gsz[g];
+  ntiles[j] = (M + Q - 1) / Q;
+  ngu[j] = gkind[g] ? M : 0;
+  nbu[j] = gkind[g] ? 0 : M;
+  ngw[j] = gkind[g] ? (M + kGreedyChunk - 1) / kGreedyChunk : 0;
 }
 
+// Members of the batch's clusters of one kind, as (slot, count-matrix index).
 __global__ void k_fill_users(const int32_t* __restrict__ gcl, const int32_t* __restrict__ cptr,
+                             const int32_t* __restrict__ gkind, int32_t want,
                              const int32_t* __restrict__ uoff, int32_t g0, int32_t ng,
-                             int32_t* __restrict__ gu_slot, int32_t* __restrict__ gu_g) {
+                             int32_t* __restrict__ u_slot, int32_t* __restrict__ u_g) {
   const int gl = blockIdx.x;
-  if (gl >= ng) return;
+  if (gl >= ng || gkind[g0 + gl] != want) return;
   const int c = gcl[g0 + gl];
   const int cs = cptr[c], M = cptr[c + 1] - cs;
   const int o = uoff[gl];
   for (int l = threadIdx.x; l < M; l += blockDim.x) {
-    gu_slot[o + l] = cs + l;
-    gu_g[o + l] = g0 + gl;
+    u_slot[o + l] = cs + l;
+    u_g[o + l] = g0 + gl;
   }
-}
-
-__global__ void k_chunk_count(const int32_t* __restrict__ gsz, int32_t g0, int32_t nb,
-                              int32_t* __restrict__ cnt) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j < nb) cnt[j] = (gsz[g0 + j] + kGreedyChunk - 1) / kGreedyChunk;
 }
 
 __global__ void k_set_count(int32_t* p, int32_t v) { *p = v; }
@@ -518,10 +725,6 @@ __global__ void k_iota(int32_t* p, int64_t n) {
   if (j < n) p[j] = (int32_t)j;
 }
 
-__global__ void k_fill_i64(int64_t* p, int64_t n, int64_t v) {
-  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (j < n) p[j] = v;
-}
 
 // ------------------------------------------------------------------ greedy rounds
 struct GreedyArgs {
@@ -815,6 +1018,44 @@ TableCfg pick_table(int strategy, int m) {
   return {0, 0};
 }
 
+int gram_smem_bytes(TableCfg c, int m) { return 4 * table_T_words(c.W, m); }
+
+template <int W, int NT>
+c2_status launch_gram_t(const GramArgs& a, cudaStream_t st) {
+  const int smem = gram_smem_bytes(TableCfg{W, NT}, a.n_items);
+  C2_CUDA_TRY(cudaFuncSetAttribute(k_gram<W, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  int per_sm = 0;
+  C2_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gram<W, NT>, NT, smem));
+  if (per_sm < 1) return C2_ERR_UNSUPPORTED;
+  C2_CUDA_TRY(cudaMemsetAsync(a.counter, 0, sizeof(unsigned), st));
+  C2_LAUNCH(k_gram<W COMMA NT>, num_sms() * per_sm, NT, smem, st, a);
+  C2_CUDA_TRY(cudaGetLastError());
+  return C2_OK;
+}
+
+c2_status launch_gram(TableCfg c, const GramArgs& a, cudaStream_t st) {
+  if (c.W == 1 && c.NT == 256) return launch_gram_t<1, 256>(a, st);
+  if (c.W == 1 && c.NT == 512) return launch_gram_t<1, 512>(a, st);
+  if (c.W == 2 && c.NT == 256) return launch_gram_t<2, 256>(a, st);
+  if (c.W == 2 && c.NT == 512) return launch_gram_t<2, 512>(a, st);
+  return C2_ERR_UNSUPPORTED;
+}
+
+bool gram_fits(TableCfg c, int m) { return gram_smem_bytes(c, m) + 1024 <= smem_optin(); }
+
+TableCfg pick_gram(int strategy, int m) {
+  static const TableCfg wide[] = {{2, 256}, {2, 512}};
+  static const TableCfg narrow[] = {{1, 512}, {1, 256}};
+  if (strategy == C2_STRATEGY_MERGE) return {0, 0};
+  if (strategy != C2_STRATEGY_TABLE32) {
+    for (const TableCfg& c : wide)
+      if (gram_fits(c, m)) return c;
+  }
+  for (const TableCfg& c : narrow)
+    if (gram_fits(c, m)) return c;
+  return {0, 0};
+}
+
 c2_status build_padded_csr(const int32_t* ptr, const int32_t* items, const Sizes& s, KnnWs& w,
                            cudaStream_t st) {
   if (s.n == 0) return C2_OK;
@@ -838,15 +1079,15 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
   const int k = s.k;
   const int thr = opt.greedy_threshold > 0 ? opt.greedy_threshold : 5 * k * k;
   const int rounds = opt.greedy_rounds >= 0 ? opt.greedy_rounds : 10;
-  const TableCfg tc = pick_table(opt.strategy, s.m);
+  const TableCfg tc = pick_gram(opt.strategy, s.m);
   const int Q = tc.W ? 32 * tc.W : 32;
+  // brute-force clusters smaller than small_cut go to the warp-per-query merge
+  // kernel; larger ones and every greedy cluster get a count matrix
+  const int small_cut = tc.W ? kSmallCut : (1 << 30);
 
   Prof p_prep(st, "knn_prep");
-  // brute-force clusters smaller than small_cut go to the warp-per-query
-  // merge kernel, the others to the shared-memory table kernel
-  const int small_cut = tc.W ? kSmallCut : (1 << 30);
-  C2_LAUNCH(k_prep, div_up(S, T), T, 0, st, cptr, n_clusters, S, thr, small_cut, Q, k, w.ntiles,
-            w.gflag, lid, lin, lun, w.hdr);
+  C2_LAUNCH(k_prep, div_up(S, T), T, 0, st, cptr, n_clusters, S, thr, small_cut, k, w.gflag,
+            w.gkind_c, lid, lin, lun, w.hdr);
   C2_LAUNCH(k_slot_info, div_up(S, T), T, 0, st, cptr, n_clusters, cusers, ptr, S, w.slot2c,
             w.slen);
   C2_CUDA_TRY(cudaGetLastError());
@@ -856,132 +1097,131 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
   }
   p_prep.end();
 
-  TableArgs ta{};
-  ta.ptr = ptr; ta.items = items; ta.pptr = w.pptr; ta.pitems = w.pitems;
-  ta.n_items = s.m; ta.k = k;
-  ta.work_c = w.work_c; ta.work_t = w.work_t; ta.n_work = &w.hdr->n_work;
-  ta.cptr = cptr; ta.cusers = cusers;
-  ta.out_id = lid; ta.out_in = lin; ta.out_un = lun;
-  ta.hdr = w.hdr;
-
-  // ---- brute-force clusters
   {
-    {
-      Prof p_small(st, "brute_merge");
-      MergeArgs a{};
-      a.ptr = ptr; a.items = items; a.k = k; a.cptr = cptr; a.cusers = cusers;
-      a.slot2c = w.slot2c; a.n_rows = S; a.thr = thr; a.max_m = small_cut; a.out_id = lid;
-      a.out_in = lin; a.out_un = lun; a.hdr = w.hdr;
-      C2_LAUNCH(k_merge_knn, div_up(S * 32, kNT), kNT, 0, st, a);
-      C2_CUDA_TRY(cudaGetLastError());
-    }
-    Prof p_brute(st, "brute_table");
-    if (tc.W) {
-      C2_CUDA_TRY(scan_exclusive(w.ntiles, w.toff, S, w.scan_tmp, st));
-      C2_LAUNCH(k_fill_work, div_up(S, T), T, 0, st, w.ntiles, w.toff, nullptr, S, w.work_c,
-                w.work_t, &w.hdr->n_work);
-      TableArgs a = ta;
-      a.gofs = nullptr;
-      a.counter = &w.hdr->work_counter[0];
-      c2_status rc = launch_table(tc, a, st);
-      if (rc) return rc;
-    }
+    Prof p_small(st, "brute_merge");
+    MergeArgs a{};
+    a.ptr = ptr; a.items = items; a.k = k; a.cptr = cptr; a.cusers = cusers;
+    a.slot2c = w.slot2c; a.n_rows = S; a.thr = thr; a.max_m = small_cut; a.out_id = lid;
+    a.out_in = lin; a.out_un = lun; a.hdr = w.hdr;
+    C2_LAUNCH(k_merge_knn, div_up(S * 32, kNT), kNT, 0, st, a);
+    C2_CUDA_TRY(cudaGetLastError());
   }
 
-  // ---- greedy clusters
-  Prof p_gsetup(st, "greedy_setup");
+  // ---- clusters with a count matrix
+  Prof p_gsetup(st, "gram_setup");
   C2_CUDA_TRY(scan_exclusive(w.gflag, w.gidx, S, w.scan_tmp, st));
-  C2_LAUNCH(k_greedy_list, div_up(S, T), T, 0, st, w.gflag, w.gidx, cptr, S, w.gcl, w.gsq, w.gsz,
-            w.hdr);
+  C2_LAUNCH(k_greedy_list, div_up(S, T), T, 0, st, w.gflag, w.gidx, w.gkind_c, cptr, S, w.gcl,
+            w.gsq, w.gsz, w.gkind, w.hdr);
   int32_t ng = 0;
-  C2_CUDA_TRY(cudaMemcpyAsync(&ng, &w.hdr->n_greedy, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  C2_CUDA_TRY(cudaMemcpyAsync(&ng, &w.hdr->n_work, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   C2_CUDA_TRY(cudaStreamSynchronize(st));
   if (ng == 0) return C2_OK;
   if (tc.W == 0) return C2_ERR_UNSUPPORTED;   // greedy needs the table kernel for its counts
   C2_CUDA_TRY(scan_exclusive64(w.gsq, w.goff, ng, w.scan_tmp64, st));
   C2_LAUNCH(k_gram_stats, 1, 1, 0, st, w.goff, ng, w.hdr);
   std::vector<int64_t> goff(ng + 1);
-  std::vector<int32_t> gsz(ng);
+  std::vector<int32_t> gsz(ng), gkind(ng);
   C2_CUDA_TRY(cudaMemcpyAsync(goff.data(), w.goff, (ng + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
   C2_CUDA_TRY(cudaMemcpyAsync(gsz.data(), w.gsz, ng * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  C2_CUDA_TRY(cudaMemcpyAsync(gkind.data(), w.gkind, ng * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   C2_CUDA_TRY(cudaStreamSynchronize(st));
   const int64_t cap = s.gram_budget / (int64_t)sizeof(uint16_t);
   for (int g = 0; g < ng; ++g) {
-    if (gsz[g] > kMaxGreedyM || goff[g + 1] - goff[g] > cap) return C2_ERR_UNSUPPORTED;
+    if ((gkind[g] && gsz[g] > kMaxGreedyM) || goff[g + 1] - goff[g] > cap) return C2_ERR_UNSUPPORTED;
   }
-  C2_LAUNCH(k_fill_i64, div_up(S, T), T, 0, st, w.gofs, S, -1);
+  C2_LAUNCH(k_iota, div_up(ng, T), T, 0, st, w.gseq, (int64_t)ng);
   const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
   p_gsetup.end();
+
+  GramArgs ga0{};
+  ga0.ptr = ptr; ga0.items = items; ga0.pptr = w.pptr; ga0.pitems = w.pitems;
+  ga0.n_items = s.m; ga0.work_c = w.work_c; ga0.work_t = w.work_t; ga0.n_work = &w.hdr->n_work;
+  ga0.cptr = cptr; ga0.cusers = cusers; ga0.ord = w.ord; ga0.gofs = w.gofs; ga0.gram = w.gram;
+  ga0.hdr = w.hdr; ga0.counter = &w.hdr->work_counter[1];
+
   int g0 = 0;
   while (g0 < ng) {
     int g1 = g0;
-    int64_t nu = 0;
+    int64_t n_greedy_users = 0, n_brute_users = 0;
     int mmax = 0;
     while (g1 < ng && goff[g1 + 1] - goff[g0] <= cap) {
-      mmax = std::max(mmax, gsz[g1]);
-      nu += gsz[g1++];
+      if (gkind[g1]) {
+        mmax = std::max(mmax, gsz[g1]);
+        n_greedy_users += gsz[g1];
+      } else {
+        n_brute_users += gsz[g1];
+      }
+      ++g1;
     }
     const int nb = g1 - g0;
     {
-      // counts of the batch's greedy clusters into their intersection matrices
-      Prof p_gram(st, "greedy_gram");
-      C2_LAUNCH(k_batch_setup, div_up(nb, T), T, 0, st, w.gcl, w.goff, w.gsz, g0, g1, Q, w.gofs,
-                w.bt_cnt, w.bu_cnt);
+      Prof p_gram(st, "gram");
+      C2_LAUNCH(k_batch_setup, div_up(nb, T), T, 0, st, w.gcl, w.goff, w.gsz, w.gkind, g0, g1, Q,
+                w.gofs, w.bt_cnt, w.bu_cnt, w.bb_cnt, w.bw_cnt);
       C2_CUDA_TRY(scan_exclusive(w.bt_cnt, w.bt_off, nb, w.scan_tmp, st));
-      C2_CUDA_TRY(scan_exclusive(w.bu_cnt, w.bu_off, nb, w.scan_tmp, st));
       C2_LAUNCH(k_fill_work, div_up(nb, T), T, 0, st, w.bt_cnt, w.bt_off, w.gcl + g0, nb,
                 w.work_c, w.work_t, &w.hdr->n_work);
-      TableArgs a = ta;
-      a.gofs = w.gofs;
-      a.gram = w.gram;
-      a.counter = &w.hdr->work_counter[1];
-      c2_status rc = launch_table(tc, a, st);
+      C2_LAUNCH(k_order, nb, 256, 0, st, w.gcl, g0, cptr, w.slen, w.ord);
+      c2_status rc = launch_gram(tc, ga0, st);
       if (rc) return rc;
     }
-    GreedyArgs ga{};
-    ga.cptr = cptr; ga.cusers = cusers; ga.slen = w.slen; ga.gcl = w.gcl; ga.gofs = w.gofs;
-    ga.gram = w.gram; ga.gu_slot = w.gu_slot; ga.gu_g = w.gu_g; ga.n_users_dev = w.bu_off + nb;
-    ga.gw_g = w.gw_g; ga.gw_t = w.gw_t; ga.n_gwork = &w.hdr->n_gwork;
-    ga.counter = &w.hdr->work_counter[2];
-    ga.k = k; ga.n_random = opt.greedy_random; ga.key = key;
-    ga.out_id = lid; ga.out_in = lin; ga.out_un = lun; ga.hdr = w.hdr;
-    ga.mcap = (mmax + 31) & ~31;
-    {
-      Prof p_init(st, "greedy_init");
-      C2_LAUNCH(k_fill_users, nb, 256, 0, st, w.gcl, cptr, w.bu_off, g0, nb, w.gu_slot, w.gu_g);
-      C2_LAUNCH(k_chunk_count, div_up(nb, T), T, 0, st, w.gsz, g0, nb, w.bw_cnt);
-      C2_CUDA_TRY(scan_exclusive(w.bw_cnt, w.bw_off, nb, w.scan_tmp, st));
-      C2_LAUNCH(k_iota, div_up(g1, T), T, 0, st, w.gseq, (int64_t)g1);
-      C2_LAUNCH(k_fill_work, div_up(nb, T), T, 0, st, w.bw_cnt, w.bw_off, w.gseq + g0, nb,
-                w.gw_g, w.gw_t, &w.hdr->n_gwork);
-      const int grid = (int)std::min<int64_t>(div_up(nu, 8), (int64_t)num_sms() * 8);
-      ga.round = 0;
-      ga.wl_in = nullptr;
-      ga.wl_out = w.wl0;
-      C2_LAUNCH(k_greedy_init, grid, kNT, 0, st, ga);
+    if (n_brute_users) {
+      Prof p_bt(st, "brute_rows");
+      C2_CUDA_TRY(scan_exclusive(w.bb_cnt, w.bb_off, nb, w.scan_tmp, st));
+      C2_LAUNCH(k_fill_users, nb, 256, 0, st, w.gcl, cptr, w.gkind, 0, w.bb_off, g0, nb,
+                w.ub_slot, w.ub_g);
+      RowTopkArgs ra{};
+      ra.cptr = cptr; ra.cusers = cusers; ra.slen = w.slen; ra.gcl = w.gcl; ra.gofs = w.gofs;
+      ra.gram = w.gram; ra.u_slot = w.ub_slot; ra.u_g = w.ub_g; ra.n_users_dev = w.bb_off + nb;
+      ra.k = k; ra.out_id = lid; ra.out_in = lin; ra.out_un = lun; ra.hdr = w.hdr;
+      C2_LAUNCH(k_gram_topk, div_up(n_brute_users * 32, kNT), kNT, 0, st, ra);
     }
-    int32_t* cur = w.wl0;
-    int32_t* nxt = w.wl1;
-    {
-      Prof p_rounds(st, "greedy_rounds");
-      const int smem = 21 * ga.mcap;
-      C2_CUDA_TRY(cudaFuncSetAttribute(k_greedy_round, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-      int per_sm = 0;
-      C2_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_greedy_round, kNT, smem));
-      if (per_sm < 1) return C2_ERR_UNSUPPORTED;
-      for (int r = 1; r <= rounds; ++r) {
-        ga.round = r;
-        ga.wl_in = cur;
-        ga.wl_out = nxt;
-        C2_CUDA_TRY(cudaMemsetAsync(ga.counter, 0, sizeof(unsigned), st));
-        C2_LAUNCH(k_greedy_round, num_sms() * per_sm, kNT, smem, st, ga);
-        std::swap(cur, nxt);
+    if (n_greedy_users) {
+      GreedyArgs ga{};
+      ga.cptr = cptr; ga.cusers = cusers; ga.slen = w.slen; ga.gcl = w.gcl; ga.gofs = w.gofs;
+      ga.gram = w.gram; ga.gu_slot = w.gu_slot; ga.gu_g = w.gu_g; ga.n_users_dev = w.bu_off + nb;
+      ga.gw_g = w.gw_g; ga.gw_t = w.gw_t; ga.n_gwork = &w.hdr->n_gwork;
+      ga.counter = &w.hdr->work_counter[2];
+      ga.k = k; ga.n_random = opt.greedy_random; ga.key = key;
+      ga.out_id = lid; ga.out_in = lin; ga.out_un = lun; ga.hdr = w.hdr;
+      ga.mcap = (mmax + 31) & ~31;
+      {
+        Prof p_init(st, "greedy_init");
+        C2_CUDA_TRY(scan_exclusive(w.bu_cnt, w.bu_off, nb, w.scan_tmp, st));
+        C2_CUDA_TRY(scan_exclusive(w.bw_cnt, w.bw_off, nb, w.scan_tmp, st));
+        C2_LAUNCH(k_fill_users, nb, 256, 0, st, w.gcl, cptr, w.gkind, 1, w.bu_off, g0, nb,
+                  w.gu_slot, w.gu_g);
+        C2_LAUNCH(k_fill_work, div_up(nb, T), T, 0, st, w.bw_cnt, w.bw_off, w.gseq + g0, nb,
+                  w.gw_g, w.gw_t, &w.hdr->n_gwork);
+        const int grid = (int)std::min<int64_t>(div_up(n_greedy_users, 8), (int64_t)num_sms() * 8);
+        ga.round = 0;
+        ga.wl_in = nullptr;
+        ga.wl_out = w.wl0;
+        C2_LAUNCH(k_greedy_init, grid, kNT, 0, st, ga);
       }
-    }
-    {
-      Prof p_emit(st, "greedy_emit");
-      ga.wl_in = cur;
-      C2_LAUNCH(k_greedy_emit, div_up(nu * 32, kNT), kNT, 0, st, ga);
+      int32_t* cur = w.wl0;
+      int32_t* nxt = w.wl1;
+      {
+        Prof p_rounds(st, "greedy_rounds");
+        const int smem = 21 * ga.mcap;
+        C2_CUDA_TRY(cudaFuncSetAttribute(k_greedy_round, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        int per_sm = 0;
+        C2_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_greedy_round, kNT, smem));
+        if (per_sm < 1) return C2_ERR_UNSUPPORTED;
+        for (int r = 1; r <= rounds; ++r) {
+          ga.round = r;
+          ga.wl_in = cur;
+          ga.wl_out = nxt;
+          C2_CUDA_TRY(cudaMemsetAsync(ga.counter, 0, sizeof(unsigned), st));
+          C2_LAUNCH(k_greedy_round, num_sms() * per_sm, kNT, smem, st, ga);
+          std::swap(cur, nxt);
+        }
+      }
+      {
+        Prof p_emit(st, "greedy_emit");
+        ga.wl_in = cur;
+        C2_LAUNCH(k_greedy_emit, div_up(n_greedy_users * 32, kNT), kNT, 0, st, ga);
+      }
     }
     C2_CUDA_TRY(cudaGetLastError());
     g0 = g1;
