@@ -209,6 +209,79 @@ __device__ __forceinline__ bool warp_list_insert(WarpList& e, int k, int32_t id,
   return true;
 }
 
+// Strict order on warp-list entries: better neighbour first, empty last.
+__device__ __forceinline__ bool entry_better(const WarpList& a, const WarpList& b) {
+  return a.id >= 0 && (b.id < 0 || nbr_better(a.c, a.u, a.id, b.c, b.u, b.id));
+}
+
+__device__ __forceinline__ WarpList shfl_entry_xor(const WarpList& e, int m) {
+  WarpList o;
+  o.id = __shfl_xor_sync(0xffffffffu, e.id, m);
+  o.c = __shfl_xor_sync(0xffffffffu, e.c, m);
+  o.u = __shfl_xor_sync(0xffffffffu, e.u, m);
+  return o;
+}
+
+// Bitonic sort of one entry per lane, best first (32 lanes).
+__device__ __forceinline__ void warp_sort32(WarpList& e) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int size = 2; size <= 32; size <<= 1) {
+#pragma unroll
+    for (int j = size >> 1; j > 0; j >>= 1) {
+      const WarpList o = shfl_entry_xor(e, j);
+      const bool best_first = size == 32 || (lane & size) == 0;
+      const bool lower = (lane & j) == 0;
+      const bool take = (lower == best_first) ? entry_better(o, e) : entry_better(e, o);
+      if (take) e = o;
+    }
+  }
+}
+
+// Merges a warp batch (one candidate per lane, `pass` marks real ones) into
+// the sorted list of length k: the batch is sorted, the two sorted runs are
+// combined into a bitonic sequence holding the best 32, which is cleaned.
+__device__ __forceinline__ void warp_list_merge(WarpList& e, int k, bool pass, int32_t id,
+                                                uint32_t c, uint32_t u) {
+  const int lane = threadIdx.x & 31;
+  WarpList b;
+  b.id = pass ? id : -1;
+  b.c = c;
+  b.u = u;
+  warp_sort32(b);
+  if (lane >= k) e.id = -1;
+  WarpList r;
+  r.id = __shfl_sync(0xffffffffu, b.id, 31 - lane);
+  r.c = __shfl_sync(0xffffffffu, b.c, 31 - lane);
+  r.u = __shfl_sync(0xffffffffu, b.u, 31 - lane);
+  if (entry_better(r, e)) e = r;
+#pragma unroll
+  for (int j = 16; j > 0; j >>= 1) {
+    const WarpList o = shfl_entry_xor(e, j);
+    const bool lower = (lane & j) == 0;
+    const bool take = lower ? entry_better(o, e) : entry_better(e, o);
+    if (take) e = o;
+  }
+  if (lane >= k) e.id = -1;
+}
+
+// Adds the lanes' candidates flagged `pass` to the list: one by one when few
+// pass, by a sort-and-merge when many do.
+__device__ __forceinline__ void warp_list_add(WarpList& e, int k, bool pass, int32_t id,
+                                              uint32_t c, uint32_t u) {
+  unsigned mask = __ballot_sync(0xffffffffu, pass);
+  if (__popc(mask) > 10) {
+    warp_list_merge(e, k, pass, id, c, u);
+    return;
+  }
+  while (mask) {
+    const int src = __ffs(mask) - 1;
+    mask &= mask - 1;
+    warp_list_insert(e, k, __shfl_sync(0xffffffffu, id, src), __shfl_sync(0xffffffffu, c, src),
+                     __shfl_sync(0xffffffffu, u, src));
+  }
+}
+
 __device__ __forceinline__ unsigned lanemask_lt() {
   unsigned m;
   asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));

@@ -248,15 +248,7 @@ __global__ void __launch_bounds__(NT) k_table(TableArgs a) {
                 pass = beats(kth, vid, cc, uu);
               }
             }
-            unsigned mask = __ballot_sync(0xffffffffu, pass);
-            while (mask) {
-              const int src = __ffs(mask) - 1;
-              mask &= mask - 1;
-              const int32_t bid = __shfl_sync(0xffffffffu, vid, src);
-              const uint32_t bc = __shfl_sync(0xffffffffu, cc, src);
-              const uint32_t bu = __shfl_sync(0xffffffffu, uu, src);
-              warp_list_insert(L[s], k, bid, bc, bu);
-            }
+            warp_list_add(L[s], k, pass, vid, cc, uu);
           }
         }
       }
@@ -468,13 +460,7 @@ __global__ void __launch_bounds__(kNT) k_gram_topk(RowTopkArgs a) {
         pass = beats(kth, v, cc, uu);   // local index order = user id order
       }
     }
-    unsigned mask = __ballot_sync(0xffffffffu, pass);
-    while (mask) {
-      const int src = __ffs(mask) - 1;
-      mask &= mask - 1;
-      warp_list_insert(L, k, __shfl_sync(0xffffffffu, v, src), __shfl_sync(0xffffffffu, cc, src),
-                       __shfl_sync(0xffffffffu, uu, src));
-    }
+    warp_list_add(L, k, pass, v, cc, uu);
   }
   if (lane < k) {
     const int64_t o = (int64_t)slot * k + lane;
@@ -581,13 +567,7 @@ __global__ void __launch_bounds__(kNT) k_merge_knn(MergeArgs a) {
     kth.c = __shfl_sync(0xffffffffu, L.c, k - 1);
     kth.u = __shfl_sync(0xffffffffu, L.u, k - 1);
     pass = v >= 0 && v != u && cc > 0 && beats(kth, v, cc, uu);
-    unsigned mask = __ballot_sync(0xffffffffu, pass);
-    while (mask) {
-      const int src = __ffs(mask) - 1;
-      mask &= mask - 1;
-      warp_list_insert(L, k, __shfl_sync(0xffffffffu, v, src), __shfl_sync(0xffffffffu, cc, src),
-                       __shfl_sync(0xffffffffu, uu, src));
-    }
+    warp_list_add(L, k, pass, v, cc, uu);
   }
   if (lane < k) {
     const int64_t o = row * k + lane;
@@ -798,15 +778,17 @@ __global__ void __launch_bounds__(kNT) k_greedy_init(GreedyArgs a) {
       cnt = min(k0, cnt + __popc(okm));
       __syncwarp();
     }
+    // the cnt <= k drawn members, one per lane, sorted best first
+    __syncwarp();
     WarpList Lst;
     Lst.id = -1; Lst.c = 0; Lst.u = 0;
-    const uint32_t my = (uint32_t)a.slen[slot];
-    for (int q = 0; q < cnt; ++q) {
-      const int v = drawn[q];
-      const uint32_t cc = G[v];
-      const uint32_t uu = my + (uint32_t)a.slen[cs + v] - cc;
-      warp_list_insert(Lst, k, v, cc, uu);
+    if (lane < cnt) {
+      const int v = drawn[lane];
+      Lst.id = v;
+      Lst.c = G[v];
+      Lst.u = (uint32_t)a.slen[slot] + (uint32_t)a.slen[cs + v] - Lst.c;
     }
+    warp_sort32(Lst);
     if (lane < k) a.wl_out[(int64_t)slot * k + lane] = Lst.id;
     __syncwarp();
     for (int q = lane; q < cnt; q += 32) {
@@ -887,13 +869,7 @@ __global__ void __launch_bounds__(kNT, 4) k_greedy_round(GreedyArgs a) {
         kth.c = __shfl_sync(0xffffffffu, Lst.c, k - 1);
         kth.u = __shfl_sync(0xffffffffu, Lst.u, k - 1);
         const bool pass = isnew && beats(kth, v, cc, uu2);
-        unsigned mask = __ballot_sync(0xffffffffu, pass);
-        while (mask) {
-          const int src = __ffs(mask) - 1;
-          mask &= mask - 1;
-          warp_list_insert(Lst, k, __shfl_sync(0xffffffffu, v, src),
-                           __shfl_sync(0xffffffffu, cc, src), __shfl_sync(0xffffffffu, uu2, src));
-        }
+        warp_list_add(Lst, k, pass, v, cc, uu2);
       };
       // neighbour rows, 16 at a time (independent loads in flight)
       for (int j0 = 0; j0 < nlist; j0 += 16) {
