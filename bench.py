@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-quality", action="store_true")
+    ap.add_argument("--gram-budget-mb", type=int, default=0,
+                    help="cap on count matrices held at once (0 = library default)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="target CPU seconds of the oracle sample")
     return ap.parse_args()
@@ -313,7 +315,8 @@ def main():
     nnz = int(items_np.size)
     ptr = torch.from_numpy(ptr_np).to(dev)
     items = torch.from_numpy(items_np).to(dev)
-    opts = c2.options(greedy_threshold=w.greedy_threshold, greedy_rounds=w.greedy_rounds)
+    opts = c2.options(greedy_threshold=w.greedy_threshold, greedy_rounds=w.greedy_rounds,
+                      gram_budget_bytes=args.gram_budget_mb << 20)
     ws = c2.workspace(c2.workspace_size(w.n_users, nnz, w.n_items, w.k, w.t, w.b, w.N, opts), dev)
     out = [torch.empty((w.n_users, w.k), dtype=torch.int32, device=dev) for _ in range(3)]
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)

@@ -241,8 +241,8 @@ __device__ __forceinline__ void warp_sort32(WarpList& e) {
 // Merges a warp batch (one candidate per lane, `pass` marks real ones) into
 // the sorted list of length k: the batch is sorted, the two sorted runs are
 // combined into a bitonic sequence holding the best 32, which is cleaned.
-__device__ __forceinline__ void warp_list_merge(WarpList& e, int k, bool pass, int32_t id,
-                                                uint32_t c, uint32_t u) {
+__device__ __noinline__ void warp_list_merge(WarpList& e, int k, bool pass, int32_t id,
+                                             uint32_t c, uint32_t u) {
   const int lane = threadIdx.x & 31;
   WarpList b;
   b.id = pass ? id : -1;
@@ -270,7 +270,7 @@ __device__ __forceinline__ void warp_list_merge(WarpList& e, int k, bool pass, i
 __device__ __forceinline__ void warp_list_add(WarpList& e, int k, bool pass, int32_t id,
                                               uint32_t c, uint32_t u) {
   unsigned mask = __ballot_sync(0xffffffffu, pass);
-  if (__popc(mask) > 10) {
+  if (__popc(mask) > 16) {
     warp_list_merge(e, k, pass, id, c, u);
     return;
   }

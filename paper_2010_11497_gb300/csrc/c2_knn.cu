@@ -1184,7 +1184,11 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
         int per_sm = 0;
         C2_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_greedy_round, kNT, smem));
         if (per_sm < 1) return C2_ERR_UNSUPPORTED;
+        static const char* kRoundName[] = {"round_01", "round_02", "round_03", "round_04",
+                                           "round_05", "round_06", "round_07", "round_08",
+                                           "round_09", "round_10", "round_11+"};
         for (int r = 1; r <= rounds; ++r) {
+          Prof p_r(st, kRoundName[std::min(r, 11) - 1]);
           ga.round = r;
           ga.wl_in = cur;
           ga.wl_out = nxt;
