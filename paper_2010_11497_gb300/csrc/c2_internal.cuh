@@ -241,7 +241,7 @@ __device__ __forceinline__ void warp_sort32(WarpList& e) {
 // Merges a warp batch (one candidate per lane, `pass` marks real ones) into
 // the sorted list of length k: the batch is sorted, the two sorted runs are
 // combined into a bitonic sequence holding the best 32, which is cleaned.
-__device__ __noinline__ void warp_list_merge(WarpList& e, int k, bool pass, int32_t id,
+static __device__ __noinline__ void warp_list_merge(WarpList& e, int k, bool pass, int32_t id,
                                              uint32_t c, uint32_t u) {
   const int lane = threadIdx.x & 31;
   WarpList b;
