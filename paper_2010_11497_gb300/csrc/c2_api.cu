@@ -83,6 +83,9 @@ void bind_knn_ws(Ws& w, const Sizes& s, KnnWs& c) {
   c.ub_slot = w.take<int32_t>(S + 1);
   c.ub_g = w.take<int32_t>(S + 1);
   c.ord = w.take<int32_t>(S + 1);
+  c.chg0 = w.take<int32_t>(S + 1);
+  c.chg1 = w.take<int32_t>(S + 1);
+  c.gfresh = w.take<int32_t>(S + 1);
   c.pptr = w.take<int32_t>((int64_t)s.n + 1);
   c.wl0 = w.take<int32_t>((S + 1) * s.k);
   c.wl1 = w.take<int32_t>((S + 1) * s.k);

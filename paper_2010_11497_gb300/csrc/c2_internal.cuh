@@ -122,6 +122,8 @@ struct KnnWs {
   int32_t *bb_cnt, *bb_off;// [S+1] brute-force users per cluster of a batch
   int32_t *ub_slot, *ub_g; // [S+1] brute-force users of a batch
   int32_t* ord;            // [S+1] candidate order inside each cluster
+  int32_t *chg0, *chg1;    // [S+1] greedy: list changed in the last round
+  int32_t* gfresh;         // [S+1] greedy: evaluations of the last computed round
   int32_t* pptr;           // [n+1] padded CSR offsets
   int32_t* pitems;         // padded CSR items: the workspace tail
   int64_t pitems_cap;      // capacity of pitems (elements)

@@ -725,6 +725,9 @@ struct GreedyArgs {
   uint2 key;               // Philox key = run seed
   const int32_t* wl_in;    // [S][k] local indices
   int32_t* wl_out;
+  const int32_t* chg_in;   // per slot: list changed in the previous round (NULL = no skipping)
+  int32_t* chg_out;
+  int32_t* fresh;          // per slot: evaluations of the last computed round
   int32_t *out_id, *out_in, *out_un;
   DevHeader* hdr;
 };
@@ -790,6 +793,7 @@ __global__ void __launch_bounds__(kNT) k_greedy_init(GreedyArgs a) {
     }
     warp_sort32(Lst);
     if (lane < k) a.wl_out[(int64_t)slot * k + lane] = Lst.id;
+    if (lane == 0 && a.chg_out) a.chg_out[slot] = 1;
     __syncwarp();
     for (int q = lane; q < cnt; q += 32) {
       const int v = drawn[q];
@@ -834,6 +838,20 @@ __global__ void __launch_bounds__(kNT, 4) k_greedy_round(GreedyArgs a) {
       const int l = chunk * kGreedyChunk + uu * 8 + warp;
       if (l >= M) break;
       const int slot = cs + l;
+      const int e = lane < k ? a.wl_in[(int64_t)slot * k + lane] : -1;
+      if (a.chg_in) {
+        // Unchanged list and unchanged neighbour lists: the candidate set,
+        // hence the new list and its evaluation count, repeat the last round.
+        const bool moved = a.chg_in[slot] != 0 || (e >= 0 && a.chg_in[cs + e] != 0);
+        if (!__any_sync(0xffffffffu, moved)) {
+          if (lane < k) a.wl_out[(int64_t)slot * k + lane] = e;
+          if (lane == 0) {
+            a.chg_out[slot] = 0;
+            evals += (unsigned)a.fresh[slot];
+          }
+          continue;
+        }
+      }
       // stage my row of counts (16-byte aligned rows) and clear my bitmap
       const uint4* g4 = reinterpret_cast<const uint4*>(Gc + (int64_t)l * Mp);
       uint4* r4 = reinterpret_cast<uint4*>(row);
@@ -841,7 +859,6 @@ __global__ void __launch_bounds__(kNT, 4) k_greedy_round(GreedyArgs a) {
       for (int i = lane; i < ((M + 31) >> 5); i += 32) bm[i] = 0;
       __syncwarp();
       const uint32_t my = (uint32_t)s_len[l];
-      const int e = lane < k ? a.wl_in[(int64_t)slot * k + lane] : -1;
       WarpList Lst;
       Lst.id = e;
       Lst.c = e >= 0 ? row[e] : 0u;
@@ -893,6 +910,16 @@ __global__ void __launch_bounds__(kNT, 4) k_greedy_round(GreedyArgs a) {
         consider(v);
       }
       if (lane < k) a.wl_out[(int64_t)slot * k + lane] = Lst.id;
+      if (a.chg_out) {
+        const bool moved = __any_sync(0xffffffffu, lane < k && Lst.id != e);
+        unsigned f = fresh;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
+        if (lane == 0) {
+          a.chg_out[slot] = moved ? 1 : 0;
+          a.fresh[slot] = (int32_t)f;
+        }
+      }
       evals += fresh;
       __syncwarp();
     }
@@ -1173,10 +1200,15 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
         ga.round = 0;
         ga.wl_in = nullptr;
         ga.wl_out = w.wl0;
+        ga.chg_out = opt.greedy_random == 0 ? w.chg0 : nullptr;
         C2_LAUNCH(k_greedy_init, grid, kNT, 0, st, ga);
       }
       int32_t* cur = w.wl0;
       int32_t* nxt = w.wl1;
+      int32_t* chg_cur = w.chg0;
+      int32_t* chg_nxt = w.chg1;
+      const bool skipping = opt.greedy_random == 0;
+      ga.fresh = w.gfresh;
       {
         Prof p_rounds(st, "greedy_rounds");
         const int smem = 21 * ga.mcap;
@@ -1192,6 +1224,10 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
           ga.round = r;
           ga.wl_in = cur;
           ga.wl_out = nxt;
+          // round 1 computes every user (no previous round to repeat)
+          ga.chg_in = (skipping && r > 1) ? chg_cur : nullptr;
+          ga.chg_out = skipping ? chg_nxt : nullptr;
+          std::swap(chg_cur, chg_nxt);
           C2_CUDA_TRY(cudaMemsetAsync(ga.counter, 0, sizeof(unsigned), st));
           C2_LAUNCH(k_greedy_round, num_sms() * per_sm, kNT, smem, st, ga);
           std::swap(cur, nxt);
