@@ -201,6 +201,27 @@ c2_status c2_get_stats(const void* d_ws, c2_stream_t stream, c2_stats* out);
 /* Clears the device status word and statistics of d_ws (asynchronous). */
 c2_status c2_reset_status(void* d_ws, c2_stream_t stream);
 
+/* Step 3 without a workspace, for callers that cannot allocate device memory
+ * when they merge (inside a stream capture without a memory pool, plug-ins
+ * whose host owns every allocation, loops that forbid allocation after
+ * start-up).  The paper has no counterpart: this is a deployment variant of
+ * c2_merge_topk with the same arguments and results, minus the workspace.
+ * Its scratch (a status word and one index per (function, user) pair) lives
+ * in an 8 MiB array inside the library that every GPU loading the library
+ * holds until the process exits, so t * n_users may not exceed
+ * c2_merge_topk_noalloc_max_slots() (2,097,088); larger inputs return
+ * C2_ERR_UNSUPPORTED.  It calls no allocation routine.  The first call on a
+ * device looks up the array's device address (once per device, with that
+ * device current); make that first call before any stream capture.  All
+ * calls share the one array: calls that overlap on the GPU (different
+ * streams, or another thread) race and must be serialised by the caller.
+ * Device-side errors are not reported through a workspace status word. */
+int64_t c2_merge_topk_noalloc_max_slots(void);
+c2_status c2_merge_topk_noalloc(const int32_t* d_cusers, int32_t n_users, int32_t t, int32_t k,
+                                const int32_t* d_loc_id, const int32_t* d_loc_inter,
+                                const int32_t* d_loc_union, int32_t* d_nbr_id,
+                                int32_t* d_nbr_inter, int32_t* d_nbr_union, c2_stream_t stream);
+
 /* Instrumentation (no counterpart in the paper; the paper reports wall-clock
  * time only, Section IV-E).  c2_kernel_launches() returns how many CUDA
  * kernels this library has launched in the process.  With profiling enabled

@@ -69,6 +69,8 @@ _SIGS = {
     "c2_get_status": (C.c_int, [P, P]),
     "c2_get_stats": (C.c_int, [P, P, C.POINTER(Stats)]),
     "c2_reset_status": (C.c_int, [P, P]),
+    "c2_merge_topk_noalloc": (C.c_int, [P, I32, I32, I32, P, P, P, P, P, P, P]),
+    "c2_merge_topk_noalloc_max_slots": (C.c_int64, []),
     "c2_kernel_launches": (C.c_int64, []),
     "c2_profile_enable": (None, [C.c_int]),
     "c2_profile_report": (C.c_size_t, [C.c_char_p, C.c_size_t]),
@@ -194,6 +196,20 @@ def c2_merge_topk(cusers, n_users, t, k, loc_id, loc_inter, loc_union, ws=None, 
                              _stream(stream))
     _check(rc, "c2_merge_topk")
     return tuple(out)
+
+
+def c2_merge_topk_noalloc(cusers, n_users, t, k, loc_id, loc_inter, loc_union, stream=None):
+    """Step 3 without a workspace (scratch in a fixed library array; see c2.h)."""
+    dev = cusers.device
+    out = [torch.empty((n_users, k), dtype=torch.int32, device=dev) for _ in range(3)]
+    rc = lib().c2_merge_topk_noalloc(_ptr(cusers), n_users, t, k, _ptr(loc_id), _ptr(loc_inter),
+                                     _ptr(loc_union), *[_ptr(x) for x in out], _stream(stream))
+    _check(rc, "c2_merge_topk_noalloc")
+    return tuple(out)
+
+
+def c2_merge_topk_noalloc_max_slots() -> int:
+    return int(lib().c2_merge_topk_noalloc_max_slots())
 
 
 def c2_build_knn_graph(ptr, items, n_items, k, t, b, N, seed, opts=None, ws=None, out=None,
