@@ -381,6 +381,45 @@ __global__ void __launch_bounds__(NT) k_gram(GramArgs a) {
   if (lane == 0 && visits) atomicAdd(&a.hdr->item_visits[1], visits);
 }
 
+__device__ __forceinline__ uint32_t merge_count(const int32_t* __restrict__ a, int la,
+                                                const int32_t* __restrict__ b, int lb);
+
+// Count-matrix rows by sorted-list merges, for item universes too large for
+// the shared table: one warp per member (row), lane per candidate (column).
+struct MergeGramArgs {
+  const int32_t* ptr;
+  const int32_t* items;
+  const int32_t* cptr;
+  const int32_t* cusers;
+  const int32_t* gcl;
+  const int64_t* gofs;
+  uint16_t* gram;
+  const int32_t* u_slot;
+  const int32_t* u_g;
+  const int32_t* n_users_dev;
+  DevHeader* hdr;
+};
+
+__global__ void __launch_bounds__(256) k_merge_gram(MergeGramArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (w >= *a.n_users_dev || dev_failed(a.hdr)) return;
+  const int slot = a.u_slot[w];
+  const int c = a.gcl[a.u_g[w]];
+  const int cs = a.cptr[c], M = a.cptr[c + 1] - cs, l = slot - cs, Mp = (M + 7) & ~7;
+  const int u = a.cusers[slot];
+  const int32_t* ur = a.items + a.ptr[u];
+  const int ul = a.ptr[u + 1] - a.ptr[u];
+  uint16_t* row = a.gram + a.gofs[c] + (int64_t)l * Mp;
+  for (int v0 = 0; v0 < M; v0 += 32) {
+    const int vl = v0 + lane;
+    if (vl < M) {
+      const int v = a.cusers[cs + vl];
+      row[vl] = (uint16_t)merge_count(ur, ul, a.items + a.ptr[v], a.ptr[v + 1] - a.ptr[v]);
+    }
+  }
+}
+
 // Candidate order of a cluster: members by decreasing profile length, in 64
 // buckets (4 per octave); one block per cluster, counting sort in shared memory.
 __device__ __forceinline__ int len_bucket(int len) {
@@ -1119,7 +1158,6 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
   C2_CUDA_TRY(cudaMemcpyAsync(&ng, &w.hdr->n_work, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   C2_CUDA_TRY(cudaStreamSynchronize(st));
   if (ng == 0) return C2_OK;
-  if (tc.W == 0) return C2_ERR_UNSUPPORTED;   // greedy needs the table kernel for its counts
   C2_CUDA_TRY(scan_exclusive64(w.gsq, w.goff, ng, w.scan_tmp64, st));
   C2_LAUNCH(k_gram_stats, 1, 1, 0, st, w.goff, ng, w.hdr);
   std::vector<int64_t> goff(ng + 1);
@@ -1164,9 +1202,21 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
       C2_CUDA_TRY(scan_exclusive(w.bt_cnt, w.bt_off, nb, w.scan_tmp, st));
       C2_LAUNCH(k_fill_work, div_up(nb, T), T, 0, st, w.bt_cnt, w.bt_off, w.gcl + g0, nb,
                 w.work_c, w.work_t, &w.hdr->n_work);
-      C2_LAUNCH(k_order, nb, 256, 0, st, w.gcl, g0, cptr, w.slen, w.ord);
-      c2_status rc = launch_gram(tc, ga0, st);
-      if (rc) return rc;
+      if (tc.W) {
+        C2_LAUNCH(k_order, nb, 256, 0, st, w.gcl, g0, cptr, w.slen, w.ord);
+        c2_status rc = launch_gram(tc, ga0, st);
+        if (rc) return rc;
+      } else {
+        // no item table fits shared memory: rows by merges (greedy clusters only here)
+        C2_CUDA_TRY(scan_exclusive(w.bu_cnt, w.bu_off, nb, w.scan_tmp, st));
+        C2_LAUNCH(k_fill_users, nb, 256, 0, st, w.gcl, cptr, w.gkind, 1, w.bu_off, g0, nb,
+                  w.gu_slot, w.gu_g);
+        MergeGramArgs ma{};
+        ma.ptr = ptr; ma.items = items; ma.cptr = cptr; ma.cusers = cusers; ma.gcl = w.gcl;
+        ma.gofs = w.gofs; ma.gram = w.gram; ma.u_slot = w.gu_slot; ma.u_g = w.gu_g;
+        ma.n_users_dev = w.bu_off + nb; ma.hdr = w.hdr;
+        C2_LAUNCH(k_merge_gram, div_up((n_greedy_users + n_brute_users) * 32, 256), 256, 0, st, ma);
+      }
     }
     if (n_brute_users) {
       Prof p_bt(st, "brute_rows");

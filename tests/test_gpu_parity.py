@@ -149,6 +149,26 @@ def test_local_greedy(c2, rounds, nrand):
     check_local(c2, ptr, items, 400, 3, 8, 600, 12, 21, 150, rounds, nrand)
 
 
+def test_local_greedy_with_merge_counts(c2):
+    # forced merge strategy: greedy clusters get their count rows by merges
+    ptr, items = synth.random_profiles(2000, 400, 20, 24, zipf_s=1.1)
+    check_local(c2, ptr, items, 400, 3, 8, 600, 10, 22, 150, 3, 0, strategy=0)
+
+
+def test_build_wide_items_with_greedy(c2):
+    # 300k items: no shared-memory item table fits; greedy clusters still build
+    ptr, items = synth.random_profiles(3000, 300000, 12, 25, zipf_s=1.05)
+    m, k, t, b, N, seed, thr = 300000, 10, 4, 8, 800, 6, 200
+    oid, oin, oun, pairs = oracle.build_graph(ptr, items, m, k, t, b, N, seed, thr, 3)
+    opts = c2.options(greedy_threshold=thr, greedy_rounds=3)
+    ws = c2.workspace(c2.workspace_size(3000, items.size, m, k, t, b, N, opts), DEV)
+    gid, gin, gun = c2.c2_build_knn_graph(to_dev(ptr), to_dev(items), m, k, t, b, N, seed,
+                                          opts=opts, ws=ws)
+    assert_same(gid, oid, "nbr_id")
+    assert_same(gin, oin, "nbr_inter")
+    assert c2.c2_get_stats(ws)["pairs"] == pairs
+
+
 def test_local_greedy_small_budget_batches(c2):
     # greedy clusters processed in several batches of intersection matrices
     ptr, items = synth.random_profiles(3000, 300, 15, 15, zipf_s=1.2)
