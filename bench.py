@@ -275,17 +275,29 @@ def roofline(phase_ms, phase_calls, stats, w, nnz, pk, pk_src, W):
                          f"({visits / calls:.3e} visits/launch); peak = 152 SMs x 128 lanes x "
                          f"{pk.get('sm_max_mhz', 2070.0):.0f} MHz"}
     if dom == "greedy_rounds":
+        # per examined neighbour-list entry: bitmap test-and-set (3), count and
+        # length lookups (3), exact cross-multiplied comparison (6) = 12 lane-ops
         ms = phase_ms[dom] / (calls * max(1, w.greedy_rounds))   # one launch per round
-        # per user and round: own row (k ids), k neighbour rows (k*k ids), one 2-byte count
-        # and one 4-byte length per candidate, k ids written
-        users = stats.get("greedy_users", 0)
-        per = 4 * k + 4 * k * k + (2 + 4) * k * k + 4 * k
-        bytes_ = users * per
-        achieved = bytes_ / (ms * 1e-3) / 1e9
-        return {"kernel": "k_greedy_round", "phase": dom, "bound": "hbm", "achieved": achieved,
-                "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": achieved / pk["hbm_gbs"],
+        visits = stats.get("greedy_visits", 0) / max(1, w.greedy_rounds)
+        ops = 12.0
+        achieved = visits * ops / (ms * 1e-3) / 1e12
+        return {"kernel": "k_greedy_round", "phase": dom, "bound": "alu", "achieved": achieved,
+                "peak": alu_peak, "unit": "Tlane-op/s", "frac": achieved / alu_peak,
                 "traffic": None, "ms_per_launch": ms,
-                "model": f"{per} B per greedy user per round, {users} users"}
+                "model": f"{ops:.0f} integer lane-ops per neighbour-list entry examined "
+                         f"({visits:.3e} entries/launch, {stats.get('greedy_computed', 0)} "
+                         f"user-rounds computed of {stats.get('greedy_users', 0) * w.greedy_rounds}); "
+                         f"peak = 152 SMs x 128 lanes x {pk.get('sm_max_mhz', 2070.0):.0f} MHz"}
+    if dom in ("brute_table", "greedy_gram", "gram"):
+        visits = stats["item_visits_brute"] + stats["item_visits_greedy"]
+        ops_per_visit = 1 + W + 12 * W + 48 * W / 12.0
+        achieved = visits / calls * ops_per_visit / (ms * 1e-3) / 1e12
+        return {"kernel": "k_gram<%d>" % W, "phase": dom, "bound": "alu", "achieved": achieved,
+                "peak": alu_peak, "unit": "Tlane-op/s", "frac": achieved / alu_peak,
+                "traffic": None, "ms_per_launch": ms,
+                "model": f"{ops_per_visit:.1f} integer lane-ops per candidate item visit "
+                         f"({visits / calls:.3e} visits/launch); peak = 152 SMs x 128 lanes x "
+                         f"{pk.get('sm_max_mhz', 2070.0):.0f} MHz"}
     if dom == "merge":
         bytes_ = 4 * S + 12 * S * k + 12 * n * k
         achieved = bytes_ / (ms * 1e-3) / 1e9

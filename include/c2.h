@@ -98,7 +98,8 @@ typedef struct {
   int32_t greedy_users;     /* users (slots) in greedy clusters                            */
   int64_t item_visits_brute;/* profile items walked by the shared-memory table kernel:     */
   int64_t item_visits_greedy; /* brute-force clusters / greedy intersection matrices       */
-  int32_t reserved[4];
+  int64_t greedy_visits;    /* neighbour-list entries examined by greedy rounds            */
+  int64_t greedy_computed;  /* (user, round) pairs a greedy round computed, not repeated  */
 } c2_stats;
 
 /* Fills *opt with the defaults described above.  Never fails. */

@@ -43,7 +43,8 @@ class Stats(C.Structure):
                 ("split_levels", C.c_int32), ("n_greedy_clusters", C.c_int32),
                 ("max_cluster", C.c_int32), ("max_profile", C.c_int32),
                 ("greedy_users", C.c_int32), ("item_visits_brute", C.c_int64),
-                ("item_visits_greedy", C.c_int64), ("reserved", C.c_int32 * 4)]
+                ("item_visits_greedy", C.c_int64), ("greedy_visits", C.c_int64),
+                ("greedy_computed", C.c_int64)]
 
 
 _lib = None
@@ -292,7 +293,8 @@ def c2_get_stats(ws, stream=None) -> dict:
     return dict(pairs=s.pairs, gram_pairs=s.gram_pairs, n_clusters=s.n_clusters,
                 split_levels=s.split_levels, n_greedy_clusters=s.n_greedy_clusters,
                 max_cluster=s.max_cluster, max_profile=s.max_profile,
-                greedy_users=s.greedy_users, item_visits_brute=s.item_visits_brute, item_visits_greedy=s.item_visits_greedy)
+                greedy_users=s.greedy_users, greedy_visits=s.greedy_visits,
+                greedy_computed=s.greedy_computed, item_visits_brute=s.item_visits_brute, item_visits_greedy=s.item_visits_greedy)
 
 
 def c2_reset_status(ws, stream=None):

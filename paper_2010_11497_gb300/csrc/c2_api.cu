@@ -242,6 +242,8 @@ c2_status c2_get_stats(const void* d_ws, c2_stream_t stream, c2_stats* out) {
   out->greedy_users = h.greedy_users;
   out->item_visits_brute = (int64_t)h.item_visits[0];
   out->item_visits_greedy = (int64_t)h.item_visits[1];
+  out->greedy_visits = (int64_t)h.greedy_visits;
+  out->greedy_computed = (int64_t)h.greedy_computed;
   return C2_OK;
 }
 

@@ -33,7 +33,9 @@ struct DevHeader {
   unsigned long long item_visits[2];  // table kernel: candidate items walked (brute, greedy)
   int32_t greedy_users;
   int32_t n_gwork;             // greedy round work items of the current batch
-  int32_t pad[20];
+  unsigned long long greedy_visits;    // candidate entries examined by computed users
+  unsigned long long greedy_computed;  // (user, round) pairs computed (not skipped)
+  int32_t pad[16];
 };
 static_assert(sizeof(DevHeader) <= 256, "header must fit 256 bytes");
 

@@ -861,7 +861,7 @@ __global__ void __launch_bounds__(kNT, 4) k_greedy_round(GreedyArgs a) {
   uint32_t* bm = s_bm + warp * (mcap >> 5);
   const int nwork = *a.n_gwork;
   const int k = a.k;
-  unsigned long long evals = 0;
+  unsigned long long evals = 0, visits = 0, computed = 0;
   for (;;) {
     if (threadIdx.x == 0) s_work = dev_failed(a.hdr) ? nwork : (int)atomicAdd(a.counter, 1u);
     __syncthreads();
@@ -907,6 +907,10 @@ __global__ void __launch_bounds__(kNT, 4) k_greedy_round(GreedyArgs a) {
       const int nlist = __popc(__ballot_sync(0xffffffffu, e >= 0));
       __syncwarp();
       unsigned fresh = 0;
+      if (lane == 0) {
+        visits += (unsigned long long)nlist * (unsigned long long)k + (unsigned)a.n_random;
+        computed += 1;
+      }
       // one candidate per lane: dedupe, count lookup, exact filter, insert
       auto consider = [&](int v) {
         bool isnew = false;
@@ -967,6 +971,8 @@ __global__ void __launch_bounds__(kNT, 4) k_greedy_round(GreedyArgs a) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) evals += __shfl_xor_sync(0xffffffffu, evals, o);
   if (lane == 0 && evals) atomicAdd(&a.hdr->pairs, evals);
+  if (lane == 0 && visits) atomicAdd(&a.hdr->greedy_visits, visits);
+  if (lane == 0 && computed) atomicAdd(&a.hdr->greedy_computed, computed);
 }
 
 // Final rows: global ids, zero-similarity entries dropped (they sort last).
