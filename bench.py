@@ -449,6 +449,7 @@ def main():
                 "gpu_launches_per_step": launches / args.steps,
                 "wall_s_timed": wall, "step_ms": step_ms,
                 "phases_ms_per_step": phase_ms, "roofline": rf, "cpu_baseline": cpu,
+                "autotune": c2.c2_autotune_report(),
                 "clocks": clocks, "stats": stats}
         print(json.dumps(line))
     if dist is not None:

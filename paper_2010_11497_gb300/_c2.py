@@ -73,6 +73,7 @@ _SIGS = {
     "c2_merge_topk_noalloc": (C.c_int, [P, I32, I32, I32, P, P, P, P, P, P, P]),
     "c2_merge_topk_noalloc_max_slots": (C.c_int64, []),
     "c2_kernel_launches": (C.c_int64, []),
+    "c2_autotune_report": (C.c_size_t, [C.c_char_p, C.c_size_t]),
     "c2_profile_enable": (None, [C.c_int]),
     "c2_profile_report": (C.c_size_t, [C.c_char_p, C.c_size_t]),
 }
@@ -303,6 +304,14 @@ def c2_reset_status(ws, stream=None):
 
 def c2_status_string(code: int) -> str:
     return lib().c2_status_string(code).decode()
+
+
+def c2_autotune_report() -> list:
+    import json
+    need = lib().c2_autotune_report(None, 0)
+    buf = C.create_string_buffer(int(need) + 1024)
+    lib().c2_autotune_report(buf, len(buf))
+    return json.loads(buf.value.decode() or "[]")
 
 
 def c2_kernel_launches() -> int:

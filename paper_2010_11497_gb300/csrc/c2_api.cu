@@ -428,4 +428,6 @@ c2_status c2_avg_sim(const int32_t* d_nbr_inter, const int32_t* d_nbr_union, int
                      (cudaStream_t)stream);
 }
 
+size_t c2_autotune_report(char* buf, size_t len) { return c2::autotune_report(buf, len); }
+
 }  // extern "C"

@@ -345,5 +345,6 @@ c2_status run_validate(const int32_t* ptr, const int32_t* items, const Sizes& s,
                        cudaStream_t st);
 
 int num_sms();
+size_t autotune_report(char* buf, size_t len);
 
 }  // namespace c2

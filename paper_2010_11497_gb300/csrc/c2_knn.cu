@@ -12,7 +12,14 @@
 //   sorted-list merge) serves item universes too large for the table.
 // Top-k lists live in warp registers (lane j = entry j) and are updated with
 // an exact cross-multiplied comparison.
+#include <stdio.h>
+#include <string.h>
+
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
 #include <vector>
 
 #include "c2_internal.cuh"
@@ -295,7 +302,8 @@ struct GramArgs {
   int32_t n_items;
   const int32_t* work_c;
   const int32_t* work_t;
-  const int32_t* n_work;
+  const int32_t* work_begin;   // device: first and one-past-last work item of this launch
+  const int32_t* work_end;
   const int32_t* cptr;
   const int32_t* cusers;
   const int32_t* ord;      // per slot: candidate order (local indices) of its cluster
@@ -314,11 +322,11 @@ __global__ void __launch_bounds__(NT) k_gram(GramArgs a) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int i = tid; i < (a.n_items + 1) * W; i += NT) T[i] = 0;
   if (tid == 0) s_next = 0;
-  const int nwork = *a.n_work;
+  const int wbeg = *a.work_begin, nwork = *a.work_end;
   unsigned long long visits = 0;
   __syncthreads();
   for (;;) {
-    if (tid == 0) s_work = dev_failed(a.hdr) ? nwork : (int)atomicAdd(a.counter, 1u);
+    if (tid == 0) s_work = dev_failed(a.hdr) ? nwork : wbeg + (int)atomicAdd(a.counter, 1u);
     __syncthreads();
     const int wi = s_work;
     if (wi >= nwork) break;
@@ -704,21 +712,35 @@ __global__ void k_greedy_list(const int32_t* __restrict__ gflag, const int32_t* 
   }
 }
 
-// Per count-matrix cluster of a batch: its matrix offset, query tiles, and
-// its members as greedy users / brute-force users / greedy work chunks.
+// Size buckets of count-matrix clusters (each gets its own table shape).
+constexpr int kBuckets = 4;
+__host__ __device__ inline int size_bucket(int M) {
+  return M < 128 ? 0 : (M < 512 ? 1 : (M < 2048 ? 2 : 3));
+}
+
+// Per count-matrix cluster of a batch: its matrix offset and its members as
+// greedy users / brute-force users / greedy work chunks.
 __global__ void k_batch_setup(const int32_t* __restrict__ gcl, const int64_t* __restrict__ goff,
                               const int32_t* __restrict__ gsz, const int32_t* __restrict__ gkind,
-                              int32_t g0, int32_t g1, int32_t Q, int64_t* __restrict__ gofs,
-                              int32_t* __restrict__ ntiles, int32_t* __restrict__ ngu,
-                              int32_t* __restrict__ nbu, int32_t* __restrict__ ngw) {
+                              int32_t g0, int32_t g1, int64_t* __restrict__ gofs,
+                              int32_t* __restrict__ ngu, int32_t* __restrict__ nbu,
+                              int32_t* __restrict__ ngw) {
   const int g = g0 + blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= g1) return;
   const int M = gsz[g], j = g - g0;
   gofs[gcl[g]] = goff[g] - goff[g0];
-  ntiles[j] = (M + Q - 1) / Q;
   ngu[j] = gkind[g] ? M : 0;
   nbu[j] = gkind[g] ? 0 : M;
   ngw[j] = gkind[g] ? (M + kGreedyChunk - 1) / kGreedyChunk : 0;
+}
+
+// Query tiles of the batch clusters of one size bucket (tile = q members).
+__global__ void k_bucket_tiles(const int32_t* __restrict__ gsz, int32_t g0, int32_t nb,
+                               int32_t bucket, int32_t q, int32_t* __restrict__ cnt) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nb) return;
+  const int M = gsz[g0 + j];
+  cnt[j] = size_bucket(M) == bucket ? (M + q - 1) / q : 0;
 }
 
 // Members of the batch's clusters of one kind, as (slot, count-matrix index).
@@ -1082,12 +1104,31 @@ c2_status launch_gram_t(const GramArgs& a, cudaStream_t st) {
 }
 
 c2_status launch_gram(TableCfg c, const GramArgs& a, cudaStream_t st) {
+  if (c.W == 1 && c.NT == 128) return launch_gram_t<1, 128>(a, st);
   if (c.W == 1 && c.NT == 256) return launch_gram_t<1, 256>(a, st);
   if (c.W == 1 && c.NT == 512) return launch_gram_t<1, 512>(a, st);
+  if (c.W == 2 && c.NT == 128) return launch_gram_t<2, 128>(a, st);
   if (c.W == 2 && c.NT == 256) return launch_gram_t<2, 256>(a, st);
   if (c.W == 2 && c.NT == 512) return launch_gram_t<2, 512>(a, st);
   return C2_ERR_UNSUPPORTED;
 }
+
+// ---- autotuner: per size bucket, the table shape measured fastest; cached by
+// problem sizes (a performance choice only: every shape gives the same counts)
+struct TuneKey {
+  int64_t n, m, t, b, N, k, thr;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(n, m, t, b, N, k, thr) < std::tie(o.n, o.m, o.t, o.b, o.N, o.k, o.thr);
+  }
+};
+struct TuneEntry {
+  TableCfg cfg[kBuckets];
+  float ms[kBuckets];
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneEntry> g_tune;
+
+const TableCfg kGramShapes[] = {{2, 256}, {2, 512}, {2, 128}, {1, 512}, {1, 256}, {1, 128}};
 
 bool gram_fits(TableCfg c, int m) { return gram_smem_bytes(c, m) + 1024 <= smem_optin(); }
 
@@ -1128,7 +1169,6 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
   const int thr = opt.greedy_threshold > 0 ? opt.greedy_threshold : 5 * k * k;
   const int rounds = opt.greedy_rounds >= 0 ? opt.greedy_rounds : 10;
   const TableCfg tc = pick_gram(opt.strategy, s.m);
-  const int Q = tc.W ? 32 * tc.W : 32;
   // brute-force clusters smaller than small_cut go to the warp-per-query merge
   // kernel; larger ones and every greedy cluster get a count matrix
   const int small_cut = tc.W ? kSmallCut : (1 << 30);
@@ -1182,7 +1222,7 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
 
   GramArgs ga0{};
   ga0.ptr = ptr; ga0.items = items; ga0.pptr = w.pptr; ga0.pitems = w.pitems;
-  ga0.n_items = s.m; ga0.work_c = w.work_c; ga0.work_t = w.work_t; ga0.n_work = &w.hdr->n_work;
+  ga0.n_items = s.m; ga0.work_c = w.work_c; ga0.work_t = w.work_t;
   ga0.cptr = cptr; ga0.cusers = cusers; ga0.ord = w.ord; ga0.gofs = w.gofs; ga0.gram = w.gram;
   ga0.hdr = w.hdr; ga0.counter = &w.hdr->work_counter[1];
 
@@ -1203,15 +1243,71 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
     const int nb = g1 - g0;
     {
       Prof p_gram(st, "gram");
-      C2_LAUNCH(k_batch_setup, div_up(nb, T), T, 0, st, w.gcl, w.goff, w.gsz, w.gkind, g0, g1, Q,
-                w.gofs, w.bt_cnt, w.bu_cnt, w.bb_cnt, w.bw_cnt);
-      C2_CUDA_TRY(scan_exclusive(w.bt_cnt, w.bt_off, nb, w.scan_tmp, st));
-      C2_LAUNCH(k_fill_work, div_up(nb, T), T, 0, st, w.bt_cnt, w.bt_off, w.gcl + g0, nb,
-                w.work_c, w.work_t, &w.hdr->n_work);
+      C2_LAUNCH(k_batch_setup, div_up(nb, T), T, 0, st, w.gcl, w.goff, w.gsz, w.gkind, g0, g1,
+                w.gofs, w.bu_cnt, w.bb_cnt, w.bw_cnt);
       if (tc.W) {
         C2_LAUNCH(k_order, nb, 256, 0, st, w.gcl, g0, cptr, w.slen, w.ord);
-        c2_status rc = launch_gram(tc, ga0, st);
-        if (rc) return rc;
+        bool present[kBuckets] = {false, false, false, false};
+        for (int g = g0; g < g1; ++g) present[size_bucket(gsz[g])] = true;
+        // one launch per size bucket, over that bucket's query tiles
+        auto run_bucket = [&](int bkt, TableCfg shape) -> c2_status {
+          C2_LAUNCH(k_bucket_tiles, div_up(nb, T), T, 0, st, w.gsz, g0, nb, bkt, 32 * shape.W,
+                    w.bt_cnt);
+          C2_CUDA_TRY(scan_exclusive(w.bt_cnt, w.bt_off, nb, w.scan_tmp, st));
+          C2_LAUNCH(k_fill_work, div_up(nb, T), T, 0, st, w.bt_cnt, w.bt_off, w.gcl + g0, nb,
+                    w.work_c, w.work_t, &w.hdr->n_work);
+          GramArgs ga = ga0;
+          ga.work_begin = w.bt_off;
+          ga.work_end = w.bt_off + nb;
+          return launch_gram(shape, ga, st);
+        };
+        TableCfg use[kBuckets] = {tc, tc, tc, tc};
+        bool have = false;
+        const TuneKey key{s.n, s.m, s.t, s.b, s.N, k, thr};
+        if (opt.strategy == C2_STRATEGY_AUTO) {
+          std::lock_guard<std::mutex> lk(g_tune_mu);
+          auto it = g_tune.find(key);
+          if (it != g_tune.end()) {
+            for (int q = 0; q < kBuckets; ++q) use[q] = it->second.cfg[q];
+            have = true;
+          }
+        }
+        if (opt.strategy == C2_STRATEGY_AUTO && !have) {
+          // first call for these sizes: time every shape that fits on each bucket
+          TuneEntry te;
+          for (int q = 0; q < kBuckets; ++q) { te.cfg[q] = tc; te.ms[q] = 0.f; }
+          cudaEvent_t e0, e1;
+          C2_CUDA_TRY(cudaEventCreate(&e0));
+          C2_CUDA_TRY(cudaEventCreate(&e1));
+          for (int q = 0; q < kBuckets; ++q) {
+            if (!present[q]) continue;
+            float best = 1e30f;
+            for (const TableCfg& shape : kGramShapes) {
+              if (!gram_fits(shape, s.m)) continue;
+              C2_CUDA_TRY(cudaEventRecord(e0, st));
+              c2_status rc = run_bucket(q, shape);
+              if (rc) return rc;
+              C2_CUDA_TRY(cudaEventRecord(e1, st));
+              C2_CUDA_TRY(cudaEventSynchronize(e1));
+              float ms = 0.f;
+              C2_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+              if (ms < best) { best = ms; te.cfg[q] = shape; te.ms[q] = ms; }
+            }
+          }
+          cudaEventDestroy(e0);
+          cudaEventDestroy(e1);
+          {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            g_tune[key] = te;
+          }
+          // the last timed shape already wrote every bucket's counts
+        } else {
+          for (int q = 0; q < kBuckets; ++q) {
+            if (!present[q]) continue;
+            c2_status rc = run_bucket(q, use[q]);
+            if (rc) return rc;
+          }
+        }
       } else {
         // no item table fits shared memory: rows by merges (greedy clusters only here)
         C2_CUDA_TRY(scan_exclusive(w.bu_cnt, w.bu_off, nb, w.scan_tmp, st));
@@ -1328,6 +1424,37 @@ c2_status run_bruteforce(const int32_t* ptr, const int32_t* items, const Sizes& 
   C2_LAUNCH(k_merge_knn, div_up((int64_t)rows * 32, kNT), kNT, 0, st, a);
   C2_CUDA_TRY(cudaGetLastError());
   return C2_OK;
+}
+
+size_t autotune_report(char* buf, size_t len) {
+  std::string out = "[";
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  bool first = true;
+  for (const auto& kv : g_tune) {
+    char tmp[512];
+    snprintf(tmp, sizeof tmp,
+             "%s{\"n\": %lld, \"m\": %lld, \"t\": %lld, \"b\": %lld, \"N\": %lld, \"k\": %lld, "
+             "\"threshold\": %lld, \"buckets\": [",
+             first ? "" : ", ", (long long)kv.first.n, (long long)kv.first.m, (long long)kv.first.t,
+             (long long)kv.first.b, (long long)kv.first.N, (long long)kv.first.k,
+             (long long)kv.first.thr);
+    out += tmp;
+    static const char* names[kBuckets] = {"32-127", "128-511", "512-2047", "2048+"};
+    for (int q = 0; q < kBuckets; ++q) {
+      snprintf(tmp, sizeof tmp, "%s{\"sizes\": \"%s\", \"words\": %d, \"threads\": %d, \"ms\": %.4f}",
+               q ? ", " : "", names[q], kv.second.cfg[q].W, kv.second.cfg[q].NT, kv.second.ms[q]);
+      out += tmp;
+    }
+    out += "]}";
+    first = false;
+  }
+  out += "]";
+  if (buf && len) {
+    const size_t n = out.size() < len - 1 ? out.size() : len - 1;
+    memcpy(buf, out.data(), n);
+    buf[n] = 0;
+  }
+  return out.size() + 1;
 }
 
 }  // namespace c2
