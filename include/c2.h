@@ -26,6 +26,9 @@
  * - Every function is asynchronous on `stream` unless stated otherwise.  The
  *   library allocates no device memory: scratch space comes from the caller's
  *   workspace `d_ws` of at least c2_workspace_size() bytes (256-byte aligned).
+ * - A workspace must start with a cleared status header (its first 256
+ *   bytes zero, or c2_reset_status()); c2_frh_cluster, c2_build_knn_graph,
+ *   c2_bruteforce_knn and c2_build_knn_graph_host clear it themselves.
  * - Host-detected argument errors are returned at once.  Errors detected on
  *   the device (an invalid CSR, a bounded wait that ran out) are recorded in
  *   a status word inside the workspace; read it with c2_get_status().  Once a

@@ -144,7 +144,10 @@ def workspace_size(n_users, nnz, n_items, k, t, b, N, opts=None) -> int:
 
 
 def workspace(nbytes: int, device="cuda") -> torch.Tensor:
-    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+    """Workspace tensor with a cleared status header (its first 256 bytes)."""
+    ws = torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+    ws[:256].zero_()
+    return ws
 
 
 # ------------------------------------------------------------------ entry points

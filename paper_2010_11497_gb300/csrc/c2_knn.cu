@@ -735,12 +735,13 @@ __global__ void k_batch_setup(const int32_t* __restrict__ gcl, const int64_t* __
 }
 
 // Query tiles of the batch clusters of one size bucket (tile = q members).
+// bucket < 0 selects every cluster of the batch.
 __global__ void k_bucket_tiles(const int32_t* __restrict__ gsz, int32_t g0, int32_t nb,
                                int32_t bucket, int32_t q, int32_t* __restrict__ cnt) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= nb) return;
   const int M = gsz[g0 + j];
-  cnt[j] = size_bucket(M) == bucket ? (M + q - 1) / q : 0;
+  cnt[j] = (bucket < 0 || size_bucket(M) == bucket) ? (M + q - 1) / q : 0;
 }
 
 // Members of the batch's clusters of one kind, as (slot, count-matrix index).
@@ -1122,6 +1123,7 @@ struct TuneKey {
   }
 };
 struct TuneEntry {
+  bool unified;            // one launch over all buckets with cfg[0]
   TableCfg cfg[kBuckets];
   float ms[kBuckets];
 };
@@ -1262,6 +1264,7 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
           return launch_gram(shape, ga, st);
         };
         TableCfg use[kBuckets] = {tc, tc, tc, tc};
+        bool unified = true;
         bool have = false;
         const TuneKey key{s.n, s.m, s.t, s.b, s.N, k, thr};
         if (opt.strategy == C2_STRATEGY_AUTO) {
@@ -1269,38 +1272,69 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
           auto it = g_tune.find(key);
           if (it != g_tune.end()) {
             for (int q = 0; q < kBuckets; ++q) use[q] = it->second.cfg[q];
+            unified = it->second.unified;
             have = true;
           }
         }
         if (opt.strategy == C2_STRATEGY_AUTO && !have) {
-          // first call for these sizes: time every shape that fits on each bucket
+          // first call for these sizes: time every shape that fits, on each
+          // bucket alone and as one launch over all buckets; keep the faster plan
           TuneEntry te;
+          te.unified = true;
           for (int q = 0; q < kBuckets; ++q) { te.cfg[q] = tc; te.ms[q] = 0.f; }
           cudaEvent_t e0, e1;
           C2_CUDA_TRY(cudaEventCreate(&e0));
           C2_CUDA_TRY(cudaEventCreate(&e1));
+          auto timed = [&](int bkt, TableCfg shape, float* ms) -> c2_status {
+            C2_CUDA_TRY(cudaEventRecord(e0, st));
+            c2_status rc = run_bucket(bkt, shape);
+            if (rc) return rc;
+            C2_CUDA_TRY(cudaEventRecord(e1, st));
+            C2_CUDA_TRY(cudaEventSynchronize(e1));
+            C2_CUDA_TRY(cudaEventElapsedTime(ms, e0, e1));
+            return C2_OK;
+          };
+          float split_total = 0.f;
+          TableCfg best_cfg[kBuckets] = {tc, tc, tc, tc};
+          float best_ms[kBuckets] = {0.f, 0.f, 0.f, 0.f};
           for (int q = 0; q < kBuckets; ++q) {
             if (!present[q]) continue;
             float best = 1e30f;
             for (const TableCfg& shape : kGramShapes) {
               if (!gram_fits(shape, s.m)) continue;
-              C2_CUDA_TRY(cudaEventRecord(e0, st));
-              c2_status rc = run_bucket(q, shape);
-              if (rc) return rc;
-              C2_CUDA_TRY(cudaEventRecord(e1, st));
-              C2_CUDA_TRY(cudaEventSynchronize(e1));
               float ms = 0.f;
-              C2_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
-              if (ms < best) { best = ms; te.cfg[q] = shape; te.ms[q] = ms; }
+              c2_status rc = timed(q, shape, &ms);
+              if (rc) return rc;
+              if (ms < best) { best = ms; best_cfg[q] = shape; best_ms[q] = ms; }
             }
+            split_total += best;
+          }
+          float uni_best = 1e30f;
+          TableCfg uni_cfg = tc;
+          for (const TableCfg& shape : kGramShapes) {
+            if (!gram_fits(shape, s.m)) continue;
+            float ms = 0.f;
+            c2_status rc = timed(-1, shape, &ms);
+            if (rc) return rc;
+            if (ms < uni_best) { uni_best = ms; uni_cfg = shape; }
           }
           cudaEventDestroy(e0);
           cudaEventDestroy(e1);
+          if (uni_best <= split_total) {
+            te.unified = true;
+            for (int q = 0; q < kBuckets; ++q) { te.cfg[q] = uni_cfg; te.ms[q] = q ? 0.f : uni_best; }
+          } else {
+            te.unified = false;
+            for (int q = 0; q < kBuckets; ++q) { te.cfg[q] = best_cfg[q]; te.ms[q] = best_ms[q]; }
+          }
           {
             std::lock_guard<std::mutex> lk(g_tune_mu);
             g_tune[key] = te;
           }
-          // the last timed shape already wrote every bucket's counts
+          // every timed launch wrote the same counts: the matrices are complete
+        } else if (unified) {
+          c2_status rc = run_bucket(-1, use[0]);
+          if (rc) return rc;
         } else {
           for (int q = 0; q < kBuckets; ++q) {
             if (!present[q]) continue;
@@ -1434,10 +1468,10 @@ size_t autotune_report(char* buf, size_t len) {
     char tmp[512];
     snprintf(tmp, sizeof tmp,
              "%s{\"n\": %lld, \"m\": %lld, \"t\": %lld, \"b\": %lld, \"N\": %lld, \"k\": %lld, "
-             "\"threshold\": %lld, \"buckets\": [",
+             "\"threshold\": %lld, \"one_launch\": %s, \"buckets\": [",
              first ? "" : ", ", (long long)kv.first.n, (long long)kv.first.m, (long long)kv.first.t,
              (long long)kv.first.b, (long long)kv.first.N, (long long)kv.first.k,
-             (long long)kv.first.thr);
+             (long long)kv.first.thr, kv.second.unified ? "true" : "false");
     out += tmp;
     static const char* names[kBuckets] = {"32-127", "128-511", "512-2047", "2048+"};
     for (int q = 0; q < kBuckets; ++q) {
