@@ -85,7 +85,11 @@ typedef struct {
                                seeded hash (a test hook for hand-worked examples)          */
   int64_t gram_budget_bytes;/* cap on the intersection-count matrices of greedy clusters
                                held at once; <= 0 selects 2 GiB                            */
-  int32_t reserved[8];      /* must be zero                                                */
+  const int32_t* d_keys;    /* optional first-level cluster keys, device int32 [t][n_users]
+                               in [0, b), e.g. from c2_model_propose; NULL = FastRandomHash.
+                               Oversized clusters are then split by FastRandomHash with no
+                               threshold (the first split key is H_i(u) itself)            */
+  int32_t reserved[6];      /* must be zero                                                */
 } c2_options;
 
 /* Run statistics, filled by c2_get_stats(). */
@@ -127,7 +131,8 @@ size_t c2_workspace_size(int32_t n_users, int64_t nnz, int32_t n_items, int32_t 
  *   d_cusers; entries past *d_n_clusters are left undefined),
  *   d_cusers[t*n_users], d_n_clusters (one int32),
  *   d_cmeta (optional, [t*n_users][4]: function, split depth, residual flag,
- *   last hash key of the cluster's path).
+ *   last key of the cluster's path -- the hash threshold its split used, -1
+ *   for a first-level key given through c2_options.d_keys).
  * This call synchronises `stream` once per split level to read the number of
  * oversized clusters. */
 c2_status c2_frh_cluster(const int32_t* d_csr_ptr, const int32_t* d_csr_items, int32_t n_users,
@@ -225,6 +230,78 @@ c2_status c2_merge_topk_noalloc(const int32_t* d_cusers, int32_t n_users, int32_
                                 const int32_t* d_loc_id, const int32_t* d_loc_inter,
                                 const int32_t* d_loc_union, int32_t* d_nbr_id,
                                 int32_t* d_nbr_inter, int32_t* d_nbr_union, c2_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * Learned cluster proposer (no counterpart in the paper: a stand-in for
+ * FastRandomHash as the source of first-level cluster keys).  For user u:
+ *   e_u = sum over items x of E[SplitMix64(seed xor x) mod 2^rows_log2]
+ *   (BF16 table, FP32 sums);  h_u = ReLU(W1^T e_u + b1) (dim -> hidden);
+ *   z_u = W2^T h_u + b2 (hidden -> t*b);  key_j(u) = argmax of head j's b
+ *   logits, ties to the lower bucket.  GEMMs run BF16 x BF16 -> FP32 on the
+ *   tensor cores.  The model lives in a caller-owned device state buffer of
+ *   c2_model_state_bytes() (FP32 masters, Adam moments, BF16 copies).
+ * Training minimises, over positive pairs (u, v) -- e.g. neighbours in
+ *   graphs built by plain C^2 -- and heads j, -log(sum_c p_u,jc p_v,jc + 1e-9)
+ *   / (P t), p = softmax of a head, plus lambda * sum_j KL(batch mean of
+ *   p_j || uniform) / t; one Adam step (beta 0.9 / 0.999, eps 1e-8) per call.
+ * --------------------------------------------------------------------------- */
+typedef struct {
+  int32_t t, b;          /* heads and buckets per head: keys for t functions in [0, b)   */
+  int32_t dim, hidden;   /* embedding width (32..128, multiple of 32) and hidden width   */
+  int32_t rows_log2;     /* embedding table rows 2^rows_log2 (4..26)                     */
+  int32_t reserved0;     /* must be zero                                                 */
+  uint64_t seed;         /* item-row hash and initialisation seed                        */
+} c2_model_config;
+
+size_t c2_model_state_bytes(const c2_model_config* cfg);
+/* Workspace of c2_model_propose (rows = users per chunk, train = 0) or of a
+ * training step on max_rows pairs (train = 1). */
+size_t c2_model_workspace_size(const c2_model_config* cfg, int32_t max_rows, int32_t train);
+/* Deterministic initialisation (uniform, Philox-seeded), zero Adam moments. */
+c2_status c2_model_init(const c2_model_config* cfg, void* d_state, size_t state_bytes,
+                        c2_stream_t stream);
+/* First-level keys d_keys[t][n_users] for every user. */
+c2_status c2_model_propose(const c2_model_config* cfg, const void* d_state,
+                           const int32_t* d_csr_ptr, const int32_t* d_csr_items, int32_t n_users,
+                           int32_t* d_keys, void* d_ws, size_t ws_bytes, c2_stream_t stream);
+/* One Adam step on n_pairs pairs d_pairs[n_pairs][2] (user ids); step counts
+ * from 1 for bias correction; d_loss[2] (optional) receives the pair loss and
+ * the balance loss of the batch before the step. */
+c2_status c2_model_train_step(const c2_model_config* cfg, void* d_state,
+                              const int32_t* d_csr_ptr, const int32_t* d_csr_items,
+                              int32_t n_users, const int32_t* d_pairs, int32_t n_pairs, float lr,
+                              float lambda, int32_t step, float* d_loss, void* d_ws,
+                              size_t ws_bytes, c2_stream_t stream);
+/* Loss and gradients of one batch without a step (for checking): shapes
+ * E [2^rows_log2][dim], W1 [dim][hidden], b1 [hidden], W2 [hidden][t*b], b2 [t*b]. */
+c2_status c2_model_gradients(const c2_model_config* cfg, const void* d_state,
+                             const int32_t* d_csr_ptr, const int32_t* d_csr_items, int32_t n_users,
+                             const int32_t* d_pairs, int32_t n_pairs, float lambda, float* d_loss,
+                             float* d_gE, float* d_gW1, float* d_gb1, float* d_gW2, float* d_gb2,
+                             void* d_ws, size_t ws_bytes, c2_stream_t stream);
+/* The learned path end to end: keys from the model, clustering (oversized
+ * learned clusters split by FastRandomHash), local KNN and merge; then a
+ * quality probe (Eq. 2 on every (n_users / n_probe)-th user against exact
+ * brute force).  If the probed quality is below quality_threshold the graph
+ * is rebuilt with FastRandomHash keys and C2_ERR_QUALITY_FALLBACK (an
+ * informational status) is returned; *h_quality (optional) receives the
+ * probed quality of the learned graph.  nnz = d_csr_ptr[n_users].
+ * Synchronises the stream.  Workspace: c2_workspace_size_learned(). */
+size_t c2_workspace_size_learned(const c2_model_config* cfg, int32_t n_users, int64_t nnz,
+                                 int32_t n_items, int32_t k, int32_t N, int32_t n_probe,
+                                 const c2_options* opt);
+c2_status c2_build_knn_graph_learned(const c2_model_config* cfg, const void* d_state,
+                                     const int32_t* d_csr_ptr, const int32_t* d_csr_items,
+                                     int32_t n_users, int64_t nnz, int32_t n_items, int32_t k,
+                                     int32_t N, uint64_t seed, const c2_options* opt,
+                                     float quality_threshold, int32_t n_probe,
+                                     int32_t* d_nbr_id, int32_t* d_nbr_inter,
+                                     int32_t* d_nbr_union, void* d_ws, size_t ws_bytes,
+                                     c2_stream_t stream, double* h_quality);
+
+/* Device addresses of the FP32 master parameters inside a state buffer. */
+c2_status c2_model_params(const c2_model_config* cfg, const void* d_state, float** E, float** W1,
+                          float** b1, float** W2, float** b2);
 
 /* Instrumentation (no counterpart in the paper; the paper reports wall-clock
  * time only, Section IV-E).  c2_kernel_launches() returns how many CUDA

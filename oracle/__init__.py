@@ -49,8 +49,8 @@ def lib():
         L.oracle_frh_keys.argtypes = [I32P, I32P, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
                                       C.c_uint64, C.c_void_p, I32P]
         L.oracle_frh_cluster.argtypes = [I32P, I32P, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
-                                         C.c_int32, C.c_uint64, C.c_void_p, I32P, I32P, I32P, I32P,
-                                         C.c_void_p]
+                                         C.c_int32, C.c_uint64, C.c_void_p, C.c_void_p, I32P, I32P,
+                                         I32P, I32P, C.c_void_p]
         L.oracle_cluster_knn.argtypes = [I32P, I32P, C.c_int32, I32P, I32P, C.c_int32, C.c_int32,
                                          C.c_uint64, C.c_int32, C.c_int32, C.c_int32, C.c_void_p,
                                          I32P, I32P, I32P, I64P]
@@ -58,7 +58,14 @@ def lib():
                                         I32P, I32P, I32P, I32P]
         L.oracle_build.argtypes = [I32P, I32P, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
                                    C.c_int32, C.c_int32, C.c_uint64, C.c_int32, C.c_int32,
-                                   C.c_int32, C.c_void_p, I32P, I32P, I32P, I64P]
+                                   C.c_int32, C.c_void_p, C.c_void_p, I32P, I32P, I32P, I64P]
+        F32P = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
+        F64P = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
+        L.oracle_model_exact.argtypes = [C.c_int32]
+        L.oracle_model_forward.argtypes = [C.c_int32] * 5 + [C.c_uint64] + [F32P] * 5 + \
+            [I32P, I32P, C.c_int32, C.c_void_p, I32P]
+        L.oracle_model_grads.argtypes = [C.c_int32] * 5 + [C.c_uint64] + [F32P] * 5 + \
+            [I32P, I32P, C.c_int32, I32P, C.c_int32, C.c_double] + [F64P] * 6
         L.oracle_bruteforce_knn.argtypes = [I32P, I32P, C.c_int32, C.c_int32, C.c_void_p,
                                             C.c_int32, I32P, I32P, I32P]
         L.oracle_avg_sim.restype = C.c_double
@@ -103,8 +110,10 @@ def frh_keys(ptr, items, m, t, b, seed, htab=None):
     return keys
 
 
-def frh_cluster(ptr, items, m, t, b, N, seed, htab=None):
-    """Returns dict(cluster_of[t,n], cptr[nc+1], cusers[t*n], n_clusters, cmeta[nc,4])."""
+def frh_cluster(ptr, items, m, t, b, N, seed, htab=None, keys=None):
+    """Returns dict(cluster_of[t,n], cptr[nc+1], cusers[t*n], n_clusters, cmeta[nc,4]).
+
+    keys: optional first-level keys [t][n] (a learned proposer) instead of FRH."""
     ptr, items = _i32(ptr), _i32(items)
     n = ptr.size - 1
     cluster_of = np.zeros((t, n), np.int32)
@@ -113,8 +122,9 @@ def frh_cluster(ptr, items, m, t, b, N, seed, htab=None):
     nc = np.zeros(1, np.int32)
     cmeta = np.zeros((max(t * n, 1), 4), np.int32)
     ht = None if htab is None else _i32(htab)
+    ky = None if keys is None else _i32(keys)
     rc = lib().oracle_frh_cluster(ptr, items if items.size else np.zeros(1, np.int32), n, m, t, b,
-                                  N, seed, _opt(ht), cluster_of, cptr, cusers, nc,
+                                  N, seed, _opt(ht), _opt(ky), cluster_of, cptr, cusers, nc,
                                   cmeta.ctypes.data_as(C.c_void_p))
     if rc:
         raise ValueError(f"oracle_frh_cluster failed with status {rc}")
@@ -150,15 +160,16 @@ def merge_topk(cptr, cusers, n, k, li, lc, lu):
 
 
 def build_graph(ptr, items, m, k, t, b, N, seed, greedy_threshold, greedy_rounds=10,
-                greedy_random=0, htab=None):
+                greedy_random=0, htab=None, keys=None):
     """The whole method.  Returns (nbr_id, nbr_inter, nbr_union, pairs)."""
     ptr, items = _i32(ptr), _i32(items)
     n = ptr.size - 1
     out = [np.zeros((n, k), np.int32) for _ in range(3)]
     pairs = np.zeros(1, np.int64)
     ht = None if htab is None else _i32(htab)
+    ky = None if keys is None else _i32(keys)
     rc = lib().oracle_build(ptr, items, n, m, k, t, b, N, seed, greedy_threshold, greedy_rounds,
-                            greedy_random, _opt(ht), *out, pairs)
+                            greedy_random, _opt(ht), _opt(ky), *out, pairs)
     if rc:
         raise ValueError(f"oracle_build failed with status {rc}")
     return out[0], out[1], out[2], int(pairs[0])
@@ -178,3 +189,41 @@ def avg_sim(nbr_inter, nbr_union) -> float:
     nbr_inter, nbr_union = _i32(nbr_inter), _i32(nbr_union)
     rows, k = nbr_inter.shape
     return float(lib().oracle_avg_sim(nbr_inter, nbr_union, rows, k))
+
+
+# ------------------------------------------------------------------ learned proposer
+def _f32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def model_forward(cfg, params, ptr, items):
+    """cfg = dict(dim, hidden, t, b, rows_log2, seed); params = (E, W1, b1, W2, b2) FP32.
+    Returns (logits [n, t*b] float64, keys [t, n])."""
+    ptr, items = _i32(ptr), _i32(items)
+    n = ptr.size - 1
+    T = cfg["t"] * cfg["b"]
+    z = np.zeros((n, T), np.float64)
+    keys = np.zeros((cfg["t"], n), np.int32)
+    E, W1, b1, W2, b2 = (_f32(x) for x in params)
+    lib().oracle_model_forward(cfg["dim"], cfg["hidden"], cfg["t"], cfg["b"], cfg["rows_log2"],
+                               cfg["seed"], E, W1, b1, W2, b2, ptr, items, n,
+                               z.ctypes.data_as(C.c_void_p), keys)
+    return z, keys
+
+
+def model_exact(on: bool):
+    """Switch the network oracle to plain FP64 (no BF16 rounding) or back."""
+    lib().oracle_model_exact(1 if on else 0)
+
+
+def model_grads(cfg, params, ptr, items, pairs, lam):
+    """FP64 loss [pair, balance] and gradients (gE, gW1, gb1, gW2, gb2)."""
+    ptr, items = _i32(ptr), _i32(items)
+    pairs = _i32(pairs).reshape(-1, 2)
+    E, W1, b1, W2, b2 = (_f32(x) for x in params)
+    loss = np.zeros(2)
+    g = [np.zeros(x.size) for x in (E, W1, b1, W2, b2)]
+    lib().oracle_model_grads(cfg["dim"], cfg["hidden"], cfg["t"], cfg["b"], cfg["rows_log2"],
+                             cfg["seed"], E, W1, b1, W2, b2, ptr, items, ptr.size - 1,
+                             pairs.ravel(), pairs.shape[0], float(lam), loss, *g)
+    return loss, [gi.reshape(x.shape) for gi, x in zip(g, (E, W1, b1, W2, b2))]

@@ -21,6 +21,7 @@
 //   R11 greedy refinement: Philox-seeded random start, synchronous rounds.
 //   R12 merge reuses the carried (c, U) counts.
 #include <algorithm>
+#include <cmath>
 #include <cstdint>
 #include <cstring>
 #include <map>
@@ -123,6 +124,8 @@ struct Cluster {
   std::vector<int32_t> path;   // (key0, eta_1, eta_2, ...) -- R7
   std::vector<int32_t> members;
   bool residual;
+  int32_t eta;                 // hash threshold of the next split: the path's last
+                               // hash key, or -1 for a first-level key given by a proposer
 };
 
 // Recursive split of Section II-D ("Balancing large clusters through
@@ -135,7 +138,7 @@ struct Cluster {
 void split_or_emit(const Csr& P, const std::vector<int32_t>& hfn, int32_t N, Cluster c,
                    std::vector<Cluster>& out) {
   if ((int32_t)c.members.size() <= N || c.residual) { out.push_back(std::move(c)); return; }
-  const int32_t eta = c.path.back();
+  const int32_t eta = c.eta;
   // H\eta(u) for every member; -1 where no item hashes above eta.
   std::vector<int32_t> next_key(c.members.size(), -1);
   std::map<int32_t, std::vector<int32_t>> groups;   // H\eta value -> users, ascending value
@@ -147,13 +150,13 @@ void split_or_emit(const Csr& P, const std::vector<int32_t>& hfn, int32_t N, Clu
     }
     if (next_key[a] >= 0) groups[next_key[a]].push_back(u);
   }
-  Cluster res{c.fn, c.path, {}, true};
+  Cluster res{c.fn, c.path, {}, true, c.eta};
   for (size_t a = 0; a < c.members.size(); ++a)
     if (next_key[a] < 0 || groups[next_key[a]].size() == 1) res.members.push_back(c.members[a]);
   if (!res.members.empty()) out.push_back(std::move(res));
   for (auto& g : groups) {
     if (g.second.size() < 2) continue;
-    Cluster child{c.fn, c.path, g.second, false};
+    Cluster child{c.fn, c.path, g.second, false, g.first};
     child.path.push_back(g.first);
     split_or_emit(P, hfn, N, std::move(child), out);
   }
@@ -161,8 +164,11 @@ void split_or_emit(const Csr& P, const std::vector<int32_t>& hfn, int32_t N, Clu
 
 // Algorithm 1 (clustering with t FastRandomHash functions, Eq. 3) followed by
 // the recursive split, for all t functions.
+// With `keys` ([t][n], from a learned proposer) the first-level key of user u
+// under function i is keys[i][u] instead of H_i(u); such clusters carry no
+// hash threshold, so their first split uses the plain FRH key (eta = -1).
 std::vector<Cluster> frh_clusters(const Csr& P, int32_t m, int32_t t, int32_t b, int32_t N,
-                                  uint64_t seed, const int32_t* htab) {
+                                  uint64_t seed, const int32_t* htab, const int32_t* keys) {
   std::vector<Cluster> out;
   for (int i = 0; i < t; ++i) {
     std::vector<int32_t> hfn(m);
@@ -172,12 +178,15 @@ std::vector<Cluster> frh_clusters(const Csr& P, int32_t m, int32_t t, int32_t b,
     std::vector<std::vector<int32_t>> B(b + 1);
     for (int32_t u = 0; u < P.n; ++u) {
       int32_t key = b;                                        // R3
-      for (int32_t j = 0; j < P.len(u); ++j) key = std::min(key, hfn[P.row(u)[j]]);
+      if (keys) key = keys[(size_t)i * P.n + u];
+      else
+        for (int32_t j = 0; j < P.len(u); ++j) key = std::min(key, hfn[P.row(u)[j]]);
       B[key].push_back(u);
     }
     for (int32_t key = 0; key <= b; ++key) {
       if (B[key].empty()) continue;
-      Cluster c{i, {key}, B[key], key == b};   // the empty-profile sentinel cannot split
+      // the empty-profile sentinel cannot split
+      Cluster c{i, {key}, B[key], key == b, keys ? -1 : key};
       split_or_emit(P, hfn, N, std::move(c), out);
     }
   }
@@ -347,11 +356,14 @@ int oracle_frh_keys(const int32_t* ptr, const int32_t* items, int32_t n, int32_t
 //   cmeta[n_clusters][4] (optional): function, depth, residual flag, last key
 int oracle_frh_cluster(const int32_t* ptr, const int32_t* items, int32_t n, int32_t m, int32_t t,
                        int32_t b, int32_t N, uint64_t seed, const int32_t* htab,
-                       int32_t* cluster_of, int32_t* cptr, int32_t* cusers, int32_t* n_clusters,
-                       int32_t* cmeta) {
+                       const int32_t* keys, int32_t* cluster_of, int32_t* cptr, int32_t* cusers,
+                       int32_t* n_clusters, int32_t* cmeta) {
   if (oracle_validate_csr(ptr, items, n, m)) return 2;
+  if (keys)
+    for (size_t s2 = 0; s2 < (size_t)t * n; ++s2)
+      if (keys[s2] < 0 || keys[s2] >= b) return 1;
   Csr P{ptr, items, n};
-  std::vector<Cluster> cl = frh_clusters(P, m, t, b, N, seed, htab);
+  std::vector<Cluster> cl = frh_clusters(P, m, t, b, N, seed, htab, keys);
   int32_t pos = 0;
   cptr[0] = 0;
   for (size_t c = 0; c < cl.size(); ++c) {
@@ -364,7 +376,7 @@ int oracle_frh_cluster(const int32_t* ptr, const int32_t* items, int32_t n, int3
       cmeta[4 * c + 0] = cl[c].fn;
       cmeta[4 * c + 1] = (int32_t)cl[c].path.size() - 1;
       cmeta[4 * c + 2] = cl[c].residual ? 1 : 0;
-      cmeta[4 * c + 3] = cl[c].path.back();
+      cmeta[4 * c + 3] = cl[c].eta;
     }
   }
   *n_clusters = (int32_t)cl.size();
@@ -426,11 +438,12 @@ int oracle_merge_topk(const int32_t* cptr, const int32_t* cusers, int32_t n_clus
 int oracle_build(const int32_t* ptr, const int32_t* items, int32_t n, int32_t m, int32_t k,
                  int32_t t, int32_t b, int32_t N, uint64_t seed, int32_t greedy_threshold,
                  int32_t greedy_rounds, int32_t greedy_random, const int32_t* htab,
-                 int32_t* nbr_id, int32_t* nbr_inter, int32_t* nbr_union, int64_t* pairs_out) {
+                 const int32_t* keys, int32_t* nbr_id, int32_t* nbr_inter, int32_t* nbr_union,
+                 int64_t* pairs_out) {
   std::vector<int32_t> cluster_of((size_t)t * n), cptr((size_t)t * n + 1), cusers((size_t)t * n);
   int32_t nc = 0;
-  int rc = oracle_frh_cluster(ptr, items, n, m, t, b, N, seed, htab, cluster_of.data(), cptr.data(),
-                              cusers.data(), &nc, nullptr);
+  int rc = oracle_frh_cluster(ptr, items, n, m, t, b, N, seed, htab, keys, cluster_of.data(),
+                              cptr.data(), cusers.data(), &nc, nullptr);
   if (rc) return rc;
   std::vector<int32_t> li((size_t)t * n * k), lc((size_t)t * n * k), lu((size_t)t * n * k);
   oracle_cluster_knn(ptr, items, n, cptr.data(), cusers.data(), nc, k, seed, greedy_threshold,
@@ -472,6 +485,208 @@ double oracle_avg_sim(const int32_t* nbr_inter, const int32_t* nbr_union, int32_
       if (nbr_union[e] > 0) s += (double)nbr_inter[e] / (double)nbr_union[e];
     }
   return s / ((double)k * (double)rows);
+}
+
+// ======================================================================
+// Learned proposer (no counterpart in the paper): the network of the
+// library's proposer written out in FP64, with the operands rounded to BF16
+// where the library stores them in BF16 (table, weights, bag sums, hidden
+// activations).  Parameters are given as FP32 masters.
+// ======================================================================
+}  // extern "C"
+
+namespace {
+
+// Round-to-nearest-even of an FP32 value to BF16 (the upper 16 bits).
+double to_bf16(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  u = (u + 0x7FFFu + ((u >> 16) & 1u)) & 0xFFFF0000u;
+  float r;
+  std::memcpy(&r, &u, 4);
+  return (double)r;
+}
+
+struct Net {
+  int D, H, t, b, T, rows;
+  uint64_t seed;
+  std::vector<double> E, W1, b1, W2, b2;   // E, W1, W2 rounded to BF16
+};
+
+bool g_exact = false;   // true: no BF16 rounding anywhere (finite-difference checks)
+
+double rnd(float f) { return g_exact ? (double)f : to_bf16(f); }
+
+Net make_net(int D, int H, int t, int b, int rows_log2, uint64_t seed, const float* E,
+             const float* W1, const float* b1, const float* W2, const float* b2) {
+  Net n{D, H, t, b, t * b, 1 << rows_log2, seed, {}, {}, {}, {}, {}};
+  n.E.resize((size_t)n.rows * D);
+  for (size_t i = 0; i < n.E.size(); ++i) n.E[i] = rnd(E[i]);
+  n.W1.resize((size_t)D * H);
+  for (size_t i = 0; i < n.W1.size(); ++i) n.W1[i] = rnd(W1[i]);
+  n.b1.assign(b1, b1 + H);
+  n.W2.resize((size_t)H * n.T);
+  for (size_t i = 0; i < n.W2.size(); ++i) n.W2[i] = rnd(W2[i]);
+  n.b2.assign(b2, b2 + n.T);
+  return n;
+}
+
+size_t emb_row(const Net& n, int32_t x) {
+  return (size_t)(splitmix64_mix(n.seed ^ (uint64_t)(uint32_t)x) & (uint64_t)(n.rows - 1));
+}
+
+struct Fwd {
+  std::vector<double> e, e16, hpre, h16, z;
+};
+
+// e = bag of rows; hpre = W1^T e16 + b1; h16 = bf16(ReLU(hpre)); z = W2^T h16 + b2
+Fwd forward(const Net& n, const Csr& P, int32_t u) {
+  Fwd f;
+  f.e.assign(n.D, 0.0);
+  for (int32_t j = 0; j < P.len(u); ++j) {
+    const size_t r = emb_row(n, P.row(u)[j]);
+    for (int d = 0; d < n.D; ++d) f.e[d] += n.E[r * n.D + d];
+  }
+  f.e16.resize(n.D);
+  for (int d = 0; d < n.D; ++d) f.e16[d] = g_exact ? f.e[d] : to_bf16((float)f.e[d]);
+  f.hpre.assign(n.H, 0.0);
+  f.h16.assign(n.H, 0.0);
+  for (int h = 0; h < n.H; ++h) {
+    double s = n.b1[h];
+    for (int d = 0; d < n.D; ++d) s += f.e16[d] * n.W1[(size_t)d * n.H + h];
+    f.hpre[h] = s;
+    f.h16[h] = g_exact ? std::max(s, 0.0) : to_bf16((float)std::max(s, 0.0));
+  }
+  f.z.assign(n.T, 0.0);
+  for (int c = 0; c < n.T; ++c) {
+    double s = n.b2[c];
+    for (int h = 0; h < n.H; ++h) s += f.h16[h] * n.W2[(size_t)h * n.T + c];
+    f.z[c] = s;
+  }
+  return f;
+}
+
+}  // namespace
+
+extern "C" {
+
+// 1: compute the network in plain FP64 without BF16 rounding (for finite
+// differences); 0 (default): round where the library stores BF16.
+void oracle_model_exact(int32_t on) { g_exact = on != 0; }
+
+// Logits z[n_users][t*b] of every user and keys[t][n_users] = argmax per head
+// (ties to the lower bucket).
+int oracle_model_forward(int32_t D, int32_t H, int32_t t, int32_t b, int32_t rows_log2,
+                         uint64_t seed, const float* E, const float* W1, const float* b1,
+                         const float* W2, const float* b2, const int32_t* ptr,
+                         const int32_t* items, int32_t n, double* z, int32_t* keys) {
+  Net net = make_net(D, H, t, b, rows_log2, seed, E, W1, b1, W2, b2);
+  Csr P{ptr, items, n};
+  for (int32_t u = 0; u < n; ++u) {
+    Fwd f = forward(net, P, u);
+    if (z) std::copy(f.z.begin(), f.z.end(), z + (size_t)u * net.T);
+    for (int j = 0; j < t; ++j) {
+      int best = 0;
+      for (int c = 1; c < b; ++c)
+        if (f.z[(size_t)j * b + c] > f.z[(size_t)j * b + best]) best = c;
+      keys[(size_t)j * n + u] = best;
+    }
+  }
+  return 0;
+}
+
+// Loss of a batch of pairs and its gradients, in FP64 (the library's training
+// objective): rows 0..P-1 are the pairs' first users, P..2P-1 the second;
+//   L = sum_{i,j} -log(S_ij + 1e-9) / (P t) + lambda sum_j sum_c m_jc log(b m_jc) / t,
+//   S_ij = sum_c p_{u_i,jc} p_{v_i,jc},  m_jc = mean over the 2P rows of p_jc.
+int oracle_model_grads(int32_t D, int32_t H, int32_t t, int32_t b, int32_t rows_log2,
+                       uint64_t seed, const float* E, const float* W1, const float* b1,
+                       const float* W2, const float* b2, const int32_t* ptr,
+                       const int32_t* items, int32_t n, const int32_t* pairs, int32_t Pn,
+                       double lambda, double* loss, double* gE, double* gW1, double* gb1,
+                       double* gW2, double* gb2) {
+  Net net = make_net(D, H, t, b, rows_log2, seed, E, W1, b1, W2, b2);
+  Csr P{ptr, items, n};
+  const int R = 2 * Pn, T = net.T;
+  std::vector<Fwd> f(R);
+  std::vector<double> p((size_t)R * T);
+  for (int r = 0; r < R; ++r) {
+    const int32_t u = r < Pn ? pairs[2 * r] : pairs[2 * (r - Pn) + 1];
+    f[r] = forward(net, P, u);
+    for (int j = 0; j < t; ++j) {
+      double mx = -1e300, sum = 0.0;
+      for (int c = 0; c < b; ++c) mx = std::max(mx, f[r].z[(size_t)j * b + c]);
+      for (int c = 0; c < b; ++c) sum += std::exp(f[r].z[(size_t)j * b + c] - mx);
+      for (int c = 0; c < b; ++c)
+        p[(size_t)r * T + (size_t)j * b + c] = std::exp(f[r].z[(size_t)j * b + c] - mx) / sum;
+    }
+  }
+  std::vector<double> m(T, 0.0);
+  for (int r = 0; r < R; ++r)
+    for (int c = 0; c < T; ++c) m[c] += p[(size_t)r * T + c] / R;
+  // dL/dp
+  std::vector<double> g((size_t)R * T, 0.0);
+  double lp = 0.0, lb = 0.0;
+  const double scale = 1.0 / ((double)Pn * t), eps = 1e-9;
+  for (int i = 0; i < Pn; ++i)
+    for (int j = 0; j < t; ++j) {
+      const double* pu = &p[(size_t)i * T + (size_t)j * b];
+      const double* pv = &p[(size_t)(i + Pn) * T + (size_t)j * b];
+      double S = 0.0;
+      for (int c = 0; c < b; ++c) S += pu[c] * pv[c];
+      lp += -std::log(S + eps) * scale;
+      for (int c = 0; c < b; ++c) {
+        g[(size_t)i * T + (size_t)j * b + c] += -pv[c] / (S + eps) * scale;
+        g[(size_t)(i + Pn) * T + (size_t)j * b + c] += -pu[c] / (S + eps) * scale;
+      }
+    }
+  for (int c = 0; c < T; ++c) {
+    if (m[c] > 0) lb += lambda * m[c] * std::log((double)b * m[c]) / t;
+    const double gb = lambda * (std::log(std::max((double)b * m[c], 1e-300)) + 1.0) / ((double)R * t);
+    for (int r = 0; r < R; ++r) g[(size_t)r * T + c] += gb;
+  }
+  loss[0] = lp;
+  loss[1] = lb;
+  // softmax backward, then the layers
+  std::fill(gE, gE + (size_t)net.rows * D, 0.0);
+  std::fill(gW1, gW1 + (size_t)D * H, 0.0);
+  std::fill(gb1, gb1 + H, 0.0);
+  std::fill(gW2, gW2 + (size_t)H * T, 0.0);
+  std::fill(gb2, gb2 + T, 0.0);
+  for (int r = 0; r < R; ++r) {
+    std::vector<double> dz(T);
+    for (int j = 0; j < t; ++j) {
+      double s = 0.0;
+      for (int c = 0; c < b; ++c) s += p[(size_t)r * T + (size_t)j * b + c] * g[(size_t)r * T + (size_t)j * b + c];
+      for (int c = 0; c < b; ++c) {
+        const size_t q = (size_t)j * b + c;
+        dz[q] = p[(size_t)r * T + q] * (g[(size_t)r * T + q] - s);
+      }
+    }
+    std::vector<double> dh(H, 0.0);
+    for (int c = 0; c < T; ++c) {
+      gb2[c] += dz[c];
+      for (int h = 0; h < H; ++h) {
+        gW2[(size_t)h * T + c] += f[r].h16[h] * dz[c];
+        dh[h] += dz[c] * net.W2[(size_t)h * T + c];
+      }
+    }
+    std::vector<double> de(D, 0.0);
+    for (int h = 0; h < H; ++h) {
+      if (f[r].hpre[h] <= 0.0) continue;
+      gb1[h] += dh[h];
+      for (int d = 0; d < D; ++d) {
+        gW1[(size_t)d * H + h] += f[r].e16[d] * dh[h];
+        de[d] += dh[h] * net.W1[(size_t)d * H + h];
+      }
+    }
+    const int32_t u = r < Pn ? pairs[2 * r] : pairs[2 * (r - Pn) + 1];
+    for (int32_t j = 0; j < P.len(u); ++j) {
+      const size_t row = emb_row(net, P.row(u)[j]);
+      for (int d = 0; d < D; ++d) gE[row * D + d] += de[d];
+    }
+  }
+  return 0;
 }
 
 }  // extern "C"

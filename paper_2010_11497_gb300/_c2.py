@@ -35,7 +35,12 @@ class Options(C.Structure):
     _fields_ = [("greedy_threshold", C.c_int32), ("greedy_rounds", C.c_int32),
                 ("greedy_random", C.c_int32), ("strategy", C.c_int32),
                 ("d_hash_table", C.c_void_p), ("gram_budget_bytes", C.c_int64),
-                ("reserved", C.c_int32 * 8)]
+                ("d_keys", C.c_void_p), ("reserved", C.c_int32 * 6)]
+
+
+class ModelConfig(C.Structure):
+    _fields_ = [("t", C.c_int32), ("b", C.c_int32), ("dim", C.c_int32), ("hidden", C.c_int32),
+                ("rows_log2", C.c_int32), ("reserved0", C.c_int32), ("seed", C.c_uint64)]
 
 
 class Stats(C.Structure):
@@ -71,6 +76,22 @@ _SIGS = {
     "c2_get_stats": (C.c_int, [P, P, C.POINTER(Stats)]),
     "c2_reset_status": (C.c_int, [P, P]),
     "c2_merge_topk_noalloc": (C.c_int, [P, I32, I32, I32, P, P, P, P, P, P, P]),
+    "c2_model_state_bytes": (SZ, [C.POINTER(ModelConfig)]),
+    "c2_workspace_size_learned": (SZ, [C.POINTER(ModelConfig), I32, I64, I32, I32, I32, I32,
+                                       C.POINTER(Options)]),
+    "c2_build_knn_graph_learned": (C.c_int, [C.POINTER(ModelConfig), P, P, P, I32, I64, I32, I32,
+                                             I32, U64, C.POINTER(Options), C.c_float, I32, P, P,
+                                             P, P, SZ, P, C.POINTER(C.c_double)]),
+    "c2_model_workspace_size": (SZ, [C.POINTER(ModelConfig), I32, I32]),
+    "c2_model_init": (C.c_int, [C.POINTER(ModelConfig), P, SZ, P]),
+    "c2_model_propose": (C.c_int, [C.POINTER(ModelConfig), P, P, P, I32, P, P, SZ, P]),
+    "c2_model_train_step": (C.c_int, [C.POINTER(ModelConfig), P, P, P, I32, P, I32, C.c_float,
+                                      C.c_float, I32, P, P, SZ, P]),
+    "c2_model_gradients": (C.c_int, [C.POINTER(ModelConfig), P, P, P, I32, P, I32, C.c_float, P,
+                                     P, P, P, P, P, P, SZ, P]),
+    "c2_model_params": (C.c_int, [C.POINTER(ModelConfig), P, C.POINTER(C.c_void_p),
+                                  C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                                  C.POINTER(C.c_void_p), C.POINTER(C.c_void_p)]),
     "c2_merge_topk_noalloc_max_slots": (C.c_int64, []),
     "c2_kernel_launches": (C.c_int64, []),
     "c2_autotune_report": (C.c_size_t, [C.c_char_p, C.c_size_t]),
@@ -102,7 +123,8 @@ def lib():
 
 
 def options(greedy_threshold=0, greedy_rounds=-1, greedy_random=0, strategy=STRATEGY_AUTO,
-            hash_table: torch.Tensor | None = None, gram_budget_bytes=0) -> Options:
+            hash_table: torch.Tensor | None = None, gram_budget_bytes=0,
+            keys: torch.Tensor | None = None) -> Options:
     o = Options()
     lib().c2_default_options(C.byref(o))
     o.greedy_threshold = greedy_threshold
@@ -111,7 +133,8 @@ def options(greedy_threshold=0, greedy_rounds=-1, greedy_random=0, strategy=STRA
     o.strategy = strategy
     o.d_hash_table = None if hash_table is None else hash_table.data_ptr()
     o.gram_budget_bytes = gram_budget_bytes
-    o._keep = hash_table      # keep the table alive with the options
+    o.d_keys = None if keys is None else keys.data_ptr()
+    o._keep = (hash_table, keys)      # keep the tensors alive with the options
     return o
 
 
@@ -331,3 +354,138 @@ def c2_profile_report() -> dict:
     buf = C.create_string_buffer(int(need) + 4096)
     lib().c2_profile_report(buf, len(buf))
     return json.loads(buf.value.decode() or "{}")
+
+
+# ------------------------------------------------------------------ learned proposer
+class Model:
+    """Device state of the learned cluster proposer (include/c2.h, c2_model_*)."""
+
+    def __init__(self, t, b, dim=64, hidden=256, rows_log2=18, seed=2010, device="cuda"):
+        self.cfg = ModelConfig(t, b, dim, hidden, rows_log2, 0, seed)
+        nbytes = lib().c2_model_state_bytes(C.byref(self.cfg))
+        if nbytes == 0:
+            raise C2Error(3, "c2_model_state_bytes")
+        self.state = torch.zeros(int(nbytes), dtype=torch.uint8, device=device)
+        self._train_ws = None
+        self._prop_ws = None
+        self.step = 0
+
+    def init(self, stream=None):
+        _check(lib().c2_model_init(C.byref(self.cfg), _ptr(self.state), self.state.numel(),
+                                   _stream(stream)), "c2_model_init")
+        self.step = 0
+        return self
+
+    def config(self) -> dict:
+        c = self.cfg
+        return dict(t=c.t, b=c.b, dim=c.dim, hidden=c.hidden, rows_log2=c.rows_log2, seed=c.seed)
+
+    def params(self):
+        """FP32 master tensors (E, W1, b1, W2, b2) as views into the state buffer."""
+        ptrs = [C.c_void_p() for _ in range(5)]
+        _check(lib().c2_model_params(C.byref(self.cfg), _ptr(self.state), *[C.byref(p) for p in ptrs]),
+               "c2_model_params")
+        c = self.cfg
+        T = c.t * c.b
+        shapes = [(1 << c.rows_log2, c.dim), (c.dim, c.hidden), (c.hidden,), (c.hidden, T), (T,)]
+        base = self.state.data_ptr()
+        f = self.state.view(torch.uint8)
+        out = []
+        for p, shp in zip(ptrs, shapes):
+            off = p.value - base
+            n = int(np.prod(shp))
+            out.append(f[off:off + 4 * n].view(torch.float32).view(*shp))
+        return out
+
+    def propose(self, ptr, items, stream=None, chunk=8192):
+        n = ptr.numel() - 1
+        keys = torch.empty((self.cfg.t, max(n, 1)), dtype=torch.int32, device=ptr.device)
+        if self._prop_ws is None:
+            self._prop_ws = workspace(lib().c2_model_workspace_size(C.byref(self.cfg), chunk, 0),
+                                      ptr.device)
+        _check(lib().c2_model_propose(C.byref(self.cfg), _ptr(self.state), _ptr(ptr), _ptr(items),
+                                      n, _ptr(keys), _ptr(self._prop_ws), self._prop_ws.numel(),
+                                      _stream(stream)), "c2_model_propose")
+        return keys[:, :n]
+
+    def _ws(self, n_pairs, device):
+        need = int(lib().c2_model_workspace_size(C.byref(self.cfg), n_pairs, 1))
+        if self._train_ws is None or self._train_ws.numel() < need:
+            self._train_ws = workspace(need, device)
+        return self._train_ws
+
+    def train_step(self, ptr, items, pairs, lr=1e-3, lam=0.1, stream=None):
+        """One Adam step on pairs [P, 2] (int32, device).  Returns the device loss [2]."""
+        P = pairs.shape[0]
+        ws = self._ws(P, ptr.device)
+        loss = torch.zeros(2, dtype=torch.float32, device=ptr.device)
+        self.step += 1
+        _check(lib().c2_model_train_step(C.byref(self.cfg), _ptr(self.state), _ptr(ptr), _ptr(items),
+                                         ptr.numel() - 1, _ptr(pairs), P, lr, lam, self.step,
+                                         _ptr(loss), _ptr(ws), ws.numel(), _stream(stream)),
+               "c2_model_train_step")
+        return loss
+
+    def gradients(self, ptr, items, pairs, lam=0.1, stream=None):
+        P = pairs.shape[0]
+        ws = self._ws(P, ptr.device)
+        E, W1, b1, W2, b2 = self.params()
+        grads = [torch.empty_like(x) for x in (E, W1, b1, W2, b2)]
+        loss = torch.zeros(2, dtype=torch.float32, device=ptr.device)
+        _check(lib().c2_model_gradients(C.byref(self.cfg), _ptr(self.state), _ptr(ptr), _ptr(items),
+                                        ptr.numel() - 1, _ptr(pairs), P, lam, _ptr(loss),
+                                        *[_ptr(g) for g in grads], _ptr(ws), ws.numel(),
+                                        _stream(stream)), "c2_model_gradients")
+        return loss, grads
+
+    def build_knn_graph(self, ptr, items, n_items, k, N, seed, opts=None, quality_threshold=0.95,
+                        n_probe=2048, ws=None, stream=None):
+        """Learned-proposer build with the FastRandomHash fallback.
+
+        Returns ((nbr_id, nbr_inter, nbr_union), probed quality, fell_back)."""
+        n = ptr.numel() - 1
+        nnz = items.numel()
+        o = opts if opts is not None else options()
+        need = int(lib().c2_workspace_size_learned(C.byref(self.cfg), n, nnz, n_items, k, N,
+                                                   n_probe, C.byref(o)))
+        if need == 0:
+            raise C2Error(1, "c2_workspace_size_learned")
+        if ws is None or ws.numel() < need:
+            ws = workspace(need, ptr.device)
+        out = [torch.empty((n, k), dtype=torch.int32, device=ptr.device) for _ in range(3)]
+        q = C.c_double(0.0)
+        rc = lib().c2_build_knn_graph_learned(C.byref(self.cfg), _ptr(self.state), _ptr(ptr),
+                                              _ptr(items), n, nnz, n_items, k, N, seed, C.byref(o),
+                                              quality_threshold, n_probe, *[_ptr(x) for x in out],
+                                              _ptr(ws), ws.numel(), _stream(stream), C.byref(q))
+        if rc not in (0, 7):
+            raise C2Error(rc, "c2_build_knn_graph_learned")
+        return tuple(out), q.value, rc == 7
+
+    def save(self, path):
+        """Parameters and optimiser state, with a header (format, config, step)."""
+        import json
+        torch.cuda.synchronize()
+        hdr = json.dumps(dict(format="c2-model-1", config=self.config(), step=self.step,
+                              nbytes=self.state.numel())).encode()
+        with open(path, "wb") as f:
+            f.write(len(hdr).to_bytes(4, "little"))
+            f.write(hdr)
+            f.write(self.state.cpu().numpy().tobytes())
+
+    @classmethod
+    def load(cls, path, device="cuda"):
+        import json
+        with open(path, "rb") as f:
+            n = int.from_bytes(f.read(4), "little")
+            hdr = json.loads(f.read(n))
+            data = np.frombuffer(f.read(), dtype=np.uint8)
+        if hdr.get("format") != "c2-model-1":
+            raise ValueError("not a c2 model file")
+        c = hdr["config"]
+        m = cls(c["t"], c["b"], c["dim"], c["hidden"], c["rows_log2"], c["seed"], device)
+        if data.size != m.state.numel():
+            raise ValueError("model file does not match its config")
+        m.state.copy_(torch.from_numpy(data.copy()))
+        m.step = hdr["step"]
+        return m

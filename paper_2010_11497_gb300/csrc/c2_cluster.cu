@@ -119,6 +119,23 @@ __global__ void k_minhash(const int32_t* __restrict__ ptr, const int32_t* __rest
   }
 }
 
+// First-level keys given by the caller (a learned proposer): copy, check the
+// range, count the level-0 histogram.
+__global__ void k_keys_given(const int32_t* __restrict__ given, int64_t S, int32_t n, int32_t b,
+                             int32_t* __restrict__ key, int32_t* __restrict__ hist,
+                             DevHeader* hdr) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= S || dev_failed(hdr)) return;
+  const int32_t kv = given[s];
+  if (kv < 0 || kv >= b) {
+    dev_fail(hdr, C2_ERR_INVALID_ARG);
+    key[s] = 0;
+    return;
+  }
+  key[s] = kv;
+  atomicAdd(&hist[(s / n) * (b + 1) + kv], 1);
+}
+
 // ------------------------------------------------------------------ A3: level 0
 __global__ void k_flag_nonzero(const int32_t* __restrict__ hist, int32_t* __restrict__ flag,
                                int64_t nbins) {
@@ -128,16 +145,18 @@ __global__ void k_flag_nonzero(const int32_t* __restrict__ hist, int32_t* __rest
 
 // One cluster per non-empty (function, key) bin, in (function, key) order.
 __global__ void k_level0_meta(const int32_t* __restrict__ hist, const int32_t* __restrict__ binlab,
-                              int64_t nbins, int32_t b, int32_t* __restrict__ lsize,
-                              int32_t* __restrict__ leta, int32_t* __restrict__ lflag,
-                              DevHeader* hdr) {
+                              int64_t nbins, int32_t b, int32_t given_keys,
+                              int32_t* __restrict__ lsize, int32_t* __restrict__ leta,
+                              int32_t* __restrict__ lflag, DevHeader* hdr) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j == 0) hdr->n_labels = binlab[nbins];
   if (j >= nbins || hist[j] == 0) return;
   const int32_t l = binlab[j];
   const int32_t i = (int32_t)(j / (b + 1)), kv = (int32_t)(j % (b + 1));
   lsize[l] = hist[j];
-  leta[l] = kv;
+  // a learned first-level key carries no hash threshold: its split keys are
+  // the plain FastRandomHash keys (every hash value counts)
+  leta[l] = given_keys ? -1 : kv;
   // the empty-profile bucket b cannot be split: terminal, listed as a residual
   lflag[l] = lf_pack(kv == b, kv == b, i, 0);
 }
@@ -195,11 +214,11 @@ __global__ void k_split_keys(const int32_t* __restrict__ ptr, const int32_t* __r
     const int64_t s = s0 + src;
     const int32_t ls = __shfl_sync(0xffffffffu, l, src);
     const int64_t i = s / n, u = s % n;
-    const uint32_t eta = (uint32_t)leta[ls];
+    const int32_t eta = leta[ls];
     uint32_t best = (uint32_t)b;
     for (int32_t j = ptr[u] + lane; j < ptr[u + 1]; j += 32) {
       const uint32_t hv = htab[(int64_t)items[j] * tp + i];
-      if (hv > eta) best = min(best, hv);
+      if ((int32_t)hv > eta) best = min(best, hv);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(0xffffffffu, best, o));
@@ -400,14 +419,16 @@ c2_status run_frh_cluster(const int32_t* ptr, const int32_t* items, const Sizes&
     C2_LAUNCH(k_build_htab, div_up((int64_t)s.m * s.tp, T), T, 0, st, w.htab, s.m, s.t, s.tp, s.b, seed,
                                                                  opt.d_hash_table, w.hdr);
   C2_CUDA_TRY(cudaMemsetAsync(w.hist, 0, (nbins + 1) * sizeof(int32_t), st));
-  if (s.n > 0)
-    C2_LAUNCH(k_minhash, div_up((int64_t)s.n * 32, T), T, 0, st, ptr, items, w.htab, s.n, s.t, s.tp, s.b,
-                                                           w.key, w.hist, w.hdr);
+  if (s.n > 0 && opt.d_keys)
+    C2_LAUNCH(k_keys_given, div_up(S, T), T, 0, st, opt.d_keys, S, s.n, s.b, w.key, w.hist, w.hdr);
+  else if (s.n > 0)
+    C2_LAUNCH(k_minhash, div_up((int64_t)s.n * 32, T), T, 0, st, ptr, items, w.htab, s.n, s.t,
+              s.tp, s.b, w.key, w.hist, w.hdr);
   C2_LAUNCH(k_flag_nonzero, div_up(nbins, T), T, 0, st, w.hist, w.binlab, nbins);
   C2_CUDA_TRY(scan_exclusive(w.binlab, w.binlab, nbins, w.scan_tmp, st));
   C2_CUDA_TRY(cudaMemsetAsync(w.lsize, 0, (S + 1) * sizeof(int32_t), st));
-  C2_LAUNCH(k_level0_meta, div_up(nbins, T), T, 0, st, w.hist, w.binlab, nbins, s.b, w.lsize, w.leta,
-                                                 w.lflag, w.hdr);
+  C2_LAUNCH(k_level0_meta, div_up(nbins, T), T, 0, st, w.hist, w.binlab, nbins, s.b,
+            opt.d_keys ? 1 : 0, w.lsize, w.leta, w.lflag, w.hdr);
   if (S > 0) C2_LAUNCH(k_level0_labels, div_up(S, T), T, 0, st, w.key, w.binlab, s.n, S, s.b, w.lab, w.hdr);
   C2_CUDA_TRY(cudaGetLastError());
 

@@ -1,6 +1,7 @@
 // Internal declarations of the sm_103a Cluster-and-Conquer library.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 

@@ -185,16 +185,19 @@ def _first_distinct(users, ranks, m, L):
     return ku[sel], kr[sel], np.minimum(n_local, L)
 
 
-def _rejection_rows(rng, L, cdf):
-    """Per user: draw ranks with replacement, keep first occurrences, stop at L distinct.
+def _rejection_rows(rng, L, cdf, to_id=None):
+    """Per user: draw items with replacement, keep first occurrences, stop at L distinct.
 
-    All users' streams are drawn at once (with a coupon-collector estimate of the
-    draws needed); users still short get their stream extended and re-scanned.
+    A draw picks a Zipf rank; to_id(users, ranks) maps it to an item id (the
+    identity when None).  All users' streams are drawn at once (with a
+    coupon-collector estimate of the draws needed); users still short get
+    their stream extended and re-scanned.
     """
     n, m = L.shape[0], cdf.size
+    to_id = to_id or (lambda u, r: r)
     D = np.where(L > 0, (_expected_draws(cdf, L) * 1.15).astype(np.int64) + 16, 0)
     users = np.repeat(np.arange(n, dtype=np.int64), D)
-    ranks = np.minimum(np.searchsorted(cdf, rng.random(users.size), side="right"), m - 1)
+    ranks = to_id(users, np.minimum(np.searchsorted(cdf, rng.random(users.size), side="right"), m - 1))
     ku, kr, got = _first_distinct(users, ranks, m, L)
     short = np.nonzero(got < L)[0]
     if short.size == 0:
@@ -206,7 +209,7 @@ def _rejection_rows(rng, L, cdf):
     extra = np.maximum(D[short], 64)
     while True:
         nu = np.repeat(short, extra)
-        nr = np.minimum(np.searchsorted(cdf, rng.random(nu.size), side="right"), m - 1)
+        nr = to_id(nu, np.minimum(np.searchsorted(cdf, rng.random(nu.size), side="right"), m - 1))
         su = np.concatenate([su, nu])
         sr = np.concatenate([sr, nr])
         order = np.argsort(su, kind="stable")      # user-major, draw order kept
@@ -242,8 +245,13 @@ def _es_rows(rng, users, L, weights):
     return np.concatenate(out_u), np.concatenate(out_r)
 
 
-def generate(w: Workload, seed: int | None = None):
-    """Return (ptr int32[n+1], items int32[nnz], manifest dict) for workload w."""
+def generate(w: Workload, seed: int | None = None, mu: float = 0.0, n_comm: int = 64):
+    """Return (ptr int32[n+1], items int32[nnz], manifest dict) for workload w.
+
+    mu > 0 adds neighbourhood structure: every user belongs to one of n_comm
+    communities (uniformly), and each draw takes, with probability mu, its
+    item from the community's own rank order (a fixed permutation per
+    community, part of the world) instead of the global one."""
     seed = w.seed if seed is None else seed
     rng = np.random.default_rng([seed, 0xC2])
     L, fit = draw_lengths(w, rng)
@@ -251,14 +259,25 @@ def generate(w: Workload, seed: int | None = None):
     perm = world_permutation(m)
     cdf = _zipf_cdf(m, w.zipf_s)
     small = L <= m // 8
-    us, rs = _rejection_rows(rng, np.where(small, L, 0), cdf)
+    to_id = None
+    if mu > 0:
+        comm = rng.integers(0, n_comm, w.n_users)
+        cperm = np.stack([np.random.default_rng([WORLD_SEED, m, c + 1]).permutation(m)
+                          for c in range(n_comm)])
+
+        def to_id(users, ranks, _rng=np.random.default_rng([seed, 0xC3])):
+            local = _rng.random(users.size) < mu
+            return np.where(local, cperm[comm[users], ranks], perm[ranks])
+    us, rs = _rejection_rows(rng, np.where(small, L, 0), cdf, to_id)
+    if to_id is None:
+        rs = perm[rs]
     big = np.nonzero(~small)[0]
     if big.size:
         weights = np.arange(1, m + 1, dtype=np.float64) ** (-w.zipf_s)
         bu, br = _es_rows(rng, big, L[big], weights)
         us = np.concatenate([us, bu])
-        rs = np.concatenate([rs, br])
-    items = perm[rs]
+        rs = np.concatenate([rs, perm[br]])
+    items = rs
     order = np.lexsort((items, us))
     us, items = us[order], items[order]
     counts = np.bincount(us, minlength=w.n_users)
@@ -297,10 +316,12 @@ def load(name: str, seed: int | None = None):
 
 
 def random_profiles(n_users: int, n_items: int, mean_len: float, seed: int,
-                    zipf_s: float = 1.0, lmin: int = 1, lmax: int | None = None):
-    """Small random CSR for unit tests (log-normal lengths, Zipf items)."""
+                    zipf_s: float = 1.0, lmin: int = 1, lmax: int | None = None,
+                    mu: float = 0.0, n_comm: int = 64):
+    """Small random CSR for unit tests (log-normal lengths, Zipf items,
+    optional community structure mu)."""
     lmax = n_items if lmax is None else min(lmax, n_items)
     w = Workload("adhoc", n_users, n_items, ("lognormal", float(mean_len), 0.8, lmin, lmax),
                  zipf_s, seed, k=1, t=1, b=2, N=2, greedy_threshold=2)
-    ptr, items, _ = generate(w, seed)
+    ptr, items, _ = generate(w, seed, mu=mu, n_comm=n_comm)
     return ptr, items

@@ -1,0 +1,156 @@
+"""GPU checks of the learned cluster proposer against the CPU oracle.
+
+- clustering and whole builds with caller-given first-level keys: bit-exact;
+- model keys: equal to the oracle's argmax (FP64 logits on the same BF16
+  operands) except where the oracle's two best logits are within 1e-3;
+- gradients (BF16 operands, FP32 sums): relative L2 error against the FP64
+  oracle below 3e-2 per tensor, loss within 1e-3;
+- training lowers the loss and raises the co-assignment of positive pairs;
+- the learned build with its quality probe and FastRandomHash fallback.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2010_11497_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def c2():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2010_11497_gb300 import build
+    build.build()
+    import paper_2010_11497_gb300 as pkg
+    pkg.lib()
+    return pkg
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.int32)).cuda()
+
+
+def same(g, r, what):
+    g = g.cpu().numpy() if hasattr(g, "cpu") else np.asarray(g)
+    bad = np.argwhere(g != np.asarray(r))
+    assert bad.size == 0, f"{what}: {len(bad)} mismatches, first {tuple(bad[0])}"
+
+
+def test_cluster_and_build_with_given_keys(c2):
+    ptr, items = synth.random_profiles(3000, 500, 20, 41, zipf_s=1.1)
+    m, t, b, N, k, seed, thr = 500, 4, 16, 300, 10, 3, 200
+    keys = np.random.default_rng(1).integers(0, b, (t, 3000)).astype(np.int32)
+    keys[:, :900] = 5                  # one oversized learned cluster per function
+    g = c2.c2_frh_cluster(dev(ptr), dev(items), m, t, b, N, seed,
+                          opts=c2.options(keys=dev(keys)))
+    o = oracle.frh_cluster(ptr, items, m, t, b, N, seed, keys=keys)
+    assert g["n_clusters"] == o["n_clusters"]
+    same(g["cptr"], o["cptr"], "cptr")
+    same(g["cusers"], o["cusers"], "cusers")
+    same(g["cmeta"], o["cmeta"], "cmeta")
+    oid, oin, oun, pairs = oracle.build_graph(ptr, items, m, k, t, b, N, seed, thr, 3, keys=keys)
+    opts = c2.options(greedy_threshold=thr, greedy_rounds=3, keys=dev(keys))
+    ws = c2.workspace(c2.workspace_size(3000, items.size, m, k, t, b, N, opts), "cuda")
+    gid, gin, gun = c2.c2_build_knn_graph(dev(ptr), dev(items), m, k, t, b, N, seed, opts=opts,
+                                          ws=ws)
+    same(gid, oid, "nbr_id")
+    same(gun, oun, "nbr_union")
+    assert c2.c2_get_stats(ws)["pairs"] == pairs
+
+
+def _model(c2, t=4, b=32, dim=64, hidden=64, rows_log2=10, seed=11):
+    return c2.Model(t, b, dim, hidden, rows_log2, seed).init()
+
+
+def test_model_keys_match_oracle(c2):
+    m = _model(c2)
+    ptr, items = synth.random_profiles(1500, 800, 25, 42)
+    keys = m.propose(dev(ptr), dev(items)).cpu().numpy()
+    params = [x.cpu().numpy() for x in m.params()]
+    z, okeys = oracle.model_forward(m.config(), params, ptr, items)
+    b = m.cfg.b
+    diff = np.argwhere(keys != okeys)
+    for j, u in diff:
+        zz = np.sort(z[u, j * b:(j + 1) * b])
+        assert zz[-1] - zz[-2] < 1e-3 * max(1.0, abs(zz[-1])), (j, u)
+    assert len(diff) <= 0.01 * keys.size
+
+
+def test_model_gradients_match_oracle(c2):
+    m = _model(c2)
+    ptr, items = synth.random_profiles(600, 400, 20, 43)
+    rng = np.random.default_rng(4)
+    pairs = rng.integers(0, 600, (256, 2)).astype(np.int32)
+    lam = 0.1
+    loss, grads = m.gradients(dev(ptr), dev(items), dev(pairs), lam)
+    params = [x.cpu().numpy() for x in m.params()]
+    oloss, ograds = oracle.model_grads(m.config(), params, ptr, items, pairs, lam)
+    loss = loss.cpu().numpy()
+    assert abs(loss[0] - oloss[0]) <= 1e-3 * abs(oloss[0]) + 1e-6
+    assert abs(loss[1] - oloss[1]) <= 1e-3 * abs(oloss[1]) + 1e-5
+    for name, g, og in zip(["E", "W1", "b1", "W2", "b2"], grads, ograds):
+        g = g.cpu().numpy().astype(np.float64)
+        err = np.linalg.norm(g - og) / max(np.linalg.norm(og), 1e-12)
+        assert err < 3e-2, (name, err)
+
+
+def _coassign(keys, pairs):
+    return float((keys[:, pairs[:, 0]] == keys[:, pairs[:, 1]]).mean())
+
+
+def test_training_lowers_loss_and_groups_pairs(c2):
+    ptr, items = synth.random_profiles(4000, 2000, 30, 44, mu=0.8, n_comm=16)
+    n, m_items, k, t, b, N, seed = 4000, 2000, 10, 4, 32, 400, 5
+    dptr, ditems = dev(ptr), dev(items)
+    gid, _, _ = c2.c2_build_knn_graph(dptr, ditems, m_items, k, t, b, N, seed)
+    nid = gid.cpu().numpy()
+    u = np.repeat(np.arange(n), k)
+    v = nid.ravel()
+    pairs = np.stack([u[v >= 0], v[v >= 0]], 1).astype(np.int32)
+    model = _model(c2, t=t, b=b, seed=7)
+    before = _coassign(model.propose(dptr, ditems).cpu().numpy(), pairs)
+    rng = np.random.default_rng(0)
+    losses = []
+    for step in range(150):
+        batch = dev(pairs[rng.integers(0, len(pairs), 2048)])
+        losses.append(model.train_step(dptr, ditems, batch, lr=3e-3, lam=0.1))
+    losses = torch.stack(losses).cpu().numpy()
+    assert losses[-10:, 0].mean() < 0.8 * losses[:10, 0].mean()
+    after = _coassign(model.propose(dptr, ditems).cpu().numpy(), pairs)
+    assert after > before + 0.1, (before, after)
+
+
+def test_learned_build_probe_and_fallback(c2):
+    ptr, items = synth.random_profiles(3000, 1500, 30, 45, mu=0.8, n_comm=16)
+    n, m_items, k, t, b, N, seed = 3000, 1500, 10, 4, 32, 300, 6
+    model = _model(c2, t=t, b=b, seed=8)
+    dptr, ditems = dev(ptr), dev(items)
+    # threshold 0 never falls back: the graph is the keys' graph
+    (gid, gin, gun), q, fell = model.build_knn_graph(dptr, ditems, m_items, k, N, seed,
+                                                     quality_threshold=0.0, n_probe=500)
+    assert not fell and 0.0 < q <= 1.0
+    keys = model.propose(dptr, ditems).cpu().numpy()
+    oid, oin, oun, _ = oracle.build_graph(ptr, items, m_items, k, t, b, N, seed, 5 * k * k, 10,
+                                          keys=keys)
+    same(gid, oid, "learned graph ids")
+    # threshold above any quality falls back to the FastRandomHash graph
+    (fid, fin, fun), q2, fell2 = model.build_knn_graph(dptr, ditems, m_items, k, N, seed,
+                                                       quality_threshold=1.01, n_probe=500)
+    assert fell2 and abs(q2 - q) < 1e-12
+    rid, rin, run = c2.c2_build_knn_graph(dptr, ditems, m_items, k, t, b, N, seed)
+    same(fid, rid.cpu().numpy(), "fallback graph ids")
+
+
+def test_model_save_load_roundtrip(c2, tmp_path):
+    m = _model(c2, seed=9)
+    ptr, items = synth.random_profiles(300, 200, 10, 46)
+    pairs = dev(np.random.default_rng(1).integers(0, 300, (64, 2)))
+    m.train_step(dev(ptr), dev(items), pairs)
+    path = tmp_path / "model.c2m"
+    m.save(str(path))
+    m2 = c2.Model.load(str(path))
+    assert m2.step == m.step and torch.equal(m2.state, m.state)
+    same(m2.propose(dev(ptr), dev(items)), m.propose(dev(ptr), dev(items)).cpu().numpy(), "keys")

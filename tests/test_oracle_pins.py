@@ -441,3 +441,75 @@ def test_empty_profiles_use_sentinel_bucket():
     cl = oracle.frh_cluster(ptr, items, 2, 1, 4, 1, 0, htab=np.array([[2, 3]], np.int32))
     assert np.diff(cl["cptr"]).tolist() == [1, 1, 2]
     assert cl["cusers"].tolist() == [0, 2, 1, 3]
+
+
+# ------------------------------------------------------------------ learned proposer (oracle)
+def test_given_keys_one_cluster_split_equals_frh_groups():
+    # One learned cluster holding everybody, split once (N < n): its sub-clusters
+    # are the FastRandomHash clusters of >= 2 users, the rest is the residual.
+    ptr, items = synth.random_profiles(400, 60, 6, 31, zipf_s=1.3)
+    m, t, b, seed = 60, 2, 16, 7
+    keys = np.zeros((t, 400), np.int32)
+    cl = oracle.frh_cluster(ptr, items, m, t, b, 399, seed, keys=keys)
+    frh = oracle.frh_cluster(ptr, items, m, t, b, 10 ** 6, seed)
+    for i in range(t):
+        sub = cl["cmeta"][:, 0] == i
+        meta = cl["cmeta"][sub]
+        sizes = np.diff(cl["cptr"])[sub]
+        fsub = frh["cmeta"][:, 0] == i
+        fsizes = np.diff(frh["cptr"])[fsub]
+        assert meta[0, 2] == 1 and meta[0, 3] == -1        # residual of the learned cluster
+        assert sizes[0] == (fsizes == 1).sum()
+        assert sorted(sizes[1:].tolist()) == sorted(fsizes[fsizes >= 2].tolist())
+        assert (meta[1:, 3] == frh["cmeta"][fsub][fsizes >= 2, 3]).all()
+
+
+def _tiny_net(seed):
+    rng = np.random.default_rng(seed)
+    cfg = dict(dim=32, hidden=16, t=2, b=8, rows_log2=6, seed=5)
+    T = cfg["t"] * cfg["b"]
+    params = [rng.normal(0, 0.3, (64, 32)).astype(np.float32),
+              rng.normal(0, 0.3, (32, 16)).astype(np.float32),
+              rng.normal(0, 0.1, 16).astype(np.float32),
+              rng.normal(0, 0.3, (16, T)).astype(np.float32),
+              rng.normal(0, 0.1, T).astype(np.float32)]
+    return cfg, params
+
+
+def test_model_gradient_matches_finite_differences():
+    # the oracle's backward pass against central differences of its own loss
+    # (plain FP64, no BF16 rounding)
+    cfg, params = _tiny_net(1)
+    ptr, items = synth.random_profiles(30, 50, 5, 9)
+    pairs = np.array([[0, 1], [2, 3], [4, 9], [7, 7], [11, 20]], np.int32)
+    lam = 0.3
+    oracle.model_exact(True)
+    try:
+        loss, grads = oracle.model_grads(cfg, params, ptr, items, pairs, lam)
+        rng = np.random.default_rng(3)
+        h = 1e-4
+        for pi in range(5):
+            flat = params[pi].ravel()
+            for idx in rng.choice(flat.size, size=min(6, flat.size), replace=False):
+                p_plus = [x.astype(np.float64).copy() for x in params]
+                p_minus = [x.astype(np.float64).copy() for x in params]
+                p_plus[pi].ravel()[idx] += h
+                p_minus[pi].ravel()[idx] -= h
+                # the oracle takes FP32 parameters: use a step FP32 represents well
+                lp, _ = oracle.model_grads(cfg, [x.astype(np.float32) for x in p_plus], ptr, items, pairs, lam)
+                lm, _ = oracle.model_grads(cfg, [x.astype(np.float32) for x in p_minus], ptr, items, pairs, lam)
+                dp = (np.float32(p_plus[pi].ravel()[idx]) - np.float32(p_minus[pi].ravel()[idx]))
+                fd = (lp.sum() - lm.sum()) / float(dp)
+                an = grads[pi].ravel()[idx]
+                assert abs(fd - an) <= 2e-3 * max(1.0, abs(an)) + 1e-5, (pi, idx, fd, an)
+    finally:
+        oracle.model_exact(False)
+
+
+def test_model_keys_are_argmax_of_logits():
+    cfg, params = _tiny_net(2)
+    ptr, items = synth.random_profiles(40, 50, 6, 10)
+    z, keys = oracle.model_forward(cfg, params, ptr, items)
+    b = cfg["b"]
+    for j in range(cfg["t"]):
+        assert (keys[j] == np.argmax(z[:, j * b:(j + 1) * b], axis=1)).all()
