@@ -1,0 +1,141 @@
+"""Train the learned cluster proposer and compare it with FastRandomHash.
+
+Positive pairs are the edges of KNN graphs built by plain Cluster-and-Conquer
+(FastRandomHash clustering) on training datasets drawn with other seeds from
+the same workload shape; the item universe is shared (same world seed), so a
+model trained there applies to the target dataset.  The comparison builds the
+target's graph both ways with the same t, b, N, k and reports build time and
+quality (Eq. 2 against exact brute force).
+
+    python -m paper_2010_11497_gb300.train_proposer --workload learned_ml20m \\
+        --train-seeds 6 7 8 9 --steps 400
+
+Every step runs in libc2 (graph builds, forward/backward kernels, Adam).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+import torch
+
+from . import _c2 as c2
+from . import synth
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.int32)).cuda()
+
+
+def positive_pairs(nbr_id: torch.Tensor) -> torch.Tensor:
+    n, k = nbr_id.shape
+    u = torch.arange(n, device=nbr_id.device, dtype=torch.int32).repeat_interleave(k)
+    v = nbr_id.reshape(-1)
+    keep = v >= 0
+    return torch.stack([u[keep], v[keep]], 1).contiguous()
+
+
+def timed(fn, reps=3):
+    torch.cuda.synchronize()
+    best = None
+    out = None
+    for _ in range(reps):
+        a = time.perf_counter()
+        out = fn()
+        torch.cuda.synchronize()
+        t = time.perf_counter() - a
+        best = t if best is None else min(best, t)
+    return out, best
+
+
+def quality(ptr, items, n_items, k, nbr_inter, nbr_union, judge=None):
+    if judge is None:
+        _, jin, jun = c2.c2_bruteforce_knn(ptr, items, n_items, k)
+        judge = c2.c2_avg_sim(jin, jun)
+    return c2.c2_avg_sim(nbr_inter, nbr_union) / judge, judge
+
+
+def run(workload="learned_ml20m", train_seeds=(6, 7, 8, 9), steps=400, batch=8192, lr=2e-3,
+        lam=0.1, dim=64, hidden=256, rows_log2=18, model_seed=2010, mu=0.0, log=print):
+    w = synth.WORKLOADS[workload]
+    k, t, b, N, thr = w.k, w.t, w.b, w.N, w.greedy_threshold
+    opts = c2.options(greedy_threshold=thr, greedy_rounds=w.greedy_rounds)
+    # training graphs (plain C^2 on other seeds)
+    train = []
+    t0 = time.perf_counter()
+    for s in train_seeds:
+        ptr, items, _ = synth.generate(w, s, mu=mu) if mu else synth.load(workload, s)
+        dptr, ditems = dev(ptr), dev(items)
+        nid, _, _ = c2.c2_build_knn_graph(dptr, ditems, w.n_items, k, t, b, N, s, opts=opts)
+        train.append((dptr, ditems, positive_pairs(nid)))
+    t_graphs = time.perf_counter() - t0
+    model = c2.Model(t, b, dim, hidden, rows_log2, model_seed).init()
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(model_seed)
+    losses = []
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    for step in range(steps):
+        dptr, ditems, pairs = train[step % len(train)]
+        idx = torch.randint(0, pairs.shape[0], (batch,), device="cuda", generator=gen)
+        losses.append(model.train_step(dptr, ditems, pairs[idx].contiguous(), lr=lr, lam=lam))
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t1
+    losses = torch.stack(losses).cpu().numpy()
+    # target dataset
+    ptr, items, _ = synth.generate(w, w.seed, mu=mu) if mu else synth.load(workload, w.seed)
+    dptr, ditems = dev(ptr), dev(items)
+    nnz = items.size
+    ws = c2.workspace(c2.workspace_size(w.n_users, nnz, w.n_items, k, t, b, N, opts), "cuda")
+    (fid, fin, fun), t_frh = timed(lambda: c2.c2_build_knn_graph(
+        dptr, ditems, w.n_items, k, t, b, N, w.seed, opts=opts, ws=ws))
+    frh_stats = c2.c2_get_stats(ws)
+    q_frh, judge = quality(dptr, ditems, w.n_items, k, fin, fun)
+    keys, t_prop = timed(lambda: model.propose(dptr, ditems))
+    lopts = c2.options(greedy_threshold=thr, greedy_rounds=w.greedy_rounds, keys=keys)
+    (lid, lin, lun), t_lbuild = timed(lambda: c2.c2_build_knn_graph(
+        dptr, ditems, w.n_items, k, t, b, N, w.seed, opts=lopts, ws=ws))
+    l_stats = c2.c2_get_stats(ws)
+    q_learned, _ = quality(dptr, ditems, w.n_items, k, lin, lun, judge)
+    co_pairs = positive_pairs(fid)
+    kk = keys.cpu().numpy()
+    cp = co_pairs.cpu().numpy()
+    res = dict(
+        workload=workload, n_users=w.n_users, n_items=w.n_items, nnz=int(nnz), k=k, t=t, b=b, N=N,
+        train_seeds=list(train_seeds), steps=steps, batch=batch, lr=lr, lam=lam,
+        loss_first=losses[:10].mean(0).tolist(), loss_last=losses[-10:].mean(0).tolist(),
+        train_graphs_s=t_graphs, train_s=t_train,
+        frh=dict(build_ms=t_frh * 1e3, quality=q_frh, pairs=frh_stats["pairs"],
+                 n_clusters=frh_stats["n_clusters"], max_cluster=frh_stats["max_cluster"]),
+        learned=dict(propose_ms=t_prop * 1e3, build_ms=t_lbuild * 1e3,
+                     total_ms=(t_prop + t_lbuild) * 1e3, quality=q_learned,
+                     pairs=l_stats["pairs"], n_clusters=l_stats["n_clusters"],
+                     max_cluster=l_stats["max_cluster"],
+                     frh_neighbour_pairs_sharing_a_key=float(
+                         (kk[:, cp[:, 0]] == kk[:, cp[:, 1]]).any(0).mean())),
+        gain_quality=q_learned - q_frh,
+        speedup=t_frh / (t_prop + t_lbuild))
+    log(json.dumps(res))
+    return res, model
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="learned_ml20m")
+    ap.add_argument("--train-seeds", type=int, nargs="+", default=[6, 7, 8, 9])
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--batch", type=int, default=8192)
+    ap.add_argument("--lr", type=float, default=2e-3)
+    ap.add_argument("--lam", type=float, default=0.1)
+    ap.add_argument("--mu", type=float, default=0.0)
+    ap.add_argument("--save", default="")
+    a = ap.parse_args()
+    _, model = run(a.workload, tuple(a.train_seeds), a.steps, a.batch, a.lr, a.lam, mu=a.mu)
+    if a.save:
+        model.save(a.save)
+
+
+if __name__ == "__main__":
+    main()
