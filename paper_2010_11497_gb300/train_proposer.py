@@ -58,7 +58,12 @@ def quality(ptr, items, n_items, k, nbr_inter, nbr_union, judge=None):
 
 
 def run(workload="learned_ml20m", train_seeds=(6, 7, 8, 9), steps=400, batch=8192, lr=2e-3,
-        lam=0.1, dim=64, hidden=256, rows_log2=18, model_seed=2010, mu=0.0, log=print):
+        lam=3.0, dim=64, hidden=256, rows_log2=18, model_seed=2010, mu=0.0, log=print,
+        lams=None):
+    """Trains one model per balance weight in `lams` (default: [lam]) on the
+    same training graphs; returns the results and the model of the best
+    quality on the target."""
+    lams = list(lams) if lams else [lam]
     w = synth.WORKLOADS[workload]
     k, t, b, N, thr = w.k, w.t, w.b, w.N, w.greedy_threshold
     opts = c2.options(greedy_threshold=thr, greedy_rounds=w.greedy_rounds)
@@ -71,20 +76,7 @@ def run(workload="learned_ml20m", train_seeds=(6, 7, 8, 9), steps=400, batch=819
         nid, _, _ = c2.c2_build_knn_graph(dptr, ditems, w.n_items, k, t, b, N, s, opts=opts)
         train.append((dptr, ditems, positive_pairs(nid)))
     t_graphs = time.perf_counter() - t0
-    model = c2.Model(t, b, dim, hidden, rows_log2, model_seed).init()
-    gen = torch.Generator(device="cuda")
-    gen.manual_seed(model_seed)
-    losses = []
-    torch.cuda.synchronize()
-    t1 = time.perf_counter()
-    for step in range(steps):
-        dptr, ditems, pairs = train[step % len(train)]
-        idx = torch.randint(0, pairs.shape[0], (batch,), device="cuda", generator=gen)
-        losses.append(model.train_step(dptr, ditems, pairs[idx].contiguous(), lr=lr, lam=lam))
-    torch.cuda.synchronize()
-    t_train = time.perf_counter() - t1
-    losses = torch.stack(losses).cpu().numpy()
-    # target dataset
+    # target dataset and the FastRandomHash reference
     ptr, items, _ = synth.generate(w, w.seed, mu=mu) if mu else synth.load(workload, w.seed)
     dptr, ditems = dev(ptr), dev(items)
     nnz = items.size
@@ -93,31 +85,60 @@ def run(workload="learned_ml20m", train_seeds=(6, 7, 8, 9), steps=400, batch=819
         dptr, ditems, w.n_items, k, t, b, N, w.seed, opts=opts, ws=ws))
     frh_stats = c2.c2_get_stats(ws)
     q_frh, judge = quality(dptr, ditems, w.n_items, k, fin, fun)
+    best = None
+    results = []
+    for lam in lams:
+        r, model = _train_eval(w, train, steps, batch, lr, lam, dim, hidden, rows_log2, model_seed,
+                               dptr, ditems, nnz, ws, opts, fid, judge, log)
+        r.update(workload=workload, n_users=w.n_users, n_items=w.n_items, nnz=int(nnz), k=k, t=t,
+                 b=b, N=N, mu=mu, train_seeds=list(train_seeds), train_graphs_s=t_graphs,
+                 frh=dict(build_ms=t_frh * 1e3, quality=q_frh, pairs=frh_stats["pairs"],
+                          n_clusters=frh_stats["n_clusters"],
+                          max_cluster=frh_stats["max_cluster"]))
+        r["gain_quality"] = r["learned"]["quality"] - q_frh
+        r["speedup"] = t_frh * 1e3 / r["learned"]["total_ms"]
+        log(json.dumps(r))
+        results.append(r)
+        if best is None or r["learned"]["quality"] > best[0]["learned"]["quality"]:
+            best = (r, model)
+    return results, best[1]
+
+
+def _train_eval(w, train, steps, batch, lr, lam, dim, hidden, rows_log2, model_seed, dptr, ditems,
+                nnz, ws, opts, fid, judge, log):
+    k, t, b, N, thr = w.k, w.t, w.b, w.N, w.greedy_threshold
+    model = c2.Model(t, b, dim, hidden, rows_log2, model_seed).init()
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(model_seed)
+    losses = []
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    for step in range(steps):
+        tptr, titems, pairs = train[step % len(train)]
+        idx = torch.randint(0, pairs.shape[0], (batch,), device="cuda", generator=gen)
+        losses.append(model.train_step(tptr, titems, pairs[idx].contiguous(), lr=lr, lam=lam))
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t1
+    losses = torch.stack(losses).cpu().numpy()
     keys, t_prop = timed(lambda: model.propose(dptr, ditems))
     lopts = c2.options(greedy_threshold=thr, greedy_rounds=w.greedy_rounds, keys=keys)
     (lid, lin, lun), t_lbuild = timed(lambda: c2.c2_build_knn_graph(
         dptr, ditems, w.n_items, k, t, b, N, w.seed, opts=lopts, ws=ws))
     l_stats = c2.c2_get_stats(ws)
     q_learned, _ = quality(dptr, ditems, w.n_items, k, lin, lun, judge)
-    co_pairs = positive_pairs(fid)
     kk = keys.cpu().numpy()
-    cp = co_pairs.cpu().numpy()
+    cp = positive_pairs(fid).cpu().numpy()
+    used = [int(np.unique(kk[j]).size) for j in range(t)]
     res = dict(
-        workload=workload, n_users=w.n_users, n_items=w.n_items, nnz=int(nnz), k=k, t=t, b=b, N=N,
-        train_seeds=list(train_seeds), steps=steps, batch=batch, lr=lr, lam=lam,
+        steps=steps, batch=batch, lr=lr, lam=lam,
         loss_first=losses[:10].mean(0).tolist(), loss_last=losses[-10:].mean(0).tolist(),
-        train_graphs_s=t_graphs, train_s=t_train,
-        frh=dict(build_ms=t_frh * 1e3, quality=q_frh, pairs=frh_stats["pairs"],
-                 n_clusters=frh_stats["n_clusters"], max_cluster=frh_stats["max_cluster"]),
+        train_s=t_train,
         learned=dict(propose_ms=t_prop * 1e3, build_ms=t_lbuild * 1e3,
                      total_ms=(t_prop + t_lbuild) * 1e3, quality=q_learned,
                      pairs=l_stats["pairs"], n_clusters=l_stats["n_clusters"],
-                     max_cluster=l_stats["max_cluster"],
+                     max_cluster=l_stats["max_cluster"], buckets_used_per_head=used,
                      frh_neighbour_pairs_sharing_a_key=float(
-                         (kk[:, cp[:, 0]] == kk[:, cp[:, 1]]).any(0).mean())),
-        gain_quality=q_learned - q_frh,
-        speedup=t_frh / (t_prop + t_lbuild))
-    log(json.dumps(res))
+                         (kk[:, cp[:, 0]] == kk[:, cp[:, 1]]).any(0).mean())))
     return res, model
 
 
@@ -128,11 +149,13 @@ def main():
     ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--batch", type=int, default=8192)
     ap.add_argument("--lr", type=float, default=2e-3)
-    ap.add_argument("--lam", type=float, default=0.1)
+    ap.add_argument("--lam", type=float, default=3.0)
+    ap.add_argument("--lams", type=float, nargs="*", default=None)
     ap.add_argument("--mu", type=float, default=0.0)
     ap.add_argument("--save", default="")
     a = ap.parse_args()
-    _, model = run(a.workload, tuple(a.train_seeds), a.steps, a.batch, a.lr, a.lam, mu=a.mu)
+    _, model = run(a.workload, tuple(a.train_seeds), a.steps, a.batch, a.lr, a.lam, mu=a.mu,
+                   lams=a.lams)
     if a.save:
         model.save(a.save)
 
