@@ -288,6 +288,189 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(GemmArgs g) {
       }
 }
 
+// Faster GEMM for row-major operands: C[M][N] = A[M][K] B[K][N] (+ bias),
+// N % 128 == 0, K % 32 == 0.  Block tile 128 x 128 x 32, eight warps of
+// 64 x 32, cp.async double buffering, ldmatrix fragment loads (B transposed
+// on load).  Epilogue: FP32 / BF16 outputs, or -- for proposals -- the
+// (max, argmax) of every 128-column slice of each row, ties to the lower column.
+constexpr int FBM = 128, FBN = 128, FBK = 32, FPAD = 8;
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool valid) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  const int bytes = valid ? 16 : 0;
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(bytes));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+__device__ __forceinline__ void ldsm_x4(uint32_t* r, const void* smem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(s));
+}
+__device__ __forceinline__ void ldsm_x4_t(uint32_t* r, const void* smem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(s));
+}
+
+struct FastGemmArgs {
+  const __nv_bfloat16* A;  // [M][lda]
+  int64_t lda;
+  const __nv_bfloat16* B;  // [K][ldb]
+  int64_t ldb;
+  float* C;                // optional [M][ldc]
+  __nv_bfloat16* C16;      // optional [M][ldc]
+  int64_t ldc;
+  const float* bias;       // optional [N]
+  int relu;                // ReLU on the BF16 copy
+  float2* part;            // optional [M][N/128]: (max, argmax column) per slice
+  int M, N, K;
+};
+
+__global__ void __launch_bounds__(256) k_gemm_fast(FastGemmArgs g) {
+  __shared__ __align__(16) __nv_bfloat16 As[2][FBM][FBK + FPAD];
+  __shared__ __align__(16) __nv_bfloat16 Bs[2][FBK][FBN + FPAD];
+  __shared__ float2 red[FBM][4];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int m0 = blockIdx.y * FBM, n0 = blockIdx.x * FBN;
+  const int wm = (warp >> 2) * 64, wn = (warp & 3) * 32;
+  float acc[4][4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
+  auto load = [&](int buf, int k0) {
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const int c = tid + r * 256;            // 512 16-byte chunks per operand tile
+      const int am = c >> 2, ak = (c & 3) * 8;
+      const int gm = m0 + am;
+      cp_async16(&As[buf][am][ak], g.A + (int64_t)min(gm, g.M - 1) * g.lda + k0 + ak, gm < g.M);
+      const int bk = c >> 4, bn = (c & 15) * 8;
+      cp_async16(&Bs[buf][bk][bn], g.B + (int64_t)(k0 + bk) * g.ldb + n0 + bn, true);
+    }
+    cp_async_commit();
+  };
+  const int nk = g.K / FBK;
+  load(0, 0);
+  for (int kt = 0; kt < nk; ++kt) {
+    const int buf = kt & 1;
+    if (kt + 1 < nk) {
+      load(buf ^ 1, (kt + 1) * FBK);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+#pragma unroll
+    for (int ks = 0; ks < FBK; ks += 16) {
+      uint32_t af[4][4], bf[4][2];
+      const int li = lane >> 3, lr = lane & 7;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int row = wm + i * 16 + lr + ((li & 1) ? 8 : 0);
+        const int col = ks + ((li & 2) ? 8 : 0);
+        ldsm_x4(af[i], &As[buf][row][col]);
+      }
+#pragma unroll
+      for (int jj = 0; jj < 2; ++jj) {
+        const int krow = ks + lr + ((li & 1) ? 8 : 0);
+        const int ncol = wn + jj * 16 + ((li & 2) ? 8 : 0);
+        uint32_t r[4];
+        ldsm_x4_t(r, &Bs[buf][krow][ncol]);
+        bf[2 * jj][0] = r[0];
+        bf[2 * jj][1] = r[1];
+        bf[2 * jj + 1][0] = r[2];
+        bf[2 * jj + 1][1] = r[3];
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], af[i], bf[j]);
+    }
+    __syncthreads();
+  }
+  const int gq = lane >> 2, tq = lane & 3;
+  if (!g.part) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int m = m0 + wm + i * 16 + gq + (q >= 2 ? 8 : 0);
+          const int n = n0 + wn + j * 8 + 2 * tq + (q & 1);
+          if (m < g.M) {
+            const float v = acc[i][j][q] + (g.bias ? g.bias[n] : 0.f);
+            if (g.C) g.C[(int64_t)m * g.ldc + n] = v;
+            if (g.C16) g.C16[(int64_t)m * g.ldc + n] = __float2bfloat16_rn(g.relu ? fmaxf(v, 0.f) : v);
+          }
+        }
+    return;
+  }
+  // (max, argmax) per row over the block's 128 columns
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      float best = -INFINITY;
+      int arg = 0x7fffffff;
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const int n = n0 + wn + j * 8 + 2 * tq + e;
+          const float v = acc[i][j][2 * h + e] + (g.bias ? g.bias[n] : 0.f);
+          if (v > best || (v == best && n < arg)) { best = v; arg = n; }
+        }
+#pragma unroll
+      for (int o = 1; o < 4; o <<= 1) {
+        const float ov = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oa = __shfl_xor_sync(0xffffffffu, arg, o);
+        if (ov > best || (ov == best && oa < arg)) { best = ov; arg = oa; }
+      }
+      if (tq == 0) red[wm + i * 16 + gq + 8 * h][warp & 3] = make_float2(best, __int_as_float(arg));
+    }
+  __syncthreads();
+  if (tid < FBM && m0 + tid < g.M) {
+    float2 b2 = red[tid][0];
+#pragma unroll
+    for (int w2 = 1; w2 < 4; ++w2) {
+      const float2 o = red[tid][w2];
+      if (o.x > b2.x || (o.x == b2.x && __float_as_int(o.y) < __float_as_int(b2.y))) b2 = o;
+    }
+    g.part[(int64_t)(m0 + tid) * (g.N / FBN) + blockIdx.x] = b2;
+  }
+}
+
+// Key of every (row, head) from the per-slice partials (b % 128 == 0).
+__global__ void k_argmax_parts(const float2* __restrict__ part, int nrows, int t, int b, int T,
+                               const int32_t* __restrict__ rowlist, int n_users,
+                               int32_t* __restrict__ keys) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nrows * t) return;
+  const int r = idx / t, j = idx % t;
+  const int per = b / FBN, slices = T / FBN;
+  float2 best = part[(int64_t)r * slices + j * per];
+  for (int q = 1; q < per; ++q) {
+    const float2 o = part[(int64_t)r * slices + j * per + q];
+    if (o.x > best.x || (o.x == best.x && __float_as_int(o.y) < __float_as_int(best.y))) best = o;
+  }
+  keys[(int64_t)j * n_users + rowlist[r]] = __float_as_int(best.y) - j * b;
+}
+
+c2_status gemm_fast(const FastGemmArgs& g, cudaStream_t st) {
+  if (g.M <= 0) return C2_OK;
+  dim3 grid(g.N / FBN, div_up(g.M, FBM));
+  C2_LAUNCH(k_gemm_fast, grid, 256, 0, st, g);
+  C2_CUDA_TRY(cudaGetLastError());
+  return C2_OK;
+}
+
 c2_status gemm(const GemmArgs& g, cudaStream_t st) {
   if (g.M <= 0 || g.N <= 0) return C2_OK;
   dim3 grid(div_up(g.N, GBN), div_up(g.M, GBM));
@@ -485,10 +668,28 @@ __global__ void k_rowlist_range(int32_t* __restrict__ rowlist, int start, int co
 
 // ---------------------------------------------------------------- drivers
 // Forward pass over nrows rows of scratch (rowlist filled): e, h, z logits.
+bool fast_ok(int N, int K) { return N % FBN == 0 && K % FBK == 0; }
+
+// Forward pass over nrows rows; with `part` the second GEMM only leaves the
+// per-slice (max, argmax) partials instead of the logits.
 c2_status model_forward(const ModelDims& d, const ModelParams& p, const ModelScratch& s,
-                        const int32_t* ptr, const int32_t* items, int nrows, cudaStream_t st) {
+                        const int32_t* ptr, const int32_t* items, int nrows, cudaStream_t st,
+                        float2* part = nullptr) {
   C2_LAUNCH(k_embbag_fwd, div_up((int64_t)nrows * 32, 256), 256, 0, st, ptr, items, s.rowlist,
             nrows, p.E16, d.D, d.rows, d.seed, s.e, s.e16);
+  if (fast_ok(d.H, d.D) && fast_ok(d.T, d.H)) {
+    FastGemmArgs f1{};
+    f1.A = s.e16; f1.lda = d.D; f1.B = p.W1_16; f1.ldb = d.H;
+    f1.C = s.hpre; f1.C16 = s.h16; f1.ldc = d.H; f1.bias = p.b1; f1.relu = 1;
+    f1.M = nrows; f1.N = d.H; f1.K = d.D;
+    c2_status rc = gemm_fast(f1, st);
+    if (rc) return rc;
+    FastGemmArgs f2{};
+    f2.A = s.h16; f2.lda = d.H; f2.B = p.W2_16; f2.ldb = d.T;
+    f2.C = part ? nullptr : s.z; f2.ldc = d.T; f2.bias = p.b2; f2.part = part;
+    f2.M = nrows; f2.N = d.T; f2.K = d.H;
+    return gemm_fast(f2, st);
+  }
   GemmArgs g1{};
   g1.A = s.e16; g1.sam = d.D; g1.sak = 1;
   g1.B = p.W1_16; g1.sbk = d.H; g1.sbn = 1;
@@ -507,13 +708,23 @@ c2_status model_forward(const ModelDims& d, const ModelParams& p, const ModelScr
 c2_status model_propose(const ModelDims& d, const ModelParams& p, const ModelScratch& s,
                         int chunk, const int32_t* ptr, const int32_t* items, int n,
                         int32_t* keys, cudaStream_t st) {
+  // fused argmax when every head spans whole 128-column slices
+  const bool fused = fast_ok(d.H, d.D) && fast_ok(d.T, d.H) && d.b % FBN == 0;
   for (int start = 0; start < n; start += chunk) {
     const int rows = std::min(chunk, n - start);
     C2_LAUNCH(k_rowlist_range, div_up(rows, 256), 256, 0, st, s.rowlist, start, rows);
-    c2_status rc = model_forward(d, p, s, ptr, items, rows, st);
-    if (rc) return rc;
-    C2_LAUNCH(k_argmax, div_up((int64_t)rows * d.t * 32, 256), 256, 0, st, s.z, rows, d.t, d.b,
-              d.T, s.rowlist, n, keys);
+    if (fused) {
+      float2* part = reinterpret_cast<float2*>(s.z);   // [rows][T/128] fits in z
+      c2_status rc = model_forward(d, p, s, ptr, items, rows, st, part);
+      if (rc) return rc;
+      C2_LAUNCH(k_argmax_parts, div_up((int64_t)rows * d.t, 256), 256, 0, st, part, rows, d.t,
+                d.b, d.T, s.rowlist, n, keys);
+    } else {
+      c2_status rc = model_forward(d, p, s, ptr, items, rows, st);
+      if (rc) return rc;
+      C2_LAUNCH(k_argmax, div_up((int64_t)rows * d.t * 32, 256), 256, 0, st, s.z, rows, d.t, d.b,
+                d.T, s.rowlist, n, keys);
+    }
   }
   C2_CUDA_TRY(cudaGetLastError());
   return C2_OK;

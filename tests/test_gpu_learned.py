@@ -154,3 +154,18 @@ def test_model_save_load_roundtrip(c2, tmp_path):
     m2 = c2.Model.load(str(path))
     assert m2.step == m.step and torch.equal(m2.state, m.state)
     same(m2.propose(dev(ptr), dev(items)), m.propose(dev(ptr), dev(items)).cpu().numpy(), "keys")
+
+
+def test_model_keys_fused_argmax_match_oracle(c2):
+    # heads of 128 buckets: the argmax is fused into the logits GEMM
+    m = _model(c2, t=2, b=256, dim=64, hidden=128, rows_log2=11, seed=12)
+    ptr, items = synth.random_profiles(2500, 900, 25, 47)
+    keys = m.propose(dev(ptr), dev(items)).cpu().numpy()
+    params = [x.cpu().numpy() for x in m.params()]
+    z, okeys = oracle.model_forward(m.config(), params, ptr, items)
+    b = m.cfg.b
+    diff = np.argwhere(keys != okeys)
+    for j, u in diff:
+        zz = np.sort(z[u, j * b:(j + 1) * b])
+        assert zz[-1] - zz[-2] < 1e-3 * max(1.0, abs(zz[-1])), (j, u)
+    assert len(diff) <= 0.01 * keys.size
