@@ -36,7 +36,8 @@ struct DevHeader {
   int32_t n_gwork;             // greedy round work items of the current batch
   unsigned long long greedy_visits;    // candidate entries examined by computed users
   unsigned long long greedy_computed;  // (user, round) pairs computed (not skipped)
-  int32_t pad[16];
+  int32_t knn_max_len;         // longest profile among the clustered users
+  int32_t pad[15];
 };
 static_assert(sizeof(DevHeader) <= 256, "header must fit 256 bytes");
 
@@ -243,16 +244,12 @@ __device__ __forceinline__ void warp_sort32(WarpList& e) {
   }
 }
 
-// Merges a warp batch (one candidate per lane, `pass` marks real ones) into
-// the sorted list of length k: the batch is sorted, the two sorted runs are
-// combined into a bitonic sequence holding the best 32, which is cleaned.
-static __device__ __noinline__ void warp_list_merge(WarpList& e, int k, bool pass, int32_t id,
-                                             uint32_t c, uint32_t u) {
+// Merges a warp batch `b` (one candidate per lane, id -1 = none) into the
+// sorted list `e` of length k and returns the new list: the batch is sorted,
+// the two sorted runs form a bitonic sequence holding the best 32, which is
+// cleaned.  Not inlined (large; called on a uniform branch).
+static __device__ __noinline__ WarpList warp_list_merge(WarpList e, int k, WarpList b) {
   const int lane = threadIdx.x & 31;
-  WarpList b;
-  b.id = pass ? id : -1;
-  b.c = c;
-  b.u = u;
   warp_sort32(b);
   if (lane >= k) e.id = -1;
   WarpList r;
@@ -268,6 +265,7 @@ static __device__ __noinline__ void warp_list_merge(WarpList& e, int k, bool pas
     if (take) e = o;
   }
   if (lane >= k) e.id = -1;
+  return e;
 }
 
 // Adds the lanes' candidates flagged `pass` to the list: one by one when few
@@ -276,7 +274,11 @@ __device__ __forceinline__ void warp_list_add(WarpList& e, int k, bool pass, int
                                               uint32_t c, uint32_t u) {
   unsigned mask = __ballot_sync(0xffffffffu, pass);
   if (__popc(mask) > 16) {
-    warp_list_merge(e, k, pass, id, c, u);
+    WarpList b;
+    b.id = pass ? id : -1;
+    b.c = c;
+    b.u = u;
+    e = warp_list_merge(e, k, b);
     return;
   }
   while (mask) {
@@ -292,6 +294,228 @@ __device__ __forceinline__ unsigned lanemask_lt() {
   asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
   return m;
 }
+
+// Streaming top-k of one warp.  Candidates that beat the current k-th entry
+// (the filter `T`, the same in all lanes) are staged in a per-warp shared
+// buffer of 64 entries; every 32 staged candidates are merged at once and the
+// filter is refreshed.  The final list is the k best of all offered
+// candidates under the neighbour order whatever the offering order, so long
+// as the offered candidates are distinct and not already in the list.
+struct WarpTopk {
+  WarpList L;      // lane i < k: i-th best (id -1 = empty)
+  WarpList T;      // k-th entry
+  int n, k;        // staged entries (uniform), list length
+  int32_t* sid;    // shared [64]
+  uint2* scu;      // shared [64]: (intersection, union)
+
+  __device__ __forceinline__ void refresh() {
+    T.id = __shfl_sync(0xffffffffu, L.id, k - 1);
+    T.c = __shfl_sync(0xffffffffu, L.c, k - 1);
+    T.u = __shfl_sync(0xffffffffu, L.u, k - 1);
+  }
+  __device__ __forceinline__ void start(const WarpList& l0, int k_, int32_t* sid_, uint2* scu_) {
+    L = l0;
+    k = k_;
+    n = 0;
+    sid = sid_;
+    scu = scu_;
+    refresh();
+  }
+  // True iff the candidate may enter the list (it beats the k-th entry).
+  __device__ __forceinline__ bool filter(int32_t id, uint32_t c, uint32_t u) const {
+    return beats(T, id, c, u);
+  }
+  __device__ __forceinline__ void drain32() {
+    const int lane = threadIdx.x & 31;
+    __syncwarp();
+    WarpList b;
+    b.id = sid[lane];
+    const uint2 cu = scu[lane];
+    b.c = cu.x;
+    b.u = cu.y;
+    const int rest = n - 32;
+    int32_t rid = 0;
+    uint2 rcu = make_uint2(0u, 0u);
+    if (lane < rest) { rid = sid[32 + lane]; rcu = scu[32 + lane]; }
+    __syncwarp();
+    if (lane < rest) { sid[lane] = rid; scu[lane] = rcu; }
+    __syncwarp();
+    n = rest;
+    L = warp_list_merge(L, k, b);
+    refresh();
+  }
+  // Stages the lanes' candidates flagged `pass` (already filtered).
+  __device__ __forceinline__ void stage(bool pass, int32_t id, uint32_t c, uint32_t u) {
+    const unsigned m = __ballot_sync(0xffffffffu, pass);
+    if (m == 0u) return;
+    if (pass) {
+      const int p = n + __popc(m & lanemask_lt());
+      sid[p] = id;
+      scu[p] = make_uint2(c, u);
+    }
+    n += __popc(m);
+    if (n >= 32) drain32();
+  }
+  // Merges what is still staged; the buffer is free again afterwards.
+  __device__ __forceinline__ void finish() {
+    if (n == 0) return;
+    const int lane = threadIdx.x & 31;
+    __syncwarp();
+    const bool pass = lane < n;
+    int32_t id = -1;
+    uint2 cu = make_uint2(0u, 0u);
+    if (pass) { id = sid[lane]; cu = scu[lane]; }
+    __syncwarp();
+    n = 0;
+    warp_list_add(L, k, pass, id, cu.x, cu.y);
+    refresh();
+  }
+};
+
+// ------------------------------------------------------------ keyed lists
+// Exact order key of a neighbour (c common items, u union, local id) when
+// u < 2^16 (hence c <= u < 2^16): K = floor(c * 2^32 / u) keeps equal Jaccard
+// values equal and separates different ones (they differ by at least
+// 1/(u u') > 2^-32), and the low 16 bits hold 0xffff - id so that equal
+// values rank the lower id first.  Larger key = better neighbour; 0 = empty.
+// K is assembled from two 32-bit divisions: c*2^16 = q1*u + r1, then
+// r1*2^16 / u, both exact because c, r1 < 2^16.
+__device__ __forceinline__ uint64_t nbr_key(uint32_t c, uint32_t u, int32_t lid) {
+  const uint32_t ud = u ? u : 1u;            // c = u = 0 only for two empty profiles
+  const uint32_t a = c << 16;
+  const uint32_t q1 = a / ud, r1 = a - q1 * ud;
+  const uint32_t q2 = (r1 << 16) / ud;
+  const uint64_t K = c ? (((uint64_t)q1 << 16) | q2) : 0ull;
+  return (K << 16) | (uint64_t)(0xffffu - (uint32_t)lid);
+}
+__device__ __forceinline__ int32_t key_id(uint64_t key) {
+  return key ? (int32_t)(0xffffu - (uint32_t)(key & 0xffffu)) : -1;
+}
+
+// Bitonic sort of one key per lane, largest first (32 lanes).
+__device__ __forceinline__ uint64_t warp_sort32_keys(uint64_t x) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int size = 2; size <= 32; size <<= 1) {
+#pragma unroll
+    for (int j = size >> 1; j > 0; j >>= 1) {
+      const uint64_t o = __shfl_xor_sync(0xffffffffu, x, j);
+      const bool best_first = size == 32 || (lane & size) == 0;
+      const bool lower = (lane & j) == 0;
+      const bool take = (lower == best_first) ? (o > x) : (x > o);
+      x = take ? o : x;
+    }
+  }
+  return x;
+}
+
+// Merges a batch of keys (one per lane, 0 = none) into the sorted key list
+// `e` of length k: max of the list and the reversed sorted batch is a bitonic
+// sequence holding the best 32, which is cleaned.  Not inlined (called on a
+// uniform branch).
+static __device__ __noinline__ uint64_t key_list_merge(uint64_t e, int k, uint64_t b) {
+  const int lane = threadIdx.x & 31;
+  b = warp_sort32_keys(b);
+  if (lane >= k) e = 0ull;
+  const uint64_t r = __shfl_sync(0xffffffffu, b, 31 - lane);
+  e = r > e ? r : e;
+#pragma unroll
+  for (int j = 16; j > 0; j >>= 1) {
+    const uint64_t o = __shfl_xor_sync(0xffffffffu, e, j);
+    const bool lower = (lane & j) == 0;
+    e = lower ? (o > e ? o : e) : (o < e ? o : e);
+  }
+  return lane < k ? e : 0ull;
+}
+
+// Inserts a key known to all lanes into the key list (keys are distinct).
+__device__ __forceinline__ void key_list_insert(uint64_t& e, int k, uint64_t key) {
+  const int lane = threadIdx.x & 31;
+  const int pos = __popc(__ballot_sync(0xffffffffu, lane < k && e > key));
+  if (pos >= k) return;
+  const uint64_t p = __shfl_up_sync(0xffffffffu, e, 1);
+  if (lane > pos) e = p;
+  if (lane == pos) e = key;
+  if (lane >= k) e = 0ull;
+}
+
+// WarpTopk on order keys, for rows whose unions are below 2^16: the filter
+// compares 32-bit cross products against the k-th entry, staged candidates
+// get their keys in one batch, and lists are merged and shifted as single
+// 64-bit keys.  CU maps a local id to its (common, union) counts; it is used
+// to refresh the filter after the list changed.
+template <class CU>
+struct KeyTopk {
+  uint64_t L;      // lane i < k: key of the i-th best (0 = empty)
+  uint32_t Tc, Tu;
+  uint32_t Tid;    // k-th entry, (0, 1, 0x7fffffff) while the list is not full
+  int n, k;        // staged entries (uniform), list length
+  uint2* stg;      // shared [64]: (id, c | u << 16)
+  CU cu;
+
+  __device__ __forceinline__ void refresh() {
+    const uint64_t kth = __shfl_sync(0xffffffffu, L, k - 1);
+    if (kth == 0ull) {
+      Tc = 0u; Tu = 1u; Tid = 0x7fffffffu;
+    } else {
+      Tid = (uint32_t)key_id(kth);
+      const uint2 x = cu((int32_t)Tid);
+      Tc = x.x; Tu = x.y;
+    }
+  }
+  __device__ __forceinline__ void start(uint64_t key0, int k_, uint2* stg_, CU cu_) {
+    L = key0;
+    k = k_;
+    n = 0;
+    stg = stg_;
+    cu = cu_;
+    refresh();
+  }
+  __device__ __forceinline__ bool filter(int32_t id, uint32_t c, uint32_t u) const {
+    const uint32_t l = c * Tu, r = Tc * u;
+    return l > r || (l == r && (uint32_t)id < Tid);
+  }
+  __device__ __forceinline__ void drain32() {
+    const int lane = threadIdx.x & 31;
+    __syncwarp();
+    const uint2 x = stg[lane];
+    const int rest = n - 32;
+    uint2 y = make_uint2(0u, 0u);
+    if (lane < rest) y = stg[32 + lane];
+    __syncwarp();
+    if (lane < rest) stg[lane] = y;
+    __syncwarp();
+    n = rest;
+    L = key_list_merge(L, k, nbr_key(x.y & 0xffffu, x.y >> 16, (int32_t)x.x));
+    refresh();
+  }
+  __device__ __forceinline__ void stage(bool pass, int32_t id, uint32_t c, uint32_t u) {
+    const unsigned m = __ballot_sync(0xffffffffu, pass);
+    if (m == 0u) return;
+    if (pass) stg[n + __popc(m & lanemask_lt())] = make_uint2((uint32_t)id, c | (u << 16));
+    n += __popc(m);
+    if (n >= 32) drain32();
+  }
+  __device__ __forceinline__ void finish() {
+    if (n == 0) return;
+    const int lane = threadIdx.x & 31;
+    __syncwarp();
+    uint64_t key = 0ull;
+    if (lane < n) {
+      const uint2 x = stg[lane];
+      key = nbr_key(x.y & 0xffffu, x.y >> 16, (int32_t)x.x);
+    }
+    __syncwarp();
+    if (n > 8) {
+      L = key_list_merge(L, k, key);
+    } else {
+      for (int j = 0; j < n; ++j) key_list_insert(L, k, __shfl_sync(0xffffffffu, key, j));
+    }
+    n = 0;
+    refresh();
+  }
+  __device__ __forceinline__ int32_t id() const { return key_id(L); }
+};
 
 inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 

@@ -20,6 +20,7 @@
 #include <mutex>
 #include <string>
 #include <tuple>
+#include <type_traits>
 #include <vector>
 
 #include "c2_internal.cuh"
@@ -480,8 +481,27 @@ struct RowTopkArgs {
   DevHeader* hdr;
 };
 
+// (common, union) counts of a member of the warp's cluster from the global
+// row of counts and slot lengths.
+struct GlobalCU {
+  const uint16_t* row;
+  const int32_t* len;      // slot lengths from the cluster's first slot
+  uint32_t my;
+  __device__ __forceinline__ uint2 operator()(int32_t v) const {
+    const uint32_t c = row[v];
+    return make_uint2(c, my + (uint32_t)len[v] - c);
+  }
+};
+
+// One warp per user of a brute-force cluster: the top k of the user's row of
+// intersection counts, 256 candidates per step (8 per lane, coalesced),
+// staged and merged; `Keyed` (every union below 2^16) holds the list as exact
+// 64-bit order keys.
+template <bool Keyed>
 __global__ void __launch_bounds__(kNT) k_gram_topk(RowTopkArgs a) {
-  const int lane = threadIdx.x & 31;
+  __shared__ int32_t s_sid[Keyed ? 1 : kNT / 32][64];
+  __shared__ uint2 s_scu[kNT / 32][64];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (w >= *a.n_users_dev || dev_failed(a.hdr)) return;
   const int slot = a.u_slot[w];
@@ -490,31 +510,53 @@ __global__ void __launch_bounds__(kNT) k_gram_topk(RowTopkArgs a) {
   const uint16_t* row = a.gram + a.gofs[c] + (int64_t)l * Mp;
   const uint32_t my = (uint32_t)a.slen[slot];
   const int k = a.k;
-  WarpList L;
-  L.id = -1; L.c = 0; L.u = 0;
-  for (int v0 = 0; v0 < M; v0 += 32) {
-    const int v = v0 + lane;
-    WarpList kth;
-    kth.id = __shfl_sync(0xffffffffu, L.id, k - 1);
-    kth.c = __shfl_sync(0xffffffffu, L.c, k - 1);
-    kth.u = __shfl_sync(0xffffffffu, L.u, k - 1);
-    uint32_t cc = 0, uu = 0;
-    bool pass = false;
-    if (v < M && v != l) {
-      cc = row[v];
-      if (cc > 0) {
-        uu = my + (uint32_t)a.slen[cs + v] - cc;
-        pass = beats(kth, v, cc, uu);   // local index order = user id order
-      }
-    }
-    warp_list_add(L, k, pass, v, cc, uu);
+  typename std::conditional<Keyed, KeyTopk<GlobalCU>, WarpTopk>::type tk;
+  if constexpr (Keyed) {
+    tk.start(0ull, k, s_scu[warp], GlobalCU{row, a.slen + cs, my});
+  } else {
+    WarpList l0;
+    l0.id = -1; l0.c = 0; l0.u = 0;
+    tk.start(l0, k, s_sid[warp], s_scu[warp]);
   }
+  for (int v0 = 0; v0 < M; v0 += 256) {
+    uint32_t cc[8], ln[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int v = v0 + j * 32 + lane;
+      cc[j] = (v < M && v != l) ? (uint32_t)row[v] : 0u;
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int v = v0 + j * 32 + lane;
+      ln[j] = cc[j] > 0u ? (uint32_t)a.slen[cs + v] : 0u;
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      if (v0 + j * 32 >= M) break;
+      const int v = v0 + j * 32 + lane;
+      const uint32_t uu = my + ln[j] - cc[j];
+      // local index order = user id order
+      const bool pass = cc[j] > 0u && tk.filter(v, cc[j], uu);
+      tk.stage(pass, v, cc[j], uu);
+    }
+  }
+  tk.finish();
   if (lane < k) {
     const int64_t o = (int64_t)slot * k + lane;
-    const bool ok = L.id >= 0;
-    a.out_id[o] = ok ? a.cusers[cs + L.id] : -1;
-    a.out_in[o] = ok ? (int32_t)L.c : 0;
-    a.out_un[o] = ok ? (int32_t)L.u : 0;
+    int32_t id;
+    uint32_t oc = 0, ou = 0;
+    if constexpr (Keyed) {
+      id = tk.id();
+      if (id >= 0) {
+        const uint2 x = GlobalCU{row, a.slen + cs, my}(id);
+        oc = x.x; ou = x.y;
+      }
+    } else {
+      id = tk.L.id; oc = tk.L.c; ou = tk.L.u;
+    }
+    a.out_id[o] = id >= 0 ? a.cusers[cs + id] : -1;
+    a.out_in[o] = id >= 0 ? (int32_t)oc : 0;
+    a.out_un[o] = id >= 0 ? (int32_t)ou : 0;
   }
 }
 
@@ -582,7 +624,7 @@ __global__ void __launch_bounds__(kNT) k_merge_knn(MergeArgs a) {
     const int c = a.slot2c[row];
     cbase = a.cptr[c];
     M = a.cptr[c + 1] - cbase;
-    if (M < 2 || M >= a.thr || M >= a.max_m) return;
+    if (M < 2 || M >= a.thr || (M >= a.max_m && a.hdr->knn_max_len <= 65535)) return;
     u = a.cusers[row];
     clist = a.cusers;
   } else {
@@ -640,8 +682,12 @@ __global__ void k_prep(const int32_t* __restrict__ cptr, const int32_t* __restri
   if (c < S && c < L) M = cptr[c + 1] - cptr[c];
   const bool brute = M >= 2 && M < thr;
   const bool greedy = M >= 2 && M >= thr;
+  // counts are 16-bit: with a profile of more than 65535 items, brute-force
+  // clusters go to the merge kernel and greedy clusters are unsupported
+  const bool wide = hdr->knn_max_len > 65535;
+  if (greedy && wide) dev_fail(hdr, C2_ERR_UNSUPPORTED);
   if (c < S) {
-    gflag[c] = (greedy || (brute && M >= small_cut)) ? 1 : 0;
+    gflag[c] = (greedy || (brute && M >= small_cut && !wide)) ? 1 : 0;
     gkind[c] = greedy ? 1 : 0;
     if (M == 1) {
       const int64_t s = cptr[c];
@@ -659,20 +705,28 @@ __global__ void k_prep(const int32_t* __restrict__ cptr, const int32_t* __restri
   if (c == 0) hdr->n_labels = L;
 }
 
-// slot -> cluster by binary search in cptr; slot -> profile length.
+// slot -> cluster by binary search in cptr; slot -> profile length; the
+// longest profile.
 __global__ void k_slot_info(const int32_t* __restrict__ cptr, const int32_t* __restrict__ n_clusters,
                             const int32_t* __restrict__ cusers, const int32_t* __restrict__ ptr,
-                            int64_t S, int32_t* __restrict__ slot2c, int32_t* __restrict__ slen) {
+                            int64_t S, int32_t* __restrict__ slot2c, int32_t* __restrict__ slen,
+                            DevHeader* hdr) {
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= S) return;
-  int lo = 0, hi = *n_clusters - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (cptr[mid] <= s) lo = mid; else hi = mid - 1;
+  int len = 0;
+  if (s < S) {
+    int lo = 0, hi = *n_clusters - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (cptr[mid] <= s) lo = mid; else hi = mid - 1;
+    }
+    slot2c[s] = lo;
+    const int u = cusers[s];
+    len = ptr[u + 1] - ptr[u];
+    slen[s] = len;
   }
-  slot2c[s] = lo;
-  const int u = cusers[s];
-  slen[s] = ptr[u + 1] - ptr[u];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) len = max(len, __shfl_xor_sync(0xffffffffu, len, o));
+  if ((threadIdx.x & 31) == 0 && len > 0) atomicMax(&hdr->knn_max_len, len);
 }
 
 // Work items (cluster, tile) from per-cluster tile counts and their scan.
@@ -867,13 +921,38 @@ __global__ void __launch_bounds__(kNT) k_greedy_init(GreedyArgs a) {
   if (lane == 0 && evals) atomicAdd(&a.hdr->pairs, evals);
 }
 
+// (common, union) counts of a member of the warp's cluster from the staged
+// row of counts and profile lengths (shared memory).
+struct SmemCU {
+  const uint16_t* row;
+  const int32_t* len;
+  uint32_t my;
+  __device__ __forceinline__ uint2 operator()(int32_t v) const {
+    const uint32_t c = row[v];
+    return make_uint2(c, my + (uint32_t)len[v] - c);
+  }
+};
+
 // One synchronous round.  A block takes a chunk of users of one cluster: the
 // cluster's profile lengths are staged in shared memory once, and every warp
 // stages its user's row of intersection counts before walking the
 // candidates (own list, neighbours' lists, optional random draws),
-// deduplicated with a per-warp bitmap of the cluster.
+// deduplicated with a per-warp bitmap of the cluster.  Candidates that beat
+// the current k-th neighbour are staged and merged 32 at a time; `Keyed`
+// (every union below 2^16) holds the list as exact 64-bit order keys.
+//
+// Without random draws, from round 2 on, the list of a neighbour v is known
+// not to contribute when v was already in the user's list two rounds back and
+// v's list did not change last round: then all of v's list was a candidate
+// last round, and each such candidate is in the current list or ranks below
+// all k of its entries (the current list is the top k of last round's
+// candidates).  Those lists are only deduplicated, so that the count of
+// evaluated pairs stays that of the method.
+template <bool Keyed>
 __global__ void __launch_bounds__(kNT, 4) k_greedy_round(GreedyArgs a) {
   extern __shared__ __align__(16) uint32_t gsm[];
+  __shared__ int32_t s_sid[Keyed ? 1 : 8][64];
+  __shared__ uint2 s_scu[8][64];
   const int mcap = a.mcap;                               // multiple of 32
   int32_t* s_len = reinterpret_cast<int32_t*>(gsm);      // [mcap]
   uint16_t* s_rows = reinterpret_cast<uint16_t*>(gsm + mcap);   // [8][mcap]
@@ -884,6 +963,7 @@ __global__ void __launch_bounds__(kNT, 4) k_greedy_round(GreedyArgs a) {
   uint32_t* bm = s_bm + warp * (mcap >> 5);
   const int nwork = *a.n_gwork;
   const int k = a.k;
+  const bool prune = a.chg_in != nullptr && a.round >= 2 && a.n_random == 0;
   unsigned long long evals = 0, visits = 0, computed = 0;
   for (;;) {
     if (threadIdx.x == 0) s_work = dev_failed(a.hdr) ? nwork : (int)atomicAdd(a.counter, 1u);
@@ -896,15 +976,18 @@ __global__ void __launch_bounds__(kNT, 4) k_greedy_round(GreedyArgs a) {
     for (int v = threadIdx.x; v < M; v += kNT) s_len[v] = a.slen[cs + v];
     __syncthreads();
     const uint16_t* Gc = a.gram + a.gofs[c];
+    const int32_t* wl_c = a.wl_in + (int64_t)cs * k + lane;
     for (int uu = 0; uu < kGreedyUsersPerWarp; ++uu) {
       const int l = chunk * kGreedyChunk + uu * 8 + warp;
       if (l >= M) break;
       const int slot = cs + l;
       const int e = lane < k ? a.wl_in[(int64_t)slot * k + lane] : -1;
+      bool e_moved = false;
       if (a.chg_in) {
         // Unchanged list and unchanged neighbour lists: the candidate set,
         // hence the new list and its evaluation count, repeat the last round.
-        const bool moved = a.chg_in[slot] != 0 || (e >= 0 && a.chg_in[cs + e] != 0);
+        e_moved = e >= 0 && a.chg_in[cs + e] != 0;
+        const bool moved = a.chg_in[slot] != 0 || e_moved;
         if (!__any_sync(0xffffffffu, moved)) {
           if (lane < k) a.wl_out[(int64_t)slot * k + lane] = e;
           if (lane == 0) {
@@ -920,39 +1003,54 @@ __global__ void __launch_bounds__(kNT, 4) k_greedy_round(GreedyArgs a) {
       for (int i = lane; i < (Mp >> 3); i += 32) r4[i] = g4[i];
       for (int i = lane; i < ((M + 31) >> 5); i += 32) bm[i] = 0;
       __syncwarp();
+      // neighbour lists to deduplicate only (see above); the list of two
+      // rounds back is the row this warp is about to overwrite
+      unsigned dedupe_only = 0u;
+      if (prune) {
+        const int p = lane < k ? a.wl_out[(int64_t)slot * k + lane] : -1;
+        if (p >= 0) atomicOr(&bm[p >> 5], 1u << (p & 31));
+        __syncwarp();
+        const bool was = e >= 0 && ((bm[e >> 5] >> (e & 31)) & 1u) != 0u;
+        dedupe_only = __ballot_sync(0xffffffffu, was && !e_moved);
+        __syncwarp();
+        if (p >= 0) bm[p >> 5] = 0u;     // only these bits are set
+        __syncwarp();
+      }
       const uint32_t my = (uint32_t)s_len[l];
-      WarpList Lst;
-      Lst.id = e;
-      Lst.c = e >= 0 ? row[e] : 0u;
-      Lst.u = e >= 0 ? my + (uint32_t)s_len[e] - Lst.c : 0u;
+      const uint32_t c0 = e >= 0 ? row[e] : 0u;
+      const uint32_t u0 = e >= 0 ? my + (uint32_t)s_len[e] - c0 : 0u;
       if (e >= 0) atomicOr(&bm[e >> 5], 1u << (e & 31));
       if (lane == 0) atomicOr(&bm[l >> 5], 1u << (l & 31));
       const int nlist = __popc(__ballot_sync(0xffffffffu, e >= 0));
       __syncwarp();
+      typename std::conditional<Keyed, KeyTopk<SmemCU>, WarpTopk>::type tk;
+      if constexpr (Keyed) {
+        tk.start(e >= 0 ? nbr_key(c0, u0, e) : 0ull, k, s_scu[warp], SmemCU{row, s_len, my});
+      } else {
+        WarpList l0;
+        l0.id = e; l0.c = c0; l0.u = u0;
+        tk.start(l0, k, s_sid[warp], s_scu[warp]);
+      }
       unsigned fresh = 0;
       if (lane == 0) {
         visits += (unsigned long long)nlist * (unsigned long long)k + (unsigned)a.n_random;
         computed += 1;
       }
-      // one candidate per lane: dedupe, count lookup, exact filter, insert
+      // one candidate per lane: dedupe, count lookup, filter, stage; an
+      // absent candidate reads as the user itself, whose bit is set
       auto consider = [&](int v) {
-        bool isnew = false;
-        if (v >= 0) {
-          const uint32_t bit = 1u << (v & 31);
-          isnew = (atomicOr(&bm[v >> 5], bit) & bit) == 0;
-        }
-        uint32_t cc = 0, uu2 = 0;
-        if (isnew) {
-          ++fresh;
-          cc = row[v];
-          uu2 = my + (uint32_t)s_len[v] - cc;
-        }
-        WarpList kth;
-        kth.id = __shfl_sync(0xffffffffu, Lst.id, k - 1);
-        kth.c = __shfl_sync(0xffffffffu, Lst.c, k - 1);
-        kth.u = __shfl_sync(0xffffffffu, Lst.u, k - 1);
-        const bool pass = isnew && beats(kth, v, cc, uu2);
-        warp_list_add(Lst, k, pass, v, cc, uu2);
+        const int x = v >= 0 ? v : l;
+        const uint32_t bit = 1u << (x & 31);
+        const bool isnew = (atomicOr(&bm[x >> 5], bit) & bit) == 0u;
+        const uint32_t cc = row[x];
+        const uint32_t uu2 = my + (uint32_t)s_len[x] - cc;
+        fresh += isnew ? 1u : 0u;
+        tk.stage(isnew && tk.filter(x, cc, uu2), x, cc, uu2);
+      };
+      auto mark = [&](int v) {
+        const int x = v >= 0 ? v : l;
+        const uint32_t bit = 1u << (x & 31);
+        fresh += (atomicOr(&bm[x >> 5], bit) & bit) == 0u ? 1u : 0u;
       };
       // neighbour rows, 16 at a time (independent loads in flight)
       for (int j0 = 0; j0 < nlist; j0 += 16) {
@@ -960,11 +1058,15 @@ __global__ void __launch_bounds__(kNT, 4) k_greedy_round(GreedyArgs a) {
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
           const int nb = __shfl_sync(0xffffffffu, e, (j0 + j) & 31);
-          cand[j] = (j0 + j < nlist && lane < k) ? a.wl_in[(int64_t)(cs + nb) * k + lane] : -1;
+          cand[j] = (j0 + j < nlist && lane < k) ? wl_c[nb * k] : -1;
         }
 #pragma unroll
-        for (int j = 0; j < 16; ++j)
-          if (j0 + j < nlist) consider(cand[j]);
+        for (int j = 0; j < 16; ++j) {
+          if (j0 + j < nlist) {
+            if ((dedupe_only >> (j0 + j)) & 1u) mark(cand[j]);
+            else consider(cand[j]);
+          }
+        }
       }
       for (int d0 = 0; d0 < a.n_random; d0 += 32) {
         int v = -1;
@@ -975,9 +1077,12 @@ __global__ void __launch_bounds__(kNT, 4) k_greedy_round(GreedyArgs a) {
         }
         consider(v);
       }
-      if (lane < k) a.wl_out[(int64_t)slot * k + lane] = Lst.id;
+      tk.finish();
+      int32_t nid;
+      if constexpr (Keyed) nid = tk.id(); else nid = tk.L.id;
+      if (lane < k) a.wl_out[(int64_t)slot * k + lane] = nid;
       if (a.chg_out) {
-        const bool moved = __any_sync(0xffffffffu, lane < k && Lst.id != e);
+        const bool moved = __any_sync(0xffffffffu, lane < k && nid != e);
         unsigned f = fresh;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
@@ -1176,10 +1281,11 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
   const int small_cut = tc.W ? kSmallCut : (1 << 30);
 
   Prof p_prep(st, "knn_prep");
+  C2_LAUNCH(k_set_count, 1, 1, 0, st, &w.hdr->knn_max_len, 0);
+  C2_LAUNCH(k_slot_info, div_up(S, T), T, 0, st, cptr, n_clusters, cusers, ptr, S, w.slot2c,
+            w.slen, w.hdr);
   C2_LAUNCH(k_prep, div_up(S, T), T, 0, st, cptr, n_clusters, S, thr, small_cut, k, w.gflag,
             w.gkind_c, lid, lin, lun, w.hdr);
-  C2_LAUNCH(k_slot_info, div_up(S, T), T, 0, st, cptr, n_clusters, cusers, ptr, S, w.slot2c,
-            w.slen);
   C2_CUDA_TRY(cudaGetLastError());
   if (tc.W) {
     c2_status rc = build_padded_csr(ptr, items, s, w, st);
@@ -1202,8 +1308,10 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
   C2_CUDA_TRY(scan_exclusive(w.gflag, w.gidx, S, w.scan_tmp, st));
   C2_LAUNCH(k_greedy_list, div_up(S, T), T, 0, st, w.gflag, w.gidx, w.gkind_c, cptr, S, w.gcl,
             w.gsq, w.gsz, w.gkind, w.hdr);
-  int32_t ng = 0;
+  int32_t ng = 0, max_len = 0;
   C2_CUDA_TRY(cudaMemcpyAsync(&ng, &w.hdr->n_work, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  C2_CUDA_TRY(cudaMemcpyAsync(&max_len, &w.hdr->knn_max_len, sizeof(int32_t),
+                              cudaMemcpyDeviceToHost, st));
   C2_CUDA_TRY(cudaStreamSynchronize(st));
   if (ng == 0) return C2_OK;
   C2_CUDA_TRY(scan_exclusive64(w.gsq, w.goff, ng, w.scan_tmp64, st));
@@ -1215,8 +1323,11 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
   C2_CUDA_TRY(cudaMemcpyAsync(gkind.data(), w.gkind, ng * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   C2_CUDA_TRY(cudaStreamSynchronize(st));
   const int64_t cap = s.gram_budget / (int64_t)sizeof(uint16_t);
+  // exact 64-bit order keys need unions and local ids below 2^16
+  bool keyed = max_len <= 32767;
   for (int g = 0; g < ng; ++g) {
     if ((gkind[g] && gsz[g] > kMaxGreedyM) || goff[g + 1] - goff[g] > cap) return C2_ERR_UNSUPPORTED;
+    if (gsz[g] > 65535) keyed = false;
   }
   C2_LAUNCH(k_iota, div_up(ng, T), T, 0, st, w.gseq, (int64_t)ng);
   const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
@@ -1363,7 +1474,8 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
       ra.cptr = cptr; ra.cusers = cusers; ra.slen = w.slen; ra.gcl = w.gcl; ra.gofs = w.gofs;
       ra.gram = w.gram; ra.u_slot = w.ub_slot; ra.u_g = w.ub_g; ra.n_users_dev = w.bb_off + nb;
       ra.k = k; ra.out_id = lid; ra.out_in = lin; ra.out_un = lun; ra.hdr = w.hdr;
-      C2_LAUNCH(k_gram_topk, div_up(n_brute_users * 32, kNT), kNT, 0, st, ra);
+      if (keyed) C2_LAUNCH(k_gram_topk<true>, div_up(n_brute_users * 32, kNT), kNT, 0, st, ra);
+      else C2_LAUNCH(k_gram_topk<false>, div_up(n_brute_users * 32, kNT), kNT, 0, st, ra);
     }
     if (n_greedy_users) {
       GreedyArgs ga{};
@@ -1398,9 +1510,10 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
       {
         Prof p_rounds(st, "greedy_rounds");
         const int smem = 21 * ga.mcap;
-        C2_CUDA_TRY(cudaFuncSetAttribute(k_greedy_round, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        auto kround = keyed ? k_greedy_round<true> : k_greedy_round<false>;
+        C2_CUDA_TRY(cudaFuncSetAttribute(kround, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
         int per_sm = 0;
-        C2_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_greedy_round, kNT, smem));
+        C2_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kround, kNT, smem));
         if (per_sm < 1) return C2_ERR_UNSUPPORTED;
         static const char* kRoundName[] = {"round_01", "round_02", "round_03", "round_04",
                                            "round_05", "round_06", "round_07", "round_08",
@@ -1415,7 +1528,7 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
           ga.chg_out = skipping ? chg_nxt : nullptr;
           std::swap(chg_cur, chg_nxt);
           C2_CUDA_TRY(cudaMemsetAsync(ga.counter, 0, sizeof(unsigned), st));
-          C2_LAUNCH(k_greedy_round, num_sms() * per_sm, kNT, smem, st, ga);
+          C2_LAUNCH(kround, num_sms() * per_sm, kNT, smem, st, ga);
           std::swap(cur, nxt);
         }
       }
