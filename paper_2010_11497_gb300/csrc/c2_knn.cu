@@ -624,7 +624,7 @@ __global__ void __launch_bounds__(kNT) k_merge_knn(MergeArgs a) {
     const int c = a.slot2c[row];
     cbase = a.cptr[c];
     M = a.cptr[c + 1] - cbase;
-    if (M < 2 || M >= a.thr || (M >= a.max_m && a.hdr->knn_max_len <= 65535)) return;
+    if (M < 2 || M >= a.thr || M >= a.max_m) return;
     u = a.cusers[row];
     clist = a.cusers;
   } else {
@@ -682,12 +682,10 @@ __global__ void k_prep(const int32_t* __restrict__ cptr, const int32_t* __restri
   if (c < S && c < L) M = cptr[c + 1] - cptr[c];
   const bool brute = M >= 2 && M < thr;
   const bool greedy = M >= 2 && M >= thr;
-  // counts are 16-bit: with a profile of more than 65535 items, brute-force
-  // clusters go to the merge kernel and greedy clusters are unsupported
-  const bool wide = hdr->knn_max_len > 65535;
-  if (greedy && wide) dev_fail(hdr, C2_ERR_UNSUPPORTED);
+  // counts are 16-bit: profiles of more than 65535 items are unsupported
+  if (c == 0 && hdr->knn_max_len > 65535) dev_fail(hdr, C2_ERR_UNSUPPORTED);
   if (c < S) {
-    gflag[c] = (greedy || (brute && M >= small_cut && !wide)) ? 1 : 0;
+    gflag[c] = (greedy || (brute && M >= small_cut)) ? 1 : 0;
     gkind[c] = greedy ? 1 : 0;
     if (M == 1) {
       const int64_t s = cptr[c];

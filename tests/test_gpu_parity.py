@@ -312,3 +312,79 @@ def test_workspace_too_small(c2):
     with pytest.raises(c2.C2Error) as e:
         c2.c2_build_knn_graph(to_dev(ptr), to_dev(items), 50, 5, 2, 8, 10, 1, ws=ws)
     assert e.value.code == 4
+
+
+def _with_long_profiles(ptr, items, m, lens, seed):
+    """Appends users whose profiles hold `lens` distinct random items."""
+    rng = np.random.default_rng(seed)
+    rows = [items[ptr[u]:ptr[u + 1]] for u in range(ptr.size - 1)]
+    rows += [np.sort(rng.choice(m, L, replace=False)) for L in lens]
+    lens_all = np.array([r.size for r in rows])
+    nptr = np.concatenate([[0], np.cumsum(lens_all)]).astype(np.int32)
+    return nptr, np.concatenate(rows).astype(np.int32)
+
+
+def test_build_long_profiles_unkeyed(c2):
+    # unions may exceed 2^16: lists keep (id, inter, union) entries instead of
+    # 64-bit order keys; brute-force and greedy clusters both
+    m = 40000
+    ptr, items = synth.random_profiles(2500, m, 20, 31, zipf_s=1.05)
+    ptr, items = _with_long_profiles(ptr, items, m, [33000, 34000, 20000], 5)
+    n, k, t, b, N, seed, thr = ptr.size - 1, 10, 3, 8, 600, 7, 150
+    oid, oin, oun, pairs = oracle.build_graph(ptr, items, m, k, t, b, N, seed, thr, 3)
+    opts = c2.options(greedy_threshold=thr, greedy_rounds=3)
+    ws = c2.workspace(c2.workspace_size(n, items.size, m, k, t, b, N, opts), DEV)
+    gid, gin, gun = c2.c2_build_knn_graph(to_dev(ptr), to_dev(items), m, k, t, b, N, seed,
+                                          opts=opts, ws=ws)
+    st = c2.c2_get_stats(ws)
+    assert st["max_profile"] == 34000 and st["n_greedy_clusters"] > 0
+    assert_same(gid, oid, "nbr_id")
+    assert_same(gin, oin, "nbr_inter")
+    assert_same(gun, oun, "nbr_union")
+    assert st["pairs"] == pairs
+
+
+def test_cluster_knn_profile_beyond_limit(c2):
+    # c2_cluster_knn does not validate profiles: one longer than 65535 items
+    # (16-bit counts) is reported as unsupported on the device
+    m = 70000
+    ptr, items = synth.random_profiles(400, m, 10, 32)
+    ptr, items = _with_long_profiles(ptr, items, m, [66000], 6)
+    n = ptr.size - 1
+    cptr = np.array([0, n], np.int32)
+    cusers = np.arange(n, dtype=np.int32)
+    ws = c2.workspace(c2.workspace_size(n, items.size, m, 5, 1, 2, 1000), DEV)
+    c2.c2_reset_status(ws)
+    c2.c2_cluster_knn(to_dev(ptr), to_dev(items), m, 1, to_dev(cptr), to_dev(cusers),
+                      to_dev(np.array([1], np.int32)), 5, 1, ws=ws)
+    assert c2.c2_get_status(ws) == 3
+
+
+def test_build_duplicate_and_empty_profiles(c2):
+    # many exact ties: copies of 40 template profiles (Jaccard 1 and equal
+    # values broken by id), plus a greedy-sized cluster of empty profiles
+    rng = np.random.default_rng(33)
+    m = 600
+    tmpl = [np.sort(rng.choice(m, rng.integers(5, 40), replace=False)) for _ in range(40)]
+    rows = []
+    for u in range(2400):
+        r = tmpl[rng.integers(0, 40)]
+        if rng.random() < 0.3:
+            r = np.union1d(r, rng.choice(m, 1))
+        rows.append(r)
+    rows += [np.zeros(0, np.int64)] * 300
+    perm = rng.permutation(len(rows))
+    rows = [rows[i] for i in perm]
+    ptr = np.concatenate([[0], np.cumsum([r.size for r in rows])]).astype(np.int32)
+    items = np.concatenate(rows).astype(np.int32)
+    n, k, t, b, N, seed, thr = ptr.size - 1, 12, 3, 16, 500, 8, 120
+    oid, oin, oun, pairs = oracle.build_graph(ptr, items, m, k, t, b, N, seed, thr, 4)
+    opts = c2.options(greedy_threshold=thr, greedy_rounds=4)
+    ws = c2.workspace(c2.workspace_size(n, items.size, m, k, t, b, N, opts), DEV)
+    gid, gin, gun = c2.c2_build_knn_graph(to_dev(ptr), to_dev(items), m, k, t, b, N, seed,
+                                          opts=opts, ws=ws)
+    assert c2.c2_get_stats(ws)["n_greedy_clusters"] > 0
+    assert_same(gid, oid, "nbr_id")
+    assert_same(gin, oin, "nbr_inter")
+    assert_same(gun, oun, "nbr_union")
+    assert c2.c2_get_stats(ws)["pairs"] == pairs
