@@ -82,7 +82,8 @@ void bind_knn_ws(Ws& w, const Sizes& s, KnnWs& c) {
   c.bb_off = w.take<int32_t>(S + 1);
   c.ub_slot = w.take<int32_t>(S + 1);
   c.ub_g = w.take<int32_t>(S + 1);
-  c.ord = w.take<int32_t>(S + 1);
+  c.ipos = w.take<int32_t>(S + 1);
+  c.iinfo = w.take<int2>(S + 1);
   c.chg0 = w.take<int32_t>(S + 1);
   c.chg1 = w.take<int32_t>(S + 1);
   c.gfresh = w.take<int32_t>(S + 1);

@@ -125,7 +125,8 @@ struct KnnWs {
   int32_t* gkind;          // [S+1] per count-matrix cluster
   int32_t *bb_cnt, *bb_off;// [S+1] brute-force users per cluster of a batch
   int32_t *ub_slot, *ub_g; // [S+1] brute-force users of a batch
-  int32_t* ord;            // [S+1] candidate order inside each cluster
+  int32_t* ipos;           // [S+1] slot -> internal position in its cluster
+  int2* iinfo;             // [S+1] internal slot -> (local index, profile length)
   int32_t *chg0, *chg1;    // [S+1] greedy: list changed in the last round
   int32_t* gfresh;         // [S+1] greedy: evaluations of the last computed round
   int32_t* pptr;           // [n+1] padded CSR offsets
@@ -373,23 +374,28 @@ struct WarpTopk {
 };
 
 // ------------------------------------------------------------ keyed lists
-// Exact order key of a neighbour (c common items, u union, local id) when
-// u < 2^16 (hence c <= u < 2^16): K = floor(c * 2^32 / u) keeps equal Jaccard
-// values equal and separates different ones (they differ by at least
-// 1/(u u') > 2^-32), and the low 16 bits hold 0xffff - id so that equal
-// values rank the lower id first.  Larger key = better neighbour; 0 = empty.
-// K is assembled from two 32-bit divisions: c*2^16 = q1*u + r1, then
-// r1*2^16 / u, both exact because c, r1 < 2^16.
-__device__ __forceinline__ uint64_t nbr_key(uint32_t c, uint32_t u, int32_t lid) {
+// Exact order key of a neighbour (c common items, u union, local index `lid`
+// in the cluster's user-id order, position `pos` in the cluster's internal
+// order) when u < 2^16 (hence c <= u < 2^16) and the cluster has fewer than
+// 2^14 members.  K = floor(c * 2^32 / u) keeps equal Jaccard values equal
+// and separates different ones (they differ by at least 1/(u u') > 2^-32);
+// below K sits 16383 - lid, so that equal values rank the lower id first,
+// and then pos, which only carries the position along.  Larger key = better
+// neighbour; 0 = empty.  K comes from two 32-bit divisions: c*2^16 = q1*u +
+// r1, then r1*2^16 / u, both exact because c, r1 < 2^16.
+__device__ __forceinline__ uint64_t nbr_key(uint32_t c, uint32_t u, int32_t lid, int32_t pos) {
   const uint32_t ud = u ? u : 1u;            // c = u = 0 only for two empty profiles
   const uint32_t a = c << 16;
   const uint32_t q1 = a / ud, r1 = a - q1 * ud;
   const uint32_t q2 = (r1 << 16) / ud;
   const uint64_t K = c ? (((uint64_t)q1 << 16) | q2) : 0ull;
-  return (K << 16) | (uint64_t)(0xffffu - (uint32_t)lid);
+  return (K << 30) | ((uint64_t)(16383u - (uint32_t)lid) << 14) | (uint64_t)(uint32_t)pos;
 }
 __device__ __forceinline__ int32_t key_id(uint64_t key) {
-  return key ? (int32_t)(0xffffu - (uint32_t)(key & 0xffffu)) : -1;
+  return key ? (int32_t)(16383u - (uint32_t)((key >> 14) & 0x3fffu)) : -1;
+}
+__device__ __forceinline__ int32_t key_pos(uint64_t key) {
+  return key ? (int32_t)(key & 0x3fffu) : -1;
 }
 
 // Bitonic sort of one key per lane, largest first (32 lanes).
@@ -439,18 +445,20 @@ __device__ __forceinline__ void key_list_insert(uint64_t& e, int k, uint64_t key
   if (lane >= k) e = 0ull;
 }
 
-// WarpTopk on order keys, for rows whose unions are below 2^16: the filter
-// compares 32-bit cross products against the k-th entry, staged candidates
-// get their keys in one batch, and lists are merged and shifted as single
-// 64-bit keys.  CU maps a local id to its (common, union) counts; it is used
-// to refresh the filter after the list changed.
+// WarpTopk on order keys, for rows whose unions are below 2^16 in clusters
+// of fewer than 2^14 members: the filter compares 32-bit cross products
+// against the k-th entry, staged candidates get their keys in one batch, and
+// lists are merged and shifted as single 64-bit keys.  Candidates carry their
+// local index (order) and internal position (storage); CU maps an internal
+// position to its (common, union) counts, used to refresh the filter after
+// the list changed.
 template <class CU>
 struct KeyTopk {
   uint64_t L;      // lane i < k: key of the i-th best (0 = empty)
   uint32_t Tc, Tu;
   uint32_t Tid;    // k-th entry, (0, 1, 0x7fffffff) while the list is not full
   int n, k;        // staged entries (uniform), list length
-  uint2* stg;      // shared [64]: (id, c | u << 16)
+  uint2* stg;      // shared [64]: (pos | lid << 16, c | u << 16)
   CU cu;
 
   __device__ __forceinline__ void refresh() {
@@ -459,7 +467,7 @@ struct KeyTopk {
       Tc = 0u; Tu = 1u; Tid = 0x7fffffffu;
     } else {
       Tid = (uint32_t)key_id(kth);
-      const uint2 x = cu((int32_t)Tid);
+      const uint2 x = cu(key_pos(kth));
       Tc = x.x; Tu = x.y;
     }
   }
@@ -471,9 +479,12 @@ struct KeyTopk {
     cu = cu_;
     refresh();
   }
-  __device__ __forceinline__ bool filter(int32_t id, uint32_t c, uint32_t u) const {
+  __device__ __forceinline__ bool filter(int32_t lid, uint32_t c, uint32_t u) const {
     const uint32_t l = c * Tu, r = Tc * u;
-    return l > r || (l == r && (uint32_t)id < Tid);
+    return l > r || (l == r && (uint32_t)lid < Tid);
+  }
+  __device__ __forceinline__ static uint64_t key_of(uint2 x) {
+    return nbr_key(x.y & 0xffffu, x.y >> 16, (int32_t)(x.x >> 16), (int32_t)(x.x & 0xffffu));
   }
   __device__ __forceinline__ void drain32() {
     const int lane = threadIdx.x & 31;
@@ -486,13 +497,15 @@ struct KeyTopk {
     if (lane < rest) stg[lane] = y;
     __syncwarp();
     n = rest;
-    L = key_list_merge(L, k, nbr_key(x.y & 0xffffu, x.y >> 16, (int32_t)x.x));
+    L = key_list_merge(L, k, key_of(x));
     refresh();
   }
-  __device__ __forceinline__ void stage(bool pass, int32_t id, uint32_t c, uint32_t u) {
+  __device__ __forceinline__ void stage(bool pass, int32_t pos, int32_t lid, uint32_t c, uint32_t u) {
     const unsigned m = __ballot_sync(0xffffffffu, pass);
     if (m == 0u) return;
-    if (pass) stg[n + __popc(m & lanemask_lt())] = make_uint2((uint32_t)id, c | (u << 16));
+    if (pass)
+      stg[n + __popc(m & lanemask_lt())] =
+          make_uint2((uint32_t)pos | ((uint32_t)lid << 16), c | (u << 16));
     n += __popc(m);
     if (n >= 32) drain32();
   }
@@ -501,10 +514,7 @@ struct KeyTopk {
     const int lane = threadIdx.x & 31;
     __syncwarp();
     uint64_t key = 0ull;
-    if (lane < n) {
-      const uint2 x = stg[lane];
-      key = nbr_key(x.y & 0xffffu, x.y >> 16, (int32_t)x.x);
-    }
+    if (lane < n) key = key_of(stg[lane]);
     __syncwarp();
     if (n > 8) {
       L = key_list_merge(L, k, key);
@@ -515,6 +525,7 @@ struct KeyTopk {
     refresh();
   }
   __device__ __forceinline__ int32_t id() const { return key_id(L); }
+  __device__ __forceinline__ int32_t pos() const { return key_pos(L); }
 };
 
 inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }

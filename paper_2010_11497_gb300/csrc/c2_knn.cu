@@ -288,13 +288,15 @@ __global__ void __launch_bounds__(NT) k_table(TableArgs a) {
 }
 
 // ------------------------------------------------------------------ gram kernel
-// Count matrix of one cluster, G[v][q] = |P_v n P_q| for members v, q (local
-// indices), stored in rows of stride Mp = round_up(M, 8).  A work item is a
-// tile of Q = 32*W query members marked in the shared table; the cluster's
-// candidates are taken 32 at a time by whichever warp is free, in order of
-// decreasing profile length (so the lanes of a warp walk rows of similar
-// length), and each thread writes its candidate's counts against the tile's
-// queries as one contiguous row segment (the matrix is symmetric).
+// Count matrix of one cluster, G[p][q] = |P_p n P_q| for members at internal
+// positions p, q (the cluster's members by decreasing profile length), stored
+// in rows of stride Mp = round_up(M, 8).  A work item is a tile of Q = 32*W
+// query positions marked in the shared table; the candidates are the
+// positions from the tile on (the matrix is symmetric), taken 32 at a time by
+// whichever warp is free, so that the lanes of a warp walk profiles of
+// similar length.  Each thread writes its candidate's counts against the
+// tile's queries as one contiguous row segment and, for candidates past the
+// tile, the mirrored column (32 consecutive positions per warp store).
 struct GramArgs {
   const int32_t* ptr;
   const int32_t* items;
@@ -307,7 +309,7 @@ struct GramArgs {
   const int32_t* work_end;
   const int32_t* cptr;
   const int32_t* cusers;
-  const int32_t* ord;      // per slot: candidate order (local indices) of its cluster
+  const int2* iinfo;       // internal slot -> (local index, profile length)
   const int64_t* gofs;
   uint16_t* gram;
   DevHeader* hdr;
@@ -334,7 +336,7 @@ __global__ void __launch_bounds__(NT) k_gram(GramArgs a) {
     const int c = a.work_c[wi], tq = a.work_t[wi];
     const int cbase = a.cptr[c], M = a.cptr[c + 1] - cbase, Mp = (M + 7) & ~7;
     const int nq = min(Q, M - tq * Q);
-    if (tid < Q) q_id[tid] = tid < nq ? a.cusers[cbase + tq * Q + tid] : -1;
+    if (tid < Q) q_id[tid] = tid < nq ? a.cusers[cbase + a.iinfo[cbase + tq * Q + tid].x] : -1;
     __syncthreads();
     for (int j = warp; j < nq; j += NWARP) {
       const int u = q_id[j];
@@ -342,25 +344,26 @@ __global__ void __launch_bounds__(NT) k_gram(GramArgs a) {
         atomicOr(&T[a.items[e] * W + (j >> 5)], 1u << (j & 31));
     }
     __syncthreads();
-    uint16_t* Gc = a.gram + a.gofs[c] + tq * Q;
+    uint16_t* G0 = a.gram + a.gofs[c];
+    uint16_t* Gc = G0 + tq * Q;
     for (;;) {
       int p0 = 0;
       if (lane == 0) p0 = atomicAdd(&s_next, 32);
-      p0 = __shfl_sync(0xffffffffu, p0, 0);
+      p0 = tq * Q + __shfl_sync(0xffffffffu, p0, 0);
       if (p0 >= M) break;
       const int p = p0 + lane;
       if (p < M) {
-        const int vl = a.ord[cbase + p];
-        const int v = a.cusers[cbase + vl];
-        const int len = a.ptr[v + 1] - a.ptr[v];
+        const int2 info = a.iinfo[cbase + p];
+        const int v = a.cusers[cbase + info.x];
+        const int len = info.y;
         uint32_t C[16 * W];
 #pragma unroll
         for (int r = 0; r < 16 * W; ++r) C[r] = 0;
         count_row4<W>(reinterpret_cast<const int4*>(a.pitems + a.pptr[v]), (len + 3) >> 2, T,
                       a.n_items, C);
         visits += (unsigned)len;
-        // row vl, columns tq*Q .. tq*Q + nq (16-byte stores, padding columns allowed)
-        uint4* dst = reinterpret_cast<uint4*>(Gc + (int64_t)vl * Mp);
+        // row p, columns tq*Q .. tq*Q + nq (16-byte stores, padding columns allowed)
+        uint4* dst = reinterpret_cast<uint4*>(Gc + (int64_t)p * Mp);
 #pragma unroll
         for (int g8 = 0; g8 < Q / 8; ++g8) {
           if (g8 * 8 < nq) {
@@ -374,6 +377,13 @@ __global__ void __launch_bounds__(NT) k_gram(GramArgs a) {
             }
             dst[g8] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
           }
+        }
+        // column p of the tile's rows (the tile's own block is computed whole)
+        if (p >= (tq + 1) * Q) {
+          uint16_t* col = G0 + (int64_t)(tq * Q) * Mp + p;
+#pragma unroll
+          for (int j = 0; j < Q; ++j)
+            if (j < nq) col[(int64_t)j * Mp] = (uint16_t)((C[creg(j)] >> (16 * chalf(j))) & 0xFFFFu);
         }
       }
     }
@@ -406,31 +416,34 @@ struct MergeGramArgs {
   const int32_t* u_slot;
   const int32_t* u_g;
   const int32_t* n_users_dev;
+  const int32_t* ipos;
+  const int2* iinfo;
   DevHeader* hdr;
 };
 
+// One warp per member (a slot in user-id order): its row at its internal
+// position, columns in internal order.
 __global__ void __launch_bounds__(256) k_merge_gram(MergeGramArgs a) {
   const int lane = threadIdx.x & 31;
   const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (w >= *a.n_users_dev || dev_failed(a.hdr)) return;
   const int slot = a.u_slot[w];
   const int c = a.gcl[a.u_g[w]];
-  const int cs = a.cptr[c], M = a.cptr[c + 1] - cs, l = slot - cs, Mp = (M + 7) & ~7;
+  const int cs = a.cptr[c], M = a.cptr[c + 1] - cs, Mp = (M + 7) & ~7;
   const int u = a.cusers[slot];
   const int32_t* ur = a.items + a.ptr[u];
   const int ul = a.ptr[u + 1] - a.ptr[u];
-  uint16_t* row = a.gram + a.gofs[c] + (int64_t)l * Mp;
-  for (int v0 = 0; v0 < M; v0 += 32) {
-    const int vl = v0 + lane;
-    if (vl < M) {
-      const int v = a.cusers[cs + vl];
-      row[vl] = (uint16_t)merge_count(ur, ul, a.items + a.ptr[v], a.ptr[v + 1] - a.ptr[v]);
+  uint16_t* row = a.gram + a.gofs[c] + (int64_t)a.ipos[slot] * Mp;
+  for (int p0 = 0; p0 < M; p0 += 32) {
+    const int p = p0 + lane;
+    if (p < M) {
+      const int v = a.cusers[cs + a.iinfo[cs + p].x];
+      row[p] = (uint16_t)merge_count(ur, ul, a.items + a.ptr[v], a.ptr[v + 1] - a.ptr[v]);
     }
   }
 }
 
-// Candidate order of a cluster: members by decreasing profile length, in 64
-// buckets (4 per octave); one block per cluster, counting sort in shared memory.
+// Length bucket: exact below 4, then 4 buckets per octave (at most 63).
 __device__ __forceinline__ int len_bucket(int len) {
   if (len < 4) return len;
   const int oct = 31 - __clz(len);                 // >= 2
@@ -438,29 +451,58 @@ __device__ __forceinline__ int len_bucket(int len) {
   return min(b, 63);
 }
 
+// Internal order of a cluster with a count matrix: members by decreasing
+// profile length (64 buckets, 4 per octave), stable within a bucket; one
+// block per cluster, chunks of 256 members placed in order.
+// ipos[slot] = internal position, iinfo[cluster start + position] = (local
+// index, profile length).
 __global__ void __launch_bounds__(256) k_order(const int32_t* __restrict__ gcl, int32_t g0,
                                                const int32_t* __restrict__ cptr,
                                                const int32_t* __restrict__ slen,
-                                               int32_t* __restrict__ ord) {
-  __shared__ int32_t cnt[64];
+                                               int32_t* __restrict__ ipos,
+                                               int2* __restrict__ iinfo) {
+  __shared__ int32_t start[64];
+  __shared__ int32_t wcnt[8][64];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int c = gcl[g0 + blockIdx.x];
   const int cbase = cptr[c], M = cptr[c + 1] - cbase;
-  if (threadIdx.x < 64) cnt[threadIdx.x] = 0;
+  if (tid < 64) start[tid] = 0;
   __syncthreads();
-  for (int i = threadIdx.x; i < M; i += blockDim.x) atomicAdd(&cnt[63 - len_bucket(slen[cbase + i])], 1);
+  for (int i = tid; i < M; i += 256) atomicAdd(&start[63 - len_bucket(slen[cbase + i])], 1);
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (tid == 0) {
     int acc = 0;
     for (int b = 0; b < 64; ++b) {
-      const int x = cnt[b];
-      cnt[b] = acc;
+      const int x = start[b];
+      start[b] = acc;
       acc += x;
     }
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < M; i += blockDim.x) {
-    const int pos = atomicAdd(&cnt[63 - len_bucket(slen[cbase + i])], 1);
-    ord[cbase + pos] = i;
+  for (int base = 0; base < M; base += 256) {
+    const int i = base + tid;
+    const int len = i < M ? slen[cbase + i] : 0;
+    const int bk = i < M ? 63 - len_bucket(len) : 64;
+    const unsigned peers = __match_any_sync(0xffffffffu, bk);
+    const int rank = __popc(peers & lanemask_lt());
+    wcnt[warp][lane] = 0;
+    wcnt[warp][lane + 32] = 0;
+    __syncwarp();
+    if (i < M && rank == 0) wcnt[warp][bk] = __popc(peers);
+    __syncthreads();
+    if (i < M) {
+      int off = start[bk] + rank;
+      for (int w2 = 0; w2 < warp; ++w2) off += wcnt[w2][bk];
+      ipos[cbase + i] = off;
+      iinfo[cbase + off] = make_int2(i, len);
+    }
+    __syncthreads();
+    if (tid < 64) {
+      int sum = 0;
+      for (int w2 = 0; w2 < 8; ++w2) sum += wcnt[w2][tid];
+      start[tid] += sum;
+    }
+    __syncthreads();
   }
 }
 
@@ -476,27 +518,30 @@ struct RowTopkArgs {
   const int32_t* u_slot;
   const int32_t* u_g;
   const int32_t* n_users_dev;
+  const int32_t* ipos;
+  const int2* iinfo;
   int32_t k;
   int32_t *out_id, *out_in, *out_un;
   DevHeader* hdr;
 };
 
-// (common, union) counts of a member of the warp's cluster from the global
-// row of counts and slot lengths.
+// (common, union) counts of a member of the warp's cluster, by internal
+// position, from the global row of counts and the internal (index, length).
 struct GlobalCU {
   const uint16_t* row;
-  const int32_t* len;      // slot lengths from the cluster's first slot
+  const int2* info;        // internal (local index, length) from the cluster's start
   uint32_t my;
-  __device__ __forceinline__ uint2 operator()(int32_t v) const {
-    const uint32_t c = row[v];
-    return make_uint2(c, my + (uint32_t)len[v] - c);
+  __device__ __forceinline__ uint2 operator()(int32_t p) const {
+    const uint32_t c = row[p];
+    return make_uint2(c, my + (uint32_t)info[p].y - c);
   }
 };
 
 // One warp per user of a brute-force cluster: the top k of the user's row of
 // intersection counts, 256 candidates per step (8 per lane, coalesced),
 // staged and merged; `Keyed` (every union below 2^16) holds the list as exact
-// 64-bit order keys.
+// 64-bit order keys.  Rows and columns are in internal order; candidates are
+// ranked by local index (user-id order).
 template <bool Keyed>
 __global__ void __launch_bounds__(kNT) k_gram_topk(RowTopkArgs a) {
   __shared__ int32_t s_sid[Keyed ? 1 : kNT / 32][64];
@@ -506,38 +551,41 @@ __global__ void __launch_bounds__(kNT) k_gram_topk(RowTopkArgs a) {
   if (w >= *a.n_users_dev || dev_failed(a.hdr)) return;
   const int slot = a.u_slot[w];
   const int c = a.gcl[a.u_g[w]];
-  const int cs = a.cptr[c], M = a.cptr[c + 1] - cs, l = slot - cs, Mp = (M + 7) & ~7;
-  const uint16_t* row = a.gram + a.gofs[c] + (int64_t)l * Mp;
+  const int cs = a.cptr[c], M = a.cptr[c + 1] - cs, Mp = (M + 7) & ~7;
+  const int P = a.ipos[slot];
+  const uint16_t* row = a.gram + a.gofs[c] + (int64_t)P * Mp;
+  const int2* info = a.iinfo + cs;
   const uint32_t my = (uint32_t)a.slen[slot];
   const int k = a.k;
   typename std::conditional<Keyed, KeyTopk<GlobalCU>, WarpTopk>::type tk;
   if constexpr (Keyed) {
-    tk.start(0ull, k, s_scu[warp], GlobalCU{row, a.slen + cs, my});
+    tk.start(0ull, k, s_scu[warp], GlobalCU{row, info, my});
   } else {
     WarpList l0;
     l0.id = -1; l0.c = 0; l0.u = 0;
     tk.start(l0, k, s_sid[warp], s_scu[warp]);
   }
-  for (int v0 = 0; v0 < M; v0 += 256) {
-    uint32_t cc[8], ln[8];
+  for (int p0 = 0; p0 < M; p0 += 256) {
+    uint32_t cc[8];
+    int2 in[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-      const int v = v0 + j * 32 + lane;
-      cc[j] = (v < M && v != l) ? (uint32_t)row[v] : 0u;
+      const int p = p0 + j * 32 + lane;
+      cc[j] = (p < M && p != P) ? (uint32_t)row[p] : 0u;
     }
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-      const int v = v0 + j * 32 + lane;
-      ln[j] = cc[j] > 0u ? (uint32_t)a.slen[cs + v] : 0u;
+      const int p = p0 + j * 32 + lane;
+      in[j] = cc[j] > 0u ? info[p] : make_int2(0, 0);
     }
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-      if (v0 + j * 32 >= M) break;
-      const int v = v0 + j * 32 + lane;
-      const uint32_t uu = my + ln[j] - cc[j];
-      // local index order = user id order
-      const bool pass = cc[j] > 0u && tk.filter(v, cc[j], uu);
-      tk.stage(pass, v, cc[j], uu);
+      if (p0 + j * 32 >= M) break;
+      const int p = p0 + j * 32 + lane;
+      const uint32_t uu = my + (uint32_t)in[j].y - cc[j];
+      const bool pass = cc[j] > 0u && tk.filter(in[j].x, cc[j], uu);
+      if constexpr (Keyed) tk.stage(pass, p, in[j].x, cc[j], uu);
+      else tk.stage(pass, in[j].x, cc[j], uu);
     }
   }
   tk.finish();
@@ -548,7 +596,7 @@ __global__ void __launch_bounds__(kNT) k_gram_topk(RowTopkArgs a) {
     if constexpr (Keyed) {
       id = tk.id();
       if (id >= 0) {
-        const uint2 x = GlobalCU{row, a.slen + cs, my}(id);
+        const uint2 x = GlobalCU{row, info, my}(tk.pos());
         oc = x.x; ou = x.y;
       }
     } else {
@@ -828,7 +876,7 @@ struct GreedyArgs {
   const int32_t* gcl;
   const int64_t* gofs;     // per cluster
   const uint16_t* gram;    // count rows of stride round_up(M, 8)
-  const int32_t* gu_slot;  // per-user launches: slot and greedy index
+  const int32_t* gu_slot;  // per-user launches: internal slot and greedy index
   const int32_t* gu_g;
   const int32_t* n_users_dev;
   const int32_t* gw_g;     // per-block launches: greedy index and user chunk
@@ -837,7 +885,9 @@ struct GreedyArgs {
   unsigned* counter;
   int32_t k, round, n_random, mcap;
   uint2 key;               // Philox key = run seed
-  const int32_t* wl_in;    // [S][k] local indices
+  const int32_t* ipos;     // slot -> internal position
+  const int2* iinfo;       // internal slot -> (local index, profile length)
+  const int32_t* wl_in;    // [S][k] internal positions, by internal slot
   int32_t* wl_out;
   const int32_t* chg_in;   // per slot: list changed in the previous round (NULL = no skipping)
   int32_t* chg_out;
@@ -853,6 +903,7 @@ __device__ __forceinline__ int draw_other(uint32_t r, int l, int M) {
 }
 
 // Round 0: k distinct random members per user (in draw order), then sorted.
+// Draws are local indices (user-id order); lists hold internal positions.
 __global__ void __launch_bounds__(kNT) k_greedy_init(GreedyArgs a) {
   __shared__ uint32_t bm_all[8][kBitmapWords];
   __shared__ int32_t drawn_all[8][kMaxK];
@@ -868,8 +919,10 @@ __global__ void __launch_bounds__(kNT) k_greedy_init(GreedyArgs a) {
     if (dev_failed(a.hdr)) break;
     const int slot = a.gu_slot[w];
     const int c = a.gcl[a.gu_g[w]];
-    const int cs = a.cptr[c], M = a.cptr[c + 1] - cs, l = slot - cs;
-    const uint16_t* G = a.gram + a.gofs[c] + (int64_t)l * ((M + 7) & ~7);
+    const int cs = a.cptr[c], M = a.cptr[c + 1] - cs, p = slot - cs;
+    const int2 me = a.iinfo[slot];
+    const int l = me.x;
+    const uint16_t* G = a.gram + a.gofs[c] + (int64_t)p * ((M + 7) & ~7);
     const int k = a.k, k0 = min(k, M - 1);
     int cnt = 0;
     // rejection sampling of distinct members; bounded so that no warp can
@@ -902,11 +955,11 @@ __global__ void __launch_bounds__(kNT) k_greedy_init(GreedyArgs a) {
     if (lane < cnt) {
       const int v = drawn[lane];
       Lst.id = v;
-      Lst.c = G[v];
-      Lst.u = (uint32_t)a.slen[slot] + (uint32_t)a.slen[cs + v] - Lst.c;
+      Lst.c = G[a.ipos[cs + v]];
+      Lst.u = (uint32_t)me.y + (uint32_t)a.slen[cs + v] - Lst.c;
     }
     warp_sort32(Lst);
-    if (lane < k) a.wl_out[(int64_t)slot * k + lane] = Lst.id;
+    if (lane < k) a.wl_out[(int64_t)slot * k + lane] = Lst.id >= 0 ? a.ipos[cs + Lst.id] : -1;
     if (lane == 0 && a.chg_out) a.chg_out[slot] = 1;
     __syncwarp();
     for (int q = lane; q < cnt; q += 32) {
@@ -919,25 +972,28 @@ __global__ void __launch_bounds__(kNT) k_greedy_init(GreedyArgs a) {
   if (lane == 0 && evals) atomicAdd(&a.hdr->pairs, evals);
 }
 
-// (common, union) counts of a member of the warp's cluster from the staged
-// row of counts and profile lengths (shared memory).
+// (common, union) counts of a member of the warp's cluster, by internal
+// position, from the staged row of counts and the packed (local index,
+// length) words (shared memory).
 struct SmemCU {
   const uint16_t* row;
-  const int32_t* len;
+  const uint32_t* info;
   uint32_t my;
-  __device__ __forceinline__ uint2 operator()(int32_t v) const {
-    const uint32_t c = row[v];
-    return make_uint2(c, my + (uint32_t)len[v] - c);
+  __device__ __forceinline__ uint2 operator()(int32_t p) const {
+    const uint32_t c = row[p];
+    return make_uint2(c, my + (info[p] & 0xffffu) - c);
   }
 };
 
 // One synchronous round.  A block takes a chunk of users of one cluster: the
-// cluster's profile lengths are staged in shared memory once, and every warp
-// stages its user's row of intersection counts before walking the
-// candidates (own list, neighbours' lists, optional random draws),
-// deduplicated with a per-warp bitmap of the cluster.  Candidates that beat
-// the current k-th neighbour are staged and merged 32 at a time; `Keyed`
-// (every union below 2^16) holds the list as exact 64-bit order keys.
+// cluster's (local index, profile length) words are staged in shared memory
+// once, and every warp stages its user's row of intersection counts before
+// walking the candidates (own list, neighbours' lists, optional random
+// draws), deduplicated with a per-warp bitmap of the cluster.  Candidates
+// that beat the current k-th neighbour are staged and merged 32 at a time;
+// `Keyed` (every union below 2^16) holds the list as exact 64-bit order keys.
+// Users, lists and rows are in internal order; candidates are ranked by
+// local index (user-id order).
 //
 // Without random draws, from round 2 on, the list of a neighbour v is known
 // not to contribute when v was already in the user's list two rounds back and
@@ -952,7 +1008,8 @@ __global__ void __launch_bounds__(kNT, 4) k_greedy_round(GreedyArgs a) {
   __shared__ int32_t s_sid[Keyed ? 1 : 8][64];
   __shared__ uint2 s_scu[8][64];
   const int mcap = a.mcap;                               // multiple of 32
-  int32_t* s_len = reinterpret_cast<int32_t*>(gsm);      // [mcap]
+  // keyed: local index << 16 | length; otherwise the length alone
+  uint32_t* s_info = gsm;                                // [mcap]
   uint16_t* s_rows = reinterpret_cast<uint16_t*>(gsm + mcap);   // [8][mcap]
   uint32_t* s_bm = gsm + mcap + 4 * mcap;                // [8][mcap/32]
   __shared__ int s_work;
@@ -971,10 +1028,23 @@ __global__ void __launch_bounds__(kNT, 4) k_greedy_round(GreedyArgs a) {
     const int g = a.gw_g[wi], chunk = a.gw_t[wi];
     const int c = a.gcl[g];
     const int cs = a.cptr[c], M = a.cptr[c + 1] - cs, Mp = (M + 7) & ~7;
-    for (int v = threadIdx.x; v < M; v += kNT) s_len[v] = a.slen[cs + v];
+    const int2* info_g = a.iinfo + cs;
+    for (int v = threadIdx.x; v < M; v += kNT) {
+      const int2 x = info_g[v];
+      s_info[v] = Keyed ? (((uint32_t)x.x << 16) | (uint32_t)x.y) : (uint32_t)x.y;
+    }
     __syncthreads();
     const uint16_t* Gc = a.gram + a.gofs[c];
     const int32_t* wl_c = a.wl_in + (int64_t)cs * k + lane;
+    // local index and length of the member at internal position x
+    auto lid_of = [&](int x) -> int {
+      if constexpr (Keyed) return (int)(s_info[x] >> 16);
+      else return info_g[x].x;
+    };
+    auto len_of = [&](int x) -> uint32_t {
+      if constexpr (Keyed) return s_info[x] & 0xffffu;
+      else return s_info[x];
+    };
     for (int uu = 0; uu < kGreedyUsersPerWarp; ++uu) {
       const int l = chunk * kGreedyChunk + uu * 8 + warp;
       if (l >= M) break;
@@ -1014,19 +1084,22 @@ __global__ void __launch_bounds__(kNT, 4) k_greedy_round(GreedyArgs a) {
         if (p >= 0) bm[p >> 5] = 0u;     // only these bits are set
         __syncwarp();
       }
-      const uint32_t my = (uint32_t)s_len[l];
+      const uint32_t my = len_of(l);
+      const int lid_me = lid_of(l);
       const uint32_t c0 = e >= 0 ? row[e] : 0u;
-      const uint32_t u0 = e >= 0 ? my + (uint32_t)s_len[e] - c0 : 0u;
+      const uint32_t u0 = e >= 0 ? my + len_of(e) - c0 : 0u;
+      const int lid0 = e >= 0 ? lid_of(e) : -1;
       if (e >= 0) atomicOr(&bm[e >> 5], 1u << (e & 31));
       if (lane == 0) atomicOr(&bm[l >> 5], 1u << (l & 31));
       const int nlist = __popc(__ballot_sync(0xffffffffu, e >= 0));
       __syncwarp();
       typename std::conditional<Keyed, KeyTopk<SmemCU>, WarpTopk>::type tk;
       if constexpr (Keyed) {
-        tk.start(e >= 0 ? nbr_key(c0, u0, e) : 0ull, k, s_scu[warp], SmemCU{row, s_len, my});
+        tk.start(e >= 0 ? nbr_key(c0, u0, lid0, e) : 0ull, k, s_scu[warp],
+                 SmemCU{row, s_info, my});
       } else {
         WarpList l0;
-        l0.id = e; l0.c = c0; l0.u = u0;
+        l0.id = lid0; l0.c = c0; l0.u = u0;
         tk.start(l0, k, s_sid[warp], s_scu[warp]);
       }
       unsigned fresh = 0;
@@ -1041,9 +1114,20 @@ __global__ void __launch_bounds__(kNT, 4) k_greedy_round(GreedyArgs a) {
         const uint32_t bit = 1u << (x & 31);
         const bool isnew = (atomicOr(&bm[x >> 5], bit) & bit) == 0u;
         const uint32_t cc = row[x];
-        const uint32_t uu2 = my + (uint32_t)s_len[x] - cc;
+        uint32_t uu2;
+        int lx;
+        if constexpr (Keyed) {
+          const uint32_t inf = s_info[x];
+          uu2 = my + (inf & 0xffffu) - cc;
+          lx = (int)(inf >> 16);
+        } else {
+          uu2 = my + s_info[x] - cc;
+          lx = info_g[x].x;
+        }
         fresh += isnew ? 1u : 0u;
-        tk.stage(isnew && tk.filter(x, cc, uu2), x, cc, uu2);
+        const bool pass = isnew && tk.filter(lx, cc, uu2);
+        if constexpr (Keyed) tk.stage(pass, x, lx, cc, uu2);
+        else tk.stage(pass, lx, cc, uu2);
       };
       auto mark = [&](int v) {
         const int x = v >= 0 ? v : l;
@@ -1069,15 +1153,19 @@ __global__ void __launch_bounds__(kNT, 4) k_greedy_round(GreedyArgs a) {
       for (int d0 = 0; d0 < a.n_random; d0 += 32) {
         int v = -1;
         if (d0 + lane < a.n_random) {
-          const uint4 r = philox10(make_uint4((uint32_t)c, (uint32_t)l, (uint32_t)a.round,
+          const uint4 r = philox10(make_uint4((uint32_t)c, (uint32_t)lid_me, (uint32_t)a.round,
                                               (uint32_t)(d0 + lane)), a.key);
-          v = draw_other(r.x, l, M);
+          v = a.ipos[cs + draw_other(r.x, lid_me, M)];
         }
         consider(v);
       }
       tk.finish();
       int32_t nid;
-      if constexpr (Keyed) nid = tk.id(); else nid = tk.L.id;
+      if constexpr (Keyed) {
+        nid = tk.pos();
+      } else {
+        nid = tk.L.id >= 0 ? a.ipos[cs + tk.L.id] : -1;
+      }
       if (lane < k) a.wl_out[(int64_t)slot * k + lane] = nid;
       if (a.chg_out) {
         const bool moved = __any_sync(0xffffffffu, lane < k && nid != e);
@@ -1101,24 +1189,27 @@ __global__ void __launch_bounds__(kNT, 4) k_greedy_round(GreedyArgs a) {
   if (lane == 0 && computed) atomicAdd(&a.hdr->greedy_computed, computed);
 }
 
-// Final rows: global ids, zero-similarity entries dropped (they sort last).
+// Final rows: global ids, zero-similarity entries dropped (they sort last);
+// the row of internal slot cs + p is written at its user's slot.
 __global__ void __launch_bounds__(kNT) k_greedy_emit(GreedyArgs a) {
   const int lane = threadIdx.x & 31;
   const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (w >= *a.n_users_dev || dev_failed(a.hdr)) return;
   const int slot = a.gu_slot[w];
   const int c = a.gcl[a.gu_g[w]];
-  const int cs = a.cptr[c], M = a.cptr[c + 1] - cs, l = slot - cs;
-  const uint16_t* G = a.gram + a.gofs[c] + (int64_t)l * ((M + 7) & ~7);
+  const int cs = a.cptr[c], M = a.cptr[c + 1] - cs, p = slot - cs;
+  const uint16_t* G = a.gram + a.gofs[c] + (int64_t)p * ((M + 7) & ~7);
   const int k = a.k;
   if (lane >= k) return;
+  const int2 me = a.iinfo[slot];
   const int e = a.wl_in[(int64_t)slot * k + lane];
-  const int64_t o = (int64_t)slot * k + lane;
+  const int64_t o = (int64_t)(cs + me.x) * k + lane;
   uint32_t cc = e >= 0 ? G[e] : 0u;
   if (e >= 0 && cc > 0) {
-    a.out_id[o] = a.cusers[cs + e];
+    const int2 x = a.iinfo[cs + e];
+    a.out_id[o] = a.cusers[cs + x.x];
     a.out_in[o] = (int32_t)cc;
-    a.out_un[o] = a.slen[slot] + a.slen[cs + e] - (int32_t)cc;
+    a.out_un[o] = me.y + x.y - (int32_t)cc;
   } else {
     a.out_id[o] = -1;
     a.out_in[o] = 0;
@@ -1321,11 +1412,11 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
   C2_CUDA_TRY(cudaMemcpyAsync(gkind.data(), w.gkind, ng * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   C2_CUDA_TRY(cudaStreamSynchronize(st));
   const int64_t cap = s.gram_budget / (int64_t)sizeof(uint16_t);
-  // exact 64-bit order keys need unions and local ids below 2^16
+  // exact 64-bit order keys need unions below 2^16 and clusters below 2^14
   bool keyed = max_len <= 32767;
   for (int g = 0; g < ng; ++g) {
     if ((gkind[g] && gsz[g] > kMaxGreedyM) || goff[g + 1] - goff[g] > cap) return C2_ERR_UNSUPPORTED;
-    if (gsz[g] > 65535) keyed = false;
+    if (gsz[g] > 16383) keyed = false;
   }
   C2_LAUNCH(k_iota, div_up(ng, T), T, 0, st, w.gseq, (int64_t)ng);
   const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
@@ -1334,7 +1425,7 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
   GramArgs ga0{};
   ga0.ptr = ptr; ga0.items = items; ga0.pptr = w.pptr; ga0.pitems = w.pitems;
   ga0.n_items = s.m; ga0.work_c = w.work_c; ga0.work_t = w.work_t;
-  ga0.cptr = cptr; ga0.cusers = cusers; ga0.ord = w.ord; ga0.gofs = w.gofs; ga0.gram = w.gram;
+  ga0.cptr = cptr; ga0.cusers = cusers; ga0.iinfo = w.iinfo; ga0.gofs = w.gofs; ga0.gram = w.gram;
   ga0.hdr = w.hdr; ga0.counter = &w.hdr->work_counter[1];
 
   int g0 = 0;
@@ -1356,8 +1447,10 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
       Prof p_gram(st, "gram");
       C2_LAUNCH(k_batch_setup, div_up(nb, T), T, 0, st, w.gcl, w.goff, w.gsz, w.gkind, g0, g1,
                 w.gofs, w.bu_cnt, w.bb_cnt, w.bw_cnt);
+      // internal order (members by decreasing profile length) of every
+      // count-matrix cluster of the batch
+      C2_LAUNCH(k_order, nb, 256, 0, st, w.gcl, g0, cptr, w.slen, w.ipos, w.iinfo);
       if (tc.W) {
-        C2_LAUNCH(k_order, nb, 256, 0, st, w.gcl, g0, cptr, w.slen, w.ord);
         bool present[kBuckets] = {false, false, false, false};
         for (int g = g0; g < g1; ++g) present[size_bucket(gsz[g])] = true;
         // one launch per size bucket, over that bucket's query tiles
@@ -1459,7 +1552,7 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
         MergeGramArgs ma{};
         ma.ptr = ptr; ma.items = items; ma.cptr = cptr; ma.cusers = cusers; ma.gcl = w.gcl;
         ma.gofs = w.gofs; ma.gram = w.gram; ma.u_slot = w.gu_slot; ma.u_g = w.gu_g;
-        ma.n_users_dev = w.bu_off + nb; ma.hdr = w.hdr;
+        ma.n_users_dev = w.bu_off + nb; ma.ipos = w.ipos; ma.iinfo = w.iinfo; ma.hdr = w.hdr;
         C2_LAUNCH(k_merge_gram, div_up((n_greedy_users + n_brute_users) * 32, 256), 256, 0, st, ma);
       }
     }
@@ -1471,6 +1564,7 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
       RowTopkArgs ra{};
       ra.cptr = cptr; ra.cusers = cusers; ra.slen = w.slen; ra.gcl = w.gcl; ra.gofs = w.gofs;
       ra.gram = w.gram; ra.u_slot = w.ub_slot; ra.u_g = w.ub_g; ra.n_users_dev = w.bb_off + nb;
+      ra.ipos = w.ipos; ra.iinfo = w.iinfo;
       ra.k = k; ra.out_id = lid; ra.out_in = lin; ra.out_un = lun; ra.hdr = w.hdr;
       if (keyed) C2_LAUNCH(k_gram_topk<true>, div_up(n_brute_users * 32, kNT), kNT, 0, st, ra);
       else C2_LAUNCH(k_gram_topk<false>, div_up(n_brute_users * 32, kNT), kNT, 0, st, ra);
@@ -1481,6 +1575,7 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
       ga.gram = w.gram; ga.gu_slot = w.gu_slot; ga.gu_g = w.gu_g; ga.n_users_dev = w.bu_off + nb;
       ga.gw_g = w.gw_g; ga.gw_t = w.gw_t; ga.n_gwork = &w.hdr->n_gwork;
       ga.counter = &w.hdr->work_counter[2];
+      ga.ipos = w.ipos; ga.iinfo = w.iinfo;
       ga.k = k; ga.n_random = opt.greedy_random; ga.key = key;
       ga.out_id = lid; ga.out_in = lin; ga.out_un = lun; ga.hdr = w.hdr;
       ga.mcap = (mmax + 31) & ~31;
