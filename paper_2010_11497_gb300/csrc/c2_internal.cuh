@@ -445,6 +445,27 @@ __device__ __forceinline__ void key_list_insert(uint64_t& e, int k, uint64_t key
   if (lane >= k) e = 0ull;
 }
 
+// Key of a staged candidate (pos | lid << 16, c | u << 16).
+__device__ __forceinline__ uint64_t staged_key(uint2 x) {
+  return nbr_key(x.y & 0xffffu, x.y >> 16, (int32_t)(x.x >> 16), (int32_t)(x.x & 0xffffu));
+}
+
+// Merges the 32 oldest of n >= 32 staged candidates into the key list and
+// moves the rest down; returns the new list.  Not inlined, so that the call
+// sites in unrolled candidate loops stay small.
+static __device__ __noinline__ uint64_t key_drain32(uint64_t L, int k, uint2* stg, int n) {
+  const int lane = threadIdx.x & 31;
+  __syncwarp();
+  const uint2 x = stg[lane];
+  const int rest = n - 32;
+  uint2 y = make_uint2(0u, 0u);
+  if (lane < rest) y = stg[32 + lane];
+  __syncwarp();
+  if (lane < rest) stg[lane] = y;
+  __syncwarp();
+  return key_list_merge(L, k, staged_key(x));
+}
+
 // WarpTopk on order keys, for rows whose unions are below 2^16 in clusters
 // of fewer than 2^14 members: the filter compares 32-bit cross products
 // against the k-th entry, staged candidates get their keys in one batch, and
@@ -483,21 +504,9 @@ struct KeyTopk {
     const uint32_t l = c * Tu, r = Tc * u;
     return l > r || (l == r && (uint32_t)lid < Tid);
   }
-  __device__ __forceinline__ static uint64_t key_of(uint2 x) {
-    return nbr_key(x.y & 0xffffu, x.y >> 16, (int32_t)(x.x >> 16), (int32_t)(x.x & 0xffffu));
-  }
   __device__ __forceinline__ void drain32() {
-    const int lane = threadIdx.x & 31;
-    __syncwarp();
-    const uint2 x = stg[lane];
-    const int rest = n - 32;
-    uint2 y = make_uint2(0u, 0u);
-    if (lane < rest) y = stg[32 + lane];
-    __syncwarp();
-    if (lane < rest) stg[lane] = y;
-    __syncwarp();
-    n = rest;
-    L = key_list_merge(L, k, key_of(x));
+    L = key_drain32(L, k, stg, n);
+    n -= 32;
     refresh();
   }
   __device__ __forceinline__ void stage(bool pass, int32_t pos, int32_t lid, uint32_t c, uint32_t u) {
@@ -514,7 +523,7 @@ struct KeyTopk {
     const int lane = threadIdx.x & 31;
     __syncwarp();
     uint64_t key = 0ull;
-    if (lane < n) key = key_of(stg[lane]);
+    if (lane < n) key = staged_key(stg[lane]);
     __syncwarp();
     if (n > 8) {
       L = key_list_merge(L, k, key);

@@ -538,9 +538,9 @@ struct GlobalCU {
 };
 
 // One warp per user of a brute-force cluster: the top k of the user's row of
-// intersection counts, 256 candidates per step (8 per lane, coalesced),
-// staged and merged; `Keyed` (every union below 2^16) holds the list as exact
-// 64-bit order keys.  Rows and columns are in internal order; candidates are
+// intersection counts, 32 candidates per step (coalesced), staged and
+// merged; `Keyed` (every union below 2^16) holds the list as exact 64-bit
+// order keys.  Rows and columns are in internal order; candidates are
 // ranked by local index (user-id order).
 template <bool Keyed>
 __global__ void __launch_bounds__(kNT) k_gram_topk(RowTopkArgs a) {
@@ -565,28 +565,30 @@ __global__ void __launch_bounds__(kNT) k_gram_topk(RowTopkArgs a) {
     l0.id = -1; l0.c = 0; l0.u = 0;
     tk.start(l0, k, s_sid[warp], s_scu[warp]);
   }
-  for (int p0 = 0; p0 < M; p0 += 256) {
-    uint32_t cc[8];
-    int2 in[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int p = p0 + j * 32 + lane;
-      cc[j] = (p < M && p != P) ? (uint32_t)row[p] : 0u;
-    }
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int p = p0 + j * 32 + lane;
-      in[j] = cc[j] > 0u ? info[p] : make_int2(0, 0);
-    }
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      if (p0 + j * 32 >= M) break;
-      const int p = p0 + j * 32 + lane;
-      const uint32_t uu = my + (uint32_t)in[j].y - cc[j];
-      const bool pass = cc[j] > 0u && tk.filter(in[j].x, cc[j], uu);
-      if constexpr (Keyed) tk.stage(pass, p, in[j].x, cc[j], uu);
-      else tk.stage(pass, in[j].x, cc[j], uu);
-    }
+  // steps of 32 candidates, through a ring of 4 steps of loads in flight (a
+  // rolled loop keeps the kernel small enough for the instruction cache)
+  auto fetch = [&](int j, uint32_t& cc, int2& in) {
+    const int p = j * 32 + lane;
+    cc = (p < M && p != P) ? (uint32_t)row[p] : 0u;
+    in = p < M ? info[p] : make_int2(0, 0);
+  };
+  uint32_t c0, c1, c2, c3;
+  int2 i0, i1, i2, i3;
+  fetch(0, c0, i0); fetch(1, c1, i1); fetch(2, c2, i2); fetch(3, c3, i3);
+  const int nsteps = (M + 31) >> 5;
+#pragma unroll 1
+  for (int j = 0; j < nsteps; ++j) {
+    uint32_t cn;
+    int2 in_;
+    fetch(j + 4, cn, in_);
+    const int p = j * 32 + lane;
+    const uint32_t uu = my + (uint32_t)i0.y - c0;
+    // local index order = user id order
+    const bool pass = c0 > 0u && tk.filter(i0.x, c0, uu);
+    if constexpr (Keyed) tk.stage(pass, p, i0.x, c0, uu);
+    else tk.stage(pass, i0.x, c0, uu);
+    c0 = c1; c1 = c2; c2 = c3; c3 = cn;
+    i0 = i1; i1 = i2; i2 = i3; i3 = in_;
   }
   tk.finish();
   if (lane < k) {
@@ -1134,21 +1136,20 @@ __global__ void __launch_bounds__(kNT, 4) k_greedy_round(GreedyArgs a) {
         const uint32_t bit = 1u << (x & 31);
         fresh += (atomicOr(&bm[x >> 5], bit) & bit) == 0u ? 1u : 0u;
       };
-      // neighbour rows, 16 at a time (independent loads in flight)
-      for (int j0 = 0; j0 < nlist; j0 += 16) {
-        int cand[16];
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int nb = __shfl_sync(0xffffffffu, e, (j0 + j) & 31);
-          cand[j] = (j0 + j < nlist && lane < k) ? wl_c[nb * k] : -1;
-        }
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          if (j0 + j < nlist) {
-            if ((dedupe_only >> (j0 + j)) & 1u) mark(cand[j]);
-            else consider(cand[j]);
-          }
-        }
+      // neighbour lists in order, through a ring of 8 loads in flight (a
+      // rolled loop keeps the kernel small enough for the instruction cache)
+      auto fetch = [&](int j) -> int {
+        const int nb = __shfl_sync(0xffffffffu, e, j & 31);
+        return (j < nlist && lane < k) ? wl_c[nb * k] : -1;
+      };
+      int q0 = fetch(0), q1 = fetch(1), q2 = fetch(2), q3 = fetch(3);
+      int q4 = fetch(4), q5 = fetch(5), q6 = fetch(6), q7 = fetch(7);
+#pragma unroll 1
+      for (int j = 0; j < nlist; ++j) {
+        const int nxt = fetch(j + 8);
+        if ((dedupe_only >> j) & 1u) mark(q0);
+        else consider(q0);
+        q0 = q1; q1 = q2; q2 = q3; q3 = q4; q4 = q5; q5 = q6; q6 = q7; q7 = nxt;
       }
       for (int d0 = 0; d0 < a.n_random; d0 += 32) {
         int v = -1;
