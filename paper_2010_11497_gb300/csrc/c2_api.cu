@@ -54,8 +54,9 @@ void bind_knn_ws(Ws& w, const Sizes& s, KnnWs& c) {
   const int64_t S = s.S;
   c.slot2c = w.take<int32_t>(S + 1);
   c.slen = w.take<int32_t>(S + 1);
-  c.ntiles = w.take<int32_t>(S + 1);
-  c.toff = w.take<int32_t>(S + 1);
+  c.small_cnt = w.take<int32_t>(S + 1);
+  c.small_off = w.take<int32_t>(S + 1);
+  c.small_slot = w.take<int32_t>(S + 1);
   c.gflag = w.take<int32_t>(S + 1);
   c.gidx = w.take<int32_t>(S + 1);
   c.work_c = w.take<int32_t>(S + 1);

@@ -105,8 +105,9 @@ struct KnnWs {
   DevHeader* hdr;
   int32_t* slot2c;         // [S] slot -> cluster
   int32_t* slen;           // [S] profile length of the slot's user
-  int32_t* ntiles;         // [S+1] brute-force tiles per cluster
-  int32_t* toff;           // [S+1]
+  int32_t* small_cnt;      // [S+1] members of clusters for the merge kernel, per cluster
+  int32_t* small_off;      // [S+1] their prefix sums
+  int32_t* small_slot;     // [S+1] slots of those clusters
   int32_t* gflag;          // [S+1] greedy cluster flag
   int32_t* gidx;           // [S+1]
   int32_t* work_c;         // [S+1] work item -> cluster

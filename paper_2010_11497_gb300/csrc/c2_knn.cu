@@ -36,7 +36,7 @@ constexpr int kNT = 256;
 constexpr int kMaxGreedyM = 10240;            // greedy cluster size limit (shared staging)
 constexpr int kBitmapWords = kMaxGreedyM / 32;
 constexpr int kGreedyUsersPerWarp = 4;
-constexpr int kSmallCut = 32;    // brute clusters below this size use the merge kernel
+constexpr int kSmallCut = 9;     // brute clusters below this size: warp-per-cluster kernel (<= 33)
 constexpr int kGreedyChunk = 8 * kGreedyUsersPerWarp;   // users per block work item
 
 // ------------------------------------------------------------------ table kernel
@@ -652,60 +652,37 @@ struct MergeArgs {
   const int32_t* ptr;
   const int32_t* items;
   int32_t k;
-  const int32_t* cptr;
-  const int32_t* cusers;
-  const int32_t* slot2c;
-  int64_t n_rows;          // slots (cluster mode) or queries (judge mode)
-  int32_t thr;             // brute force iff |C| < thr
-  int32_t max_m;           // cluster mode: only clusters with |C| < max_m
-  const int32_t* queries;  // judge mode when cptr == NULL
+  int64_t n_rows;          // queries
+  const int32_t* queries;  // NULL = 0 .. n_rows-1
   int32_t n_users;
   int32_t *out_id, *out_in, *out_un;
   DevHeader* hdr;
 };
 
-__global__ void __launch_bounds__(kNT) k_merge_knn(MergeArgs a) {
+// Top k of query `row` against every user, by sorted-list merges (lane i
+// compares the query with candidate i of a chunk of 32).
+__device__ __forceinline__ void merge_knn_row(const MergeArgs& a, int64_t row) {
   const int lane = threadIdx.x & 31;
-  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (row >= a.n_rows || dev_failed(a.hdr)) return;
-  int u, M, cbase;
-  const int32_t* clist;
-  if (a.cptr) {
-    const int c = a.slot2c[row];
-    cbase = a.cptr[c];
-    M = a.cptr[c + 1] - cbase;
-    if (M < 2 || M >= a.thr || M >= a.max_m) return;
-    u = a.cusers[row];
-    clist = a.cusers;
-  } else {
-    u = a.queries ? a.queries[row] : (int)row;
-    M = a.n_users;
-    cbase = 0;
-    clist = nullptr;
-  }
+  const int u = a.queries ? a.queries[row] : (int)row;
+  const int M = a.n_users;
   const int k = a.k;
   const int32_t* ur = a.items + a.ptr[u];
   const int ul = a.ptr[u + 1] - a.ptr[u];
   WarpList L;
   L.id = -1; L.c = 0; L.u = 0;
   for (int cb = 0; cb < M; cb += 32) {
-    const int vl = cb + lane;
-    bool pass = false;
+    const int v = cb + lane;
     uint32_t cc = 0, uu = 0;
-    int v = -1;
-    if (vl < M) {
-      v = clist ? clist[cbase + vl] : vl;
-      if (v != u) {
-        const int vlen = a.ptr[v + 1] - a.ptr[v];
-        cc = merge_count(ur, ul, a.items + a.ptr[v], vlen);
-        uu = (uint32_t)(ul + vlen) - cc;
-      }
+    if (v < M && v != u) {
+      const int vlen = a.ptr[v + 1] - a.ptr[v];
+      cc = merge_count(ur, ul, a.items + a.ptr[v], vlen);
+      uu = (uint32_t)(ul + vlen) - cc;
     }
     WarpList kth;
     kth.id = __shfl_sync(0xffffffffu, L.id, k - 1);
     kth.c = __shfl_sync(0xffffffffu, L.c, k - 1);
     kth.u = __shfl_sync(0xffffffffu, L.u, k - 1);
-    pass = v >= 0 && v != u && cc > 0 && beats(kth, v, cc, uu);
+    const bool pass = v < M && v != u && cc > 0 && beats(kth, v, cc, uu);
     warp_list_add(L, k, pass, v, cc, uu);
   }
   if (lane < k) {
@@ -717,13 +694,141 @@ __global__ void __launch_bounds__(kNT) k_merge_knn(MergeArgs a) {
   }
 }
 
+// Judge mode: one warp per query against every user.
+__global__ void __launch_bounds__(kNT) k_merge_knn(MergeArgs a) {
+  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (w >= a.n_rows || dev_failed(a.hdr)) return;
+  merge_knn_row(a, w);
+}
+
+// Small brute-force clusters (2 <= M <= 32 members, at most kSmallItems
+// profile items in all): one warp per cluster (persistent grid over the
+// listed clusters).  The members' profiles are staged in shared memory, the
+// M(M-1)/2 intersections are counted by sorted-list merges spread over the
+// lanes, and each member's row is one warp sort of its M-1 candidates (exact
+// order, lower id first on ties; candidates with no common item dropped).
+constexpr int kSmallItems = 2048;   // staged profile items per warp
+constexpr int kSmallWarps = 4;      // warps per block
+
+// merge_count for profiles that may sit in shared memory (generic loads).
+__device__ __forceinline__ uint32_t merge_count_any(const int32_t* a, int la, const int32_t* b,
+                                                    int lb) {
+  int i = 0, j = 0;
+  uint32_t c = 0;
+  while (i < la && j < lb) {
+    const int x = a[i], y = b[j];
+    c += (x == y);
+    i += (x <= y);
+    j += (y <= x);
+  }
+  return c;
+}
+
+struct SmallArgs {
+  const int32_t* ptr;
+  const int32_t* items;
+  const int32_t* cptr;
+  const int32_t* cusers;
+  const int32_t* list;      // small clusters
+  const int32_t* n_list;    // their device count
+  int32_t k;
+  int32_t *out_id, *out_in, *out_un;
+  DevHeader* hdr;
+};
+
+__global__ void __launch_bounds__(32 * kSmallWarps) k_small_knn(SmallArgs a) {
+  __shared__ int32_t s_items[kSmallWarps][kSmallItems];
+  __shared__ uint16_t s_cnt[kSmallWarps][32 * 32];
+  __shared__ int32_t s_beg[kSmallWarps][32], s_len[kSmallWarps][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int32_t* sit = s_items[warp];
+  uint16_t* cnt = s_cnt[warp];
+  int32_t* mbeg = s_beg[warp];
+  int32_t* mlen = s_len[warp];
+  const int n = *a.n_list;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  const int k = a.k;
+  for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < n; r += nw) {
+    if (dev_failed(a.hdr)) return;
+    const int c = a.list[r];
+    const int cbase = a.cptr[c], M = a.cptr[c + 1] - cbase;
+    // member lane: its user, profile start and length; staged offsets
+    const int u = lane < M ? a.cusers[cbase + lane] : 0;
+    const int ps = lane < M ? a.ptr[u] : 0;
+    const int len = lane < M ? a.ptr[u + 1] - ps : 0;
+    int incl = len;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    const bool staged = total <= kSmallItems;
+    const int32_t* base = staged ? sit : a.items;
+    if (lane < M) {
+      mbeg[lane] = staged ? incl - len : ps;
+      mlen[lane] = len;
+    }
+    if (staged) {
+      for (int m = 0; m < M; ++m) {
+        const int s0 = __shfl_sync(0xffffffffu, ps, m), l0 = __shfl_sync(0xffffffffu, len, m);
+        const int d0 = __shfl_sync(0xffffffffu, incl - len, m);
+        for (int i = lane; i < l0; i += 32) sit[d0 + i] = a.items[s0 + i];
+      }
+    }
+    __syncwarp();
+    // pairs (i, j), i < j, in row order, spread over the lanes
+    const int npairs = M * (M - 1) / 2;
+    for (int q = lane; q < npairs; q += 32) {
+      int i = 0, rem = q;
+      while (rem >= M - 1 - i) { rem -= M - 1 - i; ++i; }
+      const int j = i + 1 + rem;
+      const uint32_t x = merge_count_any(base + mbeg[i], mlen[i], base + mbeg[j], mlen[j]);
+      cnt[i * 32 + j] = (uint16_t)x;
+      cnt[j * 32 + i] = (uint16_t)x;
+    }
+    __syncwarp();
+    // rows: member i against the others, one warp sort each
+    for (int i = 0; i < M; ++i) {
+      WarpList e;
+      e.id = -1; e.c = 0; e.u = 0;
+      if (lane < M && lane != i) {
+        const uint32_t x = cnt[i * 32 + lane];
+        if (x > 0) {
+          e.id = lane;                       // local index order = user id order
+          e.c = x;
+          e.u = (uint32_t)(mlen[i] + len) - x;
+        }
+      }
+      warp_sort32(e);
+      if (lane < k) {
+        const int64_t o = (int64_t)(cbase + i) * k + lane;
+        const bool ok = e.id >= 0;
+        a.out_id[o] = ok ? a.cusers[cbase + e.id] : -1;
+        a.out_in[o] = ok ? (int32_t)e.c : 0;
+        a.out_un[o] = ok ? (int32_t)e.u : 0;
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// Clusters that the small-cluster kernel computes (flag set), listed.
+__global__ void k_fill_small(const int32_t* __restrict__ flag, const int32_t* __restrict__ off,
+                             int64_t S, int32_t* __restrict__ list) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < S && flag[c]) list[off[c]] = (int32_t)c;
+}
+
 // ------------------------------------------------------------------ preparation
 // Per cluster: does it get a count matrix (every greedy cluster, and brute-
 // force clusters of at least small_cut members), is it greedy, pair count;
 // singletons get an empty row (nobody else is in their cluster).
 __global__ void k_prep(const int32_t* __restrict__ cptr, const int32_t* __restrict__ n_clusters,
-                       int64_t S, int32_t thr, int32_t small_cut, int32_t k,
+                       const int32_t* __restrict__ cusers, const int32_t* __restrict__ ptr,
+                       int64_t S, int32_t thr, int32_t small_cut, int32_t small_items, int32_t k,
                        int32_t* __restrict__ gflag, int32_t* __restrict__ gkind,
+                       int32_t* __restrict__ small_cnt,
                        int32_t* __restrict__ lid, int32_t* __restrict__ lin,
                        int32_t* __restrict__ lun, DevHeader* hdr) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -732,11 +837,23 @@ __global__ void k_prep(const int32_t* __restrict__ cptr, const int32_t* __restri
   if (c < S && c < L) M = cptr[c + 1] - cptr[c];
   const bool brute = M >= 2 && M < thr;
   const bool greedy = M >= 2 && M >= thr;
+  // small brute-force clusters whose profiles fit the per-warp stage go to
+  // the warp-per-cluster kernel
+  bool small = false;
+  if (brute && M < small_cut) {
+    int64_t tot = 0;
+    for (int j = 0; j < M; ++j) {
+      const int u = cusers[cptr[c] + j];
+      tot += ptr[u + 1] - ptr[u];
+    }
+    small = tot <= small_items;
+  }
   // counts are 16-bit: profiles of more than 65535 items are unsupported
   if (c == 0 && hdr->knn_max_len > 65535) dev_fail(hdr, C2_ERR_UNSUPPORTED);
   if (c < S) {
-    gflag[c] = (greedy || (brute && M >= small_cut)) ? 1 : 0;
+    gflag[c] = (greedy || (brute && !small)) ? 1 : 0;
     gkind[c] = greedy ? 1 : 0;
+    small_cnt[c] = small ? 1 : 0;
     if (M == 1) {
       const int64_t s = cptr[c];
       for (int j = 0; j < k; ++j) {
@@ -1366,16 +1483,17 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
   const int thr = opt.greedy_threshold > 0 ? opt.greedy_threshold : 5 * k * k;
   const int rounds = opt.greedy_rounds >= 0 ? opt.greedy_rounds : 10;
   const TableCfg tc = pick_gram(opt.strategy, s.m);
-  // brute-force clusters smaller than small_cut go to the warp-per-query merge
-  // kernel; larger ones and every greedy cluster get a count matrix
-  const int small_cut = tc.W ? kSmallCut : (1 << 30);
+  // brute-force clusters smaller than small_cut (at most 33) go to the
+  // warp-per-cluster kernel; larger ones and every greedy cluster get a count
+  // matrix
+  const int small_cut = kSmallCut;
 
   Prof p_prep(st, "knn_prep");
   C2_LAUNCH(k_set_count, 1, 1, 0, st, &w.hdr->knn_max_len, 0);
   C2_LAUNCH(k_slot_info, div_up(S, T), T, 0, st, cptr, n_clusters, cusers, ptr, S, w.slot2c,
             w.slen, w.hdr);
-  C2_LAUNCH(k_prep, div_up(S, T), T, 0, st, cptr, n_clusters, S, thr, small_cut, k, w.gflag,
-            w.gkind_c, lid, lin, lun, w.hdr);
+  C2_LAUNCH(k_prep, div_up(S, T), T, 0, st, cptr, n_clusters, cusers, ptr, S, thr, small_cut,
+            kSmallItems, k, w.gflag, w.gkind_c, w.small_cnt, lid, lin, lun, w.hdr);
   C2_CUDA_TRY(cudaGetLastError());
   if (tc.W) {
     c2_status rc = build_padded_csr(ptr, items, s, w, st);
@@ -1385,11 +1503,14 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
 
   {
     Prof p_small(st, "brute_merge");
-    MergeArgs a{};
-    a.ptr = ptr; a.items = items; a.k = k; a.cptr = cptr; a.cusers = cusers;
-    a.slot2c = w.slot2c; a.n_rows = S; a.thr = thr; a.max_m = small_cut; a.out_id = lid;
-    a.out_in = lin; a.out_un = lun; a.hdr = w.hdr;
-    C2_LAUNCH(k_merge_knn, div_up(S * 32, kNT), kNT, 0, st, a);
+    C2_CUDA_TRY(scan_exclusive(w.small_cnt, w.small_off, S, w.scan_tmp, st));
+    C2_LAUNCH(k_fill_small, div_up(S, T), T, 0, st, w.small_cnt, w.small_off, S, w.small_slot);
+    SmallArgs sa{};
+    sa.ptr = ptr; sa.items = items; sa.cptr = cptr; sa.cusers = cusers; sa.list = w.small_slot;
+    sa.n_list = w.small_off + S; sa.k = k; sa.out_id = lid; sa.out_in = lin; sa.out_un = lun;
+    sa.hdr = w.hdr;
+    C2_LAUNCH(k_small_knn, (int)std::min<int64_t>(div_up(S, kSmallWarps), (int64_t)num_sms() * 5),
+              32 * kSmallWarps, 0, st, sa);
     C2_CUDA_TRY(cudaGetLastError());
   }
 
@@ -1546,15 +1667,25 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
           }
         }
       } else {
-        // no item table fits shared memory: rows by merges (greedy clusters only here)
-        C2_CUDA_TRY(scan_exclusive(w.bu_cnt, w.bu_off, nb, w.scan_tmp, st));
-        C2_LAUNCH(k_fill_users, nb, 256, 0, st, w.gcl, cptr, w.gkind, 1, w.bu_off, g0, nb,
-                  w.gu_slot, w.gu_g);
+        // no item table fits shared memory: rows by merges, greedy clusters'
+        // members then brute-force clusters' members
         MergeGramArgs ma{};
         ma.ptr = ptr; ma.items = items; ma.cptr = cptr; ma.cusers = cusers; ma.gcl = w.gcl;
-        ma.gofs = w.gofs; ma.gram = w.gram; ma.u_slot = w.gu_slot; ma.u_g = w.gu_g;
-        ma.n_users_dev = w.bu_off + nb; ma.ipos = w.ipos; ma.iinfo = w.iinfo; ma.hdr = w.hdr;
-        C2_LAUNCH(k_merge_gram, div_up((n_greedy_users + n_brute_users) * 32, 256), 256, 0, st, ma);
+        ma.gofs = w.gofs; ma.gram = w.gram; ma.ipos = w.ipos; ma.iinfo = w.iinfo; ma.hdr = w.hdr;
+        if (n_greedy_users) {
+          C2_CUDA_TRY(scan_exclusive(w.bu_cnt, w.bu_off, nb, w.scan_tmp, st));
+          C2_LAUNCH(k_fill_users, nb, 256, 0, st, w.gcl, cptr, w.gkind, 1, w.bu_off, g0, nb,
+                    w.gu_slot, w.gu_g);
+          ma.u_slot = w.gu_slot; ma.u_g = w.gu_g; ma.n_users_dev = w.bu_off + nb;
+          C2_LAUNCH(k_merge_gram, div_up(n_greedy_users * 32, 256), 256, 0, st, ma);
+        }
+        if (n_brute_users) {
+          C2_CUDA_TRY(scan_exclusive(w.bb_cnt, w.bb_off, nb, w.scan_tmp, st));
+          C2_LAUNCH(k_fill_users, nb, 256, 0, st, w.gcl, cptr, w.gkind, 0, w.bb_off, g0, nb,
+                    w.ub_slot, w.ub_g);
+          ma.u_slot = w.ub_slot; ma.u_g = w.ub_g; ma.n_users_dev = w.bb_off + nb;
+          C2_LAUNCH(k_merge_gram, div_up(n_brute_users * 32, 256), 256, 0, st, ma);
+        }
       }
     }
     if (n_brute_users) {
@@ -1659,7 +1790,7 @@ c2_status run_bruteforce(const int32_t* ptr, const int32_t* items, const Sizes& 
     return launch_table(tc, a, st);
   }
   MergeArgs a{};
-  a.ptr = ptr; a.items = items; a.k = s.k; a.cptr = nullptr; a.n_rows = rows;
+  a.ptr = ptr; a.items = items; a.k = s.k; a.n_rows = rows;
   a.queries = queries; a.n_users = s.n; a.out_id = nid; a.out_in = nin; a.out_un = nun;
   a.hdr = w.hdr;
   C2_LAUNCH(k_merge_knn, div_up((int64_t)rows * 32, kNT), kNT, 0, st, a);
