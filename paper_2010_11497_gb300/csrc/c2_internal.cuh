@@ -478,7 +478,8 @@ template <class CU>
 struct KeyTopk {
   uint64_t L;      // lane i < k: key of the i-th best (0 = empty)
   uint32_t Tc, Tu;
-  uint32_t Tid;    // k-th entry, (0, 1, 0x7fffffff) while the list is not full
+  uint32_t Tid;    // k-th entry; the floor while the list is not full
+  uint32_t Fc, Fu, Fid;   // floor: (0, 1, 0x7fffffff) passes every candidate
   int n, k;        // staged entries (uniform), list length
   uint2* stg;      // shared [64]: (pos | lid << 16, c | u << 16)
   CU cu;
@@ -486,7 +487,7 @@ struct KeyTopk {
   __device__ __forceinline__ void refresh() {
     const uint64_t kth = __shfl_sync(0xffffffffu, L, k - 1);
     if (kth == 0ull) {
-      Tc = 0u; Tu = 1u; Tid = 0x7fffffffu;
+      Tc = Fc; Tu = Fu; Tid = Fid;
     } else {
       Tid = (uint32_t)key_id(kth);
       const uint2 x = cu(key_pos(kth));
@@ -499,6 +500,16 @@ struct KeyTopk {
     n = 0;
     stg = stg_;
     cu = cu_;
+    Fc = 0u; Fu = 1u; Fid = 0x7fffffffu;
+    refresh();
+  }
+  // Floor for the filter while the list is not full: the key of a candidate
+  // known to rank no lower than the final k-th entry (0 = none).  That
+  // candidate itself still passes (its id is the floor's id minus one).
+  __device__ __forceinline__ void set_floor(uint64_t key) {
+    if (key == 0ull) return;
+    const uint2 x = cu(key_pos(key));
+    Fc = x.x; Fu = x.y; Fid = (uint32_t)key_id(key) + 1u;
     refresh();
   }
   __device__ __forceinline__ bool filter(int32_t lid, uint32_t c, uint32_t u) const {

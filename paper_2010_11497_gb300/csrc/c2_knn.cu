@@ -560,6 +560,22 @@ __global__ void __launch_bounds__(kNT) k_gram_topk(RowTopkArgs a) {
   typename std::conditional<Keyed, KeyTopk<GlobalCU>, WarpTopk>::type tk;
   if constexpr (Keyed) {
     tk.start(0ull, k, s_scu[warp], GlobalCU{row, info, my});
+    // first pass: each lane's best candidate; the k-th best of these 32
+    // distinct candidates ranks no higher than the row's k-th best, so it
+    // floors the filter of the second pass
+    uint32_t bc = 0u, bu = 1u, bl = 0x7fffffffu;
+    int bp = -1;
+#pragma unroll 1
+    for (int p = lane; p < M; p += 32) {
+      const uint32_t c = p != P ? (uint32_t)row[p] : 0u;
+      if (c == 0u) continue;
+      const int2 in = info[p];
+      const uint32_t u = my + (uint32_t)in.y - c;
+      const uint32_t l = c * bu, r = bc * u;
+      if (l > r || (l == r && (uint32_t)in.x < bl)) { bc = c; bu = u; bl = (uint32_t)in.x; bp = p; }
+    }
+    const uint64_t bk = warp_sort32_keys(bp >= 0 ? nbr_key(bc, bu, (int32_t)bl, bp) : 0ull);
+    tk.set_floor(__shfl_sync(0xffffffffu, bk, k - 1));
   } else {
     WarpList l0;
     l0.id = -1; l0.c = 0; l0.u = 0;
