@@ -107,6 +107,9 @@ typedef struct {
   int64_t item_visits_greedy; /* brute-force clusters / greedy intersection matrices       */
   int64_t greedy_visits;    /* neighbour-list entries examined by greedy rounds            */
   int64_t greedy_computed;  /* (user, round) pairs a greedy round computed, not repeated  */
+  int64_t greedy_evaluated; /* fresh candidates whose counts a greedy round looked up (the
+                               method's other evaluations come from neighbour lists known
+                               to repeat the previous round's candidates)                 */
 } c2_stats;
 
 /* Fills *opt with the defaults described above.  Never fails. */

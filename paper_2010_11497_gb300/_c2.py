@@ -49,7 +49,7 @@ class Stats(C.Structure):
                 ("max_cluster", C.c_int32), ("max_profile", C.c_int32),
                 ("greedy_users", C.c_int32), ("item_visits_brute", C.c_int64),
                 ("item_visits_greedy", C.c_int64), ("greedy_visits", C.c_int64),
-                ("greedy_computed", C.c_int64)]
+                ("greedy_computed", C.c_int64), ("greedy_evaluated", C.c_int64)]
 
 
 _lib = None
@@ -321,7 +321,8 @@ def c2_get_stats(ws, stream=None) -> dict:
                 split_levels=s.split_levels, n_greedy_clusters=s.n_greedy_clusters,
                 max_cluster=s.max_cluster, max_profile=s.max_profile,
                 greedy_users=s.greedy_users, greedy_visits=s.greedy_visits,
-                greedy_computed=s.greedy_computed, item_visits_brute=s.item_visits_brute, item_visits_greedy=s.item_visits_greedy)
+                greedy_computed=s.greedy_computed, greedy_evaluated=s.greedy_evaluated,
+                item_visits_brute=s.item_visits_brute, item_visits_greedy=s.item_visits_greedy)
 
 
 def c2_reset_status(ws, stream=None):

@@ -247,6 +247,7 @@ c2_status c2_get_stats(const void* d_ws, c2_stream_t stream, c2_stats* out) {
   out->item_visits_greedy = (int64_t)h.item_visits[1];
   out->greedy_visits = (int64_t)h.greedy_visits;
   out->greedy_computed = (int64_t)h.greedy_computed;
+  out->greedy_evaluated = (int64_t)h.greedy_evaluated;
   return C2_OK;
 }
 

@@ -37,7 +37,9 @@ struct DevHeader {
   unsigned long long greedy_visits;    // candidate entries examined by computed users
   unsigned long long greedy_computed;  // (user, round) pairs computed (not skipped)
   int32_t knn_max_len;         // longest profile among the clustered users
-  int32_t pad[15];
+  int32_t pad0;
+  unsigned long long greedy_evaluated;  // candidates looked up by greedy rounds
+  int32_t pad[12];
 };
 static_assert(sizeof(DevHeader) <= 256, "header must fit 256 bytes");
 
@@ -378,26 +380,30 @@ struct WarpTopk {
 // Exact order key of a neighbour (c common items, u union, local index `lid`
 // in the cluster's user-id order, position `pos` in the cluster's internal
 // order) when u < 2^16 (hence c <= u < 2^16) and the cluster has fewer than
-// 2^14 members.  K = floor(c * 2^32 / u) keeps equal Jaccard values equal
-// and separates different ones (they differ by at least 1/(u u') > 2^-32);
-// below K sits 16383 - lid, so that equal values rank the lower id first,
-// and then pos, which only carries the position along.  Larger key = better
+// 2^14 members:  K << 31 | (16383 - lid) << 17 | pos << 1 | mark.
+// K = floor(c * 2^32 / u) keeps equal Jaccard values equal and separates
+// different ones (they differ by at least 1/(u u') > 2^-32); 16383 - lid
+// ranks the lower id first among equal values; pos and the one-bit mark only
+// ride along (lid already differs between candidates).  Larger key = better
 // neighbour; 0 = empty.  K comes from two 32-bit divisions: c*2^16 = q1*u +
 // r1, then r1*2^16 / u, both exact because c, r1 < 2^16.
-__device__ __forceinline__ uint64_t nbr_key(uint32_t c, uint32_t u, int32_t lid, int32_t pos) {
+__device__ __forceinline__ uint64_t nbr_key(uint32_t c, uint32_t u, int32_t lid, int32_t pos,
+                                            uint32_t mark = 0u) {
   const uint32_t ud = u ? u : 1u;            // c = u = 0 only for two empty profiles
   const uint32_t a = c << 16;
   const uint32_t q1 = a / ud, r1 = a - q1 * ud;
   const uint32_t q2 = (r1 << 16) / ud;
   const uint64_t K = c ? (((uint64_t)q1 << 16) | q2) : 0ull;
-  return (K << 30) | ((uint64_t)(16383u - (uint32_t)lid) << 14) | (uint64_t)(uint32_t)pos;
+  return (K << 31) | ((uint64_t)(16383u - (uint32_t)lid) << 17) |
+         ((uint64_t)(uint32_t)pos << 1) | (uint64_t)(mark & 1u);
 }
 __device__ __forceinline__ int32_t key_id(uint64_t key) {
-  return key ? (int32_t)(16383u - (uint32_t)((key >> 14) & 0x3fffu)) : -1;
+  return key ? (int32_t)(16383u - (uint32_t)((key >> 17) & 0x3fffu)) : -1;
 }
 __device__ __forceinline__ int32_t key_pos(uint64_t key) {
-  return key ? (int32_t)(key & 0x3fffu) : -1;
+  return key ? (int32_t)((key >> 1) & 0x3fffu) : -1;
 }
+__device__ __forceinline__ uint32_t key_mark(uint64_t key) { return (uint32_t)key & 1u; }
 
 // Bitonic sort of one key per lane, largest first (32 lanes).
 __device__ __forceinline__ uint64_t warp_sort32_keys(uint64_t x) {

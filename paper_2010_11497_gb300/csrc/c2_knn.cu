@@ -39,6 +39,7 @@ constexpr int kGreedyUsersPerWarp = 4;
 constexpr int kSmallCut = 9;     // brute clusters below this size: warp-per-cluster kernel (<= 33)
 constexpr int kGreedyChunk = 8 * kGreedyUsersPerWarp;   // users per block work item
 
+
 // ------------------------------------------------------------------ table kernel
 struct TableArgs {
   const int32_t* ptr;      // CSR (query items, profile lengths)
@@ -1154,7 +1155,7 @@ __global__ void __launch_bounds__(kNT, 4) k_greedy_round(GreedyArgs a) {
   const int nwork = *a.n_gwork;
   const int k = a.k;
   const bool prune = a.chg_in != nullptr && a.round >= 2 && a.n_random == 0;
-  unsigned long long evals = 0, visits = 0, computed = 0;
+  unsigned long long evals = 0, visits = 0, computed = 0, evaluated = 0;
   for (;;) {
     if (threadIdx.x == 0) s_work = dev_failed(a.hdr) ? nwork : (int)atomicAdd(a.counter, 1u);
     __syncthreads();
@@ -1237,7 +1238,7 @@ __global__ void __launch_bounds__(kNT, 4) k_greedy_round(GreedyArgs a) {
         l0.id = lid0; l0.c = c0; l0.u = u0;
         tk.start(l0, k, s_sid[warp], s_scu[warp]);
       }
-      unsigned fresh = 0;
+      unsigned fresh = 0, looked = 0;
       if (lane == 0) {
         visits += (unsigned long long)nlist * (unsigned long long)k + (unsigned)a.n_random;
         computed += 1;
@@ -1260,6 +1261,7 @@ __global__ void __launch_bounds__(kNT, 4) k_greedy_round(GreedyArgs a) {
           lx = info_g[x].x;
         }
         fresh += isnew ? 1u : 0u;
+        looked += isnew ? 1u : 0u;
         const bool pass = isnew && tk.filter(lx, cc, uu2);
         if constexpr (Keyed) tk.stage(pass, x, lx, cc, uu2);
         else tk.stage(pass, lx, cc, uu2);
@@ -1312,6 +1314,7 @@ __global__ void __launch_bounds__(kNT, 4) k_greedy_round(GreedyArgs a) {
         }
       }
       evals += fresh;
+      evaluated += looked;
       __syncwarp();
     }
     __syncthreads();
@@ -1321,6 +1324,9 @@ __global__ void __launch_bounds__(kNT, 4) k_greedy_round(GreedyArgs a) {
   if (lane == 0 && evals) atomicAdd(&a.hdr->pairs, evals);
   if (lane == 0 && visits) atomicAdd(&a.hdr->greedy_visits, visits);
   if (lane == 0 && computed) atomicAdd(&a.hdr->greedy_computed, computed);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) evaluated += __shfl_xor_sync(0xffffffffu, evaluated, o);
+  if (lane == 0 && evaluated) atomicAdd(&a.hdr->greedy_evaluated, evaluated);
 }
 
 // Final rows: global ids, zero-similarity entries dropped (they sort last);
