@@ -317,8 +317,8 @@ struct GramArgs {
   unsigned* counter;
 };
 
-template <int W, int NT>
-__global__ void __launch_bounds__(NT) k_gram(GramArgs a) {
+template <int W, int NT, int MB>
+__global__ void __launch_bounds__(NT, MB > 0 ? MB : 1) k_gram(GramArgs a) {
   constexpr int Q = 32 * W, NWARP = NT / 32;
   extern __shared__ __align__(16) uint32_t T[];
   __shared__ int32_t q_id[Q];
@@ -1365,6 +1365,7 @@ __global__ void k_gram_stats(const int64_t* __restrict__ goff, int32_t ng, DevHe
 // ------------------------------------------------------------------ launch helpers
 struct TableCfg {
   int W, NT;
+  int MB;   // k_gram: minimum resident blocks per SM (register cap), 0 = none
 };
 
 int smem_optin() {
@@ -1425,26 +1426,31 @@ TableCfg pick_table(int strategy, int m) {
 
 int gram_smem_bytes(TableCfg c, int m) { return 4 * table_T_words(c.W, m); }
 
-template <int W, int NT>
+template <int W, int NT, int MB>
 c2_status launch_gram_t(const GramArgs& a, cudaStream_t st) {
-  const int smem = gram_smem_bytes(TableCfg{W, NT}, a.n_items);
-  C2_CUDA_TRY(cudaFuncSetAttribute(k_gram<W, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  const int smem = gram_smem_bytes(TableCfg{W, NT, MB}, a.n_items);
+  C2_CUDA_TRY(cudaFuncSetAttribute(k_gram<W, NT, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   int per_sm = 0;
-  C2_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gram<W, NT>, NT, smem));
+  C2_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gram<W, NT, MB>, NT, smem));
   if (per_sm < 1) return C2_ERR_UNSUPPORTED;
   C2_CUDA_TRY(cudaMemsetAsync(a.counter, 0, sizeof(unsigned), st));
-  C2_LAUNCH(k_gram<W COMMA NT>, num_sms() * per_sm, NT, smem, st, a);
+  C2_LAUNCH(k_gram<W COMMA NT COMMA MB>, num_sms() * per_sm, NT, smem, st, a);
   C2_CUDA_TRY(cudaGetLastError());
   return C2_OK;
 }
 
 c2_status launch_gram(TableCfg c, const GramArgs& a, cudaStream_t st) {
-  if (c.W == 1 && c.NT == 128) return launch_gram_t<1, 128>(a, st);
-  if (c.W == 1 && c.NT == 256) return launch_gram_t<1, 256>(a, st);
-  if (c.W == 1 && c.NT == 512) return launch_gram_t<1, 512>(a, st);
-  if (c.W == 2 && c.NT == 128) return launch_gram_t<2, 128>(a, st);
-  if (c.W == 2 && c.NT == 256) return launch_gram_t<2, 256>(a, st);
-  if (c.W == 2 && c.NT == 512) return launch_gram_t<2, 512>(a, st);
+  if (c.W == 1 && c.NT == 128 && c.MB == 0) return launch_gram_t<1, 128, 0>(a, st);
+  if (c.W == 1 && c.NT == 128 && c.MB == 5) return launch_gram_t<1, 128, 5>(a, st);
+  if (c.W == 1 && c.NT == 256 && c.MB == 0) return launch_gram_t<1, 256, 0>(a, st);
+  if (c.W == 1 && c.NT == 256 && c.MB == 3) return launch_gram_t<1, 256, 3>(a, st);
+  if (c.W == 1 && c.NT == 256 && c.MB == 4) return launch_gram_t<1, 256, 4>(a, st);
+  if (c.W == 1 && c.NT == 256 && c.MB == 5) return launch_gram_t<1, 256, 5>(a, st);
+  if (c.W == 1 && c.NT == 512 && c.MB == 0) return launch_gram_t<1, 512, 0>(a, st);
+  if (c.W == 1 && c.NT == 512 && c.MB == 2) return launch_gram_t<1, 512, 2>(a, st);
+  if (c.W == 2 && c.NT == 128 && c.MB == 0) return launch_gram_t<2, 128, 0>(a, st);
+  if (c.W == 2 && c.NT == 256 && c.MB == 0) return launch_gram_t<2, 256, 0>(a, st);
+  if (c.W == 2 && c.NT == 512 && c.MB == 0) return launch_gram_t<2, 512, 0>(a, st);
   return C2_ERR_UNSUPPORTED;
 }
 
@@ -1464,7 +1470,9 @@ struct TuneEntry {
 std::mutex g_tune_mu;
 std::map<TuneKey, TuneEntry> g_tune;
 
-const TableCfg kGramShapes[] = {{2, 256}, {2, 512}, {2, 128}, {1, 512}, {1, 256}, {1, 128}};
+const TableCfg kGramShapes[] = {{2, 256, 0}, {2, 512, 0}, {2, 128, 0}, {1, 512, 0}, {1, 256, 0},
+                                 {1, 128, 0}, {1, 256, 3}, {1, 256, 4}, {1, 256, 5}, {1, 512, 2},
+                                 {1, 128, 5}};
 
 bool gram_fits(TableCfg c, int m) { return gram_smem_bytes(c, m) + 1024 <= smem_optin(); }
 
@@ -1833,10 +1841,13 @@ size_t autotune_report(char* buf, size_t len) {
              (long long)kv.first.b, (long long)kv.first.N, (long long)kv.first.k,
              (long long)kv.first.thr, kv.second.unified ? "true" : "false");
     out += tmp;
-    static const char* names[kBuckets] = {"32-127", "128-511", "512-2047", "2048+"};
+    static const char* names[kBuckets] = {"<128", "128-511", "512-2047", "2048+"};
     for (int q = 0; q < kBuckets; ++q) {
-      snprintf(tmp, sizeof tmp, "%s{\"sizes\": \"%s\", \"words\": %d, \"threads\": %d, \"ms\": %.4f}",
-               q ? ", " : "", names[q], kv.second.cfg[q].W, kv.second.cfg[q].NT, kv.second.ms[q]);
+      snprintf(tmp, sizeof tmp,
+               "%s{\"sizes\": \"%s\", \"words\": %d, \"threads\": %d, \"min_blocks\": %d, "
+               "\"ms\": %.4f}",
+               q ? ", " : "", names[q], kv.second.cfg[q].W, kv.second.cfg[q].NT, kv.second.cfg[q].MB,
+               kv.second.ms[q]);
       out += tmp;
     }
     out += "]}";

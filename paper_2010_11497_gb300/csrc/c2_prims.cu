@@ -11,7 +11,8 @@ constexpr int kScanTile = kScanNT * kScanIPT;
 
 // Block-local exclusive scan of one 4096-element tile; writes the tile total.
 template <class T>
-__global__ void __launch_bounds__(kScanNT) k_scan_tile(const T* in, T* out, int64_t n, T* bsum) {
+__global__ void __launch_bounds__(kScanNT) k_scan_tile(const T* in, T* out, int64_t n, T* bsum,
+                                                       T* total) {
   __shared__ T warp_tot[32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanIPT;
@@ -46,7 +47,33 @@ __global__ void __launch_bounds__(kScanNT) k_scan_tile(const T* in, T* out, int6
     if (base + i < n) out[base + i] = excl;
     excl += v[i];
   }
-  if (threadIdx.x == kScanNT - 1) bsum[blockIdx.x] = warp_tot[31];
+  if (threadIdx.x == kScanNT - 1) {
+    bsum[blockIdx.x] = warp_tot[31];
+    if (total) *total = warp_tot[31];    // single-tile scans: out[n]
+  }
+}
+
+// Second pass of a two-launch scan: each block adds the sum of the tile
+// totals before it (a block reduction over at most kScanFlat values) to its
+// tile; the last block writes out[n].
+constexpr int kScanFlat = 8192;
+
+template <class T>
+__global__ void __launch_bounds__(256) k_scan_add_flat(T* out, int64_t n, const T* bsum, int nb) {
+  __shared__ T red[256];
+  T acc = 0;
+  for (int j = threadIdx.x; j < (int)blockIdx.x; j += 256) acc += bsum[j];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  const T add = red[0];
+  const int64_t base = (int64_t)blockIdx.x * kScanTile;
+  for (int i = threadIdx.x; i < kScanTile; i += 256)
+    if (base + i < n) out[base + i] += add;
+  if ((int)blockIdx.x == nb - 1 && threadIdx.x == 0) out[n] = add + bsum[nb - 1];
 }
 
 template <class T>
@@ -65,15 +92,20 @@ cudaError_t scan_impl(const T* in, T* out, int64_t n, T* tmp, cudaStream_t st) {
   if (n <= 0) return cudaMemsetAsync(out, 0, sizeof(T), st);
   const int64_t nb = (n + kScanTile - 1) / kScanTile;
   T* bsum = tmp;
-  C2_LAUNCH(k_scan_tile<T>, (unsigned)nb, kScanNT, 0, st, in, out, n, bsum);
-  if (nb > 1) {
+  // one tile: one launch; up to kScanFlat tiles: two launches
+  C2_LAUNCH(k_scan_tile<T>, (unsigned)nb, kScanNT, 0, st, in, out, n, bsum,
+            nb == 1 ? out + n : (T*)nullptr);
+  if (nb == 1) return cudaGetLastError();
+  if (nb <= kScanFlat) {
+    C2_LAUNCH(k_scan_add_flat<T>, (unsigned)nb, 256, 0, st, out, n, (const T*)bsum, (int)nb);
+    return cudaGetLastError();
+  }
+  {
     const int64_t used = ((nb + 1 + 63) / 64) * 64;
     cudaError_t e = scan_impl<T>(bsum, bsum, nb, tmp + used, st);
     if (e != cudaSuccess) return e;
     C2_LAUNCH(k_scan_add<T>, (unsigned)nb, 256, 0, st, out, n, bsum);
     C2_LAUNCH(k_store_total<T>, 1, 1, 0, st, out + n, bsum + nb);
-  } else {
-    C2_LAUNCH(k_store_total<T>, 1, 1, 0, st, out + n, bsum);
   }
   return cudaGetLastError();
 }
