@@ -272,6 +272,28 @@ static __device__ __noinline__ WarpList warp_list_merge(WarpList e, int k, WarpL
   return e;
 }
 
+// Merges a batch `b` already sorted best first (id -1 = none, at the end)
+// into the sorted list `e` of length k: max of the list and the reversed
+// batch is a bitonic sequence holding the best 32, which is cleaned.
+static __device__ __noinline__ WarpList warp_list_merge_sorted(WarpList e, int k, WarpList b) {
+  const int lane = threadIdx.x & 31;
+  if (lane >= k) e.id = -1;
+  WarpList r;
+  r.id = __shfl_sync(0xffffffffu, b.id, 31 - lane);
+  r.c = __shfl_sync(0xffffffffu, b.c, 31 - lane);
+  r.u = __shfl_sync(0xffffffffu, b.u, 31 - lane);
+  if (entry_better(r, e)) e = r;
+#pragma unroll
+  for (int j = 16; j > 0; j >>= 1) {
+    const WarpList o = shfl_entry_xor(e, j);
+    const bool lower = (lane & j) == 0;
+    const bool take = lower ? entry_better(o, e) : entry_better(e, o);
+    if (take) e = o;
+  }
+  if (lane >= k) e.id = -1;
+  return e;
+}
+
 // Adds the lanes' candidates flagged `pass` to the list: one by one when few
 // pass, by a sort-and-merge when many do.
 __device__ __forceinline__ void warp_list_add(WarpList& e, int k, bool pass, int32_t id,

@@ -16,34 +16,65 @@ __global__ void k_pos_of(const int32_t* __restrict__ cusers, int64_t S, int32_t 
   pos_of[i * n + cusers[s]] = (int32_t)s;
 }
 
-// One warp per user.  Rows are sorted, so a row is abandoned at its first
-// entry that no longer beats the current k-th; an id already held is skipped.
-__global__ void k_merge(const int32_t* __restrict__ pos_of, int32_t n, int32_t t, int32_t k,
-                        const int32_t* __restrict__ lid, const int32_t* __restrict__ lin,
-                        const int32_t* __restrict__ lun, int32_t* __restrict__ nid,
-                        int32_t* __restrict__ nin, int32_t* __restrict__ nun,
-                        const DevHeader* hdr) {
-  const int lane = threadIdx.x & 31;
+// One warp per user; rows are folded 4 at a time (their slot and entry loads
+// issued together).  The first row is the list; every later row drops the
+// ids the list already holds (equal ids carry equal counts), is compacted
+// (it stays sorted) and is merged with the list by one bitonic merge.
+__global__ void __launch_bounds__(256) k_merge(const int32_t* __restrict__ pos_of, int32_t n,
+                                               int32_t t, int32_t k,
+                                               const int32_t* __restrict__ lid,
+                                               const int32_t* __restrict__ lin,
+                                               const int32_t* __restrict__ lun,
+                                               int32_t* __restrict__ nid,
+                                               int32_t* __restrict__ nin,
+                                               int32_t* __restrict__ nun, const DevHeader* hdr) {
+  __shared__ int32_t s_id[8][32];
+  __shared__ uint2 s_cu[8][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (u >= n || dev_failed(hdr)) return;
   WarpList L;
   L.id = -1; L.c = 0; L.u = 0;
-  for (int i = 0; i < t; ++i) {
-    const int64_t s = pos_of[(int64_t)i * n + u];
-    int32_t eid = -1;
-    uint32_t ec = 0, eu = 0;
-    if (lane < k) {
-      eid = lid[s * k + lane];
-      ec = (uint32_t)lin[s * k + lane];
-      eu = (uint32_t)lun[s * k + lane];
+  for (int i0 = 0; i0 < t; i0 += 4) {
+    WarpList R[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      R[r].id = -1; R[r].c = 0; R[r].u = 0;
+      if (i0 + r < t && lane < k) {
+        const int64_t s = pos_of[(int64_t)(i0 + r) * n + u];
+        R[r].id = lid[s * k + lane];
+        R[r].c = (uint32_t)lin[s * k + lane];
+        R[r].u = (uint32_t)lun[s * k + lane];
+      }
     }
-    for (int j = 0; j < k; ++j) {
-      const int32_t id = __shfl_sync(0xffffffffu, eid, j);
-      const uint32_t c = __shfl_sync(0xffffffffu, ec, j);
-      const uint32_t uu = __shfl_sync(0xffffffffu, eu, j);
-      if (id < 0) break;
-      if (__any_sync(0xffffffffu, L.id == id)) continue;
-      if (!warp_list_insert(L, k, id, c, uu)) break;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      if (i0 + r >= t) break;
+      if (i0 + r == 0) { L = R[0]; continue; }
+      // drop ids already in the list
+      bool dup = false;
+      for (int j = 0; j < k; ++j) {
+        const int32_t lj = __shfl_sync(0xffffffffu, L.id, j);   // every lane takes part
+        dup |= R[r].id >= 0 && R[r].id == lj;
+      }
+      const unsigned keep = __ballot_sync(0xffffffffu, R[r].id >= 0 && !dup);
+      if (keep == 0u) continue;
+      // compact the survivors (still sorted) to the front
+      if ((keep >> lane) & 1u) {
+        const int d = __popc(keep & lanemask_lt());
+        s_id[warp][d] = R[r].id;
+        s_cu[warp][d] = make_uint2(R[r].c, R[r].u);
+      }
+      __syncwarp();
+      WarpList b;
+      b.id = -1; b.c = 0; b.u = 0;
+      if (lane < __popc(keep)) {
+        b.id = s_id[warp][lane];
+        const uint2 cu = s_cu[warp][lane];
+        b.c = cu.x; b.u = cu.y;
+      }
+      __syncwarp();
+      L = warp_list_merge_sorted(L, k, b);
     }
   }
   if (lane < k) {
