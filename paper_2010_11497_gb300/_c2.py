@@ -369,6 +369,7 @@ class Model:
         self.state = torch.zeros(int(nbytes), dtype=torch.uint8, device=device)
         self._train_ws = None
         self._prop_ws = None
+        self._prop_chunk = None
         self.step = 0
 
     def init(self, stream=None):
@@ -398,12 +399,13 @@ class Model:
             out.append(f[off:off + 4 * n].view(torch.float32).view(*shp))
         return out
 
-    def propose(self, ptr, items, stream=None, chunk=8192):
+    def propose(self, ptr, items, stream=None, chunk=65536):
         n = ptr.numel() - 1
         keys = torch.empty((self.cfg.t, max(n, 1)), dtype=torch.int32, device=ptr.device)
-        if self._prop_ws is None:
+        if self._prop_ws is None or self._prop_chunk != chunk:
             self._prop_ws = workspace(lib().c2_model_workspace_size(C.byref(self.cfg), chunk, 0),
                                       ptr.device)
+            self._prop_chunk = chunk
         _check(lib().c2_model_propose(C.byref(self.cfg), _ptr(self.state), _ptr(ptr), _ptr(items),
                                       n, _ptr(keys), _ptr(self._prop_ws), self._prop_ws.numel(),
                                       _stream(stream)), "c2_model_propose")

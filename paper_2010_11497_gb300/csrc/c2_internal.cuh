@@ -629,6 +629,17 @@ c2_status run_avg_sim(const int32_t* nin, const int32_t* nun, int32_t rows, int3
 c2_status run_validate(const int32_t* ptr, const int32_t* items, const Sizes& s, DevHeader* hdr,
                        cudaStream_t st);
 
+// tcgen05 logits GEMM with a fused per-slice argmax (c2_tc.cu):
+// part[r][s] = (max, argmax) of A[r] . Bt[j] + bias[j] over the tc_slice_width() columns j
+// of slice s; A [M][K] and Bt [N][K] row-major BF16.  Timeouts of its bounded
+// waits are recorded in *status.
+bool tc_logits_ok(int K, int N, int b);
+int tc_slice_width();
+c2_status tc_transpose_bf16(const __nv_bfloat16* B, int K, int N, __nv_bfloat16* Bt,
+                            cudaStream_t st);
+c2_status tc_logits_argmax(const __nv_bfloat16* A, int M, int K, const __nv_bfloat16* Bt, int N,
+                           const float* bias, float2* part, int32_t* status, cudaStream_t st);
+
 int num_sms();
 size_t autotune_report(char* buf, size_t len);
 

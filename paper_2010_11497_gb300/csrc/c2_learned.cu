@@ -84,17 +84,35 @@ struct ModelScratch {
   float* colmean;        // [T]
   float* loss;           // [4]
   int32_t* rowlist;      // [rows] user of each row
+  float2* part;          // [rows][T / slice] (max, argmax) per column slice (proposals)
+  __nv_bfloat16* w2t;    // [T][H] transposed W2 for the tcgen05 logits GEMM (proposals)
 };
+
+// How a proposal computes the per-head argmax:
+//   2: tcgen05 logits GEMM with the argmax of 256-column slices in its epilogue
+//   1: mma.sync logits GEMM with the argmax of 128-column slices in its epilogue
+//   0: logits written out, then an argmax kernel
+int propose_kind(const ModelDims& d) {
+  if (tc_logits_ok(d.H, d.T, d.b) && d.D % 32 == 0 && d.H % 128 == 0) return 2;
+  if (d.H % 128 == 0 && d.D % 32 == 0 && d.T % 128 == 0 && d.H % 32 == 0 && d.b % 128 == 0) return 1;
+  return 0;
+}
 
 size_t bind_scratch(char* base, const ModelDims& d, int rows, bool train, ModelScratch* s) {
   Ws w;
   w.base = base;
   ModelScratch q{};
-  q.e = w.take<float>((size_t)rows * d.D);
+  if (train) q.e = w.take<float>((size_t)rows * d.D);
   q.e16 = w.take<__nv_bfloat16>((size_t)rows * d.D);
-  q.hpre = w.take<float>((size_t)rows * d.H);
+  if (train) q.hpre = w.take<float>((size_t)rows * d.H);
   q.h16 = w.take<__nv_bfloat16>((size_t)rows * d.H);
-  q.z = w.take<float>((size_t)rows * d.T);
+  const int kind = train ? 0 : propose_kind(d);
+  if (kind == 0) q.z = w.take<float>((size_t)rows * d.T);
+  if (kind == 2) {
+    q.part = w.take<float2>((size_t)rows * (d.T / tc_slice_width()));
+    q.w2t = w.take<__nv_bfloat16>((size_t)d.T * d.H);
+  }
+  if (kind == 1) q.part = w.take<float2>((size_t)rows * (d.T / 128));
   q.rowlist = w.take<int32_t>(rows);
   q.loss = w.take<float>(4);
   if (train) {
@@ -136,31 +154,104 @@ __global__ void k_to_bf16(const float* __restrict__ a, __nv_bfloat16* __restrict
 }
 
 // ---------------------------------------------------------------- embedding bag
-// Warp per row: lanes own D/32 dimensions; rows of E are gathered coalesced.
-__global__ void k_embbag_fwd(const int32_t* __restrict__ ptr, const int32_t* __restrict__ items,
-                             const int32_t* __restrict__ rowlist, int nrows,
-                             const __nv_bfloat16* __restrict__ E16, int D, int R, uint64_t seed,
-                             float* __restrict__ e, __nv_bfloat16* __restrict__ e16) {
+// Warp per row, warps striding over the rows (a grid sized to the resident
+// warps, so long and short profiles even out per warp).  The row's items are
+// taken 32 at a time: lane l hashes item l of the batch (the next batch's ids
+// are fetched meanwhile), then the warp's 32 / (D/8) groups of D/8 lanes
+// gather the items' rows of E with 16-byte loads (8 dimensions per lane),
+// group g taking items g, g + G, g + 2G, ... of the batch.  Each group sums
+// its items in order and the groups are added by a fixed shuffle tree, so the
+// summation order does not depend on timing.
+template <int D>
+__global__ void __launch_bounds__(256, D <= 64 ? 4 : 2) k_embbag_fwd(const int32_t* __restrict__ ptr,
+                                                    const int32_t* __restrict__ items,
+                                                    const int32_t* __restrict__ rowlist, int nrows,
+                                                    const __nv_bfloat16* __restrict__ E16, int R,
+                                                    uint64_t seed, float* __restrict__ e,
+                                                    __nv_bfloat16* __restrict__ e16) {
+  constexpr int LPI = D / 8, G = 32 / LPI, PER = 32 / G;   // PER items per group and batch
   const int lane = threadIdx.x & 31;
-  const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (r >= nrows) return;
-  const int u = rowlist[r];
-  float acc[4] = {0.f, 0.f, 0.f, 0.f};   // D <= 128
-  for (int j = ptr[u]; j < ptr[u + 1]; ++j) {
-    const uint32_t row = emb_row(seed, items[j], R);
+  const int g = lane / LPI, sl = lane % LPI;
+  const bool active = g < G;            // D = 96 leaves 8 lanes idle
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < nrows; r += nwarps) {
+    const int u = rowlist[r];
+    const int beg = ptr[u], end = ptr[u + 1];
+    float acc[8];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int d = lane + 32 * q;
-      if (d < D) acc[q] += __bfloat162float(E16[(size_t)row * D + d]);
+    for (int i = 0; i < 8; ++i) acc[i] = 0.f;
+    int nxt = beg + lane < end ? __ldg(items + beg + lane) : -1;
+    for (int j0 = beg; j0 < end; j0 += 32) {
+      const int cur = nxt;
+      nxt = j0 + 32 + lane < end ? __ldg(items + j0 + 32 + lane) : -1;
+      const uint32_t myrow = cur >= 0 ? emb_row(seed, cur, R) : 0xffffffffu;
+#pragma unroll
+      for (int q0 = 0; q0 < PER; q0 += 4) {   // four rows in flight per lane
+        uint4 v[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const uint32_t row = __shfl_sync(0xffffffffu, myrow, (g + G * (q0 + q)) & 31);
+          v[q] = make_uint4(0u, 0u, 0u, 0u);
+          if (active && row != 0xffffffffu)
+            v[q] = __ldg(reinterpret_cast<const uint4*>(E16 + (size_t)row * D) + sl);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const uint32_t w[4] = {v[q].x, v[q].y, v[q].z, v[q].w};
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w[i]));
+            acc[2 * i] += f.x;
+            acc[2 * i + 1] += f.y;
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int off = (G / 2) * LPI; off >= LPI; off >>= 1)
+#pragma unroll
+      for (int i = 0; i < 8; ++i) acc[i] += __shfl_down_sync(0xffffffffu, acc[i], off);
+    if (lane < LPI) {
+      const size_t o = (size_t)r * D + 8 * lane;
+      if (e) {
+        *reinterpret_cast<float4*>(e + o) = make_float4(acc[0], acc[1], acc[2], acc[3]);
+        *reinterpret_cast<float4*>(e + o + 4) = make_float4(acc[4], acc[5], acc[6], acc[7]);
+      }
+      uint4 pk;
+      __nv_bfloat162 h2[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) h2[i] = __floats2bfloat162_rn(acc[2 * i], acc[2 * i + 1]);
+      pk.x = *reinterpret_cast<uint32_t*>(&h2[0]);
+      pk.y = *reinterpret_cast<uint32_t*>(&h2[1]);
+      pk.z = *reinterpret_cast<uint32_t*>(&h2[2]);
+      pk.w = *reinterpret_cast<uint32_t*>(&h2[3]);
+      *reinterpret_cast<uint4*>(e16 + o) = pk;
     }
   }
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int d = lane + 32 * q;
-    if (d < D) {
-      e[(size_t)r * D + d] = acc[q];
-      e16[(size_t)r * D + d] = __float2bfloat16_rn(acc[q]);
-    }
+}
+
+template <int D>
+c2_status embbag_launch(const int32_t* ptr, const int32_t* items, const int32_t* rowlist,
+                        int nrows, const __nv_bfloat16* E16, int R, uint64_t seed, float* e,
+                        __nv_bfloat16* e16, cudaStream_t st) {
+  int per_sm = 0;   // resident blocks per SM at this instance's register use
+  C2_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_embbag_fwd<D>, 256, 0));
+  const int grid = std::min(div_up((int64_t)nrows * 32, 256), std::max(per_sm, 1) * num_sms());
+  C2_LAUNCH(k_embbag_fwd<D>, grid, 256, 0, st, ptr, items, rowlist, nrows, E16, R, seed, e, e16);
+  C2_CUDA_TRY(cudaGetLastError());
+  return C2_OK;
+}
+
+c2_status embbag_fwd(const int32_t* ptr, const int32_t* items, const int32_t* rowlist, int nrows,
+                     const __nv_bfloat16* E16, int D, int R, uint64_t seed, float* e,
+                     __nv_bfloat16* e16, cudaStream_t st) {
+  if (nrows <= 0) return C2_OK;
+  switch (D) {
+    case 32: return embbag_launch<32>(ptr, items, rowlist, nrows, E16, R, seed, e, e16, st);
+    case 64: return embbag_launch<64>(ptr, items, rowlist, nrows, E16, R, seed, e, e16, st);
+    case 96: return embbag_launch<96>(ptr, items, rowlist, nrows, E16, R, seed, e, e16, st);
+    case 128: return embbag_launch<128>(ptr, items, rowlist, nrows, E16, R, seed, e, e16, st);
+    default: return C2_ERR_UNSUPPORTED;
   }
 }
 
@@ -449,12 +540,12 @@ __global__ void __launch_bounds__(256) k_gemm_fast(FastGemmArgs g) {
 
 // Key of every (row, head) from the per-slice partials (b % 128 == 0).
 __global__ void k_argmax_parts(const float2* __restrict__ part, int nrows, int t, int b, int T,
-                               const int32_t* __restrict__ rowlist, int n_users,
+                               int width, const int32_t* __restrict__ rowlist, int n_users,
                                int32_t* __restrict__ keys) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= nrows * t) return;
   const int r = idx / t, j = idx % t;
-  const int per = b / FBN, slices = T / FBN;
+  const int per = b / width, slices = T / width;
   float2 best = part[(int64_t)r * slices + j * per];
   for (int q = 1; q < per; ++q) {
     const float2 o = part[(int64_t)r * slices + j * per + q];
@@ -675,8 +766,8 @@ bool fast_ok(int N, int K) { return N % FBN == 0 && K % FBK == 0; }
 c2_status model_forward(const ModelDims& d, const ModelParams& p, const ModelScratch& s,
                         const int32_t* ptr, const int32_t* items, int nrows, cudaStream_t st,
                         float2* part = nullptr) {
-  C2_LAUNCH(k_embbag_fwd, div_up((int64_t)nrows * 32, 256), 256, 0, st, ptr, items, s.rowlist,
-            nrows, p.E16, d.D, d.rows, d.seed, s.e, s.e16);
+  c2_status rc0 = embbag_fwd(ptr, items, s.rowlist, nrows, p.E16, d.D, d.rows, d.seed, s.e, s.e16, st);
+  if (rc0) return rc0;
   if (fast_ok(d.H, d.D) && fast_ok(d.T, d.H)) {
     FastGemmArgs f1{};
     f1.A = s.e16; f1.lda = d.D; f1.B = p.W1_16; f1.ldb = d.H;
@@ -707,18 +798,34 @@ c2_status model_forward(const ModelDims& d, const ModelParams& p, const ModelScr
 
 c2_status model_propose(const ModelDims& d, const ModelParams& p, const ModelScratch& s,
                         int chunk, const int32_t* ptr, const int32_t* items, int n,
-                        int32_t* keys, cudaStream_t st) {
-  // fused argmax when every head spans whole 128-column slices
-  const bool fused = fast_ok(d.H, d.D) && fast_ok(d.T, d.H) && d.b % FBN == 0;
+                        int32_t* keys, DevHeader* hdr, cudaStream_t st) {
+  const int kind = propose_kind(d);
+  if (kind == 2) {
+    c2_status rc = tc_transpose_bf16(p.W2_16, d.H, d.T, s.w2t, st);
+    if (rc) return rc;
+  }
   for (int start = 0; start < n; start += chunk) {
     const int rows = std::min(chunk, n - start);
     C2_LAUNCH(k_rowlist_range, div_up(rows, 256), 256, 0, st, s.rowlist, start, rows);
-    if (fused) {
-      float2* part = reinterpret_cast<float2*>(s.z);   // [rows][T/128] fits in z
-      c2_status rc = model_forward(d, p, s, ptr, items, rows, st, part);
+    if (kind == 2) {
+      c2_status rc = embbag_fwd(ptr, items, s.rowlist, rows, p.E16, d.D, d.rows, d.seed, s.e,
+                                s.e16, st);
       if (rc) return rc;
-      C2_LAUNCH(k_argmax_parts, div_up((int64_t)rows * d.t, 256), 256, 0, st, part, rows, d.t,
-                d.b, d.T, s.rowlist, n, keys);
+      FastGemmArgs f1{};
+      f1.A = s.e16; f1.lda = d.D; f1.B = p.W1_16; f1.ldb = d.H;
+      f1.C16 = s.h16; f1.ldc = d.H; f1.bias = p.b1; f1.relu = 1;
+      f1.M = rows; f1.N = d.H; f1.K = d.D;
+      rc = gemm_fast(f1, st);
+      if (rc) return rc;
+      rc = tc_logits_argmax(s.h16, rows, d.H, s.w2t, d.T, p.b2, s.part, &hdr->status, st);
+      if (rc) return rc;
+      C2_LAUNCH(k_argmax_parts, div_up((int64_t)rows * d.t, 256), 256, 0, st, s.part, rows, d.t,
+                d.b, d.T, tc_slice_width(), s.rowlist, n, keys);
+    } else if (kind == 1) {
+      c2_status rc = model_forward(d, p, s, ptr, items, rows, st, s.part);
+      if (rc) return rc;
+      C2_LAUNCH(k_argmax_parts, div_up((int64_t)rows * d.t, 256), 256, 0, st, s.part, rows, d.t,
+                d.b, d.T, FBN, s.rowlist, n, keys);
     } else {
       c2_status rc = model_forward(d, p, s, ptr, items, rows, st);
       if (rc) return rc;
@@ -824,6 +931,12 @@ using namespace c2;
 
 namespace {
 
+// Users per proposal chunk inside the learned build: without the logits
+// written out a row of scratch is under 1 KiB.
+int32_t learned_chunk_rows(const c2_model_config* c) {
+  return propose_kind(model_dims(c)) == 0 ? 8192 : 65536;
+}
+
 c2_status check_cfg(const c2_model_config* c) {
   if (!c) return C2_ERR_INVALID_ARG;
   if (c->t < 1 || c->t > kMaxT || c->b < 2 || c->b > kMaxB) return C2_ERR_UNSUPPORTED;
@@ -878,8 +991,9 @@ c2_status c2_model_propose(const c2_model_config* cfg, const void* d_state,
   if (256 + bind_scratch(nullptr, d, chunk, false, nullptr) > ws_bytes) return C2_ERR_WORKSPACE;
   ModelScratch s;
   bind_scratch((char*)d_ws + 256, d, chunk, false, &s);
+  C2_CUDA_TRY(cudaMemsetAsync(d_ws, 0, sizeof(DevHeader), (cudaStream_t)stream));
   return model_propose(d, p, s, chunk, d_csr_ptr, d_csr_items, n_users, d_keys,
-                       (cudaStream_t)stream);
+                       reinterpret_cast<DevHeader*>(d_ws), (cudaStream_t)stream);
 }
 
 c2_status c2_model_train_step(const c2_model_config* cfg, void* d_state,
@@ -967,7 +1081,7 @@ size_t c2_workspace_size_learned(const c2_model_config* cfg, int32_t n_users, in
   const size_t base = c2_workspace_size(n_users, nnz, n_items, k, cfg->t, cfg->b, N, opt);
   if (!base) return 0;
   auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
-  const size_t model = c2_model_workspace_size(cfg, 8192, 0);
+  const size_t model = c2_model_workspace_size(cfg, learned_chunk_rows(cfg), 0);
   return up(base) + up(model) + up((size_t)cfg->t * n_users * 4) + up((size_t)n_probe * 4) +
          5 * up((size_t)n_probe * k * 4) + 2 * up(8);
 }
@@ -990,7 +1104,7 @@ c2_status c2_build_knn_graph_learned(const c2_model_config* cfg, const void* d_s
   if (!d_ws || ((uintptr_t)d_ws & 255u) || ws_bytes < need) return C2_ERR_WORKSPACE;
   auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
   const size_t base = c2_workspace_size(n_users, nnz, n_items, k, cfg->t, cfg->b, N, opt);
-  const size_t model = c2_model_workspace_size(cfg, 8192, 0);
+  const size_t model = c2_model_workspace_size(cfg, learned_chunk_rows(cfg), 0);
   char* p = (char*)d_ws + up(base);
   void* mws = p;
   p += up(model);
@@ -1016,6 +1130,8 @@ c2_status c2_build_knn_graph_learned(const c2_model_config* cfg, const void* d_s
                           &o, d_nbr_id, d_nbr_inter, d_nbr_union, d_ws, base, stream);
   if (rc) return rc;
   rc = c2_get_status(d_ws, stream);
+  if (rc) return rc;
+  rc = c2_get_status(mws, stream);   // the proposal's own device status (bounded waits)
   if (rc) return rc;
   // quality probe (Eq. 2) on every (n / n_probe)-th user against exact brute force
   std::vector<int32_t> hp(n_probe);

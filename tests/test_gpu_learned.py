@@ -169,3 +169,38 @@ def test_model_keys_fused_argmax_match_oracle(c2):
         zz = np.sort(z[u, j * b:(j + 1) * b])
         assert zz[-1] - zz[-2] < 1e-3 * max(1.0, abs(zz[-1])), (j, u)
     assert len(diff) <= 0.01 * keys.size
+
+
+def _sub_csr(ptr, items, users):
+    lens = ptr[users + 1] - ptr[users]
+    sp = np.zeros(len(users) + 1, np.int32)
+    sp[1:] = np.cumsum(lens)
+    si = np.concatenate([items[ptr[u]:ptr[u + 1]] for u in users]).astype(np.int32)
+    return sp, si
+
+
+def test_model_keys_tcgen05_full_shape(c2):
+    # the learned workload's network (8 heads of 1024 buckets, hidden 256):
+    # tcgen05 logits GEMM over 256-column slices, 157 row tiles x 32 slices
+    # spread over the SMs (several tiles and a slice change per CTA, ring and
+    # accumulator reuse), a ragged last tile (20011 = 156 * 128 + 43)
+    m = c2.Model(8, 1024, 64, 256, 18, 13).init()
+    n = 20011
+    ptr, items = synth.random_profiles(n, 5000, 40, 48)
+    keys = m.propose(dev(ptr), dev(items)).cpu().numpy()
+    rng = np.random.default_rng(5)
+    users = np.unique(np.concatenate([rng.choice(n, 500, replace=False), np.arange(128),
+                                      np.arange(n - 171, n)]))
+    sp, si = _sub_csr(ptr, items, users)
+    params = [x.cpu().numpy() for x in m.params()]
+    z, okeys = oracle.model_forward(m.config(), params, sp, si)
+    b = m.cfg.b
+    got = keys[:, users]
+    diff = np.argwhere(got != okeys)
+    for j, i in diff:
+        zz = np.sort(z[i, j * b:(j + 1) * b])
+        assert zz[-1] - zz[-2] < 1e-3 * max(1.0, abs(zz[-1])), (j, users[i])
+    assert len(diff) <= 0.01 * got.size
+    # chunked proposals (three chunks, the last ragged) give the same keys
+    keys2 = m.propose(dev(ptr), dev(items), chunk=8192)
+    same(keys2, keys, "keys with 8192-row chunks")
