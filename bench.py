@@ -281,18 +281,22 @@ def recorded_traffic(kernel, workload):
     return rec.get("bytes_per_launch")
 
 
-def roofline(phase_ms, phase_calls, stats, w, nnz, pk, pk_src, W):
-    """Roofline of the dominant kernel phase (the largest share of device time)."""
+def phase_model(dom, phase_ms, phase_calls, stats, w, nnz, pk, W):
+    """Roofline record of one phase's kernel: algorithmic work per launch over
+    the launch's device time (CUDA events), against the measured peak."""
     n, t, k = w.n_users, w.t, w.k
     S = t * n
-    candidates = {k_: v for k_, v in phase_ms.items() if v > 0 and not k_.startswith("round_")}
-    if not candidates:
-        return None
-    dom = max(candidates, key=candidates.get)
     calls = max(1, phase_calls.get(dom, 1))
     ms = phase_ms[dom] / calls
     alu_peak = N_SM * LANES_PER_SM * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12   # Tlane-op/s
     peak_note = f"peak = 152 SMs x 128 lanes x {pk.get('sm_max_mhz', 2070.0):.0f} MHz"
+
+    def hbm(kernel, bytes_, model):
+        achieved = bytes_ / (ms * 1e-3) / 1e9
+        return {"kernel": kernel, "phase": dom, "bound": "hbm", "achieved": achieved,
+                "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": achieved / pk["hbm_gbs"],
+                "traffic": None, "ms_per_launch": ms, "model": model}
+
     if dom == "greedy_rounds":
         # per examined neighbour-list entry: bitmap test-and-set (3), count and
         # length lookups (3), exact cross-multiplied comparison (6) = 12 lane-ops
@@ -316,18 +320,40 @@ def roofline(phase_ms, phase_calls, stats, w, nnz, pk, pk_src, W):
                 "traffic": recorded_traffic("k_gram", w.name), "ms_per_launch": ms,
                 "model": f"{ops_per_visit:.1f} integer lane-ops per candidate item visit "
                          f"({visits / calls:.3e} visits/launch); {peak_note}"}
+    if dom == "brute_rows" and stats.get("brute_rows"):
+        bytes_ = 2 * stats["brute_gram_elems"] + 12 * k * stats["brute_rows"]
+        return hbm("k_gram_topk", bytes_ / calls,
+                   f"count rows read once (2 B x {stats['brute_gram_elems']:.3e} elements) + "
+                   f"12 k B of list per row ({stats['brute_rows']} rows)")
     if dom == "merge":
-        bytes_ = 4 * S + 12 * S * k + 12 * n * k
-        achieved = bytes_ / (ms * 1e-3) / 1e9
-        return {"kernel": "k_merge", "phase": dom, "bound": "hbm", "achieved": achieved,
-                "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": achieved / pk["hbm_gbs"],
-                "traffic": None, "ms_per_launch": ms}
-    # minhash-like phases: CSR read once plus one key per slot
-    bytes_ = 4 * (n + 1) + 4 * nnz + 4 * S
-    achieved = bytes_ / (ms * 1e-3) / 1e9
-    return {"kernel": dom, "phase": dom, "bound": "hbm", "achieved": achieved,
-            "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": achieved / pk["hbm_gbs"],
-            "traffic": None, "ms_per_launch": ms}
+        return hbm("k_merge", 4 * S + 12 * S * k + 12 * n * k,
+                   "t rows of k (id, inter, union) read per user, one row written, slot map read")
+    if dom == "hash_minhash_level0":
+        return hbm("k_minhash", 4 * (n + 1) + 4 * nnz + 4 * S,
+                   "CSR read once plus one key per (function, user) slot")
+    return None
+
+
+def roofline(phase_ms, phase_calls, stats, w, nnz, pk, pk_src, W):
+    """Roofline of the dominant kernel phase (the largest share of device time)
+    and the records of the other modelled phases."""
+    candidates = {k_: v for k_, v in phase_ms.items() if v > 0 and not k_.startswith("round_")}
+    if not candidates:
+        return None, []
+    dom = max(candidates, key=candidates.get)
+    total = sum(candidates.values())
+    rows = []
+    for ph in sorted(candidates, key=candidates.get, reverse=True):
+        rec = phase_model(ph, phase_ms, phase_calls, stats, w, nnz, pk, W)
+        row = {"phase": ph, "share": candidates[ph] / total}
+        if rec:
+            row.update({k_: rec[k_] for k_ in ("kernel", "bound", "achieved", "peak", "unit",
+                                               "frac", "ms_per_launch")})
+        rows.append(row)
+    rf = phase_model(dom, phase_ms, phase_calls, stats, w, nnz, pk, W)
+    if rf is None:   # an unmodelled phase dominates: CSR-read model as a floor
+        rf = {"kernel": dom, "phase": dom, "bound": "hbm", "note": "no model for this phase"}
+    return rf, rows
 
 
 # ------------------------------------------------------------------ main arm
@@ -437,10 +463,11 @@ def main():
     phase_calls = {k_: v["calls"] / args.steps for k_, v in prof.items()}
     W = 2 if w.n_items * 8 + 40000 <= 227 * 1024 else 1
     stats2 = dict(stats)
-    rf = None
+    rf, kernels = None, []
     try:
-        rf = roofline({k_: v["ms"] for k_, v in prof.items()},
-                      {k_: v["calls"] for k_, v in prof.items()}, stats2, w, nnz, pk, pk_src, W)
+        rf, kernels = roofline({k_: v["ms"] for k_, v in prof.items()},
+                               {k_: v["calls"] for k_, v in prof.items()}, stats2, w, nnz, pk,
+                               pk_src, W)
         if rf:
             rf["peak_source"] = pk_src
     except Exception as e:   # the measurement stands without the model
@@ -467,7 +494,8 @@ def main():
                 "quality": quality, "e2e": e2e, "gpu_launches": launches,
                 "gpu_launches_per_step": launches / args.steps,
                 "wall_s_timed": wall, "step_ms": step_ms,
-                "phases_ms_per_step": phase_ms, "roofline": rf, "cpu_baseline": cpu,
+                "phases_ms_per_step": phase_ms, "roofline": rf, "kernels": kernels,
+                "cpu_baseline": cpu,
                 "autotune": c2.c2_autotune_report(),
                 "clocks": clocks, "stats": stats}
         print(json.dumps(line))

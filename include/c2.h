@@ -110,6 +110,10 @@ typedef struct {
   int64_t greedy_evaluated; /* fresh candidates whose counts a greedy round looked up (the
                                method's other evaluations come from neighbour lists known
                                to repeat the previous round's candidates)                 */
+  int64_t brute_gram_elems; /* count-matrix elements (rows padded to 8) of brute-force
+                               clusters with a count matrix                                */
+  int32_t brute_rows;       /* users of those clusters (rows ranked by the row kernel)     */
+  int32_t reserved;
 } c2_stats;
 
 /* Fills *opt with the defaults described above.  Never fails. */

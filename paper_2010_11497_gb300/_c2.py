@@ -49,7 +49,9 @@ class Stats(C.Structure):
                 ("max_cluster", C.c_int32), ("max_profile", C.c_int32),
                 ("greedy_users", C.c_int32), ("item_visits_brute", C.c_int64),
                 ("item_visits_greedy", C.c_int64), ("greedy_visits", C.c_int64),
-                ("greedy_computed", C.c_int64), ("greedy_evaluated", C.c_int64)]
+                ("greedy_computed", C.c_int64), ("greedy_evaluated", C.c_int64),
+                ("brute_gram_elems", C.c_int64), ("brute_rows", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 _lib = None
@@ -322,7 +324,8 @@ def c2_get_stats(ws, stream=None) -> dict:
                 max_cluster=s.max_cluster, max_profile=s.max_profile,
                 greedy_users=s.greedy_users, greedy_visits=s.greedy_visits,
                 greedy_computed=s.greedy_computed, greedy_evaluated=s.greedy_evaluated,
-                item_visits_brute=s.item_visits_brute, item_visits_greedy=s.item_visits_greedy)
+                item_visits_brute=s.item_visits_brute, item_visits_greedy=s.item_visits_greedy,
+                brute_gram_elems=s.brute_gram_elems, brute_rows=s.brute_rows)
 
 
 def c2_reset_status(ws, stream=None):

@@ -248,6 +248,8 @@ c2_status c2_get_stats(const void* d_ws, c2_stream_t stream, c2_stats* out) {
   out->greedy_visits = (int64_t)h.greedy_visits;
   out->greedy_computed = (int64_t)h.greedy_computed;
   out->greedy_evaluated = (int64_t)h.greedy_evaluated;
+  out->brute_gram_elems = (int64_t)h.brute_gram_elems;
+  out->brute_rows = h.brute_rows;
   return C2_OK;
 }
 

@@ -39,7 +39,9 @@ struct DevHeader {
   int32_t knn_max_len;         // longest profile among the clustered users
   int32_t pad0;
   unsigned long long greedy_evaluated;  // candidates looked up by greedy rounds
-  int32_t pad[12];
+  unsigned long long brute_gram_elems;  // count-matrix elements of brute-force clusters
+  int32_t brute_rows;          // users of brute-force clusters with a count matrix
+  int32_t pad[9];
 };
 static_assert(sizeof(DevHeader) <= 256, "header must fit 256 bytes");
 

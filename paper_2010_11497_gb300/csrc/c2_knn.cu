@@ -945,6 +945,9 @@ __global__ void k_greedy_list(const int32_t* __restrict__ gflag, const int32_t* 
     atomicMax(&hdr->max_cluster, M);
     atomicAdd(&hdr->greedy_users, M);
     atomicAdd(&hdr->n_greedy, 1);
+  } else {
+    atomicAdd(&hdr->brute_gram_elems, (unsigned long long)gsq[g]);
+    atomicAdd(&hdr->brute_rows, M);
   }
 }
 
