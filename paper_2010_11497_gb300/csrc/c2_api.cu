@@ -95,6 +95,7 @@ void bind_knn_ws(Ws& w, const Sizes& s, KnnWs& c) {
   c.pos_of = w.take<int32_t>(S + 1);
   c.partial = w.take<double>(1024);
   c.scan_tmp = w.take<int32_t>(scan_tmp_elems(S + 1));
+  c.scan_tmp2 = w.take<int32_t>(scan_tmp_elems(S + 1));
   c.scan_tmp64 = w.take<int64_t>(scan_tmp_elems(S + 1));
 }
 

@@ -142,6 +142,7 @@ struct KnnWs {
   int32_t* pos_of;         // [S] (function, user) -> slot
   double* partial;         // [1024] reduction partials
   int32_t* scan_tmp;
+  int32_t* scan_tmp2;      // scan scratch of work on the side stream
   int64_t* scan_tmp64;
 };
 

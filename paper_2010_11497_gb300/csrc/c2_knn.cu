@@ -1492,6 +1492,52 @@ TableCfg pick_gram(int strategy, int m) {
   return {0, 0};
 }
 
+// A second stream per device for work that is independent of the main
+// stream's next kernels (brute-force clusters while the count matrices and the
+// greedy rounds run): latency-bound kernels fill the SMs the main stream's
+// persistent kernels leave idle at their tails.  Created once, never destroyed.
+cudaStream_t side_stream() {
+  static std::mutex mu;
+  static std::map<int, cudaStream_t> streams;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = streams.find(dev);
+  if (it != streams.end()) return it->second;
+  cudaStream_t sst = nullptr;
+  if (cudaStreamCreateWithFlags(&sst, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+  streams[dev] = sst;
+  return sst;
+}
+
+// Work on `to` after everything issued so far on `from`.
+cudaError_t stream_after(cudaStream_t to, cudaStream_t from) {
+  cudaEvent_t ev;
+  cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  if (e != cudaSuccess) return e;
+  e = cudaEventRecord(ev, from);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(to, ev, 0);
+  cudaEventDestroy(ev);   // released once the wait is satisfied
+  return e;
+}
+
+// Joins the side stream back into the main stream when it goes out of scope
+// (every return path of the local-KNN step).
+struct SideJoin {
+  cudaStream_t st, side;
+  bool used = false;
+  c2_status fork() {
+    used = true;
+    return stream_after(side, st) == cudaSuccess ? C2_OK : C2_ERR_CUDA;
+  }
+  c2_status join() {
+    if (!used) return C2_OK;
+    used = false;
+    return stream_after(st, side) == cudaSuccess ? C2_OK : C2_ERR_CUDA;
+  }
+  ~SideJoin() { join(); }
+};
+
 c2_status build_padded_csr(const int32_t* ptr, const int32_t* items, const Sizes& s, KnnWs& w,
                            cudaStream_t st) {
   if (s.n == 0) return C2_OK;
@@ -1534,16 +1580,22 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
   }
   p_prep.end();
 
+  // small brute-force clusters on the side stream, beside the count matrices
+  cudaStream_t side = side_stream();
+  if (!side) return C2_ERR_CUDA;
+  SideJoin sj{st, side};
   {
-    Prof p_small(st, "brute_merge");
-    C2_CUDA_TRY(scan_exclusive(w.small_cnt, w.small_off, S, w.scan_tmp, st));
-    C2_LAUNCH(k_fill_small, div_up(S, T), T, 0, st, w.small_cnt, w.small_off, S, w.small_slot);
+    c2_status rc = sj.fork();
+    if (rc) return rc;
+    Prof p_small(side, "brute_merge");
+    C2_CUDA_TRY(scan_exclusive(w.small_cnt, w.small_off, S, w.scan_tmp2, side));
+    C2_LAUNCH(k_fill_small, div_up(S, T), T, 0, side, w.small_cnt, w.small_off, S, w.small_slot);
     SmallArgs sa{};
     sa.ptr = ptr; sa.items = items; sa.cptr = cptr; sa.cusers = cusers; sa.list = w.small_slot;
     sa.n_list = w.small_off + S; sa.k = k; sa.out_id = lid; sa.out_in = lin; sa.out_un = lun;
     sa.hdr = w.hdr;
     C2_LAUNCH(k_small_knn, (int)std::min<int64_t>(div_up(S, kSmallWarps), (int64_t)num_sms() * 5),
-              32 * kSmallWarps, 0, st, sa);
+              32 * kSmallWarps, 0, side, sa);
     C2_CUDA_TRY(cudaGetLastError());
   }
 
@@ -1722,17 +1774,21 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
       }
     }
     if (n_brute_users) {
-      Prof p_bt(st, "brute_rows");
-      C2_CUDA_TRY(scan_exclusive(w.bb_cnt, w.bb_off, nb, w.scan_tmp, st));
-      C2_LAUNCH(k_fill_users, nb, 256, 0, st, w.gcl, cptr, w.gkind, 0, w.bb_off, g0, nb,
+      // brute-force rows on the side stream, beside the greedy rounds (both
+      // only read this batch's count matrices)
+      c2_status rc = sj.fork();
+      if (rc) return rc;
+      Prof p_bt(side, "brute_rows");
+      C2_CUDA_TRY(scan_exclusive(w.bb_cnt, w.bb_off, nb, w.scan_tmp2, side));
+      C2_LAUNCH(k_fill_users, nb, 256, 0, side, w.gcl, cptr, w.gkind, 0, w.bb_off, g0, nb,
                 w.ub_slot, w.ub_g);
       RowTopkArgs ra{};
       ra.cptr = cptr; ra.cusers = cusers; ra.slen = w.slen; ra.gcl = w.gcl; ra.gofs = w.gofs;
       ra.gram = w.gram; ra.u_slot = w.ub_slot; ra.u_g = w.ub_g; ra.n_users_dev = w.bb_off + nb;
       ra.ipos = w.ipos; ra.iinfo = w.iinfo;
       ra.k = k; ra.out_id = lid; ra.out_in = lin; ra.out_un = lun; ra.hdr = w.hdr;
-      if (keyed) C2_LAUNCH(k_gram_topk<true>, div_up(n_brute_users * 32, kNT), kNT, 0, st, ra);
-      else C2_LAUNCH(k_gram_topk<false>, div_up(n_brute_users * 32, kNT), kNT, 0, st, ra);
+      if (keyed) C2_LAUNCH(k_gram_topk<true>, div_up(n_brute_users * 32, kNT), kNT, 0, side, ra);
+      else C2_LAUNCH(k_gram_topk<false>, div_up(n_brute_users * 32, kNT), kNT, 0, side, ra);
     }
     if (n_greedy_users) {
       GreedyArgs ga{};
@@ -1797,9 +1853,14 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
       }
     }
     C2_CUDA_TRY(cudaGetLastError());
+    if (g1 < ng) {
+      // the next batch rewrites the count matrices the side stream reads
+      c2_status rc = sj.join();
+      if (rc) return rc;
+    }
     g0 = g1;
   }
-  return C2_OK;
+  return sj.join();
 }
 
 c2_status run_bruteforce(const int32_t* ptr, const int32_t* items, const Sizes& s,
