@@ -36,6 +36,7 @@ constexpr int kNT = 256;
 constexpr int kMaxGreedyM = 10240;            // greedy cluster size limit (shared staging)
 constexpr int kBitmapWords = kMaxGreedyM / 32;
 constexpr int kGreedyUsersPerWarp = 4;
+constexpr int kGreedySmallItemRounds = 2;      // rounds with one user per warp and work item
 constexpr int kSmallCut = 9;     // brute clusters below this size: warp-per-cluster kernel (<= 33)
 constexpr int kGreedyChunk = 8 * kGreedyUsersPerWarp;   // users per block work item
 
@@ -1141,7 +1142,7 @@ struct SmemCU {
 // all k of its entries (the current list is the top k of last round's
 // candidates).  Those lists are only deduplicated, so that the count of
 // evaluated pairs stays that of the method.
-template <bool Keyed>
+template <bool Keyed, int UPW>
 __global__ void __launch_bounds__(kNT, 4) k_greedy_round(GreedyArgs a) {
   extern __shared__ __align__(16) uint32_t gsm[];
   __shared__ int32_t s_sid[Keyed ? 1 : 8][64];
@@ -1158,13 +1159,18 @@ __global__ void __launch_bounds__(kNT, 4) k_greedy_round(GreedyArgs a) {
   const int nwork = *a.n_gwork;
   const int k = a.k;
   const bool prune = a.chg_in != nullptr && a.round >= 2 && a.n_random == 0;
+  // a work item of the list is a chunk of kGreedyChunk users; a round splits
+  // it into nsub items of 8 * UPW users (UPW per warp)
+  constexpr int nsub = kGreedyUsersPerWarp / UPW;
+  const int nitems = nwork * nsub;
   unsigned long long evals = 0, visits = 0, computed = 0, evaluated = 0;
   for (;;) {
-    if (threadIdx.x == 0) s_work = dev_failed(a.hdr) ? nwork : (int)atomicAdd(a.counter, 1u);
+    if (threadIdx.x == 0) s_work = dev_failed(a.hdr) ? nitems : (int)atomicAdd(a.counter, 1u);
     __syncthreads();
     const int wi = s_work;
-    if (wi >= nwork) break;
-    const int g = a.gw_g[wi], chunk = a.gw_t[wi];
+    if (wi >= nitems) break;
+    const int g = a.gw_g[wi / nsub];
+    const int u0 = a.gw_t[wi / nsub] * kGreedyChunk + (wi % nsub) * 8 * UPW;   // first user
     const int c = a.gcl[g];
     const int cs = a.cptr[c], M = a.cptr[c + 1] - cs, Mp = (M + 7) & ~7;
     const int2* info_g = a.iinfo + cs;
@@ -1184,8 +1190,8 @@ __global__ void __launch_bounds__(kNT, 4) k_greedy_round(GreedyArgs a) {
       if constexpr (Keyed) return s_info[x] & 0xffffu;
       else return s_info[x];
     };
-    for (int uu = 0; uu < kGreedyUsersPerWarp; ++uu) {
-      const int l = chunk * kGreedyChunk + uu * 8 + warp;
+    for (int uu = 0; uu < UPW; ++uu) {
+      const int l = u0 + uu * 8 + warp;
       if (l >= M) break;
       const int slot = cs + l;
       const int e = lane < k ? a.wl_in[(int64_t)slot * k + lane] : -1;
@@ -1824,11 +1830,20 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
       {
         Prof p_rounds(st, "greedy_rounds");
         const int smem = 21 * ga.mcap;
-        auto kround = keyed ? k_greedy_round<true> : k_greedy_round<false>;
-        C2_CUDA_TRY(cudaFuncSetAttribute(kround, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        // the first rounds compute (nearly) every user: work items of one user
+        // per warp even out the round's tail; later rounds settle most users
+        // by the skip test, where larger items cost less to schedule
+        auto kbig = keyed ? k_greedy_round<true, kGreedyUsersPerWarp>
+                          : k_greedy_round<false, kGreedyUsersPerWarp>;
+        auto ksmall = keyed ? k_greedy_round<true, 1> : k_greedy_round<false, 1>;
         int per_sm = 0;
-        C2_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kround, kNT, smem));
-        if (per_sm < 1) return C2_ERR_UNSUPPORTED;
+        for (auto kf : {kbig, ksmall}) {
+          C2_CUDA_TRY(cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+          int ps = 0;
+          C2_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, kf, kNT, smem));
+          if (ps < 1) return C2_ERR_UNSUPPORTED;
+          per_sm = per_sm ? std::min(per_sm, ps) : ps;
+        }
         static const char* kRoundName[] = {"round_01", "round_02", "round_03", "round_04",
                                            "round_05", "round_06", "round_07", "round_08",
                                            "round_09", "round_10", "round_11+"};
@@ -1842,6 +1857,7 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
           ga.chg_out = skipping ? chg_nxt : nullptr;
           std::swap(chg_cur, chg_nxt);
           C2_CUDA_TRY(cudaMemsetAsync(ga.counter, 0, sizeof(unsigned), st));
+          auto kround = r <= kGreedySmallItemRounds ? ksmall : kbig;
           C2_LAUNCH(kround, num_sms() * per_sm, kNT, smem, st, ga);
           std::swap(cur, nxt);
         }
