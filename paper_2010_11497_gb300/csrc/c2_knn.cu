@@ -567,11 +567,11 @@ __global__ void __launch_bounds__(kNT) k_gram_topk(RowTopkArgs a) {
     // floors the filter of the second pass
     uint32_t bc = 0u, bu = 1u, bl = 0x7fffffffu;
     int bp = -1;
-#pragma unroll 1
-    for (int p = lane; p < M; p += 32) {
+#pragma unroll 4
+    for (int p = lane; p < M; p += 32) {   // unrolled: four candidates' loads in flight
       const uint32_t c = p != P ? (uint32_t)row[p] : 0u;
-      if (c == 0u) continue;
       const int2 in = info[p];
+      if (c == 0u) continue;
       const uint32_t u = my + (uint32_t)in.y - c;
       const uint32_t l = c * bu, r = bc * u;
       if (l > r || (l == r && (uint32_t)in.x < bl)) { bc = c; bu = u; bl = (uint32_t)in.x; bp = p; }
