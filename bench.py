@@ -259,7 +259,9 @@ def run_reference(args):
 # profiles/traffic.json together with a hash of the sources it was taken on;
 # null once those sources change.
 KERNEL_SOURCES = ["paper_2010_11497_gb300/csrc/c2_knn.cu",
-                  "paper_2010_11497_gb300/csrc/c2_internal.cuh"]
+                  "paper_2010_11497_gb300/csrc/c2_internal.cuh",
+                  "paper_2010_11497_gb300/csrc/c2_merge.cu",
+                  "paper_2010_11497_gb300/csrc/c2_cluster.cu"]
 
 
 def sources_sha1():
@@ -281,12 +283,15 @@ def recorded_traffic(kernel, workload):
     return rec.get("bytes_per_launch")
 
 
-def phase_model(dom, phase_ms, phase_calls, stats, w, nnz, pk, W):
+def phase_model(dom, phase_ms, phase_calls, stats, w, nnz, pk, W, steps):
     """Roofline record of one phase's kernel: algorithmic work per launch over
-    the launch's device time (CUDA events), against the measured peak."""
+    the launch's device time (CUDA events), against the measured peak.
+    phase_ms and phase_calls are totals over `steps` builds; stats are those
+    of one build."""
     n, t, k = w.n_users, w.t, w.k
     S = t * n
     calls = max(1, phase_calls.get(dom, 1))
+    per_build = max(1.0, calls / max(1, steps))   # launches of the phase in one build
     ms = phase_ms[dom] / calls
     alu_peak = N_SM * LANES_PER_SM * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12   # Tlane-op/s
     peak_note = f"peak = 152 SMs x 128 lanes x {pk.get('sm_max_mhz', 2070.0):.0f} MHz"
@@ -295,12 +300,12 @@ def phase_model(dom, phase_ms, phase_calls, stats, w, nnz, pk, W):
         achieved = bytes_ / (ms * 1e-3) / 1e9
         return {"kernel": kernel, "phase": dom, "bound": "hbm", "achieved": achieved,
                 "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": achieved / pk["hbm_gbs"],
-                "traffic": None, "ms_per_launch": ms, "model": model}
+                "traffic": recorded_traffic(kernel, w.name), "ms_per_launch": ms, "model": model}
 
     if dom == "greedy_rounds":
         # per examined neighbour-list entry: bitmap test-and-set (3), count and
         # length lookups (3), exact cross-multiplied comparison (6) = 12 lane-ops
-        ms = phase_ms[dom] / (calls * max(1, w.greedy_rounds))   # one launch per round
+        ms = phase_ms[dom] / (steps * max(1, w.greedy_rounds))   # one launch per round
         visits = stats.get("greedy_visits", 0) / max(1, w.greedy_rounds)
         ops = 12.0
         achieved = visits * ops / (ms * 1e-3) / 1e12
@@ -314,15 +319,15 @@ def phase_model(dom, phase_ms, phase_calls, stats, w, nnz, pk, W):
     if dom == "gram":
         visits = stats["item_visits_brute"] + stats["item_visits_greedy"]
         ops_per_visit = 1 + W + 12 * W + 48 * W / 12.0
-        achieved = visits / calls * ops_per_visit / (ms * 1e-3) / 1e12
+        achieved = visits / per_build * ops_per_visit / (ms * 1e-3) / 1e12
         return {"kernel": "k_gram<%d>" % W, "phase": dom, "bound": "alu", "achieved": achieved,
                 "peak": alu_peak, "unit": "Tlane-op/s", "frac": achieved / alu_peak,
                 "traffic": recorded_traffic("k_gram", w.name), "ms_per_launch": ms,
                 "model": f"{ops_per_visit:.1f} integer lane-ops per candidate item visit "
-                         f"({visits / calls:.3e} visits/launch); {peak_note}"}
+                         f"({visits / per_build:.3e} visits/launch); {peak_note}"}
     if dom == "brute_rows" and stats.get("brute_rows"):
         bytes_ = 2 * stats["brute_gram_elems"] + 12 * k * stats["brute_rows"]
-        return hbm("k_gram_topk", bytes_ / calls,
+        return hbm("k_gram_topk", bytes_ / per_build,
                    f"count rows read once (2 B x {stats['brute_gram_elems']:.3e} elements) + "
                    f"12 k B of list per row ({stats['brute_rows']} rows)")
     if dom == "merge":
@@ -334,7 +339,7 @@ def phase_model(dom, phase_ms, phase_calls, stats, w, nnz, pk, W):
     return None
 
 
-def roofline(phase_ms, phase_calls, stats, w, nnz, pk, pk_src, W):
+def roofline(phase_ms, phase_calls, stats, w, nnz, pk, pk_src, W, steps):
     """Roofline of the dominant kernel phase (the largest share of device time)
     and the records of the other modelled phases."""
     candidates = {k_: v for k_, v in phase_ms.items() if v > 0 and not k_.startswith("round_")}
@@ -344,13 +349,13 @@ def roofline(phase_ms, phase_calls, stats, w, nnz, pk, pk_src, W):
     total = sum(candidates.values())
     rows = []
     for ph in sorted(candidates, key=candidates.get, reverse=True):
-        rec = phase_model(ph, phase_ms, phase_calls, stats, w, nnz, pk, W)
+        rec = phase_model(ph, phase_ms, phase_calls, stats, w, nnz, pk, W, steps)
         row = {"phase": ph, "share": candidates[ph] / total}
         if rec:
             row.update({k_: rec[k_] for k_ in ("kernel", "bound", "achieved", "peak", "unit",
-                                               "frac", "ms_per_launch")})
+                                               "frac", "ms_per_launch", "traffic")})
         rows.append(row)
-    rf = phase_model(dom, phase_ms, phase_calls, stats, w, nnz, pk, W)
+    rf = phase_model(dom, phase_ms, phase_calls, stats, w, nnz, pk, W, steps)
     if rf is None:   # an unmodelled phase dominates: CSR-read model as a floor
         rf = {"kernel": dom, "phase": dom, "bound": "hbm", "note": "no model for this phase"}
     return rf, rows
@@ -472,7 +477,7 @@ def main():
     try:
         rf, kernels = roofline({k_: v["ms"] for k_, v in prof.items()},
                                {k_: v["calls"] for k_, v in prof.items()}, stats2, w, nnz, pk,
-                               pk_src, W)
+                               pk_src, W, args.steps)
         if rf:
             rf["peak_source"] = pk_src
     except Exception as e:   # the measurement stands without the model
