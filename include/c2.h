@@ -66,7 +66,11 @@ typedef enum {
   C2_ERR_QUALITY_FALLBACK = 7 /* informational: the learned proposer fell back to FRH    */
 } c2_status;
 
-/* Strategy used to count common items inside clusters (Step 2). */
+/* Strategy used to count common items inside clusters (Step 2).  When the
+ * item universe is too large for a shared-memory item table (more than about
+ * 57,000 items), every strategy but MERGE counts through a shared-memory hash
+ * table of the 32 query users' items instead, provided no profile exceeds
+ * 4,096 items; otherwise rows are counted by merges. */
 enum {
   C2_STRATEGY_AUTO = -1,   /* autotuned table, per (cluster size, density) bucket         */
   C2_STRATEGY_MERGE = 0,   /* sorted-list merge, one warp per query user                  */

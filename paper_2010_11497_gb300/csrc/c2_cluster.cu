@@ -18,32 +18,43 @@ namespace {
 // ------------------------------------------------------------------ K0: CSR check
 // Profiles must be sets (Section II-A): ptr non-decreasing from 0, items in
 // range and strictly increasing per row.  One warp per row.
-__global__ void k_validate(const int32_t* __restrict__ ptr, const int32_t* __restrict__ items,
-                           int32_t n, int32_t m, DevHeader* hdr) {
-  const int lane = threadIdx.x & 31;
+__global__ void __launch_bounds__(256) k_validate(const int32_t* __restrict__ ptr,
+                                                  const int32_t* __restrict__ items, int32_t n,
+                                                  int32_t m, DevHeader* hdr) {
+  __shared__ int32_t s_len[8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (row >= n) return;
-  if (row == 0 && lane == 0 && ptr[0] != 0) dev_fail(hdr, C2_ERR_INVALID_CSR);
-  const int32_t s = ptr[row], e = ptr[row + 1];
-  if (e < s) {
-    if (lane == 0) dev_fail(hdr, C2_ERR_INVALID_CSR);
-    return;
+  int32_t len = 0;
+  if (row < n) {
+    if (row == 0 && lane == 0 && ptr[0] != 0) dev_fail(hdr, C2_ERR_INVALID_CSR);
+    const int32_t s = ptr[row], e = ptr[row + 1];
+    if (e < s) {
+      if (lane == 0) dev_fail(hdr, C2_ERR_INVALID_CSR);
+    } else if (e - s > kMaxProfile) {
+      if (lane == 0) dev_fail(hdr, C2_ERR_UNSUPPORTED);
+    } else {
+      bool bad = false;
+#pragma unroll 4
+      for (int32_t j = s + lane; j < e; j += 32) {   // four items' loads in flight
+        const int32_t x = items[j];
+        bad |= x < 0 || x >= m;
+        if (j > s) bad |= items[j - 1] >= x;
+      }
+      if (__any_sync(0xffffffffu, bad) && lane == 0) dev_fail(hdr, C2_ERR_INVALID_CSR);
+      len = e - s;
+      // padded rows (multiples of 4 items) must still be addressable with int32
+      if (row == n - 1 && lane == 0 && (int64_t)e + 3 * (int64_t)n + 64 >= (int64_t(1) << 31))
+        dev_fail(hdr, C2_ERR_UNSUPPORTED);
+    }
   }
-  if (e - s > kMaxProfile) {
-    if (lane == 0) dev_fail(hdr, C2_ERR_UNSUPPORTED);
-    return;
+  // longest profile: one atomic per block (every update goes to one address)
+  if (lane == 0) s_len[warp] = len;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int32_t mx = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mx = max(mx, s_len[w]);
+    if (mx > 0) atomicMax(&hdr->max_profile, mx);
   }
-  bool bad = false;
-  for (int32_t j = s + lane; j < e; j += 32) {
-    const int32_t x = items[j];
-    bad |= x < 0 || x >= m;
-    if (j > s) bad |= items[j - 1] >= x;
-  }
-  if (__any_sync(0xffffffffu, bad) && lane == 0) dev_fail(hdr, C2_ERR_INVALID_CSR);
-  if (lane == 0) atomicMax(&hdr->max_profile, e - s);
-  // padded rows (multiples of 4 items) must still be addressable with int32
-  if (row == n - 1 && lane == 0 && (int64_t)e + 3 * (int64_t)n + 64 >= (int64_t(1) << 31))
-    dev_fail(hdr, C2_ERR_UNSUPPORTED);
 }
 
 // ------------------------------------------------------------------ A1: item hashes

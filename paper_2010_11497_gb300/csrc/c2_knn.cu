@@ -402,6 +402,179 @@ __global__ void __launch_bounds__(NT, MB > 0 ? MB : 1) k_gram(GramArgs a) {
   if (lane == 0 && visits) atomicAdd(&a.hdr->item_visits[1], visits);
 }
 
+// ------------------------------------------------------------------ hashed gram kernel
+// k_gram for item universes too large for the shared table: the tile's query
+// items go into a shared open-addressing hash table (item -> mask of the
+// tile's queries holding it, linear probing, at most half full) behind a
+// 64 Ki-bit presence filter, so most candidate items (absent from every
+// query) cost one shared load.  A tile whose queries hold more items than
+// half the table is processed in passes over consecutive query groups.
+constexpr int kHashSlots = 8192;                 // keys + masks: 64 KiB
+constexpr int kHashCap = kHashSlots / 2;         // items per pass (load factor 1/2)
+constexpr int kHashFilterWords = 2048;           // 65,536-bit presence filter
+constexpr uint32_t kHashEmpty = 0xFFFFFFFFu;
+
+__device__ __forceinline__ uint32_t hash_mix(int32_t x) { return (uint32_t)x * 0x9E3779B1u; }
+
+// Mask of the tile's queries holding item x (0 if none).
+__device__ __forceinline__ uint32_t hash_find(const uint32_t* __restrict__ hkey,
+                                              const uint32_t* __restrict__ hval,
+                                              const uint32_t* __restrict__ filt, int32_t x) {
+  const uint32_t h = hash_mix(x);
+  const uint32_t fb = h >> 16;
+  if (!((filt[fb >> 5] >> (fb & 31)) & 1u)) return 0u;
+  uint32_t slot = (h >> 3) & (kHashSlots - 1);
+  for (int probe = 0; probe < kHashSlots; ++probe) {   // ends at an empty slot (half full)
+    const uint32_t kx = hkey[slot];
+    if (kx == (uint32_t)x) return hval[slot];
+    if (kx == kHashEmpty) return 0u;
+    slot = (slot + 1) & (kHashSlots - 1);
+  }
+  return 0u;
+}
+
+__device__ __forceinline__ void hash_insert(uint32_t* hkey, uint32_t* hval, uint32_t* filt,
+                                            int32_t x, uint32_t bit) {
+  const uint32_t h = hash_mix(x);
+  const uint32_t fb = h >> 16;
+  atomicOr(&filt[fb >> 5], 1u << (fb & 31));
+  uint32_t slot = (h >> 3) & (kHashSlots - 1);
+  for (int probe = 0; probe < kHashSlots; ++probe) {
+    const uint32_t old = atomicCAS(&hkey[slot], kHashEmpty, (uint32_t)x);
+    if (old == kHashEmpty || old == (uint32_t)x) {
+      atomicOr(&hval[slot], bit);
+      return;
+    }
+    slot = (slot + 1) & (kHashSlots - 1);
+  }
+}
+
+// count_row4 with the hashed table (W = 1).
+__device__ __forceinline__ void count_row4_hash(const int4* __restrict__ r4, int n4,
+                                                const uint32_t* __restrict__ hkey,
+                                                const uint32_t* __restrict__ hval,
+                                                const uint32_t* __restrict__ filt, int sentinel,
+                                                uint32_t* C) {
+  const int4 pad = make_int4(sentinel, sentinel, sentinel, sentinel);
+  int4 cur[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) cur[j] = j < n4 ? __ldg(r4 + j) : pad;
+  uint32_t acc[4] = {0u, 0u, 0u, 0u};
+  for (int i = 0; i < n4; i += 3) {
+    int4 nxt[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) nxt[j] = (i + 3 + j < n4) ? __ldg(r4 + i + 3 + j) : pad;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const int xs[4] = {cur[j].x, cur[j].y, cur[j].z, cur[j].w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const uint32_t m = hash_find(hkey, hval, filt, xs[q]);
+        if (m) add_mask(acc, m);
+      }
+    }
+    flush(acc, C);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) cur[j] = nxt[j];
+  }
+}
+
+size_t gram_hash_smem_bytes() { return (size_t)(2 * kHashSlots + kHashFilterWords) * 4; }
+
+template <int NT, int MB>
+__global__ void __launch_bounds__(NT, MB) k_gram_hash(GramArgs a) {
+  constexpr int Q = 32, NWARP = NT / 32;
+  extern __shared__ __align__(16) uint32_t hsm[];
+  uint32_t* hkey = hsm;
+  uint32_t* hval = hsm + kHashSlots;
+  uint32_t* filt = hsm + 2 * kHashSlots;
+  __shared__ int32_t q_id[Q], q_len[Q];
+  __shared__ int s_work, s_next;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int i = tid; i < kHashSlots; i += NT) { hkey[i] = kHashEmpty; hval[i] = 0u; }
+  for (int i = tid; i < kHashFilterWords; i += NT) filt[i] = 0u;
+  if (tid == 0) s_next = 0;
+  const int wbeg = *a.work_begin, nwork = *a.work_end;
+  unsigned long long visits = 0;
+  __syncthreads();
+  for (;;) {
+    if (tid == 0) s_work = dev_failed(a.hdr) ? nwork : wbeg + (int)atomicAdd(a.counter, 1u);
+    __syncthreads();
+    const int wi = s_work;
+    if (wi >= nwork) break;
+    const int c = a.work_c[wi], tq = a.work_t[wi];
+    const int cbase = a.cptr[c], M = a.cptr[c + 1] - cbase, Mp = (M + 7) & ~7;
+    const int nq = min(Q, M - tq * Q);
+    if (tid < Q) {
+      int id = -1, len = 0;
+      if (tid < nq) {
+        const int2 in = a.iinfo[cbase + tq * Q + tid];
+        id = a.cusers[cbase + in.x];
+        len = in.y;
+      }
+      q_id[tid] = id;
+      q_len[tid] = len;
+    }
+    __syncthreads();
+    uint16_t* G0 = a.gram + a.gofs[c];
+    // passes over consecutive query groups of at most kHashCap items (every
+    // profile fits: the host checks the longest against kHashCap)
+    int j0 = 0;
+    while (j0 < nq) {
+      int j1 = j0, sum = 0;
+      while (j1 < nq && sum + q_len[j1] <= kHashCap) sum += q_len[j1++];
+      if (j1 == j0) j1 = j0 + 1;   // not reached when the host check holds
+      for (int j = j0 + warp; j < j1; j += NWARP) {
+        const int u = q_id[j];
+        for (int e = a.ptr[u] + lane; e < a.ptr[u + 1]; e += 32)
+          hash_insert(hkey, hval, filt, a.items[e], 1u << j);
+      }
+      __syncthreads();
+      for (;;) {
+        int p0 = 0;
+        if (lane == 0) p0 = atomicAdd(&s_next, 32);
+        p0 = tq * Q + __shfl_sync(0xffffffffu, p0, 0);
+        if (p0 >= M) break;
+        const int p = p0 + lane;
+        if (p < M) {
+          const int2 info = a.iinfo[cbase + p];
+          const int v = a.cusers[cbase + info.x];
+          const int len = info.y;
+          uint32_t C[16];
+#pragma unroll
+          for (int r = 0; r < 16; ++r) C[r] = 0;
+          count_row4_hash(reinterpret_cast<const int4*>(a.pitems + a.pptr[v]), (len + 3) >> 2,
+                          hkey, hval, filt, a.n_items, C);
+          visits += (unsigned)len;
+          // row p, columns tq*Q + j0 .. tq*Q + j1
+          uint16_t* rowp = G0 + (int64_t)p * Mp + tq * Q;
+#pragma unroll
+          for (int j = 0; j < Q; ++j)
+            if (j >= j0 && j < j1) rowp[j] = (uint16_t)((C[creg(j)] >> (16 * chalf(j))) & 0xFFFFu);
+          // column p of the tile's rows (the tile's own block is computed whole)
+          if (p >= (tq + 1) * Q) {
+            uint16_t* col = G0 + (int64_t)(tq * Q) * Mp + p;
+#pragma unroll
+            for (int j = 0; j < Q; ++j)
+              if (j >= j0 && j < j1)
+                col[(int64_t)j * Mp] = (uint16_t)((C[creg(j)] >> (16 * chalf(j))) & 0xFFFFu);
+          }
+        }
+      }
+      __syncthreads();
+      // empty the table for the next pass or tile
+      for (int i = tid; i < kHashSlots; i += NT) { hkey[i] = kHashEmpty; hval[i] = 0u; }
+      for (int i = tid; i < kHashFilterWords; i += NT) filt[i] = 0u;
+      if (tid == 0) s_next = 0;
+      __syncthreads();
+      j0 = j1;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) visits += __shfl_xor_sync(0xffffffffu, visits, o);
+  if (lane == 0 && visits) atomicAdd(&a.hdr->item_visits[1], visits);
+}
+
 __device__ __forceinline__ uint32_t merge_count(const int32_t* __restrict__ a, int la,
                                                 const int32_t* __restrict__ b, int lb);
 
@@ -647,6 +820,7 @@ __global__ void k_pad_copy(const int32_t* __restrict__ ptr, const int32_t* __res
     return;
   }
   const int32_t s = ptr[u], len = ptr[u + 1] - s, ps = pptr[u], plen = pptr[u + 1] - ps;
+#pragma unroll 4
   for (int j = lane; j < plen; j += 32) pitems[ps + j] = j < len ? items[s + j] : m;
 }
 
@@ -1448,6 +1622,19 @@ c2_status launch_gram_t(const GramArgs& a, cudaStream_t st) {
   return C2_OK;
 }
 
+c2_status launch_gram_hash(const GramArgs& a, cudaStream_t st) {
+  constexpr int NT = 256, MB = 3;
+  const int smem = (int)gram_hash_smem_bytes();
+  C2_CUDA_TRY(cudaFuncSetAttribute(k_gram_hash<NT, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  int per_sm = 0;
+  C2_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gram_hash<NT, MB>, NT, smem));
+  if (per_sm < 1) return C2_ERR_UNSUPPORTED;
+  C2_CUDA_TRY(cudaMemsetAsync(a.counter, 0, sizeof(unsigned), st));
+  C2_LAUNCH(k_gram_hash<NT COMMA MB>, num_sms() * per_sm, NT, smem, st, a);
+  C2_CUDA_TRY(cudaGetLastError());
+  return C2_OK;
+}
+
 c2_status launch_gram(TableCfg c, const GramArgs& a, cudaStream_t st) {
   if (c.W == 1 && c.NT == 128 && c.MB == 0) return launch_gram_t<1, 128, 0>(a, st);
   if (c.W == 1 && c.NT == 128 && c.MB == 5) return launch_gram_t<1, 128, 5>(a, st);
@@ -1580,7 +1767,10 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
   C2_LAUNCH(k_prep, div_up(S, T), T, 0, st, cptr, n_clusters, cusers, ptr, S, thr, small_cut,
             kSmallItems, k, w.gflag, w.gkind_c, w.small_cnt, lid, lin, lun, w.hdr);
   C2_CUDA_TRY(cudaGetLastError());
-  if (tc.W) {
+  // the hashed count-matrix kernel is the candidate when no item table fits
+  const bool hash_ok = !tc.W && opt.strategy != C2_STRATEGY_MERGE &&
+                       (int)gram_hash_smem_bytes() + 1024 <= smem_optin();
+  if (tc.W || hash_ok) {
     c2_status rc = build_padded_csr(ptr, items, s, w, st);
     if (rc) return rc;
   }
@@ -1627,6 +1817,8 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
   const int64_t cap = s.gram_budget / (int64_t)sizeof(uint16_t);
   // exact 64-bit order keys need unions below 2^16 and clusters below 2^14
   bool keyed = max_len <= 32767;
+  // hashed count matrices when every profile fits one pass of the hash table
+  const bool use_hash = hash_ok && max_len <= kHashCap;
   for (int g = 0; g < ng; ++g) {
     if ((gkind[g] && gsz[g] > kMaxGreedyM) || goff[g + 1] - goff[g] > cap) return C2_ERR_UNSUPPORTED;
     if (gsz[g] > 16383) keyed = false;
@@ -1757,9 +1949,22 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
             if (rc) return rc;
           }
         }
+      } else if (use_hash) {
+        // no item table fits shared memory: the tiles' items in a shared hash
+        // table, one launch over all count-matrix clusters of the batch
+        C2_LAUNCH(k_bucket_tiles, div_up(nb, T), T, 0, st, w.gsz, g0, nb, -1, 32, w.bt_cnt);
+        C2_CUDA_TRY(scan_exclusive(w.bt_cnt, w.bt_off, nb, w.scan_tmp, st));
+        C2_LAUNCH(k_fill_work, div_up(nb, T), T, 0, st, w.bt_cnt, w.bt_off, w.gcl + g0, nb,
+                  w.work_c, w.work_t, &w.hdr->n_work);
+        GramArgs ga = ga0;
+        ga.work_begin = w.bt_off;
+        ga.work_end = w.bt_off + nb;
+        c2_status rc = launch_gram_hash(ga, st);
+        if (rc) return rc;
       } else {
-        // no item table fits shared memory: rows by merges, greedy clusters'
-        // members then brute-force clusters' members
+        // no item table fits shared memory and a profile is too long for the
+        // hash table: rows by merges, greedy clusters' members then
+        // brute-force clusters' members
         MergeGramArgs ma{};
         ma.ptr = ptr; ma.items = items; ma.cptr = cptr; ma.cusers = cusers; ma.gcl = w.gcl;
         ma.gofs = w.gofs; ma.gram = w.gram; ma.ipos = w.ipos; ma.iinfo = w.iinfo; ma.hdr = w.hdr;

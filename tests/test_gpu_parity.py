@@ -344,6 +344,39 @@ def test_build_long_profiles_unkeyed(c2):
     assert st["pairs"] == pairs
 
 
+def _wide_case(c2, extra_lens, seed):
+    # 200,000 items: no dense item table fits shared memory
+    m = 200000
+    ptr, items = synth.random_profiles(3000, m, 30, 40 + seed, zipf_s=0.8)
+    ptr, items = _with_long_profiles(ptr, items, m, extra_lens, seed)
+    n, k, t, b, N, seed2, thr = ptr.size - 1, 10, 3, 8, 600, 9, 150
+    oid, oin, oun, pairs = oracle.build_graph(ptr, items, m, k, t, b, N, seed2, thr, 3)
+    opts = c2.options(greedy_threshold=thr, greedy_rounds=3)
+    ws = c2.workspace(c2.workspace_size(n, items.size, m, k, t, b, N, opts), DEV)
+    gid, gin, gun = c2.c2_build_knn_graph(to_dev(ptr), to_dev(items), m, k, t, b, N, seed2,
+                                          opts=opts, ws=ws)
+    st = c2.c2_get_stats(ws)
+    assert st["n_greedy_clusters"] > 0
+    assert_same(gid, oid, "nbr_id")
+    assert_same(gin, oin, "nbr_inter")
+    assert_same(gun, oun, "nbr_union")
+    assert st["pairs"] == pairs
+    return st
+
+
+def test_build_wide_items_hashed(c2):
+    # count matrices through the shared hash table; the longest members share
+    # a tile whose items exceed one pass (4,096), so that tile takes passes
+    st = _wide_case(c2, [1500, 2000, 2500, 3000, 3500, 4000, 4096], 1)
+    assert st["item_visits_greedy"] > 0
+
+
+def test_build_wide_items_merge_fallback(c2):
+    # a profile longer than one hash pass: count rows by merges instead
+    st = _wide_case(c2, [1500, 5000], 2)
+    assert st["item_visits_greedy"] == 0
+
+
 def test_cluster_knn_profile_beyond_limit(c2):
     # c2_cluster_knn does not validate profiles: one longer than 65535 items
     # (16-bit counts) is reported as unsupported on the device
