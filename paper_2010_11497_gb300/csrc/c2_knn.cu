@@ -575,6 +575,128 @@ __global__ void __launch_bounds__(NT, MB) k_gram_hash(GramArgs a) {
   if (lane == 0 && visits) atomicAdd(&a.hdr->item_visits[1], visits);
 }
 
+// Judge (exact global top-k of query users, Eq. 2's denominator) for item
+// universes too large for the shared table: k_table's judge mode with the
+// tile's items in the shared hash table, in passes over query groups of at
+// most kHashCap items; each query's list is updated in its own pass.
+template <int NT>
+__global__ void __launch_bounds__(NT) k_table_hash(TableArgs a) {
+  constexpr int Q = 32, NWARP = NT / 32, QPW = Q / NWARP;
+  extern __shared__ __align__(16) uint32_t tsm[];
+  uint32_t* hkey = tsm;
+  uint32_t* hval = tsm + kHashSlots;
+  uint32_t* filt = tsm + 2 * kHashSlots;
+  uint32_t* cntw = filt + kHashFilterWords;                 // [16][NT]
+  int32_t* cand_id = reinterpret_cast<int32_t*>(cntw + 16 * NT);
+  int32_t* cand_len = cand_id + NT;
+  __shared__ int32_t q_id[Q], q_len[Q];
+  __shared__ int s_work;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int k = a.k;
+  for (int i = tid; i < kHashSlots; i += NT) { hkey[i] = kHashEmpty; hval[i] = 0u; }
+  for (int i = tid; i < kHashFilterWords; i += NT) filt[i] = 0u;
+  const int nwork = *a.n_work;
+  unsigned long long visits = 0;
+  __syncthreads();
+  for (;;) {
+    if (tid == 0) s_work = dev_failed(a.hdr) ? nwork : (int)atomicAdd(a.counter, 1u);
+    __syncthreads();
+    const int wi = s_work;
+    if (wi >= nwork) break;
+    const int qbase = wi * Q, nq = min(Q, a.n_queries - qbase), M = a.n_users;
+    if (tid < Q) {
+      int id = -1, len = 0;
+      if (tid < nq) {
+        id = a.queries ? a.queries[qbase + tid] : qbase + tid;
+        len = a.ptr[id + 1] - a.ptr[id];
+      }
+      q_id[tid] = id;
+      q_len[tid] = len;
+    }
+    __syncthreads();
+    WarpList L[QPW];
+#pragma unroll
+    for (int s2 = 0; s2 < QPW; ++s2) { L[s2].id = -1; L[s2].c = 0; L[s2].u = 0; }
+    int j0 = 0;
+    while (j0 < nq) {
+      int j1 = j0, sum = 0;
+      while (j1 < nq && sum + q_len[j1] <= kHashCap) sum += q_len[j1++];
+      if (j1 == j0) j1 = j0 + 1;   // not reached: the host checks the longest profile
+      for (int j = j0 + warp; j < j1; j += NWARP) {
+        const int u = q_id[j];
+        for (int e = a.ptr[u] + lane; e < a.ptr[u + 1]; e += 32)
+          hash_insert(hkey, hval, filt, a.items[e], 1u << j);
+      }
+      __syncthreads();
+      for (int cb = 0; cb < M; cb += NT) {
+        const int v = cb + tid;
+        const bool act = v < M;
+        const int len = act ? a.ptr[v + 1] - a.ptr[v] : 0;
+        uint32_t C[16];
+#pragma unroll
+        for (int r = 0; r < 16; ++r) C[r] = 0;
+        if (act) {
+          count_row4_hash(reinterpret_cast<const int4*>(a.pitems + a.pptr[v]), (len + 3) >> 2,
+                          hkey, hval, filt, a.n_items, C);
+          visits += (unsigned)len;
+        }
+#pragma unroll
+        for (int r = 0; r < 16; ++r) cntw[r * NT + tid] = C[r];
+        cand_id[tid] = act ? v : -1;
+        cand_len[tid] = len;
+        __syncthreads();
+        const int nc = min(NT, M - cb);
+#pragma unroll
+        for (int s2 = 0; s2 < QPW; ++s2) {
+          const int j = warp + NWARP * s2;
+          if (j >= j0 && j < j1) {
+            const int qid = q_id[j], qlen = q_len[j];
+            const int r = creg(j), h = chalf(j);
+            for (int i0 = 0; i0 < nc; i0 += 32) {
+              WarpList kth;
+              kth.id = __shfl_sync(0xffffffffu, L[s2].id, k - 1);
+              kth.c = __shfl_sync(0xffffffffu, L[s2].c, k - 1);
+              kth.u = __shfl_sync(0xffffffffu, L[s2].u, k - 1);
+              const int i = i0 + lane;
+              bool pass = false;
+              uint32_t cc = 0, uu = 0;
+              int32_t vid = -1;
+              if (i < nc) {
+                cc = (cntw[r * NT + i] >> (16 * h)) & 0xFFFFu;
+                vid = cand_id[i];
+                if (vid != qid && cc > 0) {
+                  uu = (uint32_t)(qlen + cand_len[i]) - cc;
+                  pass = beats(kth, vid, cc, uu);
+                }
+              }
+              warp_list_add(L[s2], k, pass, vid, cc, uu);
+            }
+          }
+        }
+        __syncthreads();
+      }
+      for (int i = tid; i < kHashSlots; i += NT) { hkey[i] = kHashEmpty; hval[i] = 0u; }
+      for (int i = tid; i < kHashFilterWords; i += NT) filt[i] = 0u;
+      __syncthreads();
+      j0 = j1;
+    }
+#pragma unroll
+    for (int s2 = 0; s2 < QPW; ++s2) {
+      const int j = warp + NWARP * s2;
+      if (j < nq && lane < k) {
+        const int64_t row = (int64_t)(qbase + j) * k + lane;
+        const bool ok = L[s2].id >= 0;
+        a.out_id[row] = ok ? L[s2].id : -1;
+        a.out_in[row] = ok ? (int32_t)L[s2].c : 0;
+        a.out_un[row] = ok ? (int32_t)L[s2].u : 0;
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) visits += __shfl_xor_sync(0xffffffffu, visits, o);
+  if (lane == 0 && visits) atomicAdd(&a.hdr->item_visits[0], visits);
+}
+
 __device__ __forceinline__ uint32_t merge_count(const int32_t* __restrict__ a, int la,
                                                 const int32_t* __restrict__ b, int lb);
 
@@ -2103,6 +2225,34 @@ c2_status run_bruteforce(const int32_t* ptr, const int32_t* items, const Sizes& 
     a.out_id = nid; a.out_in = nin; a.out_un = nun;
     a.hdr = w.hdr; a.counter = &w.hdr->work_counter[3];
     return launch_table(tc, a, st);
+  }
+  // no item table fits: the hashed judge when every profile fits one pass
+  int32_t max_len = 0;
+  C2_CUDA_TRY(cudaMemcpyAsync(&max_len, &w.hdr->max_profile, sizeof(int32_t),
+                              cudaMemcpyDeviceToHost, st));
+  C2_CUDA_TRY(cudaStreamSynchronize(st));
+  constexpr int NT = 256;
+  const int hsmem = (int)(gram_hash_smem_bytes() + (16 * NT + 2 * NT) * sizeof(uint32_t));
+  if (max_len <= kHashCap && hsmem + 1024 <= smem_optin()) {
+    c2_status rc = build_padded_csr(ptr, items, s, w, st);
+    if (rc) return rc;
+    C2_LAUNCH(k_set_count, 1, 1, 0, st, &w.hdr->n_work, div_up(rows, 32));
+    TableArgs a{};
+    a.ptr = ptr; a.items = items; a.pptr = w.pptr; a.pitems = w.pitems;
+    a.n_items = s.m; a.k = s.k;
+    a.n_work = &w.hdr->n_work;
+    a.cptr = nullptr; a.queries = queries; a.n_queries = rows; a.n_users = s.n;
+    a.out_id = nid; a.out_in = nin; a.out_un = nun;
+    a.hdr = w.hdr; a.counter = &w.hdr->work_counter[3];
+    C2_CUDA_TRY(cudaFuncSetAttribute(k_table_hash<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     hsmem));
+    int per_sm = 0;
+    C2_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_table_hash<NT>, NT, hsmem));
+    if (per_sm < 1) return C2_ERR_UNSUPPORTED;
+    C2_CUDA_TRY(cudaMemsetAsync(a.counter, 0, sizeof(unsigned), st));
+    C2_LAUNCH(k_table_hash<NT>, num_sms() * per_sm, NT, hsmem, st, a);
+    C2_CUDA_TRY(cudaGetLastError());
+    return C2_OK;
   }
   MergeArgs a{};
   a.ptr = ptr; a.items = items; a.k = s.k; a.n_rows = rows;

@@ -267,11 +267,32 @@ def test_bruteforce_judge(c2):
     assert_same(gun, run, "judge union (queries)")
 
 
-def test_bruteforce_judge_wide_items_uses_merge(c2):
-    ptr, items = synth.random_profiles(800, 400000, 15, 19, zipf_s=0.8)
+def test_bruteforce_judge_wide_items_hashed(c2):
+    # 400,000 items: the judge counts through the shared hash table; the long
+    # profiles share one query tile, which takes several passes
+    m = 400000
+    ptr, items = synth.random_profiles(800, m, 15, 19, zipf_s=0.8)
+    ptr, items = _with_long_profiles(ptr, items, m, [1500, 2000, 2500, 3000, 4000], 3)
     k = 8
     rid, rin, run = oracle.bruteforce_knn(ptr, items, k)
-    gid, gin, gun = c2.c2_bruteforce_knn(to_dev(ptr), to_dev(items), 400000, k)
+    gid, gin, gun = c2.c2_bruteforce_knn(to_dev(ptr), to_dev(items), m, k)
+    assert_same(gid, rid, "judge id")
+    assert_same(gin, rin, "judge inter")
+    q = np.array([800, 801, 802, 803, 804, 5, 17, 600], np.int32)
+    rid, rin, run = oracle.bruteforce_knn(ptr, items, k, q)
+    gid, gin, gun = c2.c2_bruteforce_knn(to_dev(ptr), to_dev(items), m, k, to_dev(q))
+    assert_same(gid, rid, "judge id (queries)")
+    assert_same(gun, run, "judge union (queries)")
+
+
+def test_bruteforce_judge_wide_items_merge_fallback(c2):
+    # a profile longer than one hash pass: the judge merges sorted lists
+    m = 400000
+    ptr, items = synth.random_profiles(600, m, 15, 23, zipf_s=0.8)
+    ptr, items = _with_long_profiles(ptr, items, m, [5000], 4)
+    k = 8
+    rid, rin, run = oracle.bruteforce_knn(ptr, items, k)
+    gid, gin, gun = c2.c2_bruteforce_knn(to_dev(ptr), to_dev(items), m, k)
     assert_same(gid, rid, "judge id")
     assert_same(gin, rin, "judge inter")
 
