@@ -840,7 +840,7 @@ struct GlobalCU {
 // order keys.  Rows and columns are in internal order; candidates are
 // ranked by local index (user-id order).
 template <bool Keyed>
-__global__ void __launch_bounds__(kNT) k_gram_topk(RowTopkArgs a) {
+__global__ void __launch_bounds__(kNT, 6) k_gram_topk(RowTopkArgs a) {
   __shared__ int32_t s_sid[Keyed ? 1 : kNT / 32][64];
   __shared__ uint2 s_scu[kNT / 32][64];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
