@@ -2106,9 +2106,11 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
         }
       }
     }
-    if (n_brute_users) {
-      // brute-force rows on the side stream, beside the greedy rounds (both
-      // only read this batch's count matrices)
+    // brute-force rows on the side stream (they and the greedy phase only read
+    // this batch's count matrices): beside the greedy start when the round
+    // kernel fills the SMs, beside the rounds when it leaves room for them
+    // (large greedy clusters: at most two round blocks per SM)
+    auto launch_brute_rows = [&]() -> c2_status {
       c2_status rc = sj.fork();
       if (rc) return rc;
       Prof p_bt(side, "brute_rows");
@@ -2122,6 +2124,22 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
       ra.k = k; ra.out_id = lid; ra.out_in = lin; ra.out_un = lun; ra.hdr = w.hdr;
       if (keyed) C2_LAUNCH(k_gram_topk<true>, div_up(n_brute_users * 32, kNT), kNT, 0, side, ra);
       else C2_LAUNCH(k_gram_topk<false>, div_up(n_brute_users * 32, kNT), kNT, 0, side, ra);
+      C2_CUDA_TRY(cudaGetLastError());
+      return C2_OK;
+    };
+    bool brute_beside_rounds = false;
+    if (n_brute_users && n_greedy_users) {
+      const int smem_r = 21 * ((mmax + 31) & ~31);
+      auto kr = keyed ? k_greedy_round<true, kGreedyUsersPerWarp>
+                      : k_greedy_round<false, kGreedyUsersPerWarp>;
+      C2_CUDA_TRY(cudaFuncSetAttribute(kr, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_r));
+      int ps = 0;
+      C2_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, kr, kNT, smem_r));
+      brute_beside_rounds = ps <= 2;
+    }
+    if (n_brute_users && !brute_beside_rounds) {
+      c2_status rc = launch_brute_rows();
+      if (rc) return rc;
     }
     if (n_greedy_users) {
       GreedyArgs ga{};
@@ -2147,6 +2165,10 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
         ga.wl_out = w.wl0;
         ga.chg_out = opt.greedy_random == 0 ? w.chg0 : nullptr;
         C2_LAUNCH(k_greedy_init, grid, kNT, 0, st, ga);
+      }
+      if (brute_beside_rounds) {
+        c2_status rc = launch_brute_rows();
+        if (rc) return rc;
       }
       int32_t* cur = w.wl0;
       int32_t* nxt = w.wl1;
