@@ -48,6 +48,8 @@ def lib():
         L.oracle_validate_csr.argtypes = [I32P, I32P, C.c_int32, C.c_int32]
         L.oracle_frh_keys.argtypes = [I32P, I32P, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
                                       C.c_uint64, C.c_void_p, I32P]
+        L.oracle_minhash_keys.argtypes = [I32P, I32P, C.c_int32, C.c_int32, C.c_int32,
+                                          C.c_uint64, I32P]
         L.oracle_frh_cluster.argtypes = [I32P, I32P, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
                                          C.c_int32, C.c_uint64, C.c_void_p, C.c_void_p, I32P, I32P,
                                          I32P, I32P, C.c_void_p]
@@ -107,6 +109,17 @@ def frh_keys(ptr, items, m, t, b, seed, htab=None):
     ht = None if htab is None else _i32(htab)
     lib().oracle_frh_keys(ptr, items if items.size else np.zeros(1, np.int32), n, m, t, b, seed,
                           _opt(ht), keys)
+    return keys
+
+
+def minhash_keys(ptr, items, m, t, seed):
+    """Keys [t][n] of the C^2/MinHash variant: per function, the item of the
+    profile with the least 64-bit value (m for an empty profile)."""
+    ptr, items = _i32(ptr), _i32(items)
+    n = ptr.size - 1
+    keys = np.zeros((t, n), np.int32)
+    lib().oracle_minhash_keys(ptr, items if items.size else np.zeros(1, np.int32), n, m, t, seed,
+                              keys)
     return keys
 
 

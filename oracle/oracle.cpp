@@ -350,6 +350,33 @@ int oracle_frh_keys(const int32_t* ptr, const int32_t* items, int32_t n, int32_t
   return 0;
 }
 
+// MinHash keys of the C^2/MinHash variant (Section V-C, Table 4; Section
+// II-E): function i gives every item x a 64-bit value
+//   v_i(x) = SplitMix64(K_i xor (x * 0xD6E8FEB86659FD93)),  K_i = function_key(seed, i),
+// and user u's key is the item of P_u with the least value (ties to the lower
+// item); an empty profile gets m.  One cluster per item, no splitting.
+int oracle_minhash_keys(const int32_t* ptr, const int32_t* items, int32_t n, int32_t m, int32_t t,
+                        uint64_t seed, int32_t* keys) {
+  Csr P{ptr, items, n};
+  for (int i = 0; i < t; ++i) {
+    const uint64_t K = function_key(seed, i);
+    for (int32_t u = 0; u < n; ++u) {
+      int32_t key = m;
+      uint64_t best = 0;
+      for (int32_t j = 0; j < P.len(u); ++j) {
+        const int32_t x = P.row(u)[j];
+        const uint64_t v = splitmix64_mix(K ^ ((uint64_t)(uint32_t)x * 0xD6E8FEB86659FD93ULL));
+        if (key == m || v < best || (v == best && x < key)) {
+          best = v;
+          key = x;
+        }
+      }
+      keys[(size_t)i * n + u] = key;
+    }
+  }
+  return 0;
+}
+
 // Step 1 (Algorithm 1 + recursive split).  Outputs, for t functions:
 //   cluster_of[t][n]  final cluster number of user u under function i
 //   cptr[n_clusters+1], cusers[t*n]  cluster CSR, members ascending

@@ -513,3 +513,39 @@ def test_model_keys_are_argmax_of_logits():
     b = cfg["b"]
     for j in range(cfg["t"]):
         assert (keys[j] == np.argmax(z[:, j * b:(j + 1) * b], axis=1)).all()
+
+
+# ------------------------------------------------------------------ MinHash variant
+def test_minhash_keys_are_profile_items():
+    # Section V-C / Table 4 variant: one cluster per item, the key is an item
+    # of the user's own profile (m for an empty profile)
+    ptr, items = synth.random_profiles(300, 500, 12, 51)
+    ptr = np.concatenate([ptr, [ptr[-1]]])            # an empty last profile
+    keys = oracle.minhash_keys(ptr, items, 500, 6, 3)
+    n = ptr.size - 1
+    for i in range(6):
+        for u in range(n - 1):
+            assert keys[i, u] in set(items[ptr[u]:ptr[u + 1]].tolist())
+        assert keys[i, n - 1] == 500
+
+
+def test_minhash_collision_rate_is_jaccard():
+    # min-wise hashing (Broder, 1997): over random functions,
+    # P[key(A) = key(B)] = |A n B| / |A u B|.  Three pairs, 4,000 functions:
+    # J = 1/3, J = 9/11 and J = 0, each within 4.5 standard deviations.
+    A = np.arange(0, 40)
+    B = np.arange(20, 60)                 # |A n B| = 20, |A u B| = 60
+    C_ = np.arange(0, 40)                 # a copy of A
+    D = np.concatenate([np.arange(4, 40), np.arange(100, 104)])   # |C n D| = 36, |C u D| = 44
+    E = np.arange(200, 240)               # disjoint from A
+    rows = [A, B, C_, D, E]
+    ptr = np.concatenate([[0], np.cumsum([r.size for r in rows])]).astype(np.int32)
+    items = np.concatenate(rows).astype(np.int32)
+    T = 4000
+    keys = oracle.minhash_keys(ptr, items, 300, T, 12345)
+    for (a, b), J in (((0, 1), 20 / 60), ((2, 3), 36 / 44), ((0, 4), 0.0)):
+        freq = float((keys[:, a] == keys[:, b]).mean())
+        sd = math.sqrt(max(J * (1 - J), 1e-12) / T)
+        assert abs(freq - J) <= 4.5 * sd + 1e-12, (a, b, freq, J)
+    # identical profiles always share the key
+    assert (keys[:, 0] == keys[:, 2]).all()
