@@ -53,6 +53,12 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="c2", choices=["c2", "reference"])
     ap.add_argument("--workload", default="ml10m_like")
+    ap.add_argument("--clustering", default="frh", choices=["frh", "minhash"],
+                    help="first-level keys: FastRandomHash, or the MinHash variant (one cluster "
+                         "per item, no split; Table 4)")
+    ap.add_argument("--split-N", type=int, default=0,
+                    help="MinHash variant: split clusters above this size with FastRandomHash "
+                         "(0 = never, as in Table 4)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-quality", action="store_true")
@@ -379,15 +385,22 @@ def main():
     nnz = int(items_np.size)
     ptr = torch.from_numpy(ptr_np).to(dev)
     items = torch.from_numpy(items_np).to(dev)
+    minhash = args.clustering == "minhash"
+    # the MinHash variant: keys are items (b = m + 1 buckets), clusters are never split
+    wb, wN = (w.n_items + 1, args.split_N or w.n_users) if minhash else (w.b, w.N)
+    keys = torch.empty((w.t, w.n_users), dtype=torch.int32, device=dev) if minhash else None
+    kws = c2.workspace(256, dev)
     opts = c2.options(greedy_threshold=w.greedy_threshold, greedy_rounds=w.greedy_rounds,
-                      gram_budget_bytes=args.gram_budget_mb << 20)
-    ws = c2.workspace(c2.workspace_size(w.n_users, nnz, w.n_items, w.k, w.t, w.b, w.N, opts), dev)
+                      gram_budget_bytes=args.gram_budget_mb << 20, keys=keys)
+    ws = c2.workspace(c2.workspace_size(w.n_users, nnz, w.n_items, w.k, w.t, wb, wN, opts), dev)
     out = [torch.empty((w.n_users, w.k), dtype=torch.int32, device=dev) for _ in range(3)]
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
     def step():
-        c2.c2_build_knn_graph(ptr, items, w.n_items, w.k, w.t, w.b, w.N, seed, opts=opts, ws=ws,
+        if minhash:
+            c2.c2_minhash_keys(ptr, items, w.n_items, w.t, seed, out=keys, ws=kws, check=False)
+        c2.c2_build_knn_graph(ptr, items, w.n_items, w.k, w.t, wb, wN, seed, opts=opts, ws=ws,
                               out=out, check=False)
 
     for _ in range(max(3, args.warmup)):
@@ -428,7 +441,7 @@ def main():
 
     # end to end through the host-buffer entry point
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and not minhash:
         hptr = torch.from_numpy(ptr_np).pin_memory()
         hitems = torch.from_numpy(items_np).pin_memory()
         hws = c2.workspace(c2.workspace_size_host(w.n_users, nnz, w.n_items, w.k, w.t, w.b, w.N,
@@ -514,7 +527,9 @@ def main():
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "int32", "data": "synthetic",
                 "config": {"workload": w.name, "n_users": w.n_users, "n_items": w.n_items,
-                           "nnz": nnz, **w.params(), "l2": "flushed (512 MiB write) before each step",
+                           "nnz": nnz, **w.params(),
+                           **({"clustering": "minhash", "b": wb, "N": wN} if minhash else {}),
+                           "l2": "flushed (512 MiB write) before each step",
                            "parallelism": f"replicas{world}" if world > 1 else "single"},
                 "pairs_per_step": pairs, "gram_pairs_per_step": stats["gram_pairs"],
                 "quality": quality, "e2e": e2e, "gpu_launches": launches,

@@ -152,6 +152,23 @@ c2_status c2_frh_cluster(const int32_t* d_csr_ptr, const int32_t* d_csr_items, i
                          int32_t* d_cusers, int32_t* d_n_clusters, int32_t* d_cmeta, void* d_ws,
                          size_t ws_bytes, c2_stream_t stream);
 
+/* First-level keys of the C^2/MinHash variant (Section V-C, Table 4, which
+ * replaces FastRandomHash by MinHash; Section II-E compares the two).  Function
+ * i < t gives item x the 64-bit value
+ *   v_i(x) = SplitMix64(K_i ^ (x * 0xD6E8FEB86659FD93)),
+ *   K_i = SplitMix64(seed + (i + 1) * 0x9E3779B97F4A7C15)
+ * (SplitMix64 = the output function of Steele, Lea & Flood, OOPSLA 2014), and
+ * d_keys[i*n_users+u] = the item of u's profile with the least value (ties to
+ * the lower item), n_items for an empty profile.  The variant clusters users
+ * by these keys, one cluster per item and no splitting: pass d_keys through
+ * c2_options.d_keys to c2_build_knn_graph with b = n_items + 1 (at most 65,536)
+ * and N = n_users.  The CSR is validated first (C2_ERR_INVALID_CSR through the
+ * status word).  Workspace: one 256-byte status header (d_ws 256-byte aligned,
+ * ws_bytes >= 256).  Asynchronous on `stream`. */
+c2_status c2_minhash_keys(const int32_t* d_csr_ptr, const int32_t* d_csr_items, int32_t n_users,
+                          int32_t n_items, int32_t t, uint64_t seed, int32_t* d_keys, void* d_ws,
+                          size_t ws_bytes, c2_stream_t stream);
+
 /* Step 2 (Algorithm 2): the KNN graph inside every cluster given by
  * (d_cptr, d_cusers, d_n_clusters) as produced by c2_frh_cluster.  Outputs
  * one row of k per cluster slot s (a position in d_cusers):

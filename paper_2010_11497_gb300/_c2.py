@@ -63,6 +63,7 @@ _SIGS = {
     "c2_status_string": (C.c_char_p, [C.c_int]),
     "c2_workspace_size": (SZ, [I32, I64, I32, I32, I32, I32, I32, C.POINTER(Options)]),
     "c2_workspace_size_host": (SZ, [I32, I64, I32, I32, I32, I32, I32, C.POINTER(Options)]),
+    "c2_minhash_keys": (C.c_int, [P, P, I32, I32, I32, U64, P, P, SZ, P]),
     "c2_frh_cluster": (C.c_int, [P, P, I32, I32, I32, I32, I32, U64, C.POINTER(Options), P, P, P,
                                  P, P, P, SZ, P]),
     "c2_cluster_knn": (C.c_int, [P, P, I32, I32, I32, P, P, P, I32, U64, C.POINTER(Options), P, P,
@@ -176,6 +177,20 @@ def workspace(nbytes: int, device="cuda") -> torch.Tensor:
 
 
 # ------------------------------------------------------------------ entry points
+def c2_minhash_keys(ptr, items, n_items, t, seed, out=None, ws=None, check=True, stream=None):
+    """First-level keys [t, n] of the C^2/MinHash variant (one cluster per item).
+    check=False skips the status read (no host synchronisation)."""
+    dev = ptr.device
+    n = ptr.numel() - 1
+    keys = out if out is not None else torch.empty((t, max(n, 1)), dtype=torch.int32, device=dev)
+    ws = ws if ws is not None else workspace(256, dev)
+    _check(lib().c2_minhash_keys(_ptr(ptr), _ptr(items), n, n_items, t, seed, _ptr(keys),
+                                 _ptr(ws), ws.numel(), _stream(stream)), "c2_minhash_keys")
+    if check:
+        _check(c2_get_status(ws, stream), "c2_minhash_keys (device)")
+    return keys[:, :n]
+
+
 def c2_frh_cluster(ptr, items, n_items, t, b, N, seed, opts=None, ws=None, stream=None):
     """Step 1.  Returns dict(cluster_of[t,n], cptr[nc+1], cusers[t*n], n_clusters, cmeta[nc,4])."""
     dev = ptr.device

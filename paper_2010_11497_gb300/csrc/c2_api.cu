@@ -277,6 +277,21 @@ c2_status c2_frh_cluster(const int32_t* d_csr_ptr, const int32_t* d_csr_items, i
                          d_n_clusters, d_cmeta, cw, st);
 }
 
+c2_status c2_minhash_keys(const int32_t* d_csr_ptr, const int32_t* d_csr_items, int32_t n_users,
+                          int32_t n_items, int32_t t, uint64_t seed, int32_t* d_keys, void* d_ws,
+                          size_t ws_bytes, c2_stream_t stream) {
+  c2_status rc = check_common(n_users, n_items, 1, t, 2, 2, nullptr);
+  if (rc) return rc;
+  if (!d_csr_ptr || (!d_csr_items && n_users > 0) || !d_keys) return C2_ERR_INVALID_ARG;
+  rc = check_ws(d_ws, ws_bytes, sizeof(DevHeader));
+  if (rc) return rc;
+  const Sizes s = make_sizes(n_users, 0, n_items, 1, t, 2, 2, nullptr);
+  DevHeader* hdr = reinterpret_cast<DevHeader*>(d_ws);
+  cudaStream_t st = (cudaStream_t)stream;
+  C2_CUDA_TRY(cudaMemsetAsync(hdr, 0, sizeof(DevHeader), st));
+  return run_minhash_keys(d_csr_ptr, d_csr_items, s, seed, d_keys, hdr, st);
+}
+
 c2_status c2_cluster_knn(const int32_t* d_csr_ptr, const int32_t* d_csr_items, int32_t n_users,
                          int32_t n_items, int32_t t, const int32_t* d_cptr,
                          const int32_t* d_cusers, const int32_t* d_n_clusters, int32_t k,

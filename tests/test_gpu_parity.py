@@ -442,3 +442,26 @@ def test_build_duplicate_and_empty_profiles(c2):
     assert_same(gin, oin, "nbr_inter")
     assert_same(gun, oun, "nbr_union")
     assert c2.c2_get_stats(ws)["pairs"] == pairs
+
+
+# ------------------------------------------------------------------ C^2/MinHash variant
+def test_minhash_keys_and_build(c2):
+    # Section V-C / Table 4: MinHash keys (one cluster per item, no split)
+    ptr, items = synth.random_profiles(2500, 700, 20, 61, zipf_s=1.1)
+    ptr = np.concatenate([ptr, [ptr[-1]]]).astype(np.int32)      # an empty profile
+    n, m, t, k, seed = ptr.size - 1, 700, 5, 10, 17
+    keys = c2.c2_minhash_keys(to_dev(ptr), to_dev(items), m, t, seed)
+    okeys = oracle.minhash_keys(ptr, items, m, t, seed)
+    assert_same(keys, okeys, "minhash keys")
+    thr, b, N = 60, m + 1, n
+    oid, oin, oun, pairs = oracle.build_graph(ptr, items, m, k, t, b, N, seed, thr, 3, keys=okeys)
+    opts = c2.options(greedy_threshold=thr, greedy_rounds=3, keys=keys.contiguous())
+    ws = c2.workspace(c2.workspace_size(n, items.size, m, k, t, b, N, opts), DEV)
+    gid, gin, gun = c2.c2_build_knn_graph(to_dev(ptr), to_dev(items), m, k, t, b, N, seed,
+                                          opts=opts, ws=ws)
+    st = c2.c2_get_stats(ws)
+    assert st["split_levels"] == 0
+    assert_same(gid, oid, "nbr_id")
+    assert_same(gin, oin, "nbr_inter")
+    assert_same(gun, oun, "nbr_union")
+    assert st["pairs"] == pairs
