@@ -266,16 +266,21 @@ def run_reference(args):
 # DRAM traffic per launch of a kernel, from one ncu capture recorded in
 # profiles/traffic.json together with a hash of the sources it was taken on;
 # null once those sources change.
-KERNEL_SOURCES = ["paper_2010_11497_gb300/csrc/c2_knn.cu",
-                  "paper_2010_11497_gb300/csrc/c2_internal.cuh",
-                  "paper_2010_11497_gb300/csrc/c2_merge.cu",
-                  "paper_2010_11497_gb300/csrc/c2_cluster.cu"]
+_CSRC = "paper_2010_11497_gb300/csrc/"
+KERNEL_SOURCES = {
+    "k_greedy_round": ["c2_knn.cu", "c2_internal.cuh"],
+    "k_gram": ["c2_knn.cu", "c2_internal.cuh"],
+    "k_gram_topk": ["c2_knn.cu", "c2_internal.cuh"],
+    "k_merge": ["c2_merge.cu", "c2_internal.cuh"],
+    "k_minhash": ["c2_cluster.cu", "c2_internal.cuh"],
+}
 
 
-def sources_sha1():
+def sources_sha1(kernel):
+    """Hash of the source files a kernel is built from."""
     h = hashlib.sha1()
-    for f in KERNEL_SOURCES:
-        with open(os.path.join(HERE, f), "rb") as fh:
+    for f in KERNEL_SOURCES[kernel]:
+        with open(os.path.join(HERE, _CSRC + f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
 
@@ -286,7 +291,8 @@ def recorded_traffic(kernel, workload):
         return None
     with open(path) as fh:
         rec = json.load(fh).get(kernel)
-    if not rec or rec.get("workload") != workload or rec.get("sources_sha1") != sources_sha1():
+    if (not rec or kernel not in KERNEL_SOURCES or rec.get("workload") != workload
+            or rec.get("sources_sha1") != sources_sha1(kernel)):
         return None
     return rec.get("bytes_per_launch")
 

@@ -7,6 +7,10 @@
 
 namespace c2 {
 
+// MinHash keys of the C^2/MinHash variant (c2_minhash.cu).
+c2_status run_minhash_keys(const int32_t* ptr, const int32_t* items, const Sizes& s,
+                           uint64_t seed, int32_t* keys, DevHeader* hdr, cudaStream_t st);
+
 Sizes make_sizes(int32_t n, int64_t nnz, int32_t m, int32_t k, int32_t t, int32_t b, int32_t N,
                  const c2_options* opt) {
   Sizes s{};

@@ -631,8 +631,6 @@ c2_status run_avg_sim(const int32_t* nin, const int32_t* nun, int32_t rows, int3
                       DevHeader* hdr, double* partial, cudaStream_t st);
 c2_status run_validate(const int32_t* ptr, const int32_t* items, const Sizes& s, DevHeader* hdr,
                        cudaStream_t st);
-c2_status run_minhash_keys(const int32_t* ptr, const int32_t* items, const Sizes& s,
-                           uint64_t seed, int32_t* keys, DevHeader* hdr, cudaStream_t st);
 
 // tcgen05 logits GEMM with a fused per-slice argmax (c2_tc.cu):
 // part[r][s] = (max, argmax) of A[r] . Bt[j] + bias[j] over the tc_slice_width() columns j
