@@ -71,3 +71,16 @@ def test_host_argument_errors_need_no_gpu(lib):
     rc = lib.c2_build_knn_graph(fake, fake, 10, 10, 5, 2, 8, 4, 1, C.byref(o), fake, fake, fake,
                                 C.c_void_p(4096), 1 << 30, None)
     assert rc == 1
+
+
+def test_minhash_keys_argument_errors_need_no_gpu(lib):
+    fake = C.c_void_p(256)
+    # NULL outputs
+    assert lib.c2_minhash_keys(fake, fake, 10, 10, 4, 1, None, fake, 256, None) == 1
+    # t beyond the 64 functions the library supports
+    assert lib.c2_minhash_keys(fake, fake, 10, 10, 65, 1, fake, fake, 256, None) == 3
+    # workspace missing, too small for the status header, or misaligned
+    assert lib.c2_minhash_keys(fake, fake, 10, 10, 4, 1, fake, None, 256, None) == 4
+    assert lib.c2_minhash_keys(fake, fake, 10, 10, 4, 1, fake, C.c_void_p(4096), 64, None) == 4
+    assert lib.c2_minhash_keys(fake, fake, 10, 10, 4, 1, fake, C.c_void_p(4096 + 8), 256,
+                               None) == 4
