@@ -204,3 +204,19 @@ def test_model_keys_tcgen05_full_shape(c2):
     # chunked proposals (three chunks, the last ragged) give the same keys
     keys2 = m.propose(dev(ptr), dev(items), chunk=8192)
     same(keys2, keys, "keys with 8192-row chunks")
+
+
+def test_model_keys_mma_fused_argmax_match_oracle(c2):
+    # t*b = 384 (not a multiple of 512): the mma.sync logits GEMM with the
+    # argmax of 128-column slices fused into its epilogue
+    m = _model(c2, t=3, b=128, dim=64, hidden=128, rows_log2=11, seed=14)
+    ptr, items = synth.random_profiles(2100, 900, 25, 49)
+    keys = m.propose(dev(ptr), dev(items)).cpu().numpy()
+    params = [x.cpu().numpy() for x in m.params()]
+    z, okeys = oracle.model_forward(m.config(), params, ptr, items)
+    b = m.cfg.b
+    diff = np.argwhere(keys != okeys)
+    for j, u in diff:
+        zz = np.sort(z[u, j * b:(j + 1) * b])
+        assert zz[-1] - zz[-2] < 1e-3 * max(1.0, abs(zz[-1])), (j, u)
+    assert len(diff) <= 0.01 * keys.size
