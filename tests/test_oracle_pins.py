@@ -237,6 +237,14 @@ def test_clustering_invariants(N):
     _check_invariants(ptr, items, 50, 4, 8, N, 99)
 
 
+@pytest.mark.parametrize("t, b, N", [(64, 2, 2), (3, 65536, 2), (1, 2, 300)])
+def test_clustering_invariants_at_parameter_limits(t, b, N):
+    # the library's limits: 64 functions, 2 and 65,536 buckets, the smallest
+    # split limit (N = 2 recurses until every non-residual cluster is a pair)
+    ptr, items = synth.random_profiles(200, 80, 5, 6, zipf_s=1.0)
+    _check_invariants(ptr, items, 80, t, b, N, 7)
+
+
 def test_split_children_share_prefix_keys():
     # every member of a depth-d cluster has, as its d+1 smallest distinct hash
     # values, exactly the cluster's path (Section II-D: H\eta keeps values > eta)
