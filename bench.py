@@ -15,6 +15,12 @@ is timed instead, on a bounded sample of the same workload.
 Multi-GPU: every rank builds the graph of its own independent problem (the
 same workload shape with seed + rank): weak scaling, no collective on the
 data path; only the timing uses a barrier and a max over ranks.
+
+Other workloads (--workload) and the MinHash-clustering variant of the
+paper's Table 4 (--clustering minhash, optionally --split-N) use the same
+line; past 200,000 users the quality is Eq. 2 on a seeded 4,096-user sample.
+The line's `kernels` list gives each phase's share of the device time and,
+where modelled, its kernel's rate against the roofline.
 """
 from __future__ import annotations
 
