@@ -1,13 +1,17 @@
 """Benchmark: Cluster-and-Conquer KNN-graph build on one GB300 per rank.
 
 One step = one whole build (FastRandomHash clustering with recursive split,
-local KNN in every cluster, merge) of the ml10m-like synthetic workload:
-69,878 users x 10,677 items, ~10M profile entries, k=30, t=8, b=4096,
-N=2000, greedy refinement (10 rounds) in clusters of more than 500 users.
+local KNN in every cluster, merge) of the ml20m-like synthetic workload, the
+largest k=30 workload that fits one GPU: 138,493 users x 26,744 items, 20M
+profile entries, k=30, t=8, b=4096, N=2000, brute force in every cluster
+(the paper's rule rho*k^2 = 4500 > N).  --workload ml10m_like gives the
+workload with greedy refinement (10 rounds in clusters of more than 500 users).
 
 `value` is exact-Jaccard pair evaluations per second of the whole job,
 device-timed with CUDA events around each step, inputs resident in HBM and
-L2 flushed (a 512 MiB write) before every step.  `e2e` repeats the build
+L2 flushed (a 512 MiB write) before every step; `intersections_per_step`
+counts the pair intersections actually computed (brute-force pairs plus the
+greedy clusters' count matrices; greedy rounds look counts up).  `e2e` repeats the build
 through the host-buffer C entry point (pinned host CSR in, pinned host graph
 out, copies inside the timed region).  With --impl reference the CPU oracle
 is timed instead, on a bounded sample of the same workload.
@@ -58,7 +62,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="c2", choices=["c2", "reference"])
-    ap.add_argument("--workload", default="ml10m_like")
+    ap.add_argument("--workload", default="ml20m_like")
     ap.add_argument("--clustering", default="frh", choices=["frh", "minhash"],
                     help="first-level keys: FastRandomHash, or the MinHash variant (one cluster "
                          "per item, no split; Table 4)")
@@ -194,45 +198,89 @@ def sum_over_ranks(dist, x: float, dev=None) -> float:
 
 
 # ------------------------------------------------------------------ CPU oracle
-def oracle_sample(ptr, items, w, seed, budget_s, rng_seed=2010, clustering=None, t_cluster=None):
-    """Times the oracle on a seeded sample of the workload's clusters.
+def host_cpu():
+    """Host cores and CPU model (lscpu), for the CPU-baseline record."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return {"nproc": os.cpu_count(), "model": model}
 
-    Step 1 (clustering) runs on the whole workload and is charged pro rata;
-    Step 2 runs on clusters drawn in a seeded random order, each kept only if
-    its estimated oracle time still fits the budget.
-    Returns (pairs/s, description, clustering)."""
+
+SIZE_EDGES = (2, 9, 32, 128, 512, 2048, 1 << 62)
+
+
+def oracle_sample(ptr, items, w, seed, budget_s, rng_seed=2010, clustering=None, t_cluster=None):
+    """Times the oracle on a stratified systematic sample of the workload's
+    clusters and extrapolates the time of the whole build.
+
+    Step 1 (clustering) runs on the whole workload.  Every cluster of Step 2
+    gets an estimate of its oracle work from its own profile lengths (a
+    sorted-list merge per pair: (M-1) * sum of |P_u| for brute force;
+    (k + R k^2) * 2 * sum of |P_u| for R greedy rounds).  Clusters are grouped
+    into strata (brute force or greedy x size class); each stratum gets a
+    share of the budget in proportion to its estimated work (at least 3%),
+    and a systematic sample (every j-th cluster in increasing work, seeded
+    offset, at least one cluster) that fits the share is timed alone.  Its
+    time is scaled to the whole stratum by the estimated work; its pairs are
+    exact for brute-force strata (M(M-1)/2 per cluster) and scaled by the
+    members for greedy ones.  Returns (pairs/s of
+    the extrapolated whole build, description, clustering)."""
     import oracle
     t0 = time.perf_counter()
     cl = clustering or oracle.frh_cluster(ptr, items, w.n_items, w.t, w.b, w.N, seed)
     if t_cluster is None:
         t_cluster = time.perf_counter() - t0
-    sizes = np.diff(cl["cptr"]).astype(np.int64)
+    cptr, cusers = cl["cptr"], cl["cusers"]
+    sizes = np.diff(cptr).astype(np.int64)
+    lens = np.diff(ptr).astype(np.int64)
+    slot_len = lens[cusers]
+    csum = np.concatenate([[0], np.cumsum(slot_len)])
+    sum_len = (csum[cptr[1:]] - csum[cptr[:-1]]).astype(np.float64)
     greedy = sizes >= w.greedy_threshold
-    est_pairs = np.where(greedy, sizes * (w.k + w.greedy_rounds * w.k * w.k),
-                         sizes * (sizes - 1) // 2).astype(np.float64)
-    steps_per_pair = 2.0 * float(np.diff(ptr).mean()) + 20.0
-    est_s = est_pairs * steps_per_pair / 2.5e8
-    order = np.random.default_rng(rng_seed).permutation(sizes.size)
-    only = np.zeros(sizes.size, np.uint8)
-    left = budget_s
-    for c in order:
-        if sizes[c] >= 2 and est_s[c] <= left:
-            only[c] = 1
-            left -= est_s[c]
-        if left <= 0.02 * budget_s:
-            break
-    t1 = time.perf_counter()
-    _, _, _, pairs = oracle.cluster_knn(ptr, items, cl["cptr"], cl["cusers"], w.k, seed,
-                                        w.greedy_threshold, w.greedy_rounds, 0, only=only)
-    t_knn = time.perf_counter() - t1
-    sel = only.astype(bool)
-    frac = float(est_pairs[sel].sum()) / max(float(est_pairs.sum()), 1.0)
-    t_total = t_knn + t_cluster * frac
-    desc = (f"oracle Step 1 on all {w.n_users} users ({t_cluster:.1f} s, charged pro rata "
-            f"{frac:.3f}), Step 2 on {int(sel.sum())} of {sizes.size} clusters in seeded random "
-            f"order ({int((sel & greedy).sum())} greedy): {pairs} pair evaluations in "
-            f"{t_knn:.1f} s; single thread")
-    return pairs / t_total, desc, cl
+    work = np.where(greedy, (w.k + w.greedy_rounds * w.k * w.k) * 2.0 * sum_len,
+                    np.maximum(sizes - 1, 0) * sum_len)
+    est_s = work / 2.5e8
+    size_cls = np.searchsorted(np.array(SIZE_EDGES), sizes, side="right") - 1
+    stratum = np.where(sizes >= 2, size_cls * 2 + greedy.astype(np.int64), -1)
+    ids = [s_ for s_ in np.unique(stratum) if s_ >= 0]
+    est_total = float(est_s[stratum >= 0].sum())
+    rng = np.random.default_rng(rng_seed)
+    t_est, p_est, n_sampled, n_greedy_sampled, t_knn = 0.0, 0.0, 0, 0, 0.0
+    for s_ in ids:
+        members = np.flatnonzero(stratum == s_)
+        members = members[np.argsort(work[members], kind="stable")]
+        share = budget_s * max(0.03, float(est_s[members].sum()) / max(est_total, 1e-12))
+        frac = min(1.0, share / max(float(est_s[members].sum()), 1e-12))
+        step = max(1, int(round(1.0 / frac)))
+        pick = members[int(rng.integers(0, step)) % members.size::step]
+        only = np.zeros(sizes.size, np.uint8)
+        only[pick] = 1
+        t1 = time.perf_counter()
+        _, _, _, pairs = oracle.cluster_knn(ptr, items, cptr, cusers, w.k, seed,
+                                            w.greedy_threshold, w.greedy_rounds, 0, only=only)
+        dt = time.perf_counter() - t1
+        scale = float(work[members].sum()) / max(float(work[pick].sum()), 1.0)
+        t_est += dt * scale
+        if greedy[members[0]]:   # evaluations grow with the members
+            p_est += pairs * float(sizes[members].sum()) / float(sizes[pick].sum())
+        else:                    # brute force: exactly M(M-1)/2 per cluster
+            p_est += float((sizes[members] * (sizes[members] - 1) // 2).sum())
+        t_knn += dt
+        n_sampled += int(pick.size)
+        n_greedy_sampled += int(greedy[pick].sum())
+    t_total = t_est + t_cluster
+    desc = (f"oracle Step 1 on all {w.n_users} users ({t_cluster:.1f} s); Step 2 on a stratified "
+            f"systematic sample of {n_sampled} of {int((sizes >= 2).sum())} clusters "
+            f"({n_greedy_sampled} greedy; {len(ids)} strata by kind and size; {t_knn:.1f} s), "
+            f"scaled to every cluster by estimated work: {p_est:.4g} pair evaluations in an "
+            f"estimated {t_total:.1f} s for the whole build; single thread")
+    return p_est / t_total, desc, cl
 
 
 # ------------------------------------------------------------------ reference arm
@@ -261,7 +309,8 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
             "data": "synthetic", "config": {"workload": w.name, **w.params()},
             "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": 1, "kind": "oracle",
-                             "sample": desc},
+                             "sample": desc, "host": host_cpu(),
+                             "steps_values": vals},
             "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -529,7 +578,8 @@ def main():
         import oracle
         oracle.build()
         v, desc, _ = oracle_sample(ptr_np, items_np, w, seed, args.cpu_seconds)
-        cpu = {"value": v, "unit": "pairs/s", "cores": 1, "kind": "oracle", "sample": desc}
+        cpu = {"value": v, "unit": "pairs/s", "cores": 1, "kind": "oracle", "sample": desc,
+               "host": host_cpu()}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world,
@@ -544,6 +594,10 @@ def main():
                            "l2": "flushed (512 MiB write) before each step",
                            "parallelism": f"replicas{world}" if world > 1 else "single"},
                 "pairs_per_step": pairs, "gram_pairs_per_step": stats["gram_pairs"],
+                "intersections_per_step": stats["brute_pairs"] + stats["gram_pairs"],
+                "pairs_split": {"brute_force": stats["brute_pairs"],
+                                "greedy_evaluations": pairs - stats["brute_pairs"],
+                                "greedy_count_matrix_entries": stats["gram_pairs"]},
                 "quality": quality, "e2e": e2e, "gpu_launches": launches,
                 "gpu_launches_per_step": launches / args.steps,
                 "wall_s_timed": wall, "step_ms": step_ms,

@@ -93,7 +93,13 @@ typedef struct {
                                in [0, b), e.g. from c2_model_propose; NULL = FastRandomHash.
                                Oversized clusters are then split by FastRandomHash with no
                                threshold (the first split key is H_i(u) itself)            */
-  int32_t reserved[6];      /* must be zero                                                */
+  int32_t greedy_max_draws; /* bound on the Philox draws per member for the random start of
+                               a greedy cluster (round 0), made 32 at a time; <= 0 selects
+                               2^24, which uniform draws never reach.  When the bound stops
+                               the draws before min(k, M-1) distinct members are found (any
+                               bound below 32, for instance), C2_ERR_TIMEOUT is recorded in
+                               the status word                                             */
+  int32_t reserved[5];      /* must be zero                                                */
 } c2_options;
 
 /* Run statistics, filled by c2_get_stats(). */
@@ -118,6 +124,9 @@ typedef struct {
                                clusters with a count matrix                                */
   int32_t brute_rows;       /* users of those clusters (rows ranked by the row kernel)     */
   int32_t reserved;
+  int64_t brute_pairs;      /* M(M-1)/2 over brute-force clusters: with gram_pairs, the
+                               intersections actually counted (greedy rounds look counts
+                               up in their clusters' count matrices)                       */
 } c2_stats;
 
 /* Fills *opt with the defaults described above.  Never fails. */
@@ -247,7 +256,8 @@ c2_status c2_reset_status(void* d_ws, c2_stream_t stream);
  * in an 8 MiB array inside the library that every GPU loading the library
  * holds until the process exits, so t * n_users may not exceed
  * c2_merge_topk_noalloc_max_slots() (2,097,088); larger inputs return
- * C2_ERR_UNSUPPORTED.  It calls no allocation routine.  The first call on a
+ * C2_ERR_UNSUPPORTED.  Arguments are checked as c2_merge_topk checks them,
+ * with the same statuses.  It calls no allocation routine.  The first call on a
  * device looks up the array's device address (once per device, with that
  * device current); make that first call before any stream capture.  All
  * calls share the one array: calls that overlap on the GPU (different
@@ -313,7 +323,9 @@ c2_status c2_model_gradients(const c2_model_config* cfg, const void* d_state,
  * brute force).  If the probed quality is below quality_threshold the graph
  * is rebuilt with FastRandomHash keys and C2_ERR_QUALITY_FALLBACK (an
  * informational status) is returned; *h_quality (optional) receives the
- * probed quality of the learned graph.  nnz = d_csr_ptr[n_users].
+ * probed quality of the learned graph.  The device status is read after the
+ * learned build, after the probe and after the fallback build: a device
+ * error of any of them is returned instead (before any fallback status).  nnz = d_csr_ptr[n_users].
  * Synchronises the stream.  Workspace: c2_workspace_size_learned(). */
 size_t c2_workspace_size_learned(const c2_model_config* cfg, int32_t n_users, int64_t nnz,
                                  int32_t n_items, int32_t k, int32_t N, int32_t n_probe,

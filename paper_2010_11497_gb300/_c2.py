@@ -35,7 +35,8 @@ class Options(C.Structure):
     _fields_ = [("greedy_threshold", C.c_int32), ("greedy_rounds", C.c_int32),
                 ("greedy_random", C.c_int32), ("strategy", C.c_int32),
                 ("d_hash_table", C.c_void_p), ("gram_budget_bytes", C.c_int64),
-                ("d_keys", C.c_void_p), ("reserved", C.c_int32 * 6)]
+                ("d_keys", C.c_void_p), ("greedy_max_draws", C.c_int32),
+                ("reserved", C.c_int32 * 5)]
 
 
 class ModelConfig(C.Structure):
@@ -51,7 +52,7 @@ class Stats(C.Structure):
                 ("item_visits_greedy", C.c_int64), ("greedy_visits", C.c_int64),
                 ("greedy_computed", C.c_int64), ("greedy_evaluated", C.c_int64),
                 ("brute_gram_elems", C.c_int64), ("brute_rows", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("reserved", C.c_int32), ("brute_pairs", C.c_int64)]
 
 
 _lib = None
@@ -127,7 +128,7 @@ def lib():
 
 def options(greedy_threshold=0, greedy_rounds=-1, greedy_random=0, strategy=STRATEGY_AUTO,
             hash_table: torch.Tensor | None = None, gram_budget_bytes=0,
-            keys: torch.Tensor | None = None) -> Options:
+            keys: torch.Tensor | None = None, greedy_max_draws=0) -> Options:
     o = Options()
     lib().c2_default_options(C.byref(o))
     o.greedy_threshold = greedy_threshold
@@ -137,6 +138,7 @@ def options(greedy_threshold=0, greedy_rounds=-1, greedy_random=0, strategy=STRA
     o.d_hash_table = None if hash_table is None else hash_table.data_ptr()
     o.gram_budget_bytes = gram_budget_bytes
     o.d_keys = None if keys is None else keys.data_ptr()
+    o.greedy_max_draws = greedy_max_draws
     o._keep = (hash_table, keys)      # keep the tensors alive with the options
     return o
 
@@ -340,7 +342,8 @@ def c2_get_stats(ws, stream=None) -> dict:
                 greedy_users=s.greedy_users, greedy_visits=s.greedy_visits,
                 greedy_computed=s.greedy_computed, greedy_evaluated=s.greedy_evaluated,
                 item_visits_brute=s.item_visits_brute, item_visits_greedy=s.item_visits_greedy,
-                brute_gram_elems=s.brute_gram_elems, brute_rows=s.brute_rows)
+                brute_gram_elems=s.brute_gram_elems, brute_rows=s.brute_rows,
+                brute_pairs=s.brute_pairs)
 
 
 def c2_reset_status(ws, stream=None):

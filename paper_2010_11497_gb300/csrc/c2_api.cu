@@ -160,7 +160,7 @@ c2_status check_common(int32_t n, int32_t m, int32_t k, int32_t t, int32_t b, in
   if (!sizes_ok(n, m, k, t, b, N)) return C2_ERR_UNSUPPORTED;
   if ((int64_t)t * n >= (int64_t(1) << 31) - 1) return C2_ERR_UNSUPPORTED;
   if (opt) {
-    for (int i = 0; i < 6; ++i)
+    for (int i = 0; i < 5; ++i)
       if (opt->reserved[i] != 0) return C2_ERR_INVALID_ARG;
     if (opt->strategy < -1 || opt->strategy > 2) return C2_ERR_INVALID_ARG;
     if (opt->greedy_random < 0) return C2_ERR_INVALID_ARG;
@@ -197,6 +197,7 @@ void c2_default_options(c2_options* opt) {
   opt->d_hash_table = nullptr;
   opt->gram_budget_bytes = 0;
   opt->d_keys = nullptr;
+  opt->greedy_max_draws = 0;
 }
 
 const char* c2_status_string(c2_status s) {
@@ -255,6 +256,7 @@ c2_status c2_get_stats(const void* d_ws, c2_stream_t stream, c2_stats* out) {
   out->greedy_evaluated = (int64_t)h.greedy_evaluated;
   out->brute_gram_elems = (int64_t)h.brute_gram_elems;
   out->brute_rows = h.brute_rows;
+  out->brute_pairs = (int64_t)h.brute_pairs;
   return C2_OK;
 }
 

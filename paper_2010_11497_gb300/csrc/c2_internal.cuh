@@ -41,7 +41,9 @@ struct DevHeader {
   unsigned long long greedy_evaluated;  // candidates looked up by greedy rounds
   unsigned long long brute_gram_elems;  // count-matrix elements of brute-force clusters
   int32_t brute_rows;          // users of brute-force clusters with a count matrix
-  int32_t pad[9];
+  int32_t pad1;
+  unsigned long long brute_pairs;  // M(M-1)/2 over brute-force clusters (intersections computed)
+  int32_t pad[6];
 };
 static_assert(sizeof(DevHeader) <= 256, "header must fit 256 bytes");
 
@@ -146,6 +148,11 @@ struct KnnWs {
   int64_t* scan_tmp64;
 };
 
+// Host checks shared by the entry points (c2_api.cu): argument errors
+// (C2_ERR_INVALID_ARG), then sizes beyond the documented limits
+// (C2_ERR_UNSUPPORTED), then the options' reserved fields.
+c2_status check_common(int32_t n, int32_t m, int32_t k, int32_t t, int32_t b, int32_t N,
+                       const c2_options* opt);
 Sizes make_sizes(int32_t n, int64_t nnz, int32_t m, int32_t k, int32_t t, int32_t b, int32_t N,
                  const c2_options* opt);
 void bind_cluster_ws(Ws& w, const Sizes& s, ClusterWs& c);

@@ -1180,7 +1180,10 @@ __global__ void k_prep(const int32_t* __restrict__ cptr, const int32_t* __restri
   unsigned long long p = brute ? (unsigned long long)M * (M - 1) / 2 : 0ull;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
-  if ((threadIdx.x & 31) == 0 && p) atomicAdd(&hdr->pairs, p);
+  if ((threadIdx.x & 31) == 0 && p) {
+    atomicAdd(&hdr->pairs, p);
+    atomicAdd(&hdr->brute_pairs, p);
+  }
   if (c == 0) hdr->n_labels = L;
 }
 
@@ -1320,6 +1323,7 @@ struct GreedyArgs {
   const int32_t* n_gwork;
   unsigned* counter;
   int32_t k, round, n_random, mcap;
+  int32_t max_draws;       // bound on the round-0 draws per member
   uint2 key;               // Philox key = run seed
   const int32_t* ipos;     // slot -> internal position
   const int2* iinfo;       // internal slot -> (local index, profile length)
@@ -1362,9 +1366,10 @@ __global__ void __launch_bounds__(kNT) k_greedy_init(GreedyArgs a) {
     const int k = a.k, k0 = min(k, M - 1);
     int cnt = 0;
     // rejection sampling of distinct members; bounded so that no warp can
-    // loop forever (never reached for k0 <= M-1 with a uniform generator)
+    // loop forever (the default bound is never reached for k0 <= M-1 with a
+    // uniform generator)
     for (int j0 = 0; cnt < k0; j0 += 32) {
-      if (j0 >= (1 << 24)) {
+      if (j0 + 32 > a.max_draws) {   // draws come 32 at a time
         if (lane == 0) dev_fail(a.hdr, C2_ERR_TIMEOUT);
         break;
       }
@@ -2149,6 +2154,7 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
       ga.counter = &w.hdr->work_counter[2];
       ga.ipos = w.ipos; ga.iinfo = w.iinfo;
       ga.k = k; ga.n_random = opt.greedy_random; ga.key = key;
+      ga.max_draws = opt.greedy_max_draws > 0 ? opt.greedy_max_draws : (1 << 24);
       ga.out_id = lid; ga.out_in = lin; ga.out_un = lun; ga.hdr = w.hdr;
       ga.mcap = (mmax + 31) & ~31;
       {

@@ -1148,7 +1148,10 @@ c2_status c2_build_knn_graph_learned(const c2_model_config* cfg, const void* d_s
   if (rc) return rc;
   double h[2] = {0, 0};
   C2_CUDA_TRY(cudaMemcpyAsync(h, sims, sizeof h, cudaMemcpyDeviceToHost, st));
-  C2_CUDA_TRY(cudaStreamSynchronize(st));
+  // the probe's judge reset the status header: a device error of the judge
+  // or of the averages voids the probe (c2_get_status synchronises)
+  rc = c2_get_status(d_ws, stream);
+  if (rc) return rc;
   const double q = h[1] > 0 ? h[0] / h[1] : 1.0;
   if (h_quality) *h_quality = q;
   if (q >= (double)quality_threshold) return C2_OK;
@@ -1156,6 +1159,10 @@ c2_status c2_build_knn_graph_learned(const c2_model_config* cfg, const void* d_s
   o.d_keys = nullptr;
   rc = c2_build_knn_graph(d_csr_ptr, d_csr_items, n_users, n_items, k, cfg->t, cfg->b, N, seed,
                           &o, d_nbr_id, d_nbr_inter, d_nbr_union, d_ws, base, stream);
+  if (rc) return rc;
+  // a device error of the fallback build takes precedence over the
+  // informational fallback status
+  rc = c2_get_status(d_ws, stream);
   if (rc) return rc;
   return C2_ERR_QUALITY_FALLBACK;
 }

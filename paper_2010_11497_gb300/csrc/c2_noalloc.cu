@@ -56,13 +56,16 @@ c2_status c2_merge_topk_noalloc(const int32_t* d_cusers, int32_t n_users, int32_
                                 const int32_t* d_loc_id, const int32_t* d_loc_inter,
                                 const int32_t* d_loc_union, int32_t* d_nbr_id,
                                 int32_t* d_nbr_inter, int32_t* d_nbr_union, c2_stream_t stream) {
-  if (n_users < 0 || t < 1 || t > kMaxT || k < 1 || k > kMaxK) return C2_ERR_INVALID_ARG;
+  // the same argument checks and statuses as c2_merge_topk, then the cap of
+  // the fixed scratch array
+  c2_status rc = check_common(n_users, 0, k, t, 1, 2, nullptr);
+  if (rc) return rc;
   if ((int64_t)t * n_users > kStaticMaxSlots) return C2_ERR_UNSUPPORTED;
   if (!d_cusers || !d_loc_id || !d_loc_inter || !d_loc_union || !d_nbr_id || !d_nbr_inter ||
       !d_nbr_union)
     return C2_ERR_INVALID_ARG;
   void* base = nullptr;
-  c2_status rc = scratch_address(&base);
+  rc = scratch_address(&base);
   if (rc) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   KnnWs w{};

@@ -8,41 +8,37 @@
 // the hidden layer h (row-major [M][K]) and Bt the transposed output weights
 // (row-major [N][K]), so both operands are K-major.
 //
-// Structure (one CTA per SM, persistent, clusters of two CTAs): the two CTAs
-// of a cluster walk the same contiguous range of (slice pair, row tile) work
-// items, CTA rank r taking slice 2p + r of pair p.  A slice's 256 x K block of
-// Bt stays resident in shared memory (loaded by TMA once per slice); 128-row
-// tiles of A stream through a ring of stages of 128 x 64, each CTA loading
-// 64 of the rows and multicasting them to both CTAs, so A crosses from L2
-// once per pair of slices (A traffic, not the tensor pipe, bounds the
-// single-CTA form of this kernel).  A stage is refilled once the MMAs of both
-// CTAs have released it (their commits arrive on both CTAs' barriers).  One
-// thread issues tcgen05.mma (M = 128, N = 256, K = 16) into one of two TMEM
-// accumulators of 256 FP32 columns, so the epilogue of a tile overlaps the
-// MMAs of the next.  Eight epilogue warps (two per 32-lane TMEM quadrant,
-// one per 128-column half) read their rows with tcgen05.ld, add the bias and
-// reduce each row's half to (max, argmax).
+// Structure (one CTA per SM, persistent, no clusters): each CTA walks a
+// contiguous range of (256-column slice, 128-row tile) work items, slice
+// major.  The slice's 256 x K block of Bt stays resident in shared memory
+// (loaded by TMA once per slice); 128-row tiles of A stream through a ring of
+// stages of 128 x 64, each CTA loading its own tiles.  A stage is refilled
+// once the MMAs that read it have completed (their commit arrives on the
+// stage's barrier).  One thread issues tcgen05.mma (M = 128, N = 256,
+// K = 16) into one of two TMEM accumulators of 256 FP32 columns, so the
+// epilogue of a tile overlaps the MMAs of the next.  Eight epilogue warps
+// (two per 32-lane TMEM quadrant, one per 128-column half) read their rows
+// with tcgen05.ld, add the bias and reduce each row's half to (max, argmax).
 //
 // Every mbarrier wait is bounded: after TC_WAIT_CYCLES, or once another role
 // gave up, the kernel records C2_ERR_TIMEOUT in the status word, waits (again
 // bounded) for its own copies and MMAs in flight, frees its TMEM and returns.
-#include <cuda.h>
-#include <cudaTypedefs.h>
-
 #include <algorithm>
 #include <mutex>
 
 #include "c2_internal.cuh"
+#include "c2_tc.cuh"
 
 namespace c2 {
 namespace {
+
+using namespace tc;
 
 constexpr int TC_BM = 128;                     // rows per tile = TMEM lanes
 constexpr int TC_BN = 256;                     // columns per slice
 constexpr int TC_BK = 64;                      // K per TMA box: one 128-byte swizzle row
 constexpr int TC_KMAX = 256;
 constexpr int TC_STAGES = 6;
-constexpr int TC_CLUSTER = 2;                  // CTAs sharing each A tile (multicast)
 constexpr int TC_A_STAGE = TC_BM * TC_BK * 2;  // 16 KiB
 constexpr int TC_B_CHUNK = TC_BN * TC_BK * 2;  // 32 KiB
 constexpr int TC_EPI_WARPS = 8;                // two per TMEM lane quadrant
@@ -62,41 +58,9 @@ struct TcArgs {
   long long total;     // S * MT work items
 };
 
-__device__ __forceinline__ uint32_t su32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Waits for the phase of `parity` to complete; false on timeout or when the
-// CTA is aborting (check_abort).
-__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
-                                       bool check_abort) {
-  const long long t0 = clock64();
-  while (!mbar_test(bar, parity)) {
-    if (check_abort && *abort_flag) return false;
-    if (clock64() - t0 > TC_WAIT_CYCLES) return false;
-  }
-  return true;
+__device__ __forceinline__ bool tc_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                                        bool check_abort) {
+  return mbar_wait(bar, parity, abort_flag, check_abort, TC_WAIT_CYCLES);
 }
 
 __device__ __forceinline__ void tc_abort(volatile int* abort_flag, int32_t* status) {
@@ -104,114 +68,10 @@ __device__ __forceinline__ void tc_abort(volatile int* abort_flag, int32_t* stat
   atomicCAS(status, 0, (int32_t)C2_ERR_TIMEOUT);
 }
 
-// Multicast form: the box lands at the same offset in the shared memory of
-// every CTA in `mask`, and complete_tx is signalled on each one's barrier at
-// the offset of `bar`.
-__device__ __forceinline__ void tma_load_2d_mc(uint32_t dst, const CUtensorMap* tm, int x, int y,
-                                               uint32_t bar, uint16_t mask) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
-      " [%0], [%1, {%2, %3}], [%4], %5;\n" ::"r"(dst),
-      "l"((uint64_t)tm), "r"(x), "r"(y), "r"(bar), "h"(mask)
-      : "memory");
-}
-
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* tm, int x, int y,
-                                            uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3}], [%4];\n" ::"r"(dst),
-      "l"((uint64_t)tm), "r"(x), "r"(y), "r"(bar)
-      : "memory");
-}
-
-// Shared-memory matrix descriptor of a K-major operand in the 128-byte
-// swizzled layout that TMA writes: rows of 128 bytes, 8-row groups 1024
-// bytes apart (stride byte offset), descriptor version 1, swizzle mode 2.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
-  uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)1 << 16;              // leading byte offset (unused when swizzled)
-  d |= (uint64_t)(1024 >> 4) << 32;    // stride byte offset
-  d |= (uint64_t)1 << 46;              // version
-  d |= (uint64_t)2 << 61;              // 128-byte swizzle
-  return d;
-}
-
 // Instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B, both
 // K-major, N >> 3 at bit 17, M >> 4 at bit 24.
 constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_BN >> 3) << 17) |
                               ((uint32_t)(TC_BM >> 4) << 24);
-
-__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t acc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(TC_IDESC), "r"(acc)
-      : "memory");
-}
-__device__ __forceinline__ void umma_commit(uint32_t bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-                   bar)
-               : "memory");
-}
-// Arrives on the barrier at offset `bar` of every CTA in `mask` once this
-// thread's MMAs so far have finished.
-__device__ __forceinline__ void umma_commit_mc(uint32_t bar, uint16_t mask) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
-      " [%0], %1;\n" ::"r"(bar),
-      "h"(mask)
-      : "memory");
-}
-__device__ __forceinline__ uint32_t cluster_rank() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;\n" : "=r"(r));
-  return r;
-}
-__device__ __forceinline__ void cluster_sync_all() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;\n" ::
-                   : "memory");
-}
-__device__ __forceinline__ void tc_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-}
-
-#define TC_R32(r)                                                                              \
-  "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), \
-      "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]),           \
-      "r"(r[16]), "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]),          \
-      "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]),          \
-      "r"(r[30]), "r"(r[31])
-
-// Starts loading 32 consecutive FP32 columns of this warp's 32 TMEM lanes;
-// the registers are valid after tmem_wait(r) on the same array.
-__device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t* r) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
-      "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
-        "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
-        "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-}
-// Waits for this thread's TMEM loads; the in/out operands keep every use of
-// r after the wait.
-__device__ __forceinline__ void tmem_wait(uint32_t* r) {
-  asm volatile("tcgen05.wait::ld.sync.aligned;\n"
-               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]),
-                 "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]),
-                 "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]),
-                 "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]),
-                 "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]),
-                 "+r"(r[30]), "+r"(r[31])
-               :
-               : "memory");
-}
 
 // Running (max, argmax) over 32 columns col..col+31 (ascending, so ties keep
 // the lower column) with their bias.
@@ -254,16 +114,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   volatile int* abort_flag = &abort_sh;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int rank = (int)cluster_rank();
-  const int pair = blockIdx.x / TC_CLUSTER, npairs = gridDim.x / TC_CLUSTER;
-  const long long lo = g.total * pair / npairs;
-  const long long hi = g.total * (pair + 1) / npairs;
-  constexpr uint16_t kMask = (1u << TC_CLUSTER) - 1;
+  const long long lo = g.total * blockIdx.x / gridDim.x;
+  const long long hi = g.total * (blockIdx.x + 1) / gridDim.x;
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < TC_STAGES; ++i) {
       mbar_init(afull(i), 1);
-      mbar_init(aempty(i), TC_CLUSTER);
+      mbar_init(aempty(i), 1);
     }
     mbar_init(bfull, 1);
     mbar_init(bempty, 1);
@@ -274,20 +131,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     mbar_init(bdone, 1);
     abort_sh = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-    asm volatile("prefetch.tensormap [%0];\n" ::"l"((uint64_t)&tmA) : "memory");
-    asm volatile("prefetch.tensormap [%0];\n" ::"l"((uint64_t)&tmB) : "memory");
+    prefetch_map(&tmA);
+    prefetch_map(&tmB);
   }
-  if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
-                     su32(&tmem_slot)),
-                 "r"(TC_TMEM_COLS)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
-  }
+  if (warp == 1) tmem_alloc(su32(&tmem_slot), TC_TMEM_COLS);
   __syncwarp();
-  tc_fence_before();
-  cluster_sync_all();   // barriers of both CTAs initialised before any multicast
-  tc_fence_after();
+  fence_before();
+  __syncthreads();   // barriers initialised and TMEM allocated before any role starts
+  fence_after();
   const uint32_t tmem = tmem_slot;
 
   if (warp == 0 && lane == 0) {
@@ -299,9 +150,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     for (int i = 0; i < TC_STAGES; ++i) issued[i] = 0, last_par[i] = 0;
     bool ok = true;
     for (long long idx = lo; idx < hi && ok; ++idx) {
-      const int s = TC_CLUSTER * (int)(idx / g.MT) + rank, m = (int)(idx % g.MT);
+      const int s = (int)(idx / g.MT), m = (int)(idx % g.MT);
       if (s != cur_s) {
-        if (nb > 0 && !mbar_wait(bempty, (uint32_t)(nb - 1) & 1u, abort_flag, true)) {
+        if (nb > 0 && !tc_wait(bempty, (uint32_t)(nb - 1) & 1u, abort_flag, true)) {
           ok = false;
           break;
         }
@@ -312,14 +163,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         ++nb;
       }
       for (int kc = 0; kc < KC; ++kc) {
-        if (!mbar_wait(aempty(stage), phase ^ 1u, abort_flag, true)) {
+        if (!tc_wait(aempty(stage), phase ^ 1u, abort_flag, true)) {
           ok = false;
           break;
         }
-        // this CTA's rows of the tile, to both CTAs; the barrier counts both parts
         mbar_expect_tx(afull(stage), (uint32_t)TC_A_STAGE);
-        tma_load_2d_mc(sA + (uint32_t)stage * TC_A_STAGE + (uint32_t)rank * (TC_A_STAGE / TC_CLUSTER),
-                       &tmA, kc * TC_BK, m * TC_BM + rank * (TC_BM / TC_CLUSTER), afull(stage), kMask);
+        tma_load_2d(sA + (uint32_t)stage * TC_A_STAGE, &tmA, kc * TC_BK, m * TC_BM, afull(stage));
         issued[stage] = 1;
         last_par[stage] = phase;
         if (++stage == TC_STAGES) stage = 0, phase ^= 1u;
@@ -329,8 +178,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       tc_abort(abort_flag, g.status);
       // let the copies already issued land before the CTA exits
       for (int i = 0; i < TC_STAGES; ++i)
-        if (issued[i]) mbar_wait(afull(i), last_par[i], abort_flag, false);
-      if (nb > 0) mbar_wait(bfull, (uint32_t)(nb - 1) & 1u, abort_flag, false);
+        if (issued[i]) tc_wait(afull(i), last_par[i], abort_flag, false);
+      if (nb > 0) tc_wait(bfull, (uint32_t)(nb - 1) & 1u, abort_flag, false);
     }
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer
@@ -339,38 +188,38 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     long long t = 0;
     bool ok = true;
     for (long long idx = lo; idx < hi && ok; ++idx, ++t) {
-      const int s = TC_CLUSTER * (int)(idx / g.MT) + rank;
+      const int s = (int)(idx / g.MT);
       if (s != cur_s) {
         if (nb > 0) umma_commit(bempty);   // the old slice is free once its MMAs finish
-        if (!mbar_wait(bfull, (uint32_t)nb & 1u, abort_flag, true)) {
+        if (!tc_wait(bfull, (uint32_t)nb & 1u, abort_flag, true)) {
           ok = false;
           break;
         }
-        tc_fence_after();
+        fence_after();
         cur_s = s;
         ++nb;
       }
       const int a = (int)(t & 1);
       const uint32_t use = (uint32_t)(t >> 1);
-      if (!mbar_wait(accempty(a), (use & 1u) ^ 1u, abort_flag, true)) {
+      if (!tc_wait(accempty(a), (use & 1u) ^ 1u, abort_flag, true)) {
         ok = false;
         break;
       }
-      tc_fence_after();
+      fence_after();
       const uint32_t d = tmem + (uint32_t)(a * TC_BN);
       for (int kc = 0; kc < KC; ++kc) {
-        if (!mbar_wait(afull(stage), phase, abort_flag, true)) {
+        if (!tc_wait(afull(stage), phase, abort_flag, true)) {
           ok = false;
           break;
         }
-        tc_fence_after();
+        fence_after();
         const uint32_t abase = sA + (uint32_t)stage * TC_A_STAGE;
         const uint32_t bbase = sB + (uint32_t)kc * TC_B_CHUNK;
 #pragma unroll
         for (int kk = 0; kk < TC_BK / 16; ++kk)
-          umma_bf16(d, sw128_desc(abase + kk * 32), sw128_desc(bbase + kk * 32),
-                    (kc | kk) != 0 ? 1u : 0u);
-        umma_commit_mc(aempty(stage), kMask);   // released in both CTAs once these MMAs finish
+          umma_f16(d, sw128_desc(abase + kk * 32), sw128_desc(bbase + kk * 32), TC_IDESC,
+                   (kc | kk) != 0 ? 1u : 0u);
+        umma_commit(aempty(stage));   // the stage is free once these MMAs finish
         if (++stage == TC_STAGES) stage = 0, phase ^= 1u;
       }
       if (!ok) break;
@@ -379,22 +228,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (!ok) tc_abort(abort_flag, g.status);
     // every MMA issued by this thread has finished before TMEM is freed
     umma_commit(bdone);
-    mbar_wait(bdone, 0, abort_flag, false);
+    tc_wait(bdone, 0, abort_flag, false);
   } else if (warp >= 2) {
     // ---------------- epilogue: rows 32q .. 32q + 31, columns h*128 .. h*128 + 127
     const int q = warp & 3, h = (warp - 2) >> 2;
     long long t = 0;
     for (long long idx = lo; idx < hi; ++idx, ++t) {
-      const int s = TC_CLUSTER * (int)(idx / g.MT) + rank, m = (int)(idx % g.MT);
+      const int s = (int)(idx / g.MT), m = (int)(idx % g.MT);
       const int a = (int)(t & 1);
       const uint32_t use = (uint32_t)(t >> 1);
       // warp-uniform outcome: the TMEM loads below are warp-collective
-      const bool ready = __all_sync(0xffffffffu, mbar_wait(accfull(a), use & 1u, abort_flag, true));
+      const bool ready = __all_sync(0xffffffffu, tc_wait(accfull(a), use & 1u, abort_flag, true));
       if (!ready) {
         if (lane == 0) tc_abort(abort_flag, g.status);
         break;
       }
-      tc_fence_after();
+      fence_after();
       float best = -INFINITY;
       int arg = 0x7fffffff;
       const int col0 = s * TC_BN + h * TC_EPI_COLS;
@@ -414,7 +263,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       tc_scan32(ra, g.bias, col0 + 64, best, arg);
       tmem_wait(rb);
       tc_scan32(rb, g.bias, col0 + 96, best, arg);
-      tc_fence_before();
+      fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(accempty(a));
       const int row = m * TC_BM + 32 * q + lane;
@@ -423,13 +272,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
   }
   __syncwarp();          // lane 0 of the producer and MMA warps rejoins its warp
-  tc_fence_before();
-  cluster_sync_all();   // no multicast copy or commit of the peer still targets this CTA
+  fence_before();
+  __syncthreads();   // every role is done with TMEM
   if (warp == 1) {
-    tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
-                 "r"(TC_TMEM_COLS)
-                 : "memory");
+    fence_after();
+    tmem_dealloc(tmem, TC_TMEM_COLS);
   }
 }
 
@@ -449,20 +296,6 @@ __global__ void k_transpose_bf16(const __nv_bfloat16* __restrict__ B, int K, int
   }
 }
 
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  static std::once_flag once;
-  std::call_once(once, [] {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
-                                         &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-  });
-  return fn;
-}
-
 // 2-D BF16 map over a row-major [rows][K] matrix, boxes of 64 x box_rows,
 // 128-byte swizzle (the layout sw128_desc describes).
 bool make_map(CUtensorMap* tm, const void* base, int K, int rows, int box_rows) {
@@ -479,9 +312,22 @@ bool make_map(CUtensorMap* tm, const void* base, int K, int rows, int box_rows) 
 
 }  // namespace
 
+PFN_cuTensorMapEncodeTiled_v12000 tc::encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
 bool tc_logits_ok(int K, int N, int b) {
-  return K >= TC_BK && K <= TC_KMAX && K % TC_BK == 0 && N % (TC_CLUSTER * TC_BN) == 0 &&
-         b % TC_EPI_COLS == 0;
+  return K >= TC_BK && K <= TC_KMAX && K % TC_BK == 0 && N % TC_BN == 0 && b % TC_EPI_COLS == 0;
 }
 int tc_slice_width() { return TC_EPI_COLS; }
 
@@ -496,11 +342,10 @@ c2_status tc_transpose_bf16(const __nv_bfloat16* B, int K, int N, __nv_bfloat16*
 c2_status tc_logits_argmax(const __nv_bfloat16* A, int M, int K, const __nv_bfloat16* Bt, int N,
                            const float* bias, float2* part, int32_t* status, cudaStream_t st) {
   if (M <= 0) return C2_OK;
-  if (K < TC_BK || K > TC_KMAX || K % TC_BK || N % (TC_CLUSTER * TC_BN)) return C2_ERR_UNSUPPORTED;
+  if (K < TC_BK || K > TC_KMAX || K % TC_BK || N % TC_BN) return C2_ERR_UNSUPPORTED;
   if (((uintptr_t)A & 15u) || ((uintptr_t)Bt & 15u)) return C2_ERR_INVALID_ARG;
   CUtensorMap tmA, tmB;
-  if (!make_map(&tmA, A, K, M, TC_BM / TC_CLUSTER) || !make_map(&tmB, Bt, K, N, TC_BN))
-    return C2_ERR_CUDA;
+  if (!make_map(&tmA, A, K, M, TC_BM) || !make_map(&tmB, Bt, K, N, TC_BN)) return C2_ERR_CUDA;
   TcArgs g;
   g.bias = bias;
   g.part = part;
@@ -509,24 +354,12 @@ c2_status tc_logits_argmax(const __nv_bfloat16* A, int M, int K, const __nv_bflo
   g.K = K;
   g.S = N / TC_BN;
   g.MT = div_up(M, TC_BM);
-  g.total = (long long)(g.S / TC_CLUSTER) * g.MT;   // (slice pair, row tile) items
+  g.total = (long long)g.S * g.MT;   // (slice, row tile) items
   C2_CUDA_TRY(cudaFuncSetAttribute(k_logits_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)TC_SMEM));
-  const int pairs = (int)std::min<long long>(num_sms() / TC_CLUSTER, g.total);
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(pairs * TC_CLUSTER);
-  cfg.blockDim = dim3(TC_THREADS);
-  cfg.dynamicSmemBytes = TC_SMEM;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = TC_CLUSTER;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  C2_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_logits_tc, tmA, tmB, g));
-  g_launches.fetch_add(1, std::memory_order_relaxed);
+  const int grid = (int)std::min<long long>(num_sms(), g.total);
+  C2_LAUNCH(k_logits_tc, grid, TC_THREADS, TC_SMEM, st, tmA, tmB, g);
+  C2_CUDA_TRY(cudaGetLastError());
   return C2_OK;
 }
 

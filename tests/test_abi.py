@@ -31,7 +31,7 @@ def test_status_strings(lib):
 def test_default_options(lib):
     o = c2.options()
     assert o.greedy_threshold == 0 and o.greedy_rounds == -1 and o.strategy == -1
-    assert list(o.reserved) == [0] * 6 and o.d_keys is None
+    assert list(o.reserved) == [0] * 5 and o.d_keys is None and o.greedy_max_draws == 0
 
 
 def test_workspace_size_validates(lib):

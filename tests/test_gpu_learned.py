@@ -207,7 +207,7 @@ def test_model_keys_tcgen05_full_shape(c2):
 
 
 def test_model_keys_mma_fused_argmax_match_oracle(c2):
-    # t*b = 384 (not a multiple of 512): the mma.sync logits GEMM with the
+    # t*b = 384 (not a multiple of 256): the mma.sync logits GEMM with the
     # argmax of 128-column slices fused into its epilogue
     m = _model(c2, t=3, b=128, dim=64, hidden=128, rows_log2=11, seed=14)
     ptr, items = synth.random_profiles(2100, 900, 25, 49)
@@ -220,3 +220,31 @@ def test_model_keys_mma_fused_argmax_match_oracle(c2):
         zz = np.sort(z[u, j * b:(j + 1) * b])
         assert zz[-1] - zz[-2] < 1e-3 * max(1.0, abs(zz[-1])), (j, u)
     assert len(diff) <= 0.01 * keys.size
+
+
+def test_learned_fallback_device_error_is_returned(c2):
+    # A device error of the fallback build is returned, not the informational
+    # fallback status.  An all-zero explicit hash table puts every user in one
+    # FastRandomHash cluster per function (N = n: no split); the greedy
+    # threshold sends it to the greedy phase, whose random start may make no
+    # draw (greedy_max_draws = 1 is below one batch of 32): C2_ERR_TIMEOUT.
+    # Every learned cluster is below the threshold (brute force), so the
+    # learned build and its probe succeed, and a threshold above any quality
+    # forces the fallback.
+    n, m_items, k, t, b, seed = 2000, 900, 10, 4, 32, 6
+    ptr, items = synth.random_profiles(n, m_items, 25, 50)
+    model = _model(c2, t=t, b=b, seed=15)
+    dptr, ditems = dev(ptr), dev(items)
+    keys = model.propose(dptr, ditems).cpu().numpy()
+    largest = max(int(np.bincount(keys[j], minlength=b).max()) for j in range(t))
+    assert largest + 1 < n
+    zeros = dev(np.zeros((t, m_items), np.int32))
+    opts = c2.options(greedy_threshold=largest + 1, hash_table=zeros, greedy_max_draws=1)
+    # the learned graph alone (threshold 0: no fallback) is fine
+    _, q, fell = model.build_knn_graph(dptr, ditems, m_items, k, n, seed, opts=opts,
+                                       quality_threshold=0.0, n_probe=200)
+    assert not fell and 0.0 < q <= 1.0
+    with pytest.raises(c2.C2Error) as e:
+        model.build_knn_graph(dptr, ditems, m_items, k, n, seed, opts=opts,
+                              quality_threshold=2.0, n_probe=200)
+    assert e.value.code == 6

@@ -335,6 +335,32 @@ def test_workspace_too_small(c2):
     assert e.value.code == 4
 
 
+def test_greedy_draw_bound_reports_timeout(c2):
+    # The greedy random start's bounded loop: a bound below one batch of 32
+    # draws stops every member's start, C2_ERR_TIMEOUT reaches the status
+    # word, and the kernels after it (rounds, emit, merge) leave the outputs
+    # untouched.  The default bound gives the oracle's graph.
+    ptr, items = synth.random_profiles(1200, 300, 20, 51, zipf_s=1.1)
+    n, m, k, t, b, N, seed, thr = 1200, 300, 8, 2, 4, 1200, 3, 50
+    dptr, ditems = to_dev(ptr), to_dev(items)
+    opts = c2.options(greedy_threshold=thr, greedy_rounds=2, greedy_max_draws=1)
+    ws = c2.workspace(c2.workspace_size(n, items.size, m, k, t, b, N, opts), DEV)
+    out = [torch.full((n, k), -7, dtype=torch.int32, device=DEV) for _ in range(3)]
+    c2.c2_build_knn_graph(dptr, ditems, m, k, t, b, N, seed, opts=opts, ws=ws, out=out,
+                          check=False)
+    assert c2.c2_get_status(ws) == 6
+    assert c2.c2_get_stats(ws)["n_greedy_clusters"] >= 1
+    for o in out:
+        assert bool((o == -7).all())
+    # the same workspace, cleared by the next build, with the default bound
+    gid, gin, gun = c2.c2_build_knn_graph(dptr, ditems, m, k, t, b, N, seed, ws=ws,
+                                          opts=c2.options(greedy_threshold=thr, greedy_rounds=2))
+    oid, oin, oun, _ = oracle.build_graph(ptr, items, m, k, t, b, N, seed, thr, 2)
+    assert_same(gid, oid, "nbr_id")
+    assert_same(gin, oin, "nbr_inter")
+    assert_same(gun, oun, "nbr_union")
+
+
 def _with_long_profiles(ptr, items, m, lens, seed):
     """Appends users whose profiles hold `lens` distinct random items."""
     rng = np.random.default_rng(seed)
