@@ -518,7 +518,8 @@ double oracle_avg_sim(const int32_t* nbr_inter, const int32_t* nbr_union, int32_
 // Learned proposer (no counterpart in the paper): the network of the
 // library's proposer written out in FP64, with the operands rounded to BF16
 // where the library stores them in BF16 (table, weights, bag sums, hidden
-// activations).  Parameters are given as FP32 masters.
+// activations; in the backward pass the logit gradients and the ReLU-masked
+// hidden gradients).  Parameters are given as FP32 masters.
 // ======================================================================
 }  // extern "C"
 
@@ -688,6 +689,7 @@ int oracle_model_grads(int32_t D, int32_t H, int32_t t, int32_t b, int32_t rows_
       for (int c = 0; c < b; ++c) {
         const size_t q = (size_t)j * b + c;
         dz[q] = p[(size_t)r * T + q] * (g[(size_t)r * T + q] - s);
+        if (!g_exact) dz[q] = to_bf16((float)dz[q]);   // stored in BF16 for the backward GEMMs
       }
     }
     std::vector<double> dh(H, 0.0);
@@ -701,6 +703,7 @@ int oracle_model_grads(int32_t D, int32_t H, int32_t t, int32_t b, int32_t rows_
     std::vector<double> de(D, 0.0);
     for (int h = 0; h < H; ++h) {
       if (f[r].hpre[h] <= 0.0) continue;
+      if (!g_exact) dh[h] = to_bf16((float)dh[h]);     // the masked dh, stored in BF16
       gb1[h] += dh[h];
       for (int d = 0; d < D; ++d) {
         gW1[(size_t)d * H + h] += f[r].e16[d] * dh[h];

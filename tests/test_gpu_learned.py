@@ -3,8 +3,9 @@
 - clustering and whole builds with caller-given first-level keys: bit-exact;
 - model keys: equal to the oracle's argmax (FP64 logits on the same BF16
   operands) except where the oracle's two best logits are within 1e-3;
-- gradients (BF16 operands, FP32 sums): relative L2 error against the FP64
-  oracle below 3e-2 per tensor, loss within 1e-3;
+- gradients (BF16 operands, FP32 sums): element by element within 1e-2
+  relative (above a floor of 1e-4 of the tensor's largest) of the FP64
+  oracle on the same BF16 roundings, loss within 1e-3;
 - training lowers the loss and raises the co-assignment of positive pairs;
 - the learned build with its quality probe and FastRandomHash fallback.
 """
@@ -91,10 +92,15 @@ def test_model_gradients_match_oracle(c2):
     loss = loss.cpu().numpy()
     assert abs(loss[0] - oloss[0]) <= 1e-3 * abs(oloss[0]) + 1e-6
     assert abs(loss[1] - oloss[1]) <= 1e-3 * abs(oloss[1]) + 1e-5
+    # element by element: the oracle rounds to BF16 where the library stores
+    # BF16 (operands, logit gradients, masked hidden gradients), so what is
+    # left is FP32 accumulation order and the FP32 softmax: relative error
+    # 1e-2 above a floor of 1e-4 of the tensor's largest gradient
     for name, g, og in zip(["E", "W1", "b1", "W2", "b2"], grads, ograds):
         g = g.cpu().numpy().astype(np.float64)
-        err = np.linalg.norm(g - og) / max(np.linalg.norm(og), 1e-12)
-        assert err < 3e-2, (name, err)
+        floor = 1e-4 * np.abs(og).max()
+        bad = np.abs(g - og) > 1e-2 * np.abs(og) + floor
+        assert not bad.any(), (name, int(bad.sum()), np.argwhere(bad)[:3].tolist())
 
 
 def _coassign(keys, pairs):

@@ -557,3 +557,183 @@ def test_minhash_collision_rate_is_jaccard():
         assert abs(freq - J) <= 4.5 * sd + 1e-12, (a, b, freq, J)
     # identical profiles always share the key
     assert (keys[:, 0] == keys[:, 2]).all()
+
+
+# ------------------------------------------------------------------ greedy rounds, restated
+def py_greedy(sets, members, cluster_no, k, seed, rounds, n_random):
+    """Independent restatement of the synchronous greedy refinement (R11) with
+    Python sets and exact Fractions.  Philox4x32-10 words are the only part
+    taken from the oracle (the random source).  Returns the emitted rows
+    [(id, inter, union)] per member and the method's evaluation count (R13):
+    the random start's draws plus, per round, the candidates not already in
+    the member's list."""
+    M = len(members)
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+
+    def draw(a, r, j):
+        w = int(oracle.philox4x32_10([cluster_no, a, r, j], key)[0])
+        x = w % (M - 1)
+        return x + (1 if x >= a else 0)
+
+    def rank(a, v):   # best first: larger Jaccard, then lower user id
+        A, B = sets[members[a]], sets[members[v]]
+        U = len(A | B)
+        return (-(Fraction(len(A & B), U) if U else Fraction(0)), members[v])
+
+    evals = 0
+    cur = []
+    for a in range(M):
+        drawn, j = [], 0
+        while len(drawn) < min(k, M - 1):
+            v = draw(a, 0, j)
+            if v not in drawn:
+                drawn.append(v)
+            j += 1
+        evals += len(drawn)
+        cur.append(sorted(drawn, key=lambda v: rank(a, v)))
+    for r in range(1, rounds + 1):
+        nxt = []
+        for a in range(M):           # every member reads the previous round's lists
+            cand = set(cur[a])
+            for v in cur[a]:
+                cand |= set(cur[v])
+            cand |= {draw(a, r, j) for j in range(n_random)}
+            cand.discard(a)
+            evals += len(cand - set(cur[a]))
+            nxt.append(sorted(cand, key=lambda v: rank(a, v))[:k])
+        cur = nxt
+    rows = []
+    for a in range(M):
+        A = sets[members[a]]
+        row = []
+        for v in cur[a]:
+            B = sets[members[v]]
+            c = len(A & B)
+            if c > 0:
+                row.append((members[v], c, len(A | B)))
+        rows.append(row)
+    return rows, evals
+
+
+@pytest.mark.parametrize("rounds,n_random", [(1, 0), (2, 0), (3, 0), (2, 2), (3, 1)])
+def test_greedy_rounds_match_set_restatement(rounds, n_random):
+    # three greedy clusters of 23, 31 and 17 members over disjoint users,
+    # numbered 0, 1, 2 (the cluster number enters the Philox counter)
+    ptr, items = synth.random_profiles(71, 40, 7, 61, zipf_s=1.1)
+    sets = sets_from_csr(ptr, items)
+    rng = np.random.default_rng(7)
+    perm = rng.permutation(71)
+    groups = [np.sort(perm[:23]), np.sort(perm[23:54]), np.sort(perm[54:])]
+    cptr = np.array([0, 23, 54, 71], np.int32)
+    cusers = np.concatenate(groups).astype(np.int32)
+    k, seed = 4, 0x1234_5678_9ABC
+    li, lc, lu, pairs = oracle.cluster_knn(ptr, items, cptr, cusers, k, seed, 10, rounds, n_random)
+    got = rows_of(li, lc, lu)
+    total = 0
+    for c, mem in enumerate(groups):
+        rows, evals = py_greedy(sets, mem.tolist(), c, k, seed, rounds, n_random)
+        total += evals
+        for a in range(len(mem)):
+            assert got[cptr[c] + a] == rows[a], (c, a)
+    assert pairs == total
+
+
+def test_greedy_pins_fail_on_planted_mistakes():
+    # the restatement is sensitive to the mistakes it exists to catch: an
+    # asynchronous update, a candidate set missing a neighbour's list, and an
+    # evaluation count that includes listed ids each change rows or counts
+    ptr, items = synth.random_profiles(40, 30, 6, 62, zipf_s=1.1)
+    sets = sets_from_csr(ptr, items)
+    mem = list(range(40))
+    ref_rows, ref_evals = py_greedy(sets, mem, 0, 4, 99, 3, 0)
+
+    def variant(async_update=False, skip_last=False, count_all=False):
+        key = [99, 0]
+
+        def draw(a, r, j):
+            x = int(oracle.philox4x32_10([0, a, r, j], key)[0]) % 39
+            return x + (1 if x >= a else 0)
+
+        def rank(a, v):
+            A, B = sets[a], sets[v]
+            U = len(A | B)
+            return (-(Fraction(len(A & B), U) if U else Fraction(0)), v)
+
+        evals, cur = 0, []
+        for a in range(40):
+            drawn, j = [], 0
+            while len(drawn) < 4:
+                v = draw(a, 0, j)
+                if v not in drawn:
+                    drawn.append(v)
+                j += 1
+            evals += 4
+            cur.append(sorted(drawn, key=lambda v: rank(a, v)))
+        for r in range(1, 4):
+            src = cur if async_update else [list(x) for x in cur]
+            nxt = cur if async_update else [None] * 40
+            for a in range(40):
+                cand = set(src[a])
+                for v in (src[a][:-1] if skip_last else src[a]):
+                    cand |= set(src[v])
+                cand.discard(a)
+                evals += len(cand) if count_all else len(cand - set(src[a]))
+                nxt[a] = sorted(cand, key=lambda v: rank(a, v))[:4]
+            cur = nxt
+        rows = [[(v, len(sets[a] & sets[v]), len(sets[a] | sets[v])) for v in cur[a]
+                 if sets[a] & sets[v]] for a in range(40)]
+        return rows, evals
+
+    assert variant() == (ref_rows, ref_evals)
+    for kw in (dict(async_update=True), dict(skip_last=True), dict(count_all=True)):
+        assert variant(**kw) != (ref_rows, ref_evals), kw
+
+
+# ------------------------------------------------------------------ learned forward, restated
+def _splitmix64_mix(z):
+    """SplitMix64's output function (Steele, Lea & Flood, OOPSLA 2014)."""
+    m = (1 << 64) - 1
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & m
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & m
+    return z ^ (z >> 31)
+
+
+def _bf16(x):
+    """Round to the nearest BF16 value, ties to even (through torch's conversion)."""
+    torch = pytest.importorskip("torch")
+    return torch.from_numpy(np.asarray(x, np.float32)).to(torch.bfloat16).double().numpy()
+
+
+def np_forward(cfg, params, ptr, items, bf16):
+    """The proposer's network in NumPy: bag of hashed embedding rows, ReLU
+    hidden layer, logits; BF16 rounding where the library stores BF16."""
+    E, W1, b1, W2, b2 = (np.asarray(x, np.float64) for x in params)
+    rnd = _bf16 if bf16 else (lambda x: np.asarray(x, np.float64))
+    E, W1, W2 = rnd(E), rnd(W1), rnd(W2)
+    rows = 1 << cfg["rows_log2"]
+    n = ptr.size - 1
+    e = np.zeros((n, cfg["dim"]))
+    for u in range(n):
+        for x in items[ptr[u]:ptr[u + 1]]:
+            e[u] += E[_splitmix64_mix(cfg["seed"] ^ int(x)) & (rows - 1)]
+    e = rnd(e.astype(np.float32)) if bf16 else e
+    h = np.maximum(e @ W1 + np.asarray(params[2], np.float64), 0.0)
+    h = rnd(h.astype(np.float32)) if bf16 else h
+    return h @ W2 + np.asarray(params[4], np.float64)
+
+
+@pytest.mark.parametrize("exact", [True, False])
+def test_model_forward_matches_numpy_restatement(exact):
+    cfg, params = _tiny_net(3)
+    ptr, items = synth.random_profiles(50, 70, 6, 11)
+    assert all(_splitmix64_mix(z) == oracle.mix64(z) for z in (0, 1, 12345, (1 << 64) - 1))
+    oracle.model_exact(exact)
+    try:
+        z, keys = oracle.model_forward(cfg, params, ptr, items)
+    finally:
+        oracle.model_exact(False)
+    zn = np_forward(cfg, params, ptr, items, bf16=not exact)
+    assert np.allclose(z, zn, rtol=1e-12, atol=1e-12)
+    b = cfg["b"]
+    for j in range(cfg["t"]):
+        assert (keys[j] == np.argmax(zn[:, j * b:(j + 1) * b], axis=1)).all()
