@@ -72,6 +72,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-quality", action="store_true")
+    ap.add_argument("--strategy", type=int, default=-1,
+                    help="count-matrix strategy: -1 autotuned (default), 0 merge, 1-2 table, "
+                         "3 tensor cores")
     ap.add_argument("--gram-budget-mb", type=int, default=0,
                     help="cap on count matrices held at once (0 = library default)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
@@ -452,7 +455,8 @@ def main():
     keys = torch.empty((w.t, w.n_users), dtype=torch.int32, device=dev) if minhash else None
     kws = c2.workspace(256, dev)
     opts = c2.options(greedy_threshold=w.greedy_threshold, greedy_rounds=w.greedy_rounds,
-                      gram_budget_bytes=args.gram_budget_mb << 20, keys=keys)
+                      gram_budget_bytes=args.gram_budget_mb << 20, keys=keys,
+                      strategy=args.strategy)
     ws = c2.workspace(c2.workspace_size(w.n_users, nnz, w.n_items, w.k, w.t, wb, wN, opts), dev)
     out = [torch.empty((w.n_users, w.k), dtype=torch.int32, device=dev) for _ in range(3)]
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
@@ -591,6 +595,7 @@ def main():
                 "config": {"workload": w.name, "n_users": w.n_users, "n_items": w.n_items,
                            "nnz": nnz, **w.params(),
                            **({"clustering": "minhash", "b": wb, "N": wN} if minhash else {}),
+                           **({"strategy": args.strategy} if args.strategy != -1 else {}),
                            "l2": "flushed (512 MiB write) before each step",
                            "parallelism": f"replicas{world}" if world > 1 else "single"},
                 "pairs_per_step": pairs, "gram_pairs_per_step": stats["gram_pairs"],

@@ -72,10 +72,15 @@ typedef enum {
  * table of the 32 query users' items instead, provided no profile exceeds
  * 4,096 items; otherwise rows are counted by merges. */
 enum {
-  C2_STRATEGY_AUTO = -1,   /* autotuned table, per (cluster size, density) bucket         */
+  C2_STRATEGY_AUTO = -1,   /* per (cluster size, density) bucket: table or tensor cores,
+                              whichever the autotuner measured faster; tuned table shape  */
   C2_STRATEGY_MERGE = 0,   /* sorted-list merge, one warp per query user                  */
   C2_STRATEGY_TABLE32 = 1, /* shared-memory item table, 32 query users per block          */
-  C2_STRATEGY_TABLE64 = 2  /* shared-memory item table, 64 query users per block          */
+  C2_STRATEGY_TABLE64 = 2, /* shared-memory item table, 64 query users per block          */
+  C2_STRATEGY_MMA = 3      /* 0/1 FP8 products on the tensor cores (tcgen05, exact FP32
+                              sums) for every cluster of 128 members or more whose items
+                              held by two members or more number 1 to 65,536, in item
+                              universes of at most 524,288 items; the table otherwise      */
 };
 
 typedef struct {
@@ -106,7 +111,9 @@ typedef struct {
 typedef struct {
   int64_t pairs;            /* similarity evaluations of the method: M(M-1)/2 per
                                brute-force cluster plus the greedy candidate evaluations   */
-  int64_t gram_pairs;       /* intersection counts computed for greedy clusters            */
+  int64_t gram_pairs;       /* count-matrix elements (rows padded to 8) of every cluster
+                               with a count matrix (brute force of 9 members or more, and
+                               greedy)                                                     */
   int32_t n_clusters;       /* clusters after splitting, all t functions                   */
   int32_t split_levels;     /* recursive-split levels that found an oversized cluster      */
   int32_t n_greedy_clusters;
@@ -124,9 +131,13 @@ typedef struct {
                                clusters with a count matrix                                */
   int32_t brute_rows;       /* users of those clusters (rows ranked by the row kernel)     */
   int32_t reserved;
-  int64_t brute_pairs;      /* M(M-1)/2 over brute-force clusters: with gram_pairs, the
-                               intersections actually counted (greedy rounds look counts
+  int64_t brute_pairs;      /* M(M-1)/2 over brute-force clusters                          */
+  int64_t greedy_pairs;     /* M(M-1)/2 over greedy clusters: with brute_pairs, the pairs
+                               whose intersections were counted (greedy rounds look counts
                                up in their clusters' count matrices)                       */
+  int64_t tc_macs;          /* tensor-core multiply-adds issued for count matrices          */
+  int32_t tc_clusters;      /* count matrices computed on the tensor cores                 */
+  int32_t tc_tiles;         /* their 128 x 256 tiles                                       */
 } c2_stats;
 
 /* Fills *opt with the defaults described above.  Never fails. */

@@ -19,7 +19,7 @@ ROOT = os.path.dirname(HERE)
 LIB_PATH = os.path.join(HERE, "libc2.so")
 HEADER = os.path.join(ROOT, "include", "c2.h")
 
-STRATEGY_AUTO, STRATEGY_MERGE, STRATEGY_TABLE32, STRATEGY_TABLE64 = -1, 0, 1, 2
+STRATEGY_AUTO, STRATEGY_MERGE, STRATEGY_TABLE32, STRATEGY_TABLE64, STRATEGY_MMA = -1, 0, 1, 2, 3
 STATUS = {0: "C2_OK", 1: "C2_ERR_INVALID_ARG", 2: "C2_ERR_INVALID_CSR", 3: "C2_ERR_UNSUPPORTED",
           4: "C2_ERR_WORKSPACE", 5: "C2_ERR_CUDA", 6: "C2_ERR_TIMEOUT",
           7: "C2_ERR_QUALITY_FALLBACK"}
@@ -52,7 +52,9 @@ class Stats(C.Structure):
                 ("item_visits_greedy", C.c_int64), ("greedy_visits", C.c_int64),
                 ("greedy_computed", C.c_int64), ("greedy_evaluated", C.c_int64),
                 ("brute_gram_elems", C.c_int64), ("brute_rows", C.c_int32),
-                ("reserved", C.c_int32), ("brute_pairs", C.c_int64)]
+                ("reserved", C.c_int32), ("brute_pairs", C.c_int64),
+                ("greedy_pairs", C.c_int64), ("tc_macs", C.c_int64), ("tc_clusters", C.c_int32),
+                ("tc_tiles", C.c_int32)]
 
 
 _lib = None
@@ -343,7 +345,8 @@ def c2_get_stats(ws, stream=None) -> dict:
                 greedy_computed=s.greedy_computed, greedy_evaluated=s.greedy_evaluated,
                 item_visits_brute=s.item_visits_brute, item_visits_greedy=s.item_visits_greedy,
                 brute_gram_elems=s.brute_gram_elems, brute_rows=s.brute_rows,
-                brute_pairs=s.brute_pairs)
+                brute_pairs=s.brute_pairs, greedy_pairs=s.greedy_pairs, tc_macs=s.tc_macs,
+                tc_clusters=s.tc_clusters, tc_tiles=s.tc_tiles)
 
 
 def c2_reset_status(ws, stream=None):

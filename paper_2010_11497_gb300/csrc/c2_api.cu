@@ -22,6 +22,12 @@ Sizes make_sizes(int32_t n, int64_t nnz, int32_t m, int32_t k, int32_t t, int32_
   // sum over clusters of M * round_up(M, 8) <= S * (n + 7), two bytes each
   const int64_t worst = 2 * s.S * ((int64_t)std::max<int32_t>(n, 1) + 8);
   s.gram_budget = std::max<int64_t>(std::min(budget, worst), 2);
+  // remapped lists of the tensor-core count matrices: one padded profile area
+  // per function, when the item universe and the strategy allow that path
+  const int strategy = opt ? opt->strategy : C2_STRATEGY_AUTO;
+  const bool tc = (strategy == C2_STRATEGY_AUTO || strategy == C2_STRATEGY_MMA) && m >= 1 &&
+                  m <= kGramTcMaxItems && nnz > 0;
+  s.rl_pn = tc ? ((nnz + 3 * (int64_t)n + 4) & ~int64_t(3)) : 0;
   return s;
 }
 
@@ -97,6 +103,18 @@ void bind_knn_ws(Ws& w, const Sizes& s, KnnWs& c) {
   c.wl1 = w.take<int32_t>((S + 1) * s.k);
   c.gram = w.take<uint16_t>(s.gram_budget / 2);
   c.pos_of = w.take<int32_t>(S + 1);
+  c.gk2 = w.take<int32_t>(S + 1);
+  c.gsum = w.take<int64_t>(S + 1);
+  c.groute = w.take<int32_t>(S + 1);
+  c.gorder = w.take<int32_t>(S + 1);
+  c.gt_list = w.take<int32_t>(S + 1);
+  c.rl_len = w.take<int32_t>(S + 1);
+  // tiles of one batch: at most 6 M^2 / (128 * 256) per cluster of M >= 128
+  // members, and the batch's sum of M^2 is at most gram_budget / 2
+  c.gt_work_cap = s.rl_pn ? std::min<int64_t>(S + 64, 3 * s.gram_budget / 32768 + 64) : 0;
+  c.gt_work = w.take<int4>((size_t)c.gt_work_cap + 1);
+  c.rl_pn = s.rl_pn;
+  c.rl = s.rl_pn ? w.take<uint16_t>((size_t)s.t * s.rl_pn) : nullptr;
   c.partial = w.take<double>(1024);
   c.scan_tmp = w.take<int32_t>(scan_tmp_elems(S + 1));
   c.scan_tmp2 = w.take<int32_t>(scan_tmp_elems(S + 1));
@@ -162,7 +180,7 @@ c2_status check_common(int32_t n, int32_t m, int32_t k, int32_t t, int32_t b, in
   if (opt) {
     for (int i = 0; i < 5; ++i)
       if (opt->reserved[i] != 0) return C2_ERR_INVALID_ARG;
-    if (opt->strategy < -1 || opt->strategy > 2) return C2_ERR_INVALID_ARG;
+    if (opt->strategy < -1 || opt->strategy > 3) return C2_ERR_INVALID_ARG;
     if (opt->greedy_random < 0) return C2_ERR_INVALID_ARG;
   }
   return C2_OK;
@@ -257,6 +275,10 @@ c2_status c2_get_stats(const void* d_ws, c2_stream_t stream, c2_stats* out) {
   out->brute_gram_elems = (int64_t)h.brute_gram_elems;
   out->brute_rows = h.brute_rows;
   out->brute_pairs = (int64_t)h.brute_pairs;
+  out->greedy_pairs = (int64_t)h.greedy_pairs;
+  out->tc_macs = (int64_t)h.tc_macs;
+  out->tc_clusters = h.tc_clusters;
+  out->tc_tiles = h.tc_tiles;
   return C2_OK;
 }
 

@@ -43,7 +43,10 @@ struct DevHeader {
   int32_t brute_rows;          // users of brute-force clusters with a count matrix
   int32_t pad1;
   unsigned long long brute_pairs;  // M(M-1)/2 over brute-force clusters (intersections computed)
-  int32_t pad[6];
+  unsigned long long greedy_pairs; // M(M-1)/2 over greedy clusters (their count matrices)
+  unsigned long long tc_macs;      // tensor-core multiply-adds issued for count matrices
+  int32_t tc_clusters;             // count matrices computed on the tensor cores
+  int32_t tc_tiles;                // their 128 x 256 tiles
 };
 static_assert(sizeof(DevHeader) <= 256, "header must fit 256 bytes");
 
@@ -83,7 +86,12 @@ struct Sizes {
   int32_t tp;          // t rounded up to a multiple of 8 (hash-table row)
   int64_t omax;        // max oversized clusters in one split level
   int64_t gram_budget; // bytes
+  int64_t rl_pn;       // per-function stride of the remapped lists (0: no tensor-core path)
 };
+
+// Item universes up to this size can use the tensor-core count matrices (the
+// remap kernels hold three 32-bit words per 32 items in shared memory).
+constexpr int kGramTcMaxItems = 1 << 19;
 
 struct ClusterWs {
   DevHeader* hdr;
@@ -142,6 +150,17 @@ struct KnnWs {
   int32_t *wl0, *wl1;      // [S*k] greedy working lists (local indices)
   uint16_t* gram;          // gram_budget bytes
   int32_t* pos_of;         // [S] (function, user) -> slot
+  // tensor-core count matrices (c2_gram_tc.cu)
+  int32_t* gk2;            // [S+1] per count-matrix cluster: items held by two members or more
+  int64_t* gsum;           // [S+1] per count-matrix cluster: total profile length
+  int32_t* groute;         // [S+1] per count-matrix cluster: 0 table, 1 tensor cores, -1 none
+  int32_t* gorder;         // [S+1] per batch position: cluster (batch-relative), cost order
+  int32_t* gt_list;        // [S+1] tensor-core clusters (count-matrix indices)
+  int32_t* rl_len;         // [S+1] per slot: entries of its remapped list
+  int4* gt_work;           // [gt_work_cap] (cluster, row tile, column tile, stages)
+  int64_t gt_work_cap;
+  uint16_t* rl;            // [t][rl_pn] remapped lists (absent when unused)
+  int64_t rl_pn;
   double* partial;         // [1024] reduction partials
   int32_t* scan_tmp;
   int32_t* scan_tmp2;      // scan scratch of work on the side stream
@@ -649,6 +668,28 @@ c2_status tc_transpose_bf16(const __nv_bfloat16* B, int K, int N, __nv_bfloat16*
                             cudaStream_t st);
 c2_status tc_logits_argmax(const __nv_bfloat16* A, int M, int K, const __nv_bfloat16* Bt, int N,
                            const float* bias, float2* part, int32_t* status, cudaStream_t st);
+
+// Tensor-core count matrices (c2_gram_tc.cu).  gram_tc_count: per
+// count-matrix cluster g of `list` (every g < nlist when list is NULL, those of
+// fewer than min_m members skipped) the items held by two members or more and
+// the total profile length; gram_tc_remap: the remapped lists of the clusters
+// of `list`; gram_tc_run: the count matrices of the work items
+// (cluster, row tile, column tile, stages).
+c2_status gram_tc_count(const int32_t* list, int nlist, int min_m, const int32_t* gsz,
+                        const int32_t* gcl, const int32_t* cptr, const int32_t* cusers,
+                        const int32_t* ptr, const int32_t* items, int m, int32_t* k2,
+                        int64_t* sumlen, DevHeader* hdr, cudaStream_t st);
+c2_status gram_tc_remap(const int32_t* list, int nlist, const int32_t* gcl, const int32_t* cptr,
+                        const int32_t* cusers, const int32_t* ptr, const int32_t* items, int m,
+                        const int32_t* pptr, int64_t PN, int n, uint16_t* rl, int32_t* rl_len,
+                        DevHeader* hdr, cudaStream_t st);
+c2_status gram_tc_run(const int4* work, int n_work, const int32_t* cptr, const int32_t* cusers,
+                      const int2* iinfo, const int32_t* pptr, const uint16_t* rl, int64_t PN,
+                      int n, const int32_t* rl_len, const int64_t* gofs, uint16_t* gram,
+                      DevHeader* hdr, cudaStream_t st);
+int gram_tc_tile_rows();
+int gram_tc_tile_cols();
+int gram_tc_stage_cols();
 
 int num_sms();
 size_t autotune_report(char* buf, size_t len);

@@ -38,6 +38,15 @@ constexpr int kBitmapWords = kMaxGreedyM / 32;
 constexpr int kGreedyUsersPerWarp = 4;
 constexpr int kGreedySmallItemRounds = 2;      // rounds with one user per warp and work item
 constexpr int kSmallCut = 9;     // brute clusters below this size: warp-per-cluster kernel (<= 33)
+constexpr int kTcMinM = 128;     // smallest cluster for the tensor-core count matrix
+constexpr int kDensityBuckets = 5;
+// Density of a cluster for the strategy choice: the members' mean profile
+// length over the items held by two members or more, in buckets below 1/64,
+// 1/32, 1/16, 1/8 and from 1/8 on.
+inline int density_bucket(int64_t sumlen, int M, int k2) {
+  const double d = (double)sumlen / ((double)M * (double)std::max(k2, 1));
+  return d < 1.0 / 64 ? 0 : (d < 1.0 / 32 ? 1 : (d < 1.0 / 16 ? 2 : (d < 1.0 / 8 ? 3 : 4)));
+}
 constexpr int kGreedyChunk = 8 * kGreedyUsersPerWarp;   // users per block work item
 
 
@@ -1178,12 +1187,17 @@ __global__ void k_prep(const int32_t* __restrict__ cptr, const int32_t* __restri
     }
   }
   unsigned long long p = brute ? (unsigned long long)M * (M - 1) / 2 : 0ull;
+  unsigned long long pg = greedy ? (unsigned long long)M * (M - 1) / 2 : 0ull;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
+  for (int o = 16; o > 0; o >>= 1) {
+    p += __shfl_xor_sync(0xffffffffu, p, o);
+    pg += __shfl_xor_sync(0xffffffffu, pg, o);
+  }
   if ((threadIdx.x & 31) == 0 && p) {
     atomicAdd(&hdr->pairs, p);
     atomicAdd(&hdr->brute_pairs, p);
   }
+  if ((threadIdx.x & 31) == 0 && pg) atomicAdd(&hdr->greedy_pairs, pg);
   if (c == 0) hdr->n_labels = L;
 }
 
@@ -1274,13 +1288,24 @@ __global__ void k_batch_setup(const int32_t* __restrict__ gcl, const int64_t* __
 }
 
 // Query tiles of the batch clusters of one size bucket (tile = q members).
-// bucket < 0 selects every cluster of the batch.
+// bucket < 0 selects every cluster of the batch; clusters routed elsewhere
+// (route[g] != 0: tensor cores, or not in this launch) get none.
 __global__ void k_bucket_tiles(const int32_t* __restrict__ gsz, int32_t g0, int32_t nb,
-                               int32_t bucket, int32_t q, int32_t* __restrict__ cnt) {
+                               int32_t bucket, int32_t q, const int32_t* __restrict__ route,
+                               int32_t* __restrict__ cnt) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= nb) return;
   const int M = gsz[g0 + j];
-  cnt[j] = (bucket < 0 || size_bucket(M) == bucket) ? (M + q - 1) / q : 0;
+  const bool in = (bucket < 0 || size_bucket(M) == bucket) && (!route || route[g0 + j] == 0);
+  cnt[j] = in ? (M + q - 1) / q : 0;
+}
+
+// Adds the host-counted tensor-core work of a batch to the statistics.
+__global__ void k_tc_stats(DevHeader* hdr, unsigned long long macs, int32_t clusters,
+                           int32_t tiles) {
+  hdr->tc_macs += macs;
+  hdr->tc_clusters += clusters;
+  hdr->tc_tiles += tiles;
 }
 
 // Members of the batch's clusters of one kind, as (slot, count-matrix index).
@@ -1787,8 +1812,21 @@ struct TuneKey {
 };
 struct TuneEntry {
   bool unified;            // one launch over all buckets with cfg[0]
+  bool shapes_done;        // table shapes measured
   TableCfg cfg[kBuckets];
   float ms[kBuckets];
+  // per (size bucket, density bucket): -1 not measured, 0 table, 1 tensor cores,
+  // with the two times measured
+  int8_t route[kBuckets * kDensityBuckets];
+  float table_ms[kBuckets * kDensityBuckets];
+  float tc_ms[kBuckets * kDensityBuckets];
+  TuneEntry() : unified(true), shapes_done(false) {
+    for (int i = 0; i < kBuckets * kDensityBuckets; ++i) {
+      route[i] = -1;
+      table_ms[i] = tc_ms[i] = 0.f;
+    }
+    for (int q = 0; q < kBuckets; ++q) ms[q] = 0.f;
+  }
 };
 std::mutex g_tune_mu;
 std::map<TuneKey, TuneEntry> g_tune;
@@ -1897,7 +1935,10 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
   // the hashed count-matrix kernel is the candidate when no item table fits
   const bool hash_ok = !tc.W && opt.strategy != C2_STRATEGY_MERGE &&
                        (int)gram_hash_smem_bytes() + 1024 <= smem_optin();
-  if (tc.W || hash_ok) {
+  // the tensor-core count matrices need the remapped-list area of the workspace
+  const bool tc_possible = w.rl != nullptr && w.rl_pn > 0 && s.m <= kGramTcMaxItems &&
+                           (opt.strategy == C2_STRATEGY_AUTO || opt.strategy == C2_STRATEGY_MMA);
+  if (tc.W || hash_ok || tc_possible) {
     c2_status rc = build_padded_csr(ptr, items, s, w, st);
     if (rc) return rc;
   }
@@ -1933,13 +1974,29 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
                               cudaMemcpyDeviceToHost, st));
   C2_CUDA_TRY(cudaStreamSynchronize(st));
   if (ng == 0) return C2_OK;
+  // tensor-core candidates: for every cluster of kTcMinM members or more, the
+  // items held by two members or more (the width of its 0/1 operand) and the
+  // members' total profile length (its density)
+  if (tc_possible) {
+    c2_status rc = gram_tc_count(nullptr, ng, kTcMinM, w.gsz, w.gcl, cptr, cusers, ptr, items,
+                                 s.m, w.gk2, w.gsum, w.hdr, st);
+    if (rc) return rc;
+  }
   C2_CUDA_TRY(scan_exclusive64(w.gsq, w.goff, ng, w.scan_tmp64, st));
   C2_LAUNCH(k_gram_stats, 1, 1, 0, st, w.goff, ng, w.hdr);
-  std::vector<int64_t> goff(ng + 1);
-  std::vector<int32_t> gsz(ng), gkind(ng);
+  std::vector<int64_t> goff(ng + 1), gsum;
+  std::vector<int32_t> gsz(ng), gkind(ng), gk2, gclh;
   C2_CUDA_TRY(cudaMemcpyAsync(goff.data(), w.goff, (ng + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
   C2_CUDA_TRY(cudaMemcpyAsync(gsz.data(), w.gsz, ng * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   C2_CUDA_TRY(cudaMemcpyAsync(gkind.data(), w.gkind, ng * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  if (tc_possible) {
+    gk2.resize(ng);
+    gsum.resize(ng);
+    gclh.resize(ng);
+    C2_CUDA_TRY(cudaMemcpyAsync(gk2.data(), w.gk2, ng * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    C2_CUDA_TRY(cudaMemcpyAsync(gsum.data(), w.gsum, ng * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    C2_CUDA_TRY(cudaMemcpyAsync(gclh.data(), w.gcl, ng * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  }
   C2_CUDA_TRY(cudaStreamSynchronize(st));
   const int64_t cap = s.gram_budget / (int64_t)sizeof(uint16_t);
   // exact 64-bit order keys need unions below 2^16 and clusters below 2^14
@@ -1952,6 +2009,20 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
   }
   C2_LAUNCH(k_iota, div_up(ng, T), T, 0, st, w.gseq, (int64_t)ng);
   const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+  // tensor-core eligibility and strategy bucket of each count-matrix cluster
+  auto tc_eligible = [&](int g) {
+    return tc_possible && gsz[g] >= kTcMinM && gk2[g] >= 1 && gk2[g] <= 65536;
+  };
+  auto tc_bucket = [&](int g) {
+    return size_bucket(gsz[g]) * kDensityBuckets + density_bucket(gsum[g], gsz[g], gk2[g]);
+  };
+  const TuneKey tkey{s.n, s.m, s.t, s.b, s.N, k, thr};
+  TuneEntry tune;
+  if (opt.strategy == C2_STRATEGY_AUTO) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(tkey);
+    if (it != g_tune.end()) tune = it->second;
+  }
   p_gsetup.end();
 
   GramArgs ga0{};
@@ -1959,6 +2030,84 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
   ga0.n_items = s.m; ga0.work_c = w.work_c; ga0.work_t = w.work_t;
   ga0.cptr = cptr; ga0.cusers = cusers; ga0.iinfo = w.iinfo; ga0.gofs = w.gofs; ga0.gram = w.gram;
   ga0.hdr = w.hdr; ga0.counter = &w.hdr->work_counter[1];
+
+  // host -> device copy of small per-batch tables; the host buffer is reused
+  // after it, and the stream's earlier kernels have read the old contents
+  auto upload = [&](void* dst, const void* src, size_t bytes) -> c2_status {
+    if (!bytes) return C2_OK;
+    C2_CUDA_TRY(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st));
+    C2_CUDA_TRY(cudaStreamSynchronize(st));
+    return C2_OK;
+  };
+  cudaEvent_t te0 = nullptr, te1 = nullptr;
+  auto timed = [&](auto&& fn, float* ms) -> c2_status {
+    if (!te0) {
+      C2_CUDA_TRY(cudaEventCreate(&te0));
+      C2_CUDA_TRY(cudaEventCreate(&te1));
+    }
+    C2_CUDA_TRY(cudaEventRecord(te0, st));
+    c2_status rc = fn();
+    if (rc) return rc;
+    C2_CUDA_TRY(cudaEventRecord(te1, st));
+    C2_CUDA_TRY(cudaEventSynchronize(te1));
+    C2_CUDA_TRY(cudaEventElapsedTime(ms, te0, te1));
+    return C2_OK;
+  };
+  struct EventGuard {
+    cudaEvent_t* a;
+    cudaEvent_t* b;
+    ~EventGuard() {
+      if (*a) cudaEventDestroy(*a);
+      if (*b) cudaEventDestroy(*b);
+    }
+  } evg{&te0, &te1};
+
+  // count matrices of the clusters `gs` on the tensor cores: remapped lists,
+  // then the tiles, largest clusters first
+  std::vector<int4> work_h;
+  auto run_tc = [&](const std::vector<int32_t>& gs, bool count_stats) -> c2_status {
+    if (gs.empty()) return C2_OK;
+    const int BM = gram_tc_tile_rows(), BN = gram_tc_tile_cols(), BK = gram_tc_stage_cols();
+    auto tiles_of = [&](int g) {
+      const int TR = div_up(gsz[g], BM), TC = div_up(gsz[g], BN);
+      int64_t nt = 0;
+      for (int i = 0; i < TR; ++i) nt += TC - i / 2;
+      return nt;
+    };
+    std::vector<int32_t> ord(gs);
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) {
+      return tiles_of(a) * div_up(gk2[a], BK) > tiles_of(b) * div_up(gk2[b], BK);
+    });
+    work_h.clear();
+    unsigned long long macs = 0;
+    for (int g : ord) {
+      const int c = gclh[g], TR = div_up(gsz[g], BM), TC = div_up(gsz[g], BN);
+      const int nk = div_up(gk2[g], BK);
+      for (int i = 0; i < TR; ++i)
+        for (int j = i / 2; j < TC; ++j) work_h.push_back(make_int4(c, i, j, nk));
+      macs += (unsigned long long)tiles_of(g) * nk * BM * BN * BK;
+    }
+    if ((int64_t)work_h.size() > w.gt_work_cap) return C2_ERR_WORKSPACE;
+    c2_status rc = upload(w.gt_list, ord.data(), ord.size() * sizeof(int32_t));
+    if (rc) return rc;
+    rc = upload(w.gt_work, work_h.data(), work_h.size() * sizeof(int4));
+    if (rc) return rc;
+    {
+      Prof p_rm(st, "gram_tc_remap");
+      rc = gram_tc_remap(w.gt_list, (int)ord.size(), w.gcl, cptr, cusers, ptr, items, s.m, w.pptr,
+                         w.rl_pn, s.n, w.rl, w.rl_len, w.hdr, st);
+      if (rc) return rc;
+    }
+    {
+      Prof p_tc(st, "gram_tc");
+      rc = gram_tc_run(w.gt_work, (int)work_h.size(), cptr, cusers, w.iinfo, w.pptr, w.rl,
+                       w.rl_pn, s.n, w.rl_len, w.gofs, w.gram, w.hdr, st);
+      if (rc) return rc;
+    }
+    if (count_stats)
+      C2_LAUNCH(k_tc_stats, 1, 1, 0, st, w.hdr, macs, (int32_t)ord.size(), (int32_t)work_h.size());
+    return C2_OK;
+  };
 
   int g0 = 0;
   while (g0 < ng) {
@@ -1982,13 +2131,66 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
       // internal order (members by decreasing profile length) of every
       // count-matrix cluster of the batch
       C2_LAUNCH(k_order, nb, 256, 0, st, w.gcl, g0, cptr, w.slen, w.ipos, w.iinfo);
-      if (tc.W) {
+      // strategy of each cluster of the batch: 0 table, 1 tensor cores
+      std::vector<int32_t> route(nb, 0);
+      if (tc_possible && (tc.W || use_hash) && opt.strategy == C2_STRATEGY_AUTO) {
+        // first call for these sizes: every (size, density) bucket with
+        // tensor-core candidates is timed both ways on its clusters
+        std::vector<std::vector<int32_t>> members(kBuckets * kDensityBuckets);
+        for (int g = g0; g < g1; ++g)
+          if (tc_eligible(g) && tune.route[tc_bucket(g)] < 0) members[tc_bucket(g)].push_back(g);
+        for (int bk = 0; bk < kBuckets * kDensityBuckets; ++bk) {
+          if (members[bk].empty()) continue;
+          std::vector<int32_t> only(nb, 2);   // 2: in neither launch
+          for (int g : members[bk]) only[g - g0] = 0;
+          c2_status rc = upload(w.groute + g0, only.data(), nb * sizeof(int32_t));
+          if (rc) return rc;
+          float t_tab = 0.f, t_tc = 0.f;
+          rc = timed([&]() -> c2_status {
+            C2_LAUNCH(k_bucket_tiles, div_up(nb, T), T, 0, st, w.gsz, g0, nb, -1,
+                      tc.W ? 32 * tc.W : 32, w.groute, w.bt_cnt);
+            C2_CUDA_TRY(scan_exclusive(w.bt_cnt, w.bt_off, nb, w.scan_tmp, st));
+            C2_LAUNCH(k_fill_work, div_up(nb, T), T, 0, st, w.bt_cnt, w.bt_off, w.gcl + g0, nb,
+                      w.work_c, w.work_t, &w.hdr->n_work);
+            GramArgs ga = ga0;
+            ga.work_begin = w.bt_off;
+            ga.work_end = w.bt_off + nb;
+            return tc.W ? launch_gram(tc, ga, st) : launch_gram_hash(ga, st);
+          }, &t_tab);
+          if (rc) return rc;
+          rc = timed([&]() { return run_tc(members[bk], false); }, &t_tc);
+          if (rc) return rc;
+          tune.route[bk] = t_tc < t_tab ? 1 : 0;
+          tune.table_ms[bk] = t_tab;
+          tune.tc_ms[bk] = t_tc;
+        }
+      }
+      for (int g = g0; g < g1; ++g) {
+        if (!tc_eligible(g)) continue;
+        if (opt.strategy == C2_STRATEGY_MMA) route[g - g0] = 1;
+        else if (opt.strategy == C2_STRATEGY_AUTO && tune.route[tc_bucket(g)] == 1) route[g - g0] = 1;
+      }
+      std::vector<int32_t> tc_list;
+      bool any_table = false;
+      for (int g = g0; g < g1; ++g) {
+        if (route[g - g0]) tc_list.push_back(g);
+        else any_table = true;
+      }
+      if (tc_possible) {
+        c2_status rc = upload(w.groute + g0, route.data(), nb * sizeof(int32_t));
+        if (rc) return rc;
+      }
+      const int32_t* groute = tc_possible ? w.groute : nullptr;
+      if (!any_table) {
+        // every count matrix of the batch comes from the tensor cores
+      } else if (tc.W) {
         bool present[kBuckets] = {false, false, false, false};
-        for (int g = g0; g < g1; ++g) present[size_bucket(gsz[g])] = true;
+        for (int g = g0; g < g1; ++g)
+          if (!route[g - g0]) present[size_bucket(gsz[g])] = true;
         // one launch per size bucket, over that bucket's query tiles
         auto run_bucket = [&](int bkt, TableCfg shape) -> c2_status {
           C2_LAUNCH(k_bucket_tiles, div_up(nb, T), T, 0, st, w.gsz, g0, nb, bkt, 32 * shape.W,
-                    w.bt_cnt);
+                    groute, w.bt_cnt);
           C2_CUDA_TRY(scan_exclusive(w.bt_cnt, w.bt_off, nb, w.scan_tmp, st));
           C2_LAUNCH(k_fill_work, div_up(nb, T), T, 0, st, w.bt_cnt, w.bt_off, w.gcl + g0, nb,
                     w.work_c, w.work_t, &w.hdr->n_work);
@@ -1997,37 +2199,11 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
           ga.work_end = w.bt_off + nb;
           return launch_gram(shape, ga, st);
         };
-        TableCfg use[kBuckets] = {tc, tc, tc, tc};
-        bool unified = true;
-        bool have = false;
-        const TuneKey key{s.n, s.m, s.t, s.b, s.N, k, thr};
-        if (opt.strategy == C2_STRATEGY_AUTO) {
-          std::lock_guard<std::mutex> lk(g_tune_mu);
-          auto it = g_tune.find(key);
-          if (it != g_tune.end()) {
-            for (int q = 0; q < kBuckets; ++q) use[q] = it->second.cfg[q];
-            unified = it->second.unified;
-            have = true;
-          }
-        }
-        if (opt.strategy == C2_STRATEGY_AUTO && !have) {
+        if (opt.strategy == C2_STRATEGY_AUTO && !tune.shapes_done) {
           // first call for these sizes: time every shape that fits, on each
           // bucket alone and as one launch over all buckets; keep the faster plan
-          TuneEntry te;
-          te.unified = true;
-          for (int q = 0; q < kBuckets; ++q) { te.cfg[q] = tc; te.ms[q] = 0.f; }
-          cudaEvent_t e0, e1;
-          C2_CUDA_TRY(cudaEventCreate(&e0));
-          C2_CUDA_TRY(cudaEventCreate(&e1));
-          auto timed = [&](int bkt, TableCfg shape, float* ms) -> c2_status {
-            C2_CUDA_TRY(cudaEventRecord(e0, st));
-            c2_status rc = run_bucket(bkt, shape);
-            if (rc) return rc;
-            C2_CUDA_TRY(cudaEventRecord(e1, st));
-            C2_CUDA_TRY(cudaEventSynchronize(e1));
-            C2_CUDA_TRY(cudaEventElapsedTime(ms, e0, e1));
-            return C2_OK;
-          };
+          tune.unified = true;
+          for (int q = 0; q < kBuckets; ++q) { tune.cfg[q] = tc; tune.ms[q] = 0.f; }
           float split_total = 0.f;
           TableCfg best_cfg[kBuckets] = {tc, tc, tc, tc};
           float best_ms[kBuckets] = {0.f, 0.f, 0.f, 0.f};
@@ -2037,7 +2213,7 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
             for (const TableCfg& shape : kGramShapes) {
               if (!gram_fits(shape, s.m)) continue;
               float ms = 0.f;
-              c2_status rc = timed(q, shape, &ms);
+              c2_status rc = timed([&]() { return run_bucket(q, shape); }, &ms);
               if (rc) return rc;
               if (ms < best) { best = ms; best_cfg[q] = shape; best_ms[q] = ms; }
             }
@@ -2048,38 +2224,36 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
           for (const TableCfg& shape : kGramShapes) {
             if (!gram_fits(shape, s.m)) continue;
             float ms = 0.f;
-            c2_status rc = timed(-1, shape, &ms);
+            c2_status rc = timed([&]() { return run_bucket(-1, shape); }, &ms);
             if (rc) return rc;
             if (ms < uni_best) { uni_best = ms; uni_cfg = shape; }
           }
-          cudaEventDestroy(e0);
-          cudaEventDestroy(e1);
           if (uni_best <= split_total) {
-            te.unified = true;
-            for (int q = 0; q < kBuckets; ++q) { te.cfg[q] = uni_cfg; te.ms[q] = q ? 0.f : uni_best; }
+            tune.unified = true;
+            for (int q = 0; q < kBuckets; ++q) { tune.cfg[q] = uni_cfg; tune.ms[q] = q ? 0.f : uni_best; }
           } else {
-            te.unified = false;
-            for (int q = 0; q < kBuckets; ++q) { te.cfg[q] = best_cfg[q]; te.ms[q] = best_ms[q]; }
+            tune.unified = false;
+            for (int q = 0; q < kBuckets; ++q) { tune.cfg[q] = best_cfg[q]; tune.ms[q] = best_ms[q]; }
           }
-          {
-            std::lock_guard<std::mutex> lk(g_tune_mu);
-            g_tune[key] = te;
-          }
+          tune.shapes_done = true;
           // every timed launch wrote the same counts: the matrices are complete
-        } else if (unified) {
-          c2_status rc = run_bucket(-1, use[0]);
-          if (rc) return rc;
         } else {
-          for (int q = 0; q < kBuckets; ++q) {
-            if (!present[q]) continue;
-            c2_status rc = run_bucket(q, use[q]);
+          const bool auto_shapes = opt.strategy == C2_STRATEGY_AUTO && tune.shapes_done;
+          if (!auto_shapes || tune.unified) {
+            c2_status rc = run_bucket(-1, auto_shapes ? tune.cfg[0] : tc);
             if (rc) return rc;
+          } else {
+            for (int q = 0; q < kBuckets; ++q) {
+              if (!present[q]) continue;
+              c2_status rc = run_bucket(q, tune.cfg[q]);
+              if (rc) return rc;
+            }
           }
         }
       } else if (use_hash) {
         // no item table fits shared memory: the tiles' items in a shared hash
         // table, one launch over all count-matrix clusters of the batch
-        C2_LAUNCH(k_bucket_tiles, div_up(nb, T), T, 0, st, w.gsz, g0, nb, -1, 32, w.bt_cnt);
+        C2_LAUNCH(k_bucket_tiles, div_up(nb, T), T, 0, st, w.gsz, g0, nb, -1, 32, groute, w.bt_cnt);
         C2_CUDA_TRY(scan_exclusive(w.bt_cnt, w.bt_off, nb, w.scan_tmp, st));
         C2_LAUNCH(k_fill_work, div_up(nb, T), T, 0, st, w.bt_cnt, w.bt_off, w.gcl + g0, nb,
                   w.work_c, w.work_t, &w.hdr->n_work);
@@ -2109,6 +2283,14 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
           ma.u_slot = w.ub_slot; ma.u_g = w.ub_g; ma.n_users_dev = w.bb_off + nb;
           C2_LAUNCH(k_merge_gram, div_up(n_brute_users * 32, 256), 256, 0, st, ma);
         }
+      }
+      p_gram.end();
+      // the tensor-core clusters of the batch
+      c2_status rc = run_tc(tc_list, true);
+      if (rc) return rc;
+      if (opt.strategy == C2_STRATEGY_AUTO) {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune[tkey] = tune;
       }
     }
     // brute-force rows on the side stream (they and the greedy phase only read
@@ -2313,6 +2495,22 @@ size_t autotune_report(char* buf, size_t len) {
                kv.second.ms[q]);
       out += tmp;
     }
+    out += "], \"strategy\": [";
+    static const char* dnames[kDensityBuckets] = {"<1/64", "1/64-1/32", "1/32-1/16", "1/16-1/8",
+                                                  ">=1/8"};
+    bool f2 = true;
+    for (int q = 0; q < kBuckets; ++q)
+      for (int d = 0; d < kDensityBuckets; ++d) {
+        const int bk = q * kDensityBuckets + d;
+        if (kv.second.route[bk] < 0) continue;
+        snprintf(tmp, sizeof tmp,
+                 "%s{\"sizes\": \"%s\", \"density\": \"%s\", \"use\": \"%s\", "
+                 "\"table_ms\": %.4f, \"tensor_ms\": %.4f}",
+                 f2 ? "" : ", ", names[q], dnames[d], kv.second.route[bk] ? "tensor" : "table",
+                 kv.second.table_ms[bk], kv.second.tc_ms[bk]);
+        out += tmp;
+        f2 = false;
+      }
     out += "]}";
     first = false;
   }

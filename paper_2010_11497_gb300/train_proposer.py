@@ -142,8 +142,36 @@ def _train_eval(w, train, steps, batch, lr, lam, dim, hidden, rows_log2, model_s
     return res, model
 
 
+def time_propose(workload="learned_ml20m", chunk=65536, reps=10, dim=64, hidden=256,
+                 rows_log2=18, model_seed=2010, log=print):
+    """Times c2_model_propose of an untrained network (the workload's t and b)
+    on the workload's target data with CUDA events: 3 warm-ups, then the mean
+    of `reps` proposals of every user."""
+    w = synth.WORKLOADS[workload]
+    ptr, items, _ = synth.load(workload, w.seed)
+    dptr, ditems = dev(ptr), dev(items)
+    model = c2.Model(w.t, w.b, dim, hidden, rows_log2, model_seed).init()
+    for _ in range(3):
+        model.propose(dptr, ditems, chunk=chunk)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        model.propose(dptr, ditems, chunk=chunk)
+    e1.record()
+    torch.cuda.synchronize()
+    r = dict(workload=workload, n_users=w.n_users, nnz=int(items.size), t=w.t, b=w.b, dim=dim,
+             hidden=hidden, chunk=chunk, reps=reps, propose_ms=e0.elapsed_time(e1) / reps)
+    log(json.dumps(r))
+    return r
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--time-propose", action="store_true",
+                    help="time proposals of an untrained network on the target data and exit")
+    ap.add_argument("--chunk", type=int, default=65536, help="users per proposal chunk")
+    ap.add_argument("--reps", type=int, default=10)
     ap.add_argument("--workload", default="learned_ml20m")
     ap.add_argument("--train-seeds", type=int, nargs="+", default=[6, 7, 8, 9])
     ap.add_argument("--steps", type=int, default=400)
@@ -154,6 +182,9 @@ def main():
     ap.add_argument("--mu", type=float, default=0.0)
     ap.add_argument("--save", default="")
     a = ap.parse_args()
+    if a.time_propose:
+        time_propose(a.workload, a.chunk, a.reps)
+        return
     _, model = run(a.workload, tuple(a.train_seeds), a.steps, a.batch, a.lr, a.lam, mu=a.mu,
                    lams=a.lams)
     if a.save:

@@ -127,14 +127,34 @@ def check_local(c2, ptr, items, m, t, b, N, k, seed, thr, rounds=10, nrand=0, st
     assert_same(gi, li, "loc_id")
     assert_same(gc, lc, "loc_inter")
     assert_same(gu, lu, "loc_union")
-    assert c2.c2_get_stats(ws)["pairs"] == pairs
-    return g, (gi, gc, gu)
+    st = c2.c2_get_stats(ws)
+    assert st["pairs"] == pairs
+    return g, (gi, gc, gu), st
 
 
-@pytest.mark.parametrize("strategy", [-1, 0, 1, 2])
+@pytest.mark.parametrize("strategy", [-1, 0, 1, 2, 3])
 def test_local_brute_force_strategies(c2, strategy):
     ptr, items = synth.random_profiles(3000, 500, 25, 12, zipf_s=1.1)
-    check_local(c2, ptr, items, 500, 4, 32, 400, 10, 5, 10 ** 9, strategy=strategy)
+    _, _, st = check_local(c2, ptr, items, 500, 4, 32, 400, 10, 5, 10 ** 9, strategy=strategy)
+    if strategy == 3:     # clusters of 128 members or more went to the tensor cores
+        assert st["tc_clusters"] >= 1 and st["tc_macs"] > 0
+
+
+def test_local_brute_force_tensor_cores_many_tiles(c2):
+    # clusters of up to 1,771 members (14 row tiles, 7 column tiles, ragged
+    # edges; two residuals above N) over 3,000 items: operands of many
+    # 128-column stages, symmetric tiles and mirrored columns, compared with
+    # the oracle element by element
+    ptr, items = synth.random_profiles(4000, 3000, 60, 26, zipf_s=1.0)
+    _, _, st = check_local(c2, ptr, items, 3000, 2, 16, 1500, 16, 7, 10 ** 9, strategy=3)
+    assert st["tc_clusters"] >= 8 and st["tc_tiles"] >= 100
+
+
+def test_local_greedy_tensor_cores(c2):
+    # greedy clusters read count matrices made on the tensor cores
+    ptr, items = synth.random_profiles(2500, 400, 20, 14, zipf_s=1.1)
+    _, _, st = check_local(c2, ptr, items, 400, 3, 8, 600, 12, 21, 150, 4, 0, strategy=3)
+    assert st["tc_clusters"] >= 1
 
 
 @pytest.mark.parametrize("k", [1, 7, 30, 32])
@@ -238,6 +258,31 @@ def test_build_ml1m_full(c2):
     assert_same(gin, oin, "nbr_inter")
     assert_same(gun, oun, "nbr_union")
     assert c2.c2_get_stats(ws)["pairs"] == pairs
+
+
+def test_build_ml1m_full_tensor_cores(c2):
+    # the ml1m-like workload with every cluster of 128 members or more on the
+    # tensor cores, then with the autotuner's choice: both equal the oracle
+    w = synth.WORKLOADS["ml1m_like"]
+    ptr, items, _ = synth.load("ml1m_like")
+    oid, oin, oun, pairs = oracle.build_graph(ptr, items, w.n_items, w.k, w.t, w.b, w.N, w.seed,
+                                              w.greedy_threshold, w.greedy_rounds)
+    for strategy in (3, -1):
+        opts = c2.options(greedy_threshold=w.greedy_threshold, greedy_rounds=w.greedy_rounds,
+                          strategy=strategy)
+        ws = c2.workspace(c2.workspace_size(w.n_users, items.size, w.n_items, w.k, w.t, w.b, w.N,
+                                            opts), DEV)
+        gid, gin, gun = c2.c2_build_knn_graph(to_dev(ptr), to_dev(items), w.n_items, w.k, w.t,
+                                              w.b, w.N, w.seed, opts=opts, ws=ws)
+        assert_same(gid, oid, "nbr_id")
+        assert_same(gin, oin, "nbr_inter")
+        assert_same(gun, oun, "nbr_union")
+        st = c2.c2_get_stats(ws)
+        assert st["pairs"] == pairs
+        if strategy == 3:
+            assert st["tc_clusters"] >= 1
+    rep = c2.c2_autotune_report()
+    assert any(e.get("n") == w.n_users and e.get("strategy") for e in rep)
 
 
 def test_build_host_entry_matches_device(c2):
