@@ -397,6 +397,19 @@ def phase_model(dom, phase_ms, phase_calls, stats, w, nnz, pk, W, steps):
                 "traffic": recorded_traffic("k_gram", w.name), "ms_per_launch": ms,
                 "model": f"{ops_per_visit:.1f} integer lane-ops per candidate item visit "
                          f"({visits / per_build:.3e} visits/launch); {peak_note}"}
+    if dom == "gram_tc" and stats.get("tc_macs"):
+        # FP8 dense peak = the measured bf16 peak x the nominal fp8 / bf16
+        # ratio (4.5 / 2.25 PFLOP/s)
+        fp8_peak = 2.0 * pk["bf16_tflops"]
+        flops = 2.0 * stats["tc_macs"] / per_build
+        achieved = flops / (ms * 1e-3) / 1e12
+        return {"kernel": "k_gram_mma", "phase": dom, "bound": "tensor", "achieved": achieved,
+                "peak": fp8_peak, "unit": "TFLOP/s", "frac": achieved / fp8_peak,
+                "traffic": None, "ms_per_launch": ms,
+                "model": f"2 x {stats['tc_macs'] / per_build:.3e} FP8 multiply-adds issued per "
+                         f"launch ({stats.get('tc_tiles', 0)} tiles of 128 x 256 over "
+                         f"{stats.get('tc_clusters', 0)} clusters); peak = 2 x measured bf16 "
+                         f"{pk['bf16_tflops']:.0f} TFLOP/s"}
     if dom == "brute_rows" and stats.get("brute_rows"):
         bytes_ = 2 * stats["brute_gram_elems"] + 12 * k * stats["brute_rows"]
         return hbm("k_gram_topk", bytes_ / per_build,

@@ -22,12 +22,13 @@ Sizes make_sizes(int32_t n, int64_t nnz, int32_t m, int32_t k, int32_t t, int32_
   // sum over clusters of M * round_up(M, 8) <= S * (n + 7), two bytes each
   const int64_t worst = 2 * s.S * ((int64_t)std::max<int32_t>(n, 1) + 8);
   s.gram_budget = std::max<int64_t>(std::min(budget, worst), 2);
-  // remapped lists of the tensor-core count matrices: one padded profile area
-  // per function, when the item universe and the strategy allow that path
+  // tensor-core count matrices, when the item universe and the strategy allow
+  // that path; their remapped lists (one padded profile area per function)
+  // live in the workspace tail, sized here when nnz is known
   const int strategy = opt ? opt->strategy : C2_STRATEGY_AUTO;
-  const bool tc = (strategy == C2_STRATEGY_AUTO || strategy == C2_STRATEGY_MMA) && m >= 1 &&
-                  m <= kGramTcMaxItems && nnz > 0;
-  s.rl_pn = tc ? ((nnz + 3 * (int64_t)n + 4) & ~int64_t(3)) : 0;
+  s.tc = (strategy == C2_STRATEGY_AUTO || strategy == C2_STRATEGY_MMA) && m >= 1 &&
+         m <= kGramTcMaxItems;
+  s.rl_pn = s.tc && nnz > 0 ? rl_stride(nnz, n) : 0;
   return s;
 }
 
@@ -111,10 +112,10 @@ void bind_knn_ws(Ws& w, const Sizes& s, KnnWs& c) {
   c.rl_len = w.take<int32_t>(S + 1);
   // tiles of one batch: at most 6 M^2 / (128 * 256) per cluster of M >= 128
   // members, and the batch's sum of M^2 is at most gram_budget / 2
-  c.gt_work_cap = s.rl_pn ? std::min<int64_t>(S + 64, 3 * s.gram_budget / 32768 + 64) : 0;
+  c.gt_work_cap = s.tc ? std::min<int64_t>(S + 64, 3 * s.gram_budget / 32768 + 64) : 0;
   c.gt_work = w.take<int4>((size_t)c.gt_work_cap + 1);
-  c.rl_pn = s.rl_pn;
-  c.rl = s.rl_pn ? w.take<uint16_t>((size_t)s.t * s.rl_pn) : nullptr;
+  c.rl_pn = 0;        // located in the tail once nnz is known (run_cluster_knn)
+  c.rl = nullptr;
   c.partial = w.take<double>(1024);
   c.scan_tmp = w.take<int32_t>(scan_tmp_elems(S + 1));
   c.scan_tmp2 = w.take<int32_t>(scan_tmp_elems(S + 1));
@@ -157,6 +158,7 @@ size_t layout(char* base, size_t ws_bytes, const Sizes& s, DevHeader** hdr, Buil
   const size_t fixed = (std::max(a.top, k2.top) + 255) & ~size_t(255);
   kk.pitems = reinterpret_cast<int32_t*>(base + fixed);
   kk.pitems_cap = ws_bytes > fixed ? (int64_t)((ws_bytes - fixed) / 4) : 0;
+  kk.tail_bytes = ws_bytes > fixed ? (int64_t)(ws_bytes - fixed) : 0;
   if (hdr) *hdr = h;
   if (bb) *bb = b;
   if (cw) *cw = c;
@@ -236,7 +238,8 @@ size_t c2_workspace_size(int32_t n_users, int64_t nnz, int32_t n_items, int32_t 
                          int32_t b, int32_t N, const c2_options* opt) {
   if (check_common(n_users, n_items, k, t, b, N, opt) != C2_OK || nnz < 0) return 0;
   Sizes s = make_sizes(n_users, nnz, n_items, k, t, b, N, opt);
-  return layout(nullptr, 0, s, nullptr, nullptr, nullptr, nullptr) + tail_bytes(nnz, n_users);
+  return layout(nullptr, 0, s, nullptr, nullptr, nullptr, nullptr) + tail_bytes(nnz, n_users) +
+         (s.rl_pn ? rl_tail_bytes(nnz, n_users, t) : 0);
 }
 
 c2_status c2_reset_status(void* d_ws, c2_stream_t stream) {

@@ -86,8 +86,21 @@ struct Sizes {
   int32_t tp;          // t rounded up to a multiple of 8 (hash-table row)
   int64_t omax;        // max oversized clusters in one split level
   int64_t gram_budget; // bytes
-  int64_t rl_pn;       // per-function stride of the remapped lists (0: no tensor-core path)
+  int64_t rl_pn;       // per-function stride of the remapped lists (0: nnz unknown or no tensor cores)
+  bool tc;             // the tensor-core count matrices are allowed (strategy, item universe)
 };
+
+// The remapped lists of the tensor-core count matrices sit in the workspace
+// tail after the padded profiles (which take tail_bytes()): one area of
+// rl_stride() uint16 entries per function.
+inline int64_t rl_stride(int64_t nnz, int32_t n) { return (nnz + 3 * (int64_t)n + 4) & ~int64_t(3); }
+inline size_t rl_offset(int64_t nnz, int32_t n) {
+  return ((size_t)(nnz + 3 * (int64_t)n + 64) * 4 + 255) & ~size_t(255);
+}
+inline size_t rl_tail_bytes(int64_t nnz, int32_t n, int32_t t) {
+  return rl_offset(nnz, n) - (size_t)(nnz + 3 * (int64_t)n + 64) * 4 +
+         (size_t)t * rl_stride(nnz, n) * 2 + 256;
+}
 
 // Item universes up to this size can use the tensor-core count matrices (the
 // remap kernels hold three 32-bit words per 32 items in shared memory).
@@ -147,6 +160,7 @@ struct KnnWs {
   int32_t* pptr;           // [n+1] padded CSR offsets
   int32_t* pitems;         // padded CSR items: the workspace tail
   int64_t pitems_cap;      // capacity of pitems (elements)
+  int64_t tail_bytes;      // bytes of the workspace tail from pitems on
   int32_t *wl0, *wl1;      // [S*k] greedy working lists (local indices)
   uint16_t* gram;          // gram_budget bytes
   int32_t* pos_of;         // [S] (function, user) -> slot

@@ -1935,10 +1935,12 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
   // the hashed count-matrix kernel is the candidate when no item table fits
   const bool hash_ok = !tc.W && opt.strategy != C2_STRATEGY_MERGE &&
                        (int)gram_hash_smem_bytes() + 1024 <= smem_optin();
-  // the tensor-core count matrices need the remapped-list area of the workspace
-  const bool tc_possible = w.rl != nullptr && w.rl_pn > 0 && s.m <= kGramTcMaxItems &&
-                           (opt.strategy == C2_STRATEGY_AUTO || opt.strategy == C2_STRATEGY_MMA);
-  if (tc.W || hash_ok || tc_possible) {
+  // the tensor-core count matrices (allowed by the strategy and the item
+  // universe; their remapped lists need room in the workspace tail, checked
+  // once nnz is read)
+  const bool tc_allowed = s.tc && w.gt_work_cap > 0 && s.m <= kGramTcMaxItems &&
+                          (opt.strategy == C2_STRATEGY_AUTO || opt.strategy == C2_STRATEGY_MMA);
+  if (tc.W || hash_ok || tc_allowed) {
     c2_status rc = build_padded_csr(ptr, items, s, w, st);
     if (rc) return rc;
   }
@@ -1968,12 +1970,24 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
   C2_CUDA_TRY(scan_exclusive(w.gflag, w.gidx, S, w.scan_tmp, st));
   C2_LAUNCH(k_greedy_list, div_up(S, T), T, 0, st, w.gflag, w.gidx, w.gkind_c, cptr, S, w.gcl,
             w.gsq, w.gsz, w.gkind, w.hdr);
-  int32_t ng = 0, max_len = 0;
+  int32_t ng = 0, max_len = 0, nnz32 = 0;
   C2_CUDA_TRY(cudaMemcpyAsync(&ng, &w.hdr->n_work, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   C2_CUDA_TRY(cudaMemcpyAsync(&max_len, &w.hdr->knn_max_len, sizeof(int32_t),
                               cudaMemcpyDeviceToHost, st));
+  if (tc_allowed)
+    C2_CUDA_TRY(cudaMemcpyAsync(&nnz32, ptr + s.n, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   C2_CUDA_TRY(cudaStreamSynchronize(st));
   if (ng == 0) return C2_OK;
+  bool tc_possible = false;
+  if (tc_allowed && nnz32 > 0) {
+    const size_t off = rl_offset(nnz32, s.n);
+    const int64_t pn = rl_stride(nnz32, s.n);
+    if ((int64_t)(off + (size_t)s.t * pn * 2) <= w.tail_bytes) {
+      w.rl = reinterpret_cast<uint16_t*>(reinterpret_cast<char*>(w.pitems) + off);
+      w.rl_pn = pn;
+      tc_possible = true;
+    }
+  }
   // tensor-core candidates: for every cluster of kTcMinM members or more, the
   // items held by two members or more (the width of its 0/1 operand) and the
   // members' total profile length (its density)
