@@ -1813,6 +1813,7 @@ struct TuneKey {
 struct TuneEntry {
   bool unified;            // one launch over all buckets with cfg[0]
   bool shapes_done;        // table shapes measured
+  bool tc_done;            // the strategy of the tensor-core candidates measured
   TableCfg cfg[kBuckets];
   float ms[kBuckets];
   // per (size bucket, density bucket): -1 not measured, 0 table, 1 tensor cores,
@@ -1820,7 +1821,7 @@ struct TuneEntry {
   int8_t route[kBuckets * kDensityBuckets];
   float table_ms[kBuckets * kDensityBuckets];
   float tc_ms[kBuckets * kDensityBuckets];
-  TuneEntry() : unified(true), shapes_done(false) {
+  TuneEntry() : unified(true), shapes_done(false), tc_done(false) {
     for (int i = 0; i < kBuckets * kDensityBuckets; ++i) {
       route[i] = -1;
       table_ms[i] = tc_ms[i] = 0.f;
@@ -1978,8 +1979,19 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
     C2_CUDA_TRY(cudaMemcpyAsync(&nnz32, ptr + s.n, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   C2_CUDA_TRY(cudaStreamSynchronize(st));
   if (ng == 0) return C2_OK;
+  const TuneKey tkey{s.n, s.m, s.t, s.b, s.N, k, thr};
+  TuneEntry tune;
+  if (opt.strategy == C2_STRATEGY_AUTO) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(tkey);
+    if (it != g_tune.end()) tune = it->second;
+  }
+  // once measured for these sizes with no bucket faster on the tensor cores,
+  // the autotuned build skips the candidates' density count
+  bool tc_wanted = opt.strategy == C2_STRATEGY_MMA || !tune.tc_done;
+  for (int i = 0; i < kBuckets * kDensityBuckets; ++i) tc_wanted = tc_wanted || tune.route[i] == 1;
   bool tc_possible = false;
-  if (tc_allowed && nnz32 > 0) {
+  if (tc_allowed && tc_wanted && nnz32 > 0) {
     const size_t off = rl_offset(nnz32, s.n);
     const int64_t pn = rl_stride(nnz32, s.n);
     if ((int64_t)(off + (size_t)s.t * pn * 2) <= w.tail_bytes) {
@@ -2030,13 +2042,6 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
   auto tc_bucket = [&](int g) {
     return size_bucket(gsz[g]) * kDensityBuckets + density_bucket(gsum[g], gsz[g], gk2[g]);
   };
-  const TuneKey tkey{s.n, s.m, s.t, s.b, s.N, k, thr};
-  TuneEntry tune;
-  if (opt.strategy == C2_STRATEGY_AUTO) {
-    std::lock_guard<std::mutex> lk(g_tune_mu);
-    auto it = g_tune.find(tkey);
-    if (it != g_tune.end()) tune = it->second;
-  }
   p_gsetup.end();
 
   GramArgs ga0{};
@@ -2178,6 +2183,7 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
           tune.table_ms[bk] = t_tab;
           tune.tc_ms[bk] = t_tc;
         }
+        tune.tc_done = true;
       }
       for (int g = g0; g < g1; ++g) {
         if (!tc_eligible(g)) continue;
