@@ -70,6 +70,11 @@ def lib():
             [I32P, I32P, C.c_int32, I32P, C.c_int32, C.c_double] + [F64P] * 6
         L.oracle_bruteforce_knn.argtypes = [I32P, I32P, C.c_int32, C.c_int32, C.c_void_p,
                                             C.c_int32, I32P, I32P, I32P]
+        L.oracle_goldfinger.argtypes = [I32P, I32P, C.c_int32, C.c_int32, C.c_uint64, I32P, I32P]
+        L.oracle_build_sim.argtypes = [I32P, I32P, C.c_int32, C.c_int32, I32P, I32P, C.c_int32,
+                                       C.c_int32, C.c_int32, C.c_int32, C.c_uint64, C.c_int32,
+                                       C.c_int32, C.c_int32, I32P, I32P, I32P, I64P]
+        L.oracle_exact_counts.argtypes = [I32P, I32P, C.c_int32, C.c_int32, I32P, I32P, I32P]
         L.oracle_avg_sim.restype = C.c_double
         L.oracle_avg_sim.argtypes = [I32P, I32P, C.c_int32, C.c_int32]
         _lib = L
@@ -186,6 +191,43 @@ def build_graph(ptr, items, m, k, t, b, N, seed, greedy_threshold, greedy_rounds
     if rc:
         raise ValueError(f"oracle_build failed with status {rc}")
     return out[0], out[1], out[2], int(pairs[0])
+
+
+def goldfinger(ptr, items, bits, seed):
+    """GoldFinger fingerprints (R17): CSR (fptr, fitems) of each user's sorted bit positions."""
+    ptr, items = _i32(ptr), _i32(items)
+    n = ptr.size - 1
+    fptr = np.zeros(n + 1, np.int32)
+    fitems = np.zeros(max(items.size, 1), np.int32)
+    rc = lib().oracle_goldfinger(ptr, items, n, bits, seed, fptr, fitems)
+    if rc:
+        raise ValueError(f"oracle_goldfinger failed with status {rc}")
+    return fptr, fitems[:fptr[n]].copy()
+
+
+def build_graph_sim(ptr, items, m, sptr, sitems, k, t, b, N, seed, greedy_threshold,
+                    greedy_rounds=10, greedy_random=0):
+    """Step 1 on (ptr, items), Steps 2-3 on the similarity profiles (sptr, sitems).
+    Returns (nbr_id, nbr_inter, nbr_union, pairs) with the similarity profiles' counts."""
+    ptr, items, sptr, sitems = _i32(ptr), _i32(items), _i32(sptr), _i32(sitems)
+    n = ptr.size - 1
+    out = [np.zeros((n, k), np.int32) for _ in range(3)]
+    pairs = np.zeros(1, np.int64)
+    rc = lib().oracle_build_sim(ptr, items, n, m, sptr, sitems if sitems.size else np.zeros(1, np.int32),
+                                k, t, b, N, seed, greedy_threshold, greedy_rounds, greedy_random,
+                                *out, pairs)
+    if rc:
+        raise ValueError(f"oracle_build_sim failed with status {rc}")
+    return out[0], out[1], out[2], int(pairs[0])
+
+
+def exact_counts(ptr, items, nbr_id):
+    """Exact (inter, union) of given neighbour rows [n, k] (id -1 = empty slot)."""
+    ptr, items, nbr_id = _i32(ptr), _i32(items), _i32(nbr_id)
+    n, k = nbr_id.shape
+    out = [np.zeros((n, k), np.int32) for _ in range(2)]
+    lib().oracle_exact_counts(ptr, items, n, k, nbr_id, *out)
+    return tuple(out)
 
 
 def bruteforce_knn(ptr, items, k, queries=None):

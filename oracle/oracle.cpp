@@ -20,6 +20,8 @@
 //   R9  candidates with no common item are never emitted.
 //   R11 greedy refinement: Philox-seeded random start, synchronous rounds.
 //   R12 merge reuses the carried (c, U) counts.
+//   R17 GoldFinger (Section II-F) is named, not constructed: one random bit
+//       of B per item; the estimate is the Jaccard of the bit sets.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -478,6 +480,78 @@ int oracle_build(const int32_t* ptr, const int32_t* items, int32_t n, int32_t m,
                      pairs_out);
   return oracle_merge_topk(cptr.data(), cusers.data(), nc, n, k, li.data(), lc.data(), lu.data(),
                            nbr_id, nbr_inter, nbr_union);
+}
+
+// ------------------------------------------------------------------ GoldFinger
+// Section II-F computes the local KNN graphs with GoldFinger, a 64- to
+// 8096-bit summary of each profile from which Jaccard values are estimated
+// (1024 bits in Section IV-E), without giving its construction.  R17: item x
+// sets one bit of B,
+//   fp(x) = floor((SplitMix64(K_g ^ x * 0xC2B2AE3D27D4EB4F) >> 32) * B / 2^32),
+//   K_g = SplitMix64(seed ^ 0x474F4C4446494E47),
+// the fingerprint of u is the set F_u = {fp(x) : x in P_u}, and J(u, v) is
+// estimated by |F_u n F_v| / |F_u u F_v|: the Jaccard similarity of the
+// fingerprints, so Steps 2-3 run unchanged on the fingerprints as profiles.
+uint32_t fingerprint_bit(uint64_t seed, int32_t x, int32_t bits) {
+  const uint64_t key = splitmix64_mix(seed ^ 0x474F4C4446494E47ULL);
+  const uint64_t z = splitmix64_mix(key ^ ((uint64_t)(uint32_t)x * 0xC2B2AE3D27D4EB4FULL));
+  return (uint32_t)(((z >> 32) * (uint64_t)(uint32_t)bits) >> 32);
+}
+
+// Fingerprints of every user as a CSR of sorted bit positions (rows never
+// longer than the profiles, so out_items needs at most nnz entries).
+int oracle_goldfinger(const int32_t* ptr, const int32_t* items, int32_t n, int32_t bits,
+                      uint64_t seed, int32_t* out_ptr, int32_t* out_items) {
+  if (bits < 1) return 1;
+  out_ptr[0] = 0;
+  for (int32_t u = 0; u < n; ++u) {
+    std::set<int32_t> f;
+    for (int32_t e = ptr[u]; e < ptr[u + 1]; ++e) f.insert((int32_t)fingerprint_bit(seed, items[e], bits));
+    int32_t o = out_ptr[u];
+    for (int32_t x : f) out_items[o++] = x;
+    out_ptr[u + 1] = o;
+  }
+  return 0;
+}
+
+// The method with estimated similarities: Step 1 on the profiles (ptr,
+// items, m items), Steps 2 and 3 on the similarity profiles (sptr, sitems),
+// e.g. GoldFinger fingerprints.
+int oracle_build_sim(const int32_t* ptr, const int32_t* items, int32_t n, int32_t m,
+                     const int32_t* sptr, const int32_t* sitems, int32_t k, int32_t t, int32_t b,
+                     int32_t N, uint64_t seed, int32_t greedy_threshold, int32_t greedy_rounds,
+                     int32_t greedy_random, int32_t* nbr_id, int32_t* nbr_inter,
+                     int32_t* nbr_union, int64_t* pairs_out) {
+  std::vector<int32_t> cluster_of((size_t)t * n), cptr((size_t)t * n + 1), cusers((size_t)t * n);
+  int32_t nc = 0;
+  int rc = oracle_frh_cluster(ptr, items, n, m, t, b, N, seed, nullptr, nullptr, cluster_of.data(),
+                              cptr.data(), cusers.data(), &nc, nullptr);
+  if (rc) return rc;
+  std::vector<int32_t> li((size_t)t * n * k), lc((size_t)t * n * k), lu((size_t)t * n * k);
+  oracle_cluster_knn(sptr, sitems, n, cptr.data(), cusers.data(), nc, k, seed, greedy_threshold,
+                     greedy_rounds, greedy_random, nullptr, li.data(), lc.data(), lu.data(),
+                     pairs_out);
+  return oracle_merge_topk(cptr.data(), cusers.data(), nc, n, k, li.data(), lc.data(), lu.data(),
+                           nbr_id, nbr_inter, nbr_union);
+}
+
+// Exact |P_u n P_v| and |P_u u P_v| of given neighbour rows (id -1: empty
+// slot, counts 0), for Eq. 1 on exact similarities.
+int oracle_exact_counts(const int32_t* ptr, const int32_t* items, int32_t n, int32_t k,
+                        const int32_t* nbr_id, int32_t* out_inter, int32_t* out_union) {
+  Csr P{ptr, items, n};
+  for (int32_t u = 0; u < n; ++u)
+    for (int32_t j = 0; j < k; ++j) {
+      const size_t e = (size_t)u * k + j;
+      if (nbr_id[e] < 0) {
+        out_inter[e] = out_union[e] = 0;
+        continue;
+      }
+      Nbr x = make_nbr(P, u, nbr_id[e]);
+      out_inter[e] = x.inter;
+      out_union[e] = x.uni;
+    }
+  return 0;
 }
 
 // Exact KNN by global brute force (Section IV-B, "Brute force"): for each

@@ -737,3 +737,71 @@ def test_model_forward_matches_numpy_restatement(exact):
     b = cfg["b"]
     for j in range(cfg["t"]):
         assert (keys[j] == np.argmax(zn[:, j * b:(j + 1) * b], axis=1)).all()
+
+
+# ------------------------------------------------------------------ GoldFinger (R17)
+def test_goldfinger_fingerprints_are_bit_sets_of_the_profile():
+    # F_u is a set of bits in [0, B), no larger than the profile; the
+    # fingerprint of a union is the union of the fingerprints (one bit per
+    # item); an empty profile has an empty fingerprint
+    rows = [[1, 5, 9, 40], [5, 9, 77], [1, 5, 9, 40, 77], [], list(range(300))]
+    ptr, items = csr_from_sets(rows)
+    for B in (16, 64, 1024):
+        fp, fi = oracle.goldfinger(ptr, items, B, 11)
+        F = sets_from_csr(fp, fi)
+        for u, r in enumerate(rows):
+            row = fi[fp[u]:fp[u + 1]]
+            assert (np.diff(row) > 0).all() and (row >= 0).all() and (row < B).all()
+            assert len(F[u]) <= min(len(r), B)
+        assert F[2] == F[0] | F[1] and F[3] == set()
+        if B == 16:
+            assert F[4] == set(range(16))     # 300 items fill 16 bits
+
+
+def test_goldfinger_bit_occupancy_matches_balls_in_bins():
+    # over random seeds each item's bit is uniform on [0, B) and items are
+    # independent: E|F| = B (1 - (1 - 1/B)^L) for a profile of L items, and two
+    # items share a bit with probability 1/B
+    L, B, S = 50, 64, 3000
+    ptr, items = csr_from_sets([list(range(L))])
+    sizes = [np.diff(oracle.goldfinger(ptr, items, B, s)[0])[0] for s in range(S)]
+    expect = B * (1 - (1 - 1 / B) ** L)
+    se = np.std(sizes) / np.sqrt(S)
+    assert abs(np.mean(sizes) - expect) < 5 * se + 0.05, (np.mean(sizes), expect)
+    ptr2, items2 = csr_from_sets([[3, 8]])
+    same = sum(np.diff(oracle.goldfinger(ptr2, items2, B, s)[0])[0] == 1 for s in range(S))
+    p = 1 / B
+    assert abs(same / S - p) < 5 * np.sqrt(p * (1 - p) / S), same / S
+
+
+def test_goldfinger_without_collisions_gives_the_exact_graph():
+    # with B = 2^22 bits the 1,000 items of these profiles land on distinct
+    # bits, so every estimate equals the exact Jaccard value: the build on
+    # fingerprints equals the exact build, counts included
+    ptr, items = synth.random_profiles(600, 1000, 15, 71, zipf_s=1.1)
+    B, seed = 1 << 22, 5
+    alli = np.arange(1000, dtype=np.int32)
+    fpa, fia = oracle.goldfinger(np.array([0, 1000], np.int32), alli, B, seed)
+    assert fpa[1] == 1000                  # no two items share a bit
+    fp, fi = oracle.goldfinger(ptr, items, B, seed)
+    k, t, b, N, thr = 8, 3, 16, 200, 120
+    exact = oracle.build_graph(ptr, items, 1000, k, t, b, N, seed, thr, 3)
+    est = oracle.build_graph_sim(ptr, items, 1000, fp, fi, k, t, b, N, seed, thr, 3)
+    for a, e in zip(exact, est):
+        assert np.array_equal(np.asarray(a), np.asarray(e))
+
+
+def test_exact_counts_of_given_rows():
+    ptr, items = synth.random_profiles(80, 60, 8, 72)
+    sets = sets_from_csr(ptr, items)
+    rng = np.random.default_rng(3)
+    ids = rng.integers(-1, 80, (80, 5)).astype(np.int32)
+    inter, uni = oracle.exact_counts(ptr, items, ids)
+    for u in range(80):
+        for j in range(5):
+            v = ids[u, j]
+            if v < 0:
+                assert inter[u, j] == 0 and uni[u, j] == 0
+            else:
+                assert inter[u, j] == len(sets[u] & sets[v])
+                assert uni[u, j] == len(sets[u] | sets[v])
