@@ -72,6 +72,11 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-quality", action="store_true")
+    ap.add_argument("--similarity", default="exact", choices=["exact", "goldfinger"],
+                    help="local KNN graphs on exact Jaccard, or on GoldFinger fingerprints "
+                         "(Section II-F; quality is then Eq. 2 on the exact similarities of the "
+                         "neighbours found)")
+    ap.add_argument("--gf-bits", type=int, default=1024)
     ap.add_argument("--strategy", type=int, default=-1,
                     help="count-matrix strategy: -1 autotuned (default), 0 merge, 1-2 table, "
                          "3 tensor cores")
@@ -467,9 +472,19 @@ def main():
     wb, wN = (w.n_items + 1, args.split_N or w.n_users) if minhash else (w.b, w.N)
     keys = torch.empty((w.t, w.n_users), dtype=torch.int32, device=dev) if minhash else None
     kws = c2.workspace(256, dev)
+    gf = args.similarity == "goldfinger"
+    gf_out = None
+    if gf:
+        gbits = args.gf_bits
+        gf_out = (torch.empty(w.n_users + 1, dtype=torch.int32, device=dev),
+                  torch.empty(max(nnz, 1), dtype=torch.int32, device=dev),
+                  torch.empty((w.n_users, gbits // 32), dtype=torch.int32, device=dev))
+        gws = c2.workspace(int(c2.lib().c2_goldfinger_workspace_size(w.n_users)), dev)
     opts = c2.options(greedy_threshold=w.greedy_threshold, greedy_rounds=w.greedy_rounds,
                       gram_budget_bytes=args.gram_budget_mb << 20, keys=keys,
-                      strategy=args.strategy)
+                      strategy=args.strategy,
+                      sim=gf_out[:2] if gf else None, sim_n_items=args.gf_bits if gf else 0,
+                      sim_bits=gf_out[2] if gf else None)
     ws = c2.workspace(c2.workspace_size(w.n_users, nnz, w.n_items, w.k, w.t, wb, wN, opts), dev)
     out = [torch.empty((w.n_users, w.k), dtype=torch.int32, device=dev) for _ in range(3)]
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
@@ -478,6 +493,9 @@ def main():
     def step():
         if minhash:
             c2.c2_minhash_keys(ptr, items, w.n_items, w.t, seed, out=keys, ws=kws, check=False)
+        if gf:
+            c2.c2_goldfinger(ptr, items, w.n_items, args.gf_bits, seed, ws=gws, check=False,
+                             out=gf_out)
         c2.c2_build_knn_graph(ptr, items, w.n_items, w.k, w.t, wb, wN, seed, opts=opts, ws=ws,
                               out=out, check=False)
 
@@ -519,7 +537,7 @@ def main():
 
     # end to end through the host-buffer entry point
     e2e = None
-    if not args.no_e2e and not minhash:
+    if not args.no_e2e and not minhash and not gf:
         hptr = torch.from_numpy(ptr_np).pin_memory()
         hitems = torch.from_numpy(items_np).pin_memory()
         hws = c2.workspace(c2.workspace_size_host(w.n_users, nnz, w.n_items, w.k, w.t, w.b, w.N,
@@ -550,9 +568,11 @@ def main():
     # quality (Eq. 2) against the exact graph from the GPU judge
     quality = None
     if not args.no_quality and rank == 0:
+        # with estimated similarities the graph's rows are rescored exactly
+        ein, eun = c2.c2_exact_counts(ptr, items, out[0]) if gf else (out[1], out[2])
         if w.n_users <= QUALITY_ALL_USERS:
             bid, bin_, bun = c2.c2_bruteforce_knn(ptr, items, w.n_items, w.k)
-            a_c2 = c2.c2_avg_sim(out[1], out[2])
+            a_c2 = c2.c2_avg_sim(ein, eun)
             a_bf = c2.c2_avg_sim(bin_, bun)
             quality = {"avg_sim": a_c2, "avg_sim_bruteforce": a_bf, "quality": a_c2 / a_bf,
                        "users": "all"}
@@ -564,7 +584,7 @@ def main():
             qd = torch.from_numpy(q).to(ptr.device).long()
             bid, bin_, bun = c2.c2_bruteforce_knn(ptr, items, w.n_items, w.k,
                                                   queries=qd.int().contiguous())
-            a_c2 = c2.c2_avg_sim(out[1][qd].contiguous(), out[2][qd].contiguous())
+            a_c2 = c2.c2_avg_sim(ein[qd].contiguous(), eun[qd].contiguous())
             a_bf = c2.c2_avg_sim(bin_, bun)
             quality = {"avg_sim": a_c2, "avg_sim_bruteforce": a_bf, "quality": a_c2 / a_bf,
                        "users": f"{QUALITY_SAMPLE} seeded sample of {w.n_users}"}
@@ -609,6 +629,7 @@ def main():
                            "nnz": nnz, **w.params(),
                            **({"clustering": "minhash", "b": wb, "N": wN} if minhash else {}),
                            **({"strategy": args.strategy} if args.strategy != -1 else {}),
+                           **({"similarity": f"goldfinger{args.gf_bits}"} if gf else {}),
                            "l2": "flushed (512 MiB write) before each step",
                            "parallelism": f"replicas{world}" if world > 1 else "single"},
                 "pairs_per_step": pairs, "gram_pairs_per_step": stats["gram_pairs"],

@@ -104,7 +104,22 @@ typedef struct {
                                the draws before min(k, M-1) distinct members are found (any
                                bound below 32, for instance), C2_ERR_TIMEOUT is recorded in
                                the status word                                             */
-  int32_t reserved[5];      /* must be zero                                                */
+  int32_t sim_n_items;      /* item universe of d_sim_ptr/d_sim_items (below)              */
+  const int32_t* d_sim_ptr; /* optional similarity profiles for Steps 2-3 of
+                               c2_build_knn_graph (device CSR [n_users+1] / items in
+                               [0, sim_n_items), sets, no more entries than the
+                               profiles), e.g. GoldFinger fingerprints from
+                               c2_goldfinger: clusters come from the profiles, the local
+                               KNN graphs and the merge from these (Section II-F); NULL =
+                               the profiles themselves                                     */
+  const int32_t* d_sim_items;
+  const uint32_t* d_sim_bits; /* optional packed bit rows of the profiles the local KNN
+                               graphs are computed on (d_sim_* in c2_build_knn_graph, the
+                               CSR itself in c2_cluster_knn): [n_users][sim_n_items / 32]
+                               words, as c2_goldfinger's d_fp_bits; with sim_n_items a
+                               multiple of 128 the tensor-core count matrices then read
+                               whole rows (no per-cluster remap)                          */
+  int32_t reserved[2];      /* must be zero                                                */
 } c2_options;
 
 /* Run statistics, filled by c2_get_stats(). */
@@ -257,6 +272,36 @@ c2_status c2_get_stats(const void* d_ws, c2_stream_t stream, c2_stats* out);
 
 /* Clears the device status word and statistics of d_ws (asynchronous). */
 c2_status c2_reset_status(void* d_ws, c2_stream_t stream);
+
+/* GoldFinger fingerprints (Section II-F: the prototype estimates Jaccard
+ * similarities from a 64- to 8096-bit summary of each profile, 1024 bits in
+ * Section IV-E; the construction is not given, so this reading is the
+ * library's own).  Item x sets bit
+ *   fp(x) = floor((SplitMix64(K_g ^ x * 0xC2B2AE3D27D4EB4F) >> 32) * bits / 2^32),
+ *   K_g = SplitMix64(seed ^ 0x474F4C4446494E47)
+ * of the user's fingerprint, and the estimate of J(u, v) is the Jaccard
+ * similarity of the two fingerprints' bit sets.  Outputs (device):
+ * d_fp_ptr[n_users+1] and d_fp_items[<= nnz] (each user's set bits,
+ * increasing: a CSR over an item universe of `bits`), and optionally
+ * d_fp_bits[n_users][bits/32] (the packed words, bit b of word w = position
+ * 32w + b).  32 <= bits <= 8192, a multiple of 32 (C2_ERR_UNSUPPORTED
+ * otherwise).  The profiles are validated (C2_ERR_INVALID_CSR through the
+ * status word).  Workspace: c2_goldfinger_workspace_size() bytes.
+ * Asynchronous on `stream`.  Pass the fingerprints as c2_options.d_sim_* to
+ * c2_build_knn_graph for the method with estimated similarities. */
+size_t c2_goldfinger_workspace_size(int32_t n_users);
+c2_status c2_goldfinger(const int32_t* d_csr_ptr, const int32_t* d_csr_items, int32_t n_users,
+                        int32_t n_items, int32_t bits, uint64_t seed, int32_t* d_fp_ptr,
+                        int32_t* d_fp_items, uint32_t* d_fp_bits, void* d_ws, size_t ws_bytes,
+                        c2_stream_t stream);
+
+/* Exact |P_u n P_v| and |P_u u P_v| of given neighbour rows d_nbr_id[n_users][k]
+ * (id -1: empty slot, counts 0), e.g. to evaluate Eq. 1 on exact similarities
+ * for a graph built on estimated ones.  Asynchronous on `stream`; no
+ * workspace. */
+c2_status c2_exact_counts(const int32_t* d_csr_ptr, const int32_t* d_csr_items, int32_t n_users,
+                          int32_t k, const int32_t* d_nbr_id, int32_t* d_nbr_inter,
+                          int32_t* d_nbr_union, c2_stream_t stream);
 
 /* Step 3 without a workspace, for callers that cannot allocate device memory
  * when they merge (inside a stream capture without a memory pool, plug-ins

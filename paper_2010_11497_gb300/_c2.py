@@ -36,7 +36,8 @@ class Options(C.Structure):
                 ("greedy_random", C.c_int32), ("strategy", C.c_int32),
                 ("d_hash_table", C.c_void_p), ("gram_budget_bytes", C.c_int64),
                 ("d_keys", C.c_void_p), ("greedy_max_draws", C.c_int32),
-                ("reserved", C.c_int32 * 5)]
+                ("sim_n_items", C.c_int32), ("d_sim_ptr", C.c_void_p), ("d_sim_items", C.c_void_p),
+                ("d_sim_bits", C.c_void_p), ("reserved", C.c_int32 * 2)]
 
 
 class ModelConfig(C.Structure):
@@ -82,6 +83,9 @@ _SIGS = {
     "c2_get_stats": (C.c_int, [P, P, C.POINTER(Stats)]),
     "c2_reset_status": (C.c_int, [P, P]),
     "c2_merge_topk_noalloc": (C.c_int, [P, I32, I32, I32, P, P, P, P, P, P, P]),
+    "c2_goldfinger_workspace_size": (SZ, [I32]),
+    "c2_goldfinger": (C.c_int, [P, P, I32, I32, I32, U64, P, P, P, P, SZ, P]),
+    "c2_exact_counts": (C.c_int, [P, P, I32, I32, P, P, P, P]),
     "c2_model_state_bytes": (SZ, [C.POINTER(ModelConfig)]),
     "c2_workspace_size_learned": (SZ, [C.POINTER(ModelConfig), I32, I64, I32, I32, I32, I32,
                                        C.POINTER(Options)]),
@@ -130,7 +134,12 @@ def lib():
 
 def options(greedy_threshold=0, greedy_rounds=-1, greedy_random=0, strategy=STRATEGY_AUTO,
             hash_table: torch.Tensor | None = None, gram_budget_bytes=0,
-            keys: torch.Tensor | None = None, greedy_max_draws=0) -> Options:
+            keys: torch.Tensor | None = None, greedy_max_draws=0,
+            sim: tuple | None = None, sim_n_items=0,
+            sim_bits: torch.Tensor | None = None) -> Options:
+    """Options of the build; sim = (ptr, items) similarity profiles over
+    sim_n_items items (e.g. c2_goldfinger's fingerprints), sim_bits their
+    packed rows."""
     o = Options()
     lib().c2_default_options(C.byref(o))
     o.greedy_threshold = greedy_threshold
@@ -141,7 +150,11 @@ def options(greedy_threshold=0, greedy_rounds=-1, greedy_random=0, strategy=STRA
     o.gram_budget_bytes = gram_budget_bytes
     o.d_keys = None if keys is None else keys.data_ptr()
     o.greedy_max_draws = greedy_max_draws
-    o._keep = (hash_table, keys)      # keep the tensors alive with the options
+    o.sim_n_items = sim_n_items
+    o.d_sim_ptr = None if sim is None else sim[0].data_ptr()
+    o.d_sim_items = None if sim is None else sim[1].data_ptr()
+    o.d_sim_bits = None if sim_bits is None else sim_bits.data_ptr()
+    o._keep = (hash_table, keys, sim, sim_bits)   # keep the tensors alive with the options
     return o
 
 
@@ -254,6 +267,39 @@ def c2_merge_topk_noalloc(cusers, n_users, t, k, loc_id, loc_inter, loc_union, s
     rc = lib().c2_merge_topk_noalloc(_ptr(cusers), n_users, t, k, _ptr(loc_id), _ptr(loc_inter),
                                      _ptr(loc_union), *[_ptr(x) for x in out], _stream(stream))
     _check(rc, "c2_merge_topk_noalloc")
+    return tuple(out)
+
+
+def c2_goldfinger(ptr, items, n_items, bits, seed, with_bits=False, ws=None, stream=None,
+                  check=True, out=None):
+    """GoldFinger fingerprints: (fp_ptr [n+1], fp_items [nnz capacity], fp_bits
+    [n, bits/32] or None).  The CSR's rows are each user's set bits, increasing."""
+    dev = ptr.device
+    n = ptr.numel() - 1
+    if out is not None:
+        fptr, fitems, fbits = out
+    else:
+        fptr = torch.empty(n + 1, dtype=torch.int32, device=dev)
+        fitems = torch.empty(max(items.numel(), 1), dtype=torch.int32, device=dev)
+        fbits = (torch.empty((max(n, 1), bits // 32), dtype=torch.int32, device=dev)
+                 if with_bits else None)
+    if ws is None:
+        ws = workspace(int(lib().c2_goldfinger_workspace_size(n)), dev)
+    _check(lib().c2_goldfinger(_ptr(ptr), _ptr(items), n, n_items, bits, seed, _ptr(fptr),
+                               _ptr(fitems), _ptr(fbits), _ptr(ws), ws.numel(), _stream(stream)),
+           "c2_goldfinger")
+    if check:
+        _check(c2_get_status(ws, stream), "c2_goldfinger (device)")
+    return fptr, fitems, fbits
+
+
+def c2_exact_counts(ptr, items, nbr_id, out=None, stream=None):
+    """Exact (inter, union) of given neighbour rows [n, k]."""
+    n, k = nbr_id.shape
+    if out is None:
+        out = [torch.empty((n, k), dtype=torch.int32, device=nbr_id.device) for _ in range(2)]
+    _check(lib().c2_exact_counts(_ptr(ptr), _ptr(items), n, k, _ptr(nbr_id), _ptr(out[0]),
+                                 _ptr(out[1]), _stream(stream)), "c2_exact_counts")
     return tuple(out)
 
 

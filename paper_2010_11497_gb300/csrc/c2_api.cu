@@ -26,8 +26,9 @@ Sizes make_sizes(int32_t n, int64_t nnz, int32_t m, int32_t k, int32_t t, int32_
   // that path; their remapped lists (one padded profile area per function)
   // live in the workspace tail, sized here when nnz is known
   const int strategy = opt ? opt->strategy : C2_STRATEGY_AUTO;
-  s.tc = (strategy == C2_STRATEGY_AUTO || strategy == C2_STRATEGY_MMA) && m >= 1 &&
-         m <= kGramTcMaxItems;
+  const int32_t mk = (opt && opt->d_sim_ptr) ? opt->sim_n_items : m;   // local KNN universe
+  s.tc = (strategy == C2_STRATEGY_AUTO || strategy == C2_STRATEGY_MMA) && mk >= 1 &&
+         mk <= kGramTcMaxItems;
   s.rl_pn = s.tc && nnz > 0 ? rl_stride(nnz, n) : 0;
   return s;
 }
@@ -180,8 +181,12 @@ c2_status check_common(int32_t n, int32_t m, int32_t k, int32_t t, int32_t b, in
   if (!sizes_ok(n, m, k, t, b, N)) return C2_ERR_UNSUPPORTED;
   if ((int64_t)t * n >= (int64_t(1) << 31) - 1) return C2_ERR_UNSUPPORTED;
   if (opt) {
-    for (int i = 0; i < 5; ++i)
+    for (int i = 0; i < 2; ++i)
       if (opt->reserved[i] != 0) return C2_ERR_INVALID_ARG;
+    if (opt->d_sim_ptr && (opt->sim_n_items < 1 || (!opt->d_sim_items && n > 0)))
+      return C2_ERR_INVALID_ARG;
+    if (opt->d_sim_bits && (opt->sim_n_items < 1 || opt->sim_n_items % 32))
+      return C2_ERR_INVALID_ARG;
     if (opt->strategy < -1 || opt->strategy > 3) return C2_ERR_INVALID_ARG;
     if (opt->greedy_random < 0) return C2_ERR_INVALID_ARG;
   }
@@ -218,6 +223,10 @@ void c2_default_options(c2_options* opt) {
   opt->gram_budget_bytes = 0;
   opt->d_keys = nullptr;
   opt->greedy_max_draws = 0;
+  opt->sim_n_items = 0;
+  opt->d_sim_ptr = nullptr;
+  opt->d_sim_items = nullptr;
+  opt->d_sim_bits = nullptr;
 }
 
 const char* c2_status_string(c2_status s) {
@@ -387,8 +396,17 @@ c2_status c2_build_knn_graph(const int32_t* d_csr_ptr, const int32_t* d_csr_item
   rc = run_frh_cluster(d_csr_ptr, d_csr_items, s, seed, o, bb.cluster_of, bb.cptr, bb.cusers,
                        bb.ncl, nullptr, cw, st);
   if (rc) return rc;
-  rc = run_cluster_knn(d_csr_ptr, d_csr_items, s, bb.cptr, bb.cusers, bb.ncl, seed, o, bb.lid,
-                       bb.lin, bb.lun, kw, st);
+  // Steps 2-3 on the similarity profiles when given (Section II-F)
+  const int32_t* kptr = o.d_sim_ptr ? o.d_sim_ptr : d_csr_ptr;
+  const int32_t* kitems = o.d_sim_ptr ? o.d_sim_items : d_csr_items;
+  Sizes sk = s;
+  if (o.d_sim_ptr) {
+    sk.m = o.sim_n_items;
+    rc = run_validate(kptr, kitems, sk, hdr, st);
+    if (rc) return rc;
+  }
+  rc = run_cluster_knn(kptr, kitems, sk, bb.cptr, bb.cusers, bb.ncl, seed, o, bb.lid, bb.lin,
+                       bb.lun, kw, st);
   if (rc) return rc;
   return run_merge(bb.cusers, s, bb.lid, bb.lin, bb.lun, d_nbr_id, d_nbr_inter, d_nbr_union, kw,
                    st);
@@ -482,5 +500,42 @@ c2_status c2_avg_sim(const int32_t* d_nbr_inter, const int32_t* d_nbr_union, int
 }
 
 size_t c2_autotune_report(char* buf, size_t len) { return c2::autotune_report(buf, len); }
+
+size_t c2_goldfinger_workspace_size(int32_t n_users) {
+  if (n_users < 0) return 0;
+  return goldfinger_ws_bytes(n_users);
+}
+
+c2_status c2_goldfinger(const int32_t* d_csr_ptr, const int32_t* d_csr_items, int32_t n_users,
+                        int32_t n_items, int32_t bits, uint64_t seed, int32_t* d_fp_ptr,
+                        int32_t* d_fp_items, uint32_t* d_fp_bits, void* d_ws, size_t ws_bytes,
+                        c2_stream_t stream) {
+  if (n_users < 0 || n_items < 0) return C2_ERR_INVALID_ARG;
+  if (!d_csr_ptr || !d_fp_ptr || (n_users > 0 && (!d_csr_items || !d_fp_items)))
+    return C2_ERR_INVALID_ARG;
+  if (bits < 32 || bits > 8192 || bits % 32) return C2_ERR_UNSUPPORTED;
+  c2_status rc = check_ws(d_ws, ws_bytes, goldfinger_ws_bytes(n_users));
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  DevHeader* hdr = reinterpret_cast<DevHeader*>(d_ws);
+  int32_t* scan_tmp = reinterpret_cast<int32_t*>((char*)d_ws + 256);
+  C2_CUDA_TRY(cudaMemsetAsync(hdr, 0, sizeof(DevHeader), st));
+  if (n_users == 0) {
+    C2_CUDA_TRY(cudaMemsetAsync(d_fp_ptr, 0, sizeof(int32_t), st));
+    return C2_OK;
+  }
+  return run_goldfinger(d_csr_ptr, d_csr_items, n_users, n_items, bits, seed, d_fp_ptr,
+                        d_fp_items, d_fp_bits, hdr, scan_tmp, st);
+}
+
+c2_status c2_exact_counts(const int32_t* d_csr_ptr, const int32_t* d_csr_items, int32_t n_users,
+                          int32_t k, const int32_t* d_nbr_id, int32_t* d_nbr_inter,
+                          int32_t* d_nbr_union, c2_stream_t stream) {
+  if (n_users < 0 || k < 1 || k > kMaxK) return k > kMaxK ? C2_ERR_UNSUPPORTED : C2_ERR_INVALID_ARG;
+  if (!d_csr_ptr || (n_users > 0 && (!d_csr_items || !d_nbr_id || !d_nbr_inter || !d_nbr_union)))
+    return C2_ERR_INVALID_ARG;
+  return run_exact_counts(d_csr_ptr, d_csr_items, n_users, k, d_nbr_id, d_nbr_inter, d_nbr_union,
+                          (cudaStream_t)stream);
+}
 
 }  // extern "C"

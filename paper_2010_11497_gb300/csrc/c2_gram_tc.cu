@@ -81,6 +81,10 @@ struct GtArgs {
   const int64_t* gofs;     // per cluster: offset of its count matrix
   uint16_t* gram;
   DevHeader* hdr;
+  // bits mode (rl == NULL): the operand rows are the users' packed bit rows,
+  // row_words 32-bit words each (bit b of word w = column 32w + b)
+  const uint32_t* bits;
+  int32_t row_words;
 };
 
 __device__ __forceinline__ bool gt_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
@@ -138,6 +142,26 @@ struct RowList {
   }
 };
 
+// One FP8 word of 0/1 values from 4 bits: byte i = 1.0 iff bit i (the four
+// bits spread to bytes 0..3 by a multiply with no overlapping partial
+// products, then scaled to 0x38).
+__device__ __forceinline__ uint32_t nibble_fp8(uint32_t x) {
+  return ((x * 0x00204081u) & 0x01010101u) * (uint32_t)GT_ONE;
+}
+
+// Writes the 128 columns of one stage of row R from 128 packed bits.
+__device__ __forceinline__ void expand_row(uint8_t* tile, int R, uint4 b) {
+  const uint32_t w[4] = {b.x, b.y, b.z, b.w};
+  uint8_t* row = tile + (R >> 3) * 1024 + (R & 7) * 128;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {   // 16-byte chunk j = columns 16j .. 16j + 15
+    const uint32_t v = w[j >> 1] >> (16 * (j & 1));
+    *reinterpret_cast<uint4*>(row + (((j ^ R) & 7) << 4)) =
+        make_uint4(nibble_fp8(v & 0xFu), nibble_fp8((v >> 4) & 0xFu), nibble_fp8((v >> 8) & 0xFu),
+                   nibble_fp8((v >> 12) & 0xFu));
+  }
+}
+
 // Zeroes the 16-byte chunks of row R named by `mask` (8 bits).
 __device__ __forceinline__ void clear_chunks(uint8_t* tile, int R, uint32_t mask) {
   while (mask) {
@@ -189,8 +213,56 @@ __global__ void __launch_bounds__(GT_THREADS, 1) k_gram_mma(GtArgs g) {
   fence_after();
   const uint32_t tmem = tmem_slot;
 
-  if (warp < GT_PROD_WARPS) {
-    // ---------------- producers
+  if (warp < GT_PROD_WARPS && !g.rl) {
+    // ---------------- producers, bits mode: every stage of a row is 16 bytes
+    // of its packed bits (the next stage's in flight), expanded in place
+    const int r = threadIdx.x;   // A row r, B rows r and r + 128
+    int stage = 0;
+    uint32_t phase = 0;
+    bool ok = true;
+    for (int idx = blockIdx.x; idx < g.n_work && ok; idx += gridDim.x) {
+      const int4 wk = g.work[idx];
+      const int c = wk.x, cbase = g.cptr[c], M = g.cptr[c + 1] - cbase;
+      const uint4* src[3];
+      const int pos[3] = {GT_BM * wk.y + r, GT_BN * wk.z + r, GT_BN * wk.z + GT_BM + r};
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        src[q] = nullptr;
+        if (pos[q] < M) {
+          const int u = g.cusers[cbase + g.iinfo[cbase + pos[q]].x];
+          src[q] = reinterpret_cast<const uint4*>(g.bits + (int64_t)u * g.row_words);
+        }
+      }
+      uint4 cur[3];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) cur[q] = src[q] ? __ldg(src[q]) : make_uint4(0, 0, 0, 0);
+      for (int kc = 0; kc < wk.w; ++kc) {
+        uint4 nxt[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+          nxt[q] = (src[q] && kc + 1 < wk.w) ? __ldg(src[q] + kc + 1) : make_uint4(0, 0, 0, 0);
+        const bool free_ok =
+            __all_sync(0xffffffffu, gt_wait(empty(stage), phase ^ 1u, abort_flag, true));
+        if (!free_ok) {
+          if (lane == 0) gt_abort(abort_flag, g.hdr);
+          ok = false;
+          break;
+        }
+        uint8_t* A = sm + (size_t)stage * GT_STAGE_BYTES;
+        uint8_t* B = A + GT_A_BYTES;
+        expand_row(A, r, cur[0]);
+        expand_row(B, r, cur[1]);
+        expand_row(B, r + GT_BM, cur[2]);
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(full(stage));
+        if (++stage == GT_STAGES) stage = 0, phase ^= 1u;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) cur[q] = nxt[q];
+      }
+    }
+  } else if (warp < GT_PROD_WARPS) {
+    // ---------------- producers, list mode
     const int r = threadIdx.x;   // A row r, B rows r and r + 128
     uint32_t masks[GT_STAGES];
 #pragma unroll
@@ -388,7 +460,7 @@ __global__ void __launch_bounds__(1024) k_remap_count(
     const int32_t* __restrict__ list, int32_t nlist, int32_t min_m, const int32_t* __restrict__ gsz,
     const int32_t* __restrict__ gcl, const int32_t* __restrict__ cptr,
     const int32_t* __restrict__ cusers, const int32_t* __restrict__ ptr,
-    const int32_t* __restrict__ items, int32_t m, int32_t* __restrict__ k2,
+    const int32_t* __restrict__ items, int32_t m, int32_t whole, int32_t* __restrict__ k2,
     int64_t* __restrict__ sumlen, DevHeader* hdr) {
   extern __shared__ uint32_t rm_sh[];
   __shared__ int red[32];
@@ -403,15 +475,20 @@ __global__ void __launch_bounds__(1024) k_remap_count(
   }
   const int c = gcl[gi];
   const int cbase = cptr[c], M = cptr[c + 1] - cbase;
-  const int W = item_words(m);
-  uint32_t* seen1 = rm_sh;
-  uint32_t* seen2 = rm_sh + W;
-  for (int i = threadIdx.x; i < 2 * W; i += blockDim.x) rm_sh[i] = 0;
-  __syncthreads();
-  mark_items(ptr, items, cusers, cbase, M, seen1, seen2);
-  __syncthreads();
   int cnt = 0, len = 0;
-  for (int i = threadIdx.x; i < W; i += blockDim.x) cnt += __popc(seen2[i]);
+  if (whole) {
+    // whole rows (bits mode): every column is an operand column
+    if (threadIdx.x == 0) cnt = m;
+  } else {
+    const int W = item_words(m);
+    uint32_t* seen1 = rm_sh;
+    uint32_t* seen2 = rm_sh + W;
+    for (int i = threadIdx.x; i < 2 * W; i += blockDim.x) rm_sh[i] = 0;
+    __syncthreads();
+    mark_items(ptr, items, cusers, cbase, M, seen1, seen2);
+    __syncthreads();
+    for (int i = threadIdx.x; i < W; i += blockDim.x) cnt += __popc(seen2[i]);
+  }
   for (int l = threadIdx.x; l < M; l += blockDim.x) {
     const int u = cusers[cbase + l];
     len += ptr[u + 1] - ptr[u];
@@ -509,14 +586,14 @@ static_assert(12 * (kGramTcMaxItems / 32) + 1024 <= 232448,
 
 c2_status gram_tc_count(const int32_t* list, int nlist, int min_m, const int32_t* gsz,
                         const int32_t* gcl, const int32_t* cptr, const int32_t* cusers,
-                        const int32_t* ptr, const int32_t* items, int m, int32_t* k2,
+                        const int32_t* ptr, const int32_t* items, int m, bool whole, int32_t* k2,
                         int64_t* sumlen, DevHeader* hdr, cudaStream_t st) {
   if (nlist <= 0) return C2_OK;
   if (m > kGramTcMaxItems) return C2_ERR_UNSUPPORTED;
-  const int smem = 8 * item_words(m);
+  const int smem = whole ? 0 : 8 * item_words(m);
   C2_CUDA_TRY(cudaFuncSetAttribute(k_remap_count, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  C2_LAUNCH(k_remap_count, nlist, 1024, smem, st, list, nlist, min_m, gsz, gcl, cptr, cusers, ptr,
-            items, m, k2, sumlen, hdr);
+  C2_LAUNCH(k_remap_count, nlist, whole ? 256 : 1024, smem, st, list, nlist, min_m, gsz, gcl, cptr,
+            cusers, ptr, items, m, whole ? 1 : 0, k2, sumlen, hdr);
   C2_CUDA_TRY(cudaGetLastError());
   return C2_OK;
 }
@@ -538,9 +615,10 @@ c2_status gram_tc_remap(const int32_t* list, int nlist, const int32_t* gcl, cons
 c2_status gram_tc_run(const int4* work, int n_work, const int32_t* cptr, const int32_t* cusers,
                       const int2* iinfo, const int32_t* pptr, const uint16_t* rl, int64_t PN,
                       int n, const int32_t* rl_len, const int64_t* gofs, uint16_t* gram,
-                      DevHeader* hdr, cudaStream_t st) {
+                      const uint32_t* bits, int row_words, DevHeader* hdr, cudaStream_t st) {
   if (n_work <= 0) return C2_OK;
-  if (((uintptr_t)rl & 7u) || (PN & 3)) return C2_ERR_INVALID_ARG;
+  if (rl && (((uintptr_t)rl & 7u) || (PN & 3))) return C2_ERR_INVALID_ARG;
+  if (!rl && (!bits || ((uintptr_t)bits & 15u) || row_words % 4)) return C2_ERR_INVALID_ARG;
   GtArgs g;
   g.work = work;
   g.n_work = n_work;
@@ -555,6 +633,8 @@ c2_status gram_tc_run(const int4* work, int n_work, const int32_t* cptr, const i
   g.gofs = gofs;
   g.gram = gram;
   g.hdr = hdr;
+  g.bits = bits;
+  g.row_words = row_words;
   C2_CUDA_TRY(cudaFuncSetAttribute(k_gram_mma, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)GT_SMEM));
   const int grid = std::min(num_sms(), n_work);

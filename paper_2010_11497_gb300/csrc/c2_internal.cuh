@@ -691,7 +691,7 @@ c2_status tc_logits_argmax(const __nv_bfloat16* A, int M, int K, const __nv_bflo
 // (cluster, row tile, column tile, stages).
 c2_status gram_tc_count(const int32_t* list, int nlist, int min_m, const int32_t* gsz,
                         const int32_t* gcl, const int32_t* cptr, const int32_t* cusers,
-                        const int32_t* ptr, const int32_t* items, int m, int32_t* k2,
+                        const int32_t* ptr, const int32_t* items, int m, bool whole, int32_t* k2,
                         int64_t* sumlen, DevHeader* hdr, cudaStream_t st);
 c2_status gram_tc_remap(const int32_t* list, int nlist, const int32_t* gcl, const int32_t* cptr,
                         const int32_t* cusers, const int32_t* ptr, const int32_t* items, int m,
@@ -700,10 +700,18 @@ c2_status gram_tc_remap(const int32_t* list, int nlist, const int32_t* gcl, cons
 c2_status gram_tc_run(const int4* work, int n_work, const int32_t* cptr, const int32_t* cusers,
                       const int2* iinfo, const int32_t* pptr, const uint16_t* rl, int64_t PN,
                       int n, const int32_t* rl_len, const int64_t* gofs, uint16_t* gram,
-                      DevHeader* hdr, cudaStream_t st);
+                      const uint32_t* bits, int row_words, DevHeader* hdr, cudaStream_t st);
 int gram_tc_tile_rows();
 int gram_tc_tile_cols();
 int gram_tc_stage_cols();
+
+// GoldFinger fingerprints and exact rescoring (c2_goldfinger.cu).
+size_t goldfinger_ws_bytes(int32_t n);
+c2_status run_goldfinger(const int32_t* ptr, const int32_t* items, int32_t n, int32_t m,
+                         int32_t bits, uint64_t seed, int32_t* fptr, int32_t* fitems,
+                         uint32_t* fbits, DevHeader* hdr, int32_t* scan_tmp, cudaStream_t st);
+c2_status run_exact_counts(const int32_t* ptr, const int32_t* items, int32_t n, int32_t k,
+                           const int32_t* nbr, int32_t* out_in, int32_t* out_un, cudaStream_t st);
 
 int num_sms();
 size_t autotune_report(char* buf, size_t len);

@@ -1991,7 +1991,12 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
   bool tc_wanted = opt.strategy == C2_STRATEGY_MMA || !tune.tc_done;
   for (int i = 0; i < kBuckets * kDensityBuckets; ++i) tc_wanted = tc_wanted || tune.route[i] == 1;
   bool tc_possible = false;
-  if (tc_allowed && tc_wanted && nnz32 > 0) {
+  // bits mode: the operand rows are the caller's packed bit rows (whole rows,
+  // no remap, no remapped-list area)
+  const bool tc_bits = opt.d_sim_bits != nullptr && s.m % 128 == 0;
+  if (tc_allowed && tc_wanted && tc_bits) {
+    tc_possible = true;
+  } else if (tc_allowed && tc_wanted && nnz32 > 0) {
     const size_t off = rl_offset(nnz32, s.n);
     const int64_t pn = rl_stride(nnz32, s.n);
     if ((int64_t)(off + (size_t)s.t * pn * 2) <= w.tail_bytes) {
@@ -2005,7 +2010,7 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
   // members' total profile length (its density)
   if (tc_possible) {
     c2_status rc = gram_tc_count(nullptr, ng, kTcMinM, w.gsz, w.gcl, cptr, cusers, ptr, items,
-                                 s.m, w.gk2, w.gsum, w.hdr, st);
+                                 s.m, tc_bits, w.gk2, w.gsum, w.hdr, st);
     if (rc) return rc;
   }
   C2_CUDA_TRY(scan_exclusive64(w.gsq, w.goff, ng, w.scan_tmp64, st));
@@ -2111,7 +2116,7 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
     if (rc) return rc;
     rc = upload(w.gt_work, work_h.data(), work_h.size() * sizeof(int4));
     if (rc) return rc;
-    {
+    if (!tc_bits) {
       Prof p_rm(st, "gram_tc_remap");
       rc = gram_tc_remap(w.gt_list, (int)ord.size(), w.gcl, cptr, cusers, ptr, items, s.m, w.pptr,
                          w.rl_pn, s.n, w.rl, w.rl_len, w.hdr, st);
@@ -2119,8 +2124,9 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
     }
     {
       Prof p_tc(st, "gram_tc");
-      rc = gram_tc_run(w.gt_work, (int)work_h.size(), cptr, cusers, w.iinfo, w.pptr, w.rl,
-                       w.rl_pn, s.n, w.rl_len, w.gofs, w.gram, w.hdr, st);
+      rc = gram_tc_run(w.gt_work, (int)work_h.size(), cptr, cusers, w.iinfo, w.pptr,
+                       tc_bits ? nullptr : w.rl, w.rl_pn, s.n, w.rl_len, w.gofs, w.gram,
+                       tc_bits ? opt.d_sim_bits : nullptr, s.m / 32, w.hdr, st);
       if (rc) return rc;
     }
     if (count_stats)

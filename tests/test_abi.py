@@ -31,7 +31,8 @@ def test_status_strings(lib):
 def test_default_options(lib):
     o = c2.options()
     assert o.greedy_threshold == 0 and o.greedy_rounds == -1 and o.strategy == -1
-    assert list(o.reserved) == [0] * 5 and o.d_keys is None and o.greedy_max_draws == 0
+    assert list(o.reserved) == [0] * 2 and o.d_keys is None and o.greedy_max_draws == 0
+    assert o.d_sim_ptr is None and o.d_sim_bits is None and o.sim_n_items == 0
 
 
 def test_workspace_size_validates(lib):
@@ -67,7 +68,7 @@ def test_host_argument_errors_need_no_gpu(lib):
                                 C.c_void_p(4096 + 8), 1 << 30, None)
     assert rc == 4
     # non-zero reserved option fields
-    o.reserved[3] = 1
+    o.reserved[1] = 1
     rc = lib.c2_build_knn_graph(fake, fake, 10, 10, 5, 2, 8, 4, 1, C.byref(o), fake, fake, fake,
                                 C.c_void_p(4096), 1 << 30, None)
     assert rc == 1
@@ -84,3 +85,34 @@ def test_minhash_keys_argument_errors_need_no_gpu(lib):
     assert lib.c2_minhash_keys(fake, fake, 10, 10, 4, 1, fake, C.c_void_p(4096), 64, None) == 4
     assert lib.c2_minhash_keys(fake, fake, 10, 10, 4, 1, fake, C.c_void_p(4096 + 8), 256,
                                None) == 4
+
+
+def test_goldfinger_and_exact_counts_argument_errors_need_no_gpu(lib):
+    fake = C.c_void_p(256)
+    ws = c2.lib().c2_goldfinger_workspace_size(100)
+    assert ws >= 256
+    # bits out of range or not a multiple of 32
+    for bits in (16, 8224, 100):
+        assert lib.c2_goldfinger(fake, fake, 100, 50, bits, 1, fake, fake, None, C.c_void_p(4096),
+                                 ws, None) == 3
+    # NULL outputs, missing or small workspace
+    assert lib.c2_goldfinger(fake, fake, 100, 50, 1024, 1, None, fake, None, C.c_void_p(4096), ws,
+                             None) == 1
+    assert lib.c2_goldfinger(fake, fake, 100, 50, 1024, 1, fake, fake, None, None, ws, None) == 4
+    assert lib.c2_goldfinger(fake, fake, 100, 50, 1024, 1, fake, fake, None, C.c_void_p(4096), 8,
+                             None) == 4
+    # k out of range, NULL rows
+    assert lib.c2_exact_counts(fake, fake, 10, 33, fake, fake, fake, None) == 3
+    assert lib.c2_exact_counts(fake, fake, 10, 5, None, fake, fake, None) == 1
+    # similarity options: a CSR without its item universe, bit rows not in words of 32
+    o = c2.options()
+    o.d_sim_ptr = 256
+    rc = lib.c2_build_knn_graph(fake, fake, 10, 10, 5, 2, 8, 4, 1, C.byref(o), fake, fake, fake,
+                                C.c_void_p(4096), 1 << 30, None)
+    assert rc == 1
+    o = c2.options()
+    o.d_sim_bits = 256
+    o.sim_n_items = 100
+    rc = lib.c2_build_knn_graph(fake, fake, 10, 10, 5, 2, 8, 4, 1, C.byref(o), fake, fake, fake,
+                                C.c_void_p(4096), 1 << 30, None)
+    assert rc == 1
