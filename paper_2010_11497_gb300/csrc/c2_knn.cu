@@ -849,12 +849,8 @@ struct GlobalCU {
 // order keys.  Rows and columns are in internal order; candidates are
 // ranked by local index (user-id order).
 template <bool Keyed>
-__global__ void __launch_bounds__(kNT, 6) k_gram_topk(RowTopkArgs a) {
-  __shared__ int32_t s_sid[Keyed ? 1 : kNT / 32][64];
-  __shared__ uint2 s_scu[kNT / 32][64];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (w >= *a.n_users_dev || dev_failed(a.hdr)) return;
+__device__ __forceinline__ void row_topk(const RowTopkArgs& a, int w, int32_t* sid, uint2* scu) {
+  const int lane = threadIdx.x & 31;
   const int slot = a.u_slot[w];
   const int c = a.gcl[a.u_g[w]];
   const int cs = a.cptr[c], M = a.cptr[c + 1] - cs, Mp = (M + 7) & ~7;
@@ -865,7 +861,7 @@ __global__ void __launch_bounds__(kNT, 6) k_gram_topk(RowTopkArgs a) {
   const int k = a.k;
   typename std::conditional<Keyed, KeyTopk<GlobalCU>, WarpTopk>::type tk;
   if constexpr (Keyed) {
-    tk.start(0ull, k, s_scu[warp], GlobalCU{row, info, my});
+    tk.start(0ull, k, scu, GlobalCU{row, info, my});
     // first pass: each lane's best candidate; the k-th best of these 32
     // distinct candidates ranks no higher than the row's k-th best, so it
     // floors the filter of the second pass
@@ -885,7 +881,7 @@ __global__ void __launch_bounds__(kNT, 6) k_gram_topk(RowTopkArgs a) {
   } else {
     WarpList l0;
     l0.id = -1; l0.c = 0; l0.u = 0;
-    tk.start(l0, k, s_sid[warp], s_scu[warp]);
+    tk.start(l0, k, sid, scu);
   }
   // steps of 32 candidates, through a ring of 4 steps of loads in flight (a
   // rolled loop keeps the kernel small enough for the instruction cache)
@@ -929,6 +925,184 @@ __global__ void __launch_bounds__(kNT, 6) k_gram_topk(RowTopkArgs a) {
     a.out_id[o] = id >= 0 ? a.cusers[cs + id] : -1;
     a.out_in[o] = id >= 0 ? (int32_t)oc : 0;
     a.out_un[o] = id >= 0 ? (int32_t)ou : 0;
+  }
+}
+
+template <bool Keyed>
+__global__ void __launch_bounds__(kNT, 6) k_gram_topk(RowTopkArgs a) {
+  __shared__ int32_t s_sid[Keyed ? 1 : kNT / 32][64];
+  __shared__ uint2 s_scu[kNT / 32][64];
+  const int warp = threadIdx.x >> 5;
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (w >= *a.n_users_dev || dev_failed(a.hdr)) return;
+  row_topk<Keyed>(a, w, s_sid[Keyed ? 0 : warp], s_scu[warp]);
+}
+
+// The keyed row path as a call, for the rows the select kernel hands back.
+static __device__ __noinline__ void row_topk_keyed(const RowTopkArgs& a, int w, uint2* scu) {
+  row_topk<true>(a, w, nullptr, scu);
+}
+
+// Exact floor(65536 c / u) for 0 < c <= u < 2^16, clamped to 65535: a float
+// estimate corrected by one step either way (every product below 2^32).
+__device__ __forceinline__ uint32_t jac_q16(uint32_t c, uint32_t u) {
+  const uint32_t num = c << 16;
+  uint32_t q = (uint32_t)__float2uint_rz(__fmul_rn((float)num, __frcp_rn((float)u)));
+  q = min(q, 65536u);
+  if (q * u > num) --q;
+  else if ((q + 1u) * u <= num) ++q;
+  return min(q, 65535u);
+}
+
+// Brute-force rows by exact selection (keyed rows: unions below 2^16): warp
+// per member.  q = floor(65536 J) is exact and monotone in J, so the k best
+// candidates are among those whose q reaches the k-th largest q.  Pass 1
+// histograms q >> 8; the bucket b1 holding the k-th largest is found by a
+// warp scan; if that bucket is crowded, a second pass histograms its
+// candidates by q & 255.  The last pass stages the candidates at or above the
+// selected (bucket, sub-bucket) -- at most 64 -- as exact order keys, and two
+// warp sorts and a bitonic merge give the top k.  Rows with more than 64
+// candidates tied at the selection point go through the general keyed path.
+__global__ void __launch_bounds__(kNT, 5) k_gram_select(const __grid_constant__ RowTopkArgs a) {
+  __shared__ uint32_t s_hist[kNT / 32][256];
+  __shared__ uint64_t s_stage[kNT / 32][64];
+  __shared__ uint2 s_scu[kNT / 32][64];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (w >= *a.n_users_dev || dev_failed(a.hdr)) return;
+  uint32_t* hist = s_hist[warp];
+  uint64_t* stg = s_stage[warp];
+  const int slot = a.u_slot[w];
+  const int c = a.gcl[a.u_g[w]];
+  const int cs = a.cptr[c], M = a.cptr[c + 1] - cs, Mp = (M + 7) & ~7;
+  const int P = a.ipos[slot];
+  const uint16_t* row = a.gram + a.gofs[c] + (int64_t)P * Mp;
+  const int2* info = a.iinfo + cs;
+  const uint32_t my = (uint32_t)a.slen[slot];
+  const int k = a.k;
+  // level 1: q >> 8
+#pragma unroll
+  for (int i = 0; i < 8; ++i) hist[lane + 32 * i] = 0u;
+  __syncwarp();
+#pragma unroll 4
+  for (int p = lane; p < M; p += 32) {
+    const uint32_t cc = p != P ? (uint32_t)row[p] : 0u;
+    if (cc == 0u) continue;
+    const uint32_t u = my + (uint32_t)info[p].y - cc;
+    atomicAdd(&hist[jac_q16(cc, u) >> 8], 1u);
+  }
+  __syncwarp();
+  // bucket of the k-th largest: lane l holds buckets 255 - 8l .. 248 - 8l
+  auto select = [&](int need, uint32_t& above) -> int {
+    uint32_t v[8], sum = 0u;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      v[i] = hist[255 - 8 * lane - i];
+      sum += v[i];
+    }
+    uint32_t incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const unsigned hit = __ballot_sync(0xffffffffu, incl >= (uint32_t)need);
+    if (hit == 0u) {   // fewer than `need` candidates: take every bucket
+      above = 0u;
+      return -1;
+    }
+    const int L = __ffs(hit) - 1;
+    int b = -1;
+    uint32_t run = __shfl_sync(0xffffffffu, incl - sum, L), ab = 0u;
+    if (lane == L) {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        if (b < 0 && run + v[i] >= (uint32_t)need) {
+          b = 255 - 8 * lane - i;
+          ab = run;
+        }
+        run += v[i];
+      }
+    }
+    above = __shfl_sync(0xffffffffu, ab, L);
+    return __shfl_sync(0xffffffffu, b, L);
+  };
+  uint32_t above1 = 0u;
+  const int b1 = select(k, above1);                  // -1: every candidate
+  const uint32_t in_b1 = b1 >= 0 ? hist[b1] : 0u;
+  int b2 = -1;                                        // sub-bucket floor inside b1
+  bool ok = true;
+  if (b1 >= 0 && above1 + in_b1 > 64u) {
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < 8; ++i) hist[lane + 32 * i] = 0u;
+    __syncwarp();
+#pragma unroll 4
+    for (int p = lane; p < M; p += 32) {
+      const uint32_t cc = p != P ? (uint32_t)row[p] : 0u;
+      if (cc == 0u) continue;
+      const uint32_t q = jac_q16(cc, my + (uint32_t)info[p].y - cc);
+      if ((int)(q >> 8) == b1) atomicAdd(&hist[q & 255u], 1u);
+    }
+    __syncwarp();
+    uint32_t above2 = 0u;
+    b2 = select(k - (int)above1, above2);
+    ok = b2 >= 0 && above1 + above2 + hist[b2] <= 64u;
+  } else if (b1 < 0) {
+    // every nonzero candidate is wanted: fewer than k of them
+  }
+  if (!__all_sync(0xffffffffu, ok)) {
+    row_topk_keyed(a, w, s_scu[warp]);
+    return;
+  }
+  // stage the selected candidates
+  const uint32_t qmin = b1 < 0 ? 0u : ((uint32_t)b1 << 8) | (uint32_t)(b2 < 0 ? 0 : b2);
+  int n = 0;
+#pragma unroll 4
+  for (int p0 = 0; p0 < M; p0 += 32) {
+    const int p = p0 + lane;
+    bool pass = false;
+    uint32_t cc = 0u, u = 0u;
+    int2 in = make_int2(0, 0);
+    if (p < M && p != P) {
+      cc = (uint32_t)row[p];
+      if (cc) {
+        in = info[p];
+        u = my + (uint32_t)in.y - cc;
+        pass = jac_q16(cc, u) >= qmin;
+      }
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, pass);
+    if (pass) stg[n + __popc(m & lanemask_lt())] = nbr_key(cc, u, in.x, p);
+    n += __popc(m);
+  }
+  __syncwarp();
+  uint64_t x = lane < n ? stg[lane] : 0ull;
+  x = warp_sort32_keys(x);
+  if (n > 32) {
+    uint64_t y = lane + 32 < n ? stg[lane + 32] : 0ull;
+    y = warp_sort32_keys(y);
+    const uint64_t r = __shfl_sync(0xffffffffu, y, 31 - lane);
+    x = r > x ? r : x;
+#pragma unroll
+    for (int j = 16; j > 0; j >>= 1) {
+      const uint64_t o = __shfl_xor_sync(0xffffffffu, x, j);
+      const bool lower = (lane & j) == 0;
+      x = lower ? (o > x ? o : x) : (o < x ? o : x);
+    }
+  }
+  if (lane < k) {
+    const int64_t o = (int64_t)slot * k + lane;
+    const int32_t id = key_id(x);
+    uint32_t oc = 0u, ou = 0u;
+    if (id >= 0) {
+      const int pos = key_pos(x);
+      oc = (uint32_t)row[pos];
+      ou = my + (uint32_t)info[pos].y - oc;
+    }
+    a.out_id[o] = id >= 0 ? a.cusers[cs + id] : -1;
+    a.out_in[o] = (int32_t)oc;
+    a.out_un[o] = (int32_t)ou;
   }
 }
 
@@ -2335,7 +2509,7 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
       ra.gram = w.gram; ra.u_slot = w.ub_slot; ra.u_g = w.ub_g; ra.n_users_dev = w.bb_off + nb;
       ra.ipos = w.ipos; ra.iinfo = w.iinfo;
       ra.k = k; ra.out_id = lid; ra.out_in = lin; ra.out_un = lun; ra.hdr = w.hdr;
-      if (keyed) C2_LAUNCH(k_gram_topk<true>, div_up(n_brute_users * 32, kNT), kNT, 0, side, ra);
+      if (keyed) C2_LAUNCH(k_gram_select, div_up(n_brute_users * 32, kNT), kNT, 0, side, ra);
       else C2_LAUNCH(k_gram_topk<false>, div_up(n_brute_users * 32, kNT), kNT, 0, side, ra);
       C2_CUDA_TRY(cudaGetLastError());
       return C2_OK;
