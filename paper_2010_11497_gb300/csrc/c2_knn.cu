@@ -954,126 +954,164 @@ __device__ __forceinline__ uint32_t jac_q16(uint32_t c, uint32_t u) {
   return min(q, 65535u);
 }
 
-// Brute-force rows by exact selection (keyed rows: unions below 2^16): warp
-// per member.  q = floor(65536 J) is exact and monotone in J, so the k best
-// candidates are among those whose q reaches the k-th largest q.  Pass 1
-// histograms q >> 8; the bucket b1 holding the k-th largest is found by a
-// warp scan; if that bucket is crowded, a second pass histograms its
-// candidates by q & 255.  The last pass stages the candidates at or above the
-// selected (bucket, sub-bucket) -- at most 64 -- as exact order keys, and two
-// warp sorts and a bitonic merge give the top k.  Rows with more than 64
-// candidates tied at the selection point go through the general keyed path.
-__global__ void __launch_bounds__(kNT, 5) k_gram_select(const __grid_constant__ RowTopkArgs a) {
+// Brute-force rows by exact selection (keyed rows: unions below 2^16, rows of
+// at most kSelMaxM candidates): warp per member.  q = floor(65536 J) is exact
+// and monotone in J, so the k best candidates are among those whose q reaches
+// the k-th largest q.
+//  1. One pass over the count row computes q for every candidate into shared
+//     memory (0 for the member itself and for candidates with no common item)
+//     and each lane's largest q.  The k-th largest of the 32 lane maxima, T0,
+//     is at most the row's k-th largest q (k distinct candidates reach it).
+//  2. The candidates with q >= T0 -- few -- are histogrammed in 256 buckets
+//     over [T0, 65535] (a warp scan finds the bucket of the k-th largest),
+//     and if the buckets are wider than one value, the candidates of that
+//     bucket again by their low bits: the exact k-th largest q, qk.
+//  3. The candidates with q >= qk (at most 64) are staged as exact order keys
+//     and sorted (two warp sorts and a bitonic merge): the top k.
+// Rows with more than 64 candidates tied at qk, or longer than kSelMaxM, go
+// through the general keyed path.
+constexpr int kSelMaxM = 2048;
+
+// k-th largest (1-based) of the lanes' values (k <= 32): a warp bitonic sort.
+__device__ __forceinline__ uint32_t warp_kth_largest(uint32_t v, int k) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int size = 2; size <= 32; size <<= 1) {
+#pragma unroll
+    for (int j = size >> 1; j > 0; j >>= 1) {
+      const uint32_t o = __shfl_xor_sync(0xffffffffu, v, j);
+      const bool best_first = size == 32 || (lane & size) == 0;
+      const bool lower = (lane & j) == 0;
+      const bool take = (lower == best_first) ? (o > v) : (v > o);
+      v = take ? o : v;
+    }
+  }
+  return __shfl_sync(0xffffffffu, v, k - 1);
+}
+
+// Bucket (largest first) holding the need-th largest of a 256-bucket
+// histogram: lane l holds buckets 255 - 8l .. 248 - 8l.  Returns -1 when the
+// histogram holds fewer than `need`; *above = entries in higher buckets.
+__device__ __forceinline__ int hist_select(const uint32_t* hist, int need, uint32_t* above) {
+  const int lane = threadIdx.x & 31;
+  uint32_t v[8], sum = 0u;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    v[i] = hist[255 - 8 * lane - i];
+    sum += v[i];
+  }
+  uint32_t incl = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  const unsigned hit = __ballot_sync(0xffffffffu, incl >= (uint32_t)need);
+  if (hit == 0u) {
+    *above = 0u;
+    return -1;
+  }
+  const int L = __ffs(hit) - 1;
+  int b = -1;
+  uint32_t run = __shfl_sync(0xffffffffu, incl - sum, L), ab = 0u;
+  if (lane == L) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      if (b < 0 && run + v[i] >= (uint32_t)need) {
+        b = 255 - 8 * lane - i;
+        ab = run;
+      }
+      run += v[i];
+    }
+  }
+  *above = __shfl_sync(0xffffffffu, ab, L);
+  return __shfl_sync(0xffffffffu, b, L);
+}
+
+__global__ void __launch_bounds__(kNT, 4) k_gram_select(const __grid_constant__ RowTopkArgs a) {
+  __shared__ uint16_t s_q[kNT / 32][kSelMaxM];
   __shared__ uint32_t s_hist[kNT / 32][256];
   __shared__ uint64_t s_stage[kNT / 32][64];
   __shared__ uint2 s_scu[kNT / 32][64];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (w >= *a.n_users_dev || dev_failed(a.hdr)) return;
-  uint32_t* hist = s_hist[warp];
-  uint64_t* stg = s_stage[warp];
   const int slot = a.u_slot[w];
   const int c = a.gcl[a.u_g[w]];
   const int cs = a.cptr[c], M = a.cptr[c + 1] - cs, Mp = (M + 7) & ~7;
+  if (M > kSelMaxM) {
+    row_topk_keyed(a, w, s_scu[warp]);
+    return;
+  }
+  uint16_t* Q = s_q[warp];
+  uint32_t* hist = s_hist[warp];
+  uint64_t* stg = s_stage[warp];
   const int P = a.ipos[slot];
   const uint16_t* row = a.gram + a.gofs[c] + (int64_t)P * Mp;
   const int2* info = a.iinfo + cs;
   const uint32_t my = (uint32_t)a.slen[slot];
   const int k = a.k;
-  // level 1: q >> 8
-#pragma unroll
-  for (int i = 0; i < 8; ++i) hist[lane + 32 * i] = 0u;
-  __syncwarp();
+  // 1. every candidate's q into shared memory, the lanes' maxima
+  uint32_t qmax = 0u;
 #pragma unroll 4
   for (int p = lane; p < M; p += 32) {
     const uint32_t cc = p != P ? (uint32_t)row[p] : 0u;
-    if (cc == 0u) continue;
-    const uint32_t u = my + (uint32_t)info[p].y - cc;
-    atomicAdd(&hist[jac_q16(cc, u) >> 8], 1u);
+    uint32_t q = 0u;
+    if (cc) q = jac_q16(cc, my + (uint32_t)info[p].y - cc) + 1u;   // 0 = not a candidate
+    Q[p] = (uint16_t)min(q, 65535u);
+    qmax = max(qmax, q);
+  }
+  const uint32_t T0 = max(warp_kth_largest(qmax, k), 1u);   // floor of the k-th largest
+  // 2. histogram of q >= T0 over [T0, 65535] in 256 buckets of width 2^sh
+  const int sh = max(0, 32 - __clz((int)(65535u - T0)) - 8);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) hist[lane + 32 * i] = 0u;
+  __syncwarp();
+  for (int p = lane; p < M; p += 32) {
+    const uint32_t q = Q[p];
+    if (q >= T0) atomicAdd(&hist[(q - T0) >> sh], 1u);
   }
   __syncwarp();
-  // bucket of the k-th largest: lane l holds buckets 255 - 8l .. 248 - 8l
-  auto select = [&](int need, uint32_t& above) -> int {
-    uint32_t v[8], sum = 0u;
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      v[i] = hist[255 - 8 * lane - i];
-      sum += v[i];
-    }
-    uint32_t incl = sum;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += y;
-    }
-    const unsigned hit = __ballot_sync(0xffffffffu, incl >= (uint32_t)need);
-    if (hit == 0u) {   // fewer than `need` candidates: take every bucket
-      above = 0u;
-      return -1;
-    }
-    const int L = __ffs(hit) - 1;
-    int b = -1;
-    uint32_t run = __shfl_sync(0xffffffffu, incl - sum, L), ab = 0u;
-    if (lane == L) {
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        if (b < 0 && run + v[i] >= (uint32_t)need) {
-          b = 255 - 8 * lane - i;
-          ab = run;
-        }
-        run += v[i];
-      }
-    }
-    above = __shfl_sync(0xffffffffu, ab, L);
-    return __shfl_sync(0xffffffffu, b, L);
-  };
-  uint32_t above1 = 0u;
-  const int b1 = select(k, above1);                  // -1: every candidate
-  const uint32_t in_b1 = b1 >= 0 ? hist[b1] : 0u;
-  int b2 = -1;                                        // sub-bucket floor inside b1
+  uint32_t above = 0u;
+  const int b1 = hist_select(hist, k, &above);
+  uint32_t qk;    // the exact k-th largest q (T0 when fewer than k candidates reach T0)
   bool ok = true;
-  if (b1 >= 0 && above1 + in_b1 > 64u) {
+  if (b1 < 0) {
+    qk = T0;
+  } else if (sh == 0) {
+    qk = T0 + (uint32_t)b1;
+    ok = above + hist[b1] <= 64u;
+  } else {
+    const uint32_t lo = T0 + ((uint32_t)b1 << sh);
     __syncwarp();
 #pragma unroll
     for (int i = 0; i < 8; ++i) hist[lane + 32 * i] = 0u;
     __syncwarp();
-#pragma unroll 4
     for (int p = lane; p < M; p += 32) {
-      const uint32_t cc = p != P ? (uint32_t)row[p] : 0u;
-      if (cc == 0u) continue;
-      const uint32_t q = jac_q16(cc, my + (uint32_t)info[p].y - cc);
-      if ((int)(q >> 8) == b1) atomicAdd(&hist[q & 255u], 1u);
+      const uint32_t q = Q[p];
+      if (q >= lo && q < lo + (1u << sh)) atomicAdd(&hist[q - lo], 1u);
     }
     __syncwarp();
     uint32_t above2 = 0u;
-    b2 = select(k - (int)above1, above2);
-    ok = b2 >= 0 && above1 + above2 + hist[b2] <= 64u;
-  } else if (b1 < 0) {
-    // every nonzero candidate is wanted: fewer than k of them
+    const int b2 = hist_select(hist, k - (int)above, &above2);
+    qk = lo + (uint32_t)(b2 < 0 ? 0 : b2);
+    ok = b2 >= 0 && above + above2 + hist[b2] <= 64u;
   }
   if (!__all_sync(0xffffffffu, ok)) {
     row_topk_keyed(a, w, s_scu[warp]);
     return;
   }
-  // stage the selected candidates
-  const uint32_t qmin = b1 < 0 ? 0u : ((uint32_t)b1 << 8) | (uint32_t)(b2 < 0 ? 0 : b2);
+  // 3. stage the candidates with q >= qk, sort their exact keys
   int n = 0;
-#pragma unroll 4
   for (int p0 = 0; p0 < M; p0 += 32) {
     const int p = p0 + lane;
-    bool pass = false;
-    uint32_t cc = 0u, u = 0u;
-    int2 in = make_int2(0, 0);
-    if (p < M && p != P) {
-      cc = (uint32_t)row[p];
-      if (cc) {
-        in = info[p];
-        u = my + (uint32_t)in.y - cc;
-        pass = jac_q16(cc, u) >= qmin;
-      }
-    }
+    const bool pass = p < M && (uint32_t)Q[p] >= qk;
     const unsigned m = __ballot_sync(0xffffffffu, pass);
-    if (pass) stg[n + __popc(m & lanemask_lt())] = nbr_key(cc, u, in.x, p);
+    if (pass) {
+      const uint32_t cc = (uint32_t)row[p];
+      const int2 in = info[p];
+      stg[n + __popc(m & lanemask_lt())] = nbr_key(cc, my + (uint32_t)in.y - cc, in.x, p);
+    }
     n += __popc(m);
   }
   __syncwarp();
