@@ -119,7 +119,15 @@ typedef struct {
                                words, as c2_goldfinger's d_fp_bits; with sim_n_items a
                                multiple of 128 the tensor-core count matrices then read
                                whole rows (no per-cluster remap)                          */
-  int32_t reserved[2];      /* must be zero                                                */
+  int32_t fn_offset;        /* sharding by hash function: this call's functions 0 .. t-1 are
+                               the run's functions fn_offset .. fn_offset + t - 1 (their
+                               generative hashes); default 0                              */
+  int32_t cluster_base;     /* sharding by hash function: the run's number of this call's
+                               first cluster (the clusters of the functions before
+                               fn_offset), which the greedy random starts draw with;
+                               default 0.  G shards' local rows and slot maps,
+                               concatenated in function order, merge to the graph of one
+                               call with all t functions                                   */
 } c2_options;
 
 /* Run statistics, filled by c2_get_stats(). */
@@ -153,6 +161,9 @@ typedef struct {
   int64_t tc_macs;          /* tensor-core multiply-adds issued for count matrices          */
   int32_t tc_clusters;      /* count matrices computed on the tensor cores                 */
   int32_t tc_tiles;         /* their 128 x 256 tiles                                       */
+  int32_t select_general;   /* brute-force rows with more than 64 candidates tied at their
+                               k-th value, ranked by the general path                      */
+  int32_t reserved2;
 } c2_stats;
 
 /* Fills *opt with the defaults described above.  Never fails. */

@@ -70,6 +70,12 @@ def lib():
             [I32P, I32P, C.c_int32, I32P, C.c_int32, C.c_double] + [F64P] * 6
         L.oracle_bruteforce_knn.argtypes = [I32P, I32P, C.c_int32, C.c_int32, C.c_void_p,
                                             C.c_int32, I32P, I32P, I32P]
+        L.oracle_frh_cluster_shard.argtypes = [I32P, I32P, C.c_int32, C.c_int32, C.c_int32,
+                                               C.c_int32, C.c_int32, C.c_uint64, C.c_int32, I32P,
+                                               I32P, I32P, I32P]
+        L.oracle_cluster_knn_shard.argtypes = [I32P, I32P, C.c_int32, I32P, I32P, C.c_int32,
+                                               C.c_int32, C.c_uint64, C.c_int32, C.c_int32,
+                                               C.c_int32, I32P, I32P, I32P, I64P]
         L.oracle_goldfinger.argtypes = [I32P, I32P, C.c_int32, C.c_int32, C.c_uint64, I32P, I32P]
         L.oracle_build_sim.argtypes = [I32P, I32P, C.c_int32, C.c_int32, I32P, I32P, C.c_int32,
                                        C.c_int32, C.c_int32, C.c_int32, C.c_uint64, C.c_int32,
@@ -167,6 +173,38 @@ def cluster_knn(ptr, items, cptr, cusers, k, seed, greedy_threshold, greedy_roun
                              greedy_rounds, greedy_random,
                              None if mask is None else mask.ctypes.data_as(C.c_void_p),
                              li, lc, lu, pairs)
+    return li, lc, lu, int(pairs[0])
+
+
+def frh_cluster_shard(ptr, items, m, t, b, N, seed, fn_offset):
+    """Clustering of a shard: the run's functions fn_offset .. fn_offset + t - 1,
+    numbered locally.  Returns dict(cptr, cusers, n_clusters)."""
+    ptr, items = _i32(ptr), _i32(items)
+    n = ptr.size - 1
+    cluster_of = np.zeros(t * n, np.int32)
+    cptr = np.zeros(t * n + 1, np.int32)
+    cusers = np.zeros(max(t * n, 1), np.int32)
+    nc = np.zeros(1, np.int32)
+    rc = lib().oracle_frh_cluster_shard(ptr, items if items.size else np.zeros(1, np.int32), n, m,
+                                        t, b, N, seed, fn_offset, cluster_of, cptr, cusers, nc)
+    if rc:
+        raise ValueError(f"oracle_frh_cluster_shard failed with status {rc}")
+    c = int(nc[0])
+    return dict(cptr=cptr[:c + 1].copy(), cusers=cusers[:t * n].copy(), n_clusters=c)
+
+
+def cluster_knn_shard(ptr, items, cptr, cusers, k, seed, greedy_threshold, greedy_rounds,
+                      cluster_base):
+    """Local rows of a shard whose first cluster is the run's cluster_base."""
+    ptr, items, cptr, cusers = _i32(ptr), _i32(items), _i32(cptr), _i32(cusers)
+    S = cusers.size
+    li = np.full((S, k), -1, np.int32)
+    lc = np.zeros((S, k), np.int32)
+    lu = np.zeros((S, k), np.int32)
+    pairs = np.zeros(1, np.int64)
+    lib().oracle_cluster_knn_shard(ptr, items, ptr.size - 1, cptr, cusers, cptr.size - 1, k, seed,
+                                   greedy_threshold, greedy_rounds, cluster_base, li, lc, lu,
+                                   pairs)
     return li, lc, lu, int(pairs[0])
 
 

@@ -169,13 +169,16 @@ void split_or_emit(const Csr& P, const std::vector<int32_t>& hfn, int32_t N, Clu
 // With `keys` ([t][n], from a learned proposer) the first-level key of user u
 // under function i is keys[i][u] instead of H_i(u); such clusters carry no
 // hash threshold, so their first split uses the plain FRH key (eta = -1).
+// fn_offset numbers the functions of a shard: local function i is the
+// run's function fn_offset + i (its generative hash).
 std::vector<Cluster> frh_clusters(const Csr& P, int32_t m, int32_t t, int32_t b, int32_t N,
-                                  uint64_t seed, const int32_t* htab, const int32_t* keys) {
+                                  uint64_t seed, const int32_t* htab, const int32_t* keys,
+                                  int32_t fn_offset = 0) {
   std::vector<Cluster> out;
   for (int i = 0; i < t; ++i) {
     std::vector<int32_t> hfn(m);
     for (int32_t x = 0; x < m; ++x)
-      hfn[x] = htab ? htab[(size_t)i * m + x] : (int32_t)item_hash(seed, i, x, b);
+      hfn[x] = htab ? htab[(size_t)i * m + x] : (int32_t)item_hash(seed, fn_offset + i, x, b);
     // B_i[key] <- users whose FRH key is `key` (Eq. 3: H_i(u) = min h_i(x)).
     std::vector<std::vector<int32_t>> B(b + 1);
     for (int32_t u = 0; u < P.n; ++u) {
@@ -311,6 +314,19 @@ struct BoundedKnn {
 // ======================================================================
 extern "C" {
 
+// Shared bodies of the plain and sharded entry points (defined below).
+int oracle_frh_cluster_impl(const int32_t* ptr, const int32_t* items, int32_t n, int32_t m,
+                            int32_t t, int32_t b, int32_t N, uint64_t seed, const int32_t* htab,
+                            const int32_t* keys, int32_t fn_offset, int32_t* cluster_of,
+                            int32_t* cptr, int32_t* cusers, int32_t* n_clusters, int32_t* cmeta);
+int oracle_cluster_knn_impl(const int32_t* ptr, const int32_t* items, int32_t n,
+                            const int32_t* cptr, const int32_t* cusers, int32_t n_clusters,
+                            int32_t k, uint64_t seed, int32_t greedy_threshold,
+                            int32_t greedy_rounds, int32_t greedy_random, const uint8_t* only,
+                            int32_t cluster_base, int32_t* loc_id, int32_t* loc_inter,
+                            int32_t* loc_union, int64_t* pairs_out);
+
+
 uint64_t oracle_mix64(uint64_t z) { return splitmix64_mix(z); }
 
 uint32_t oracle_item_hash(uint64_t seed, int32_t i, int32_t x, int32_t b) {
@@ -383,16 +399,34 @@ int oracle_minhash_keys(const int32_t* ptr, const int32_t* items, int32_t n, int
 //   cluster_of[t][n]  final cluster number of user u under function i
 //   cptr[n_clusters+1], cusers[t*n]  cluster CSR, members ascending
 //   cmeta[n_clusters][4] (optional): function, depth, residual flag, last key
+// A shard's clustering (functions fn_offset .. fn_offset + t - 1 of the run,
+// numbered locally from 0).
+int oracle_frh_cluster_shard(const int32_t* ptr, const int32_t* items, int32_t n, int32_t m,
+                             int32_t t, int32_t b, int32_t N, uint64_t seed, int32_t fn_offset,
+                             int32_t* cluster_of, int32_t* cptr, int32_t* cusers,
+                             int32_t* n_clusters) {
+  return oracle_frh_cluster_impl(ptr, items, n, m, t, b, N, seed, nullptr, nullptr, fn_offset,
+                                 cluster_of, cptr, cusers, n_clusters, nullptr);
+}
+
 int oracle_frh_cluster(const int32_t* ptr, const int32_t* items, int32_t n, int32_t m, int32_t t,
                        int32_t b, int32_t N, uint64_t seed, const int32_t* htab,
                        const int32_t* keys, int32_t* cluster_of, int32_t* cptr, int32_t* cusers,
                        int32_t* n_clusters, int32_t* cmeta) {
+  return oracle_frh_cluster_impl(ptr, items, n, m, t, b, N, seed, htab, keys, 0, cluster_of, cptr,
+                                 cusers, n_clusters, cmeta);
+}
+
+int oracle_frh_cluster_impl(const int32_t* ptr, const int32_t* items, int32_t n, int32_t m,
+                            int32_t t, int32_t b, int32_t N, uint64_t seed, const int32_t* htab,
+                            const int32_t* keys, int32_t fn_offset, int32_t* cluster_of,
+                            int32_t* cptr, int32_t* cusers, int32_t* n_clusters, int32_t* cmeta) {
   if (oracle_validate_csr(ptr, items, n, m)) return 2;
   if (keys)
     for (size_t s2 = 0; s2 < (size_t)t * n; ++s2)
       if (keys[s2] < 0 || keys[s2] >= b) return 1;
   Csr P{ptr, items, n};
-  std::vector<Cluster> cl = frh_clusters(P, m, t, b, N, seed, htab, keys);
+  std::vector<Cluster> cl = frh_clusters(P, m, t, b, N, seed, htab, keys, fn_offset);
   int32_t pos = 0;
   cptr[0] = 0;
   for (size_t c = 0; c < cl.size(); ++c) {
@@ -417,11 +451,34 @@ int oracle_frh_cluster(const int32_t* ptr, const int32_t* items, int32_t n, int3
 // cusers), [t*n][k], sorted by R8 and padded with id -1.  `only` (optional,
 // one byte per cluster) restricts the work to the marked clusters; rows of
 // the others are left untouched.
+// cluster_base: the run's number of this shard's first cluster (the clusters
+// of the functions before it), which the greedy random start draws with.
+int oracle_cluster_knn_shard(const int32_t* ptr, const int32_t* items, int32_t n,
+                             const int32_t* cptr, const int32_t* cusers, int32_t n_clusters,
+                             int32_t k, uint64_t seed, int32_t greedy_threshold,
+                             int32_t greedy_rounds, int32_t cluster_base, int32_t* loc_id,
+                             int32_t* loc_inter, int32_t* loc_union, int64_t* pairs_out) {
+  return oracle_cluster_knn_impl(ptr, items, n, cptr, cusers, n_clusters, k, seed,
+                                 greedy_threshold, greedy_rounds, 0, nullptr, cluster_base, loc_id,
+                                 loc_inter, loc_union, pairs_out);
+}
+
 int oracle_cluster_knn(const int32_t* ptr, const int32_t* items, int32_t n, const int32_t* cptr,
                        const int32_t* cusers, int32_t n_clusters, int32_t k, uint64_t seed,
                        int32_t greedy_threshold, int32_t greedy_rounds, int32_t greedy_random,
                        const uint8_t* only, int32_t* loc_id, int32_t* loc_inter,
                        int32_t* loc_union, int64_t* pairs_out) {
+  return oracle_cluster_knn_impl(ptr, items, n, cptr, cusers, n_clusters, k, seed,
+                                 greedy_threshold, greedy_rounds, greedy_random, only, 0, loc_id,
+                                 loc_inter, loc_union, pairs_out);
+}
+
+int oracle_cluster_knn_impl(const int32_t* ptr, const int32_t* items, int32_t n,
+                            const int32_t* cptr, const int32_t* cusers, int32_t n_clusters,
+                            int32_t k, uint64_t seed, int32_t greedy_threshold,
+                            int32_t greedy_rounds, int32_t greedy_random, const uint8_t* only,
+                            int32_t cluster_base, int32_t* loc_id, int32_t* loc_inter,
+                            int32_t* loc_union, int64_t* pairs_out) {
   Csr P{ptr, items, n};
   int64_t pairs = 0;
   for (int32_t c = 0; c < n_clusters; ++c) {
@@ -431,7 +488,8 @@ int oracle_cluster_knn(const int32_t* ptr, const int32_t* items, int32_t n, cons
     if ((int32_t)mem.size() < greedy_threshold || mem.size() < 2)
       brute_force_cluster(P, mem, k, lists, pairs);
     else
-      greedy_cluster(P, mem, (uint32_t)c, k, seed, greedy_rounds, greedy_random, lists, pairs);
+      greedy_cluster(P, mem, (uint32_t)(c + cluster_base), k, seed, greedy_rounds, greedy_random,
+                     lists, pairs);
     for (size_t a = 0; a < mem.size(); ++a) {
       size_t s = (size_t)cptr[c] + a;
       write_row(lists[a], k, loc_id + s * k, loc_inter + s * k, loc_union + s * k);

@@ -37,7 +37,8 @@ class Options(C.Structure):
                 ("d_hash_table", C.c_void_p), ("gram_budget_bytes", C.c_int64),
                 ("d_keys", C.c_void_p), ("greedy_max_draws", C.c_int32),
                 ("sim_n_items", C.c_int32), ("d_sim_ptr", C.c_void_p), ("d_sim_items", C.c_void_p),
-                ("d_sim_bits", C.c_void_p), ("reserved", C.c_int32 * 2)]
+                ("d_sim_bits", C.c_void_p), ("fn_offset", C.c_int32),
+                ("cluster_base", C.c_int32)]
 
 
 class ModelConfig(C.Structure):
@@ -55,7 +56,7 @@ class Stats(C.Structure):
                 ("brute_gram_elems", C.c_int64), ("brute_rows", C.c_int32),
                 ("reserved", C.c_int32), ("brute_pairs", C.c_int64),
                 ("greedy_pairs", C.c_int64), ("tc_macs", C.c_int64), ("tc_clusters", C.c_int32),
-                ("tc_tiles", C.c_int32)]
+                ("tc_tiles", C.c_int32), ("select_general", C.c_int32), ("reserved2", C.c_int32)]
 
 
 _lib = None
@@ -136,7 +137,7 @@ def options(greedy_threshold=0, greedy_rounds=-1, greedy_random=0, strategy=STRA
             hash_table: torch.Tensor | None = None, gram_budget_bytes=0,
             keys: torch.Tensor | None = None, greedy_max_draws=0,
             sim: tuple | None = None, sim_n_items=0,
-            sim_bits: torch.Tensor | None = None) -> Options:
+            sim_bits: torch.Tensor | None = None, fn_offset=0, cluster_base=0) -> Options:
     """Options of the build; sim = (ptr, items) similarity profiles over
     sim_n_items items (e.g. c2_goldfinger's fingerprints), sim_bits their
     packed rows."""
@@ -154,6 +155,8 @@ def options(greedy_threshold=0, greedy_rounds=-1, greedy_random=0, strategy=STRA
     o.d_sim_ptr = None if sim is None else sim[0].data_ptr()
     o.d_sim_items = None if sim is None else sim[1].data_ptr()
     o.d_sim_bits = None if sim_bits is None else sim_bits.data_ptr()
+    o.fn_offset = fn_offset
+    o.cluster_base = cluster_base
     o._keep = (hash_table, keys, sim, sim_bits)   # keep the tensors alive with the options
     return o
 
@@ -392,7 +395,7 @@ def c2_get_stats(ws, stream=None) -> dict:
                 item_visits_brute=s.item_visits_brute, item_visits_greedy=s.item_visits_greedy,
                 brute_gram_elems=s.brute_gram_elems, brute_rows=s.brute_rows,
                 brute_pairs=s.brute_pairs, greedy_pairs=s.greedy_pairs, tc_macs=s.tc_macs,
-                tc_clusters=s.tc_clusters, tc_tiles=s.tc_tiles)
+                tc_clusters=s.tc_clusters, tc_tiles=s.tc_tiles, select_general=s.select_general)
 
 
 def c2_reset_status(ws, stream=None):

@@ -181,8 +181,7 @@ c2_status check_common(int32_t n, int32_t m, int32_t k, int32_t t, int32_t b, in
   if (!sizes_ok(n, m, k, t, b, N)) return C2_ERR_UNSUPPORTED;
   if ((int64_t)t * n >= (int64_t(1) << 31) - 1) return C2_ERR_UNSUPPORTED;
   if (opt) {
-    for (int i = 0; i < 2; ++i)
-      if (opt->reserved[i] != 0) return C2_ERR_INVALID_ARG;
+    if (opt->fn_offset < 0 || opt->cluster_base < 0) return C2_ERR_INVALID_ARG;
     if (opt->d_sim_ptr && (opt->sim_n_items < 1 || (!opt->d_sim_items && n > 0)))
       return C2_ERR_INVALID_ARG;
     if (opt->d_sim_bits && (opt->sim_n_items < 1 || opt->sim_n_items % 32))
@@ -227,6 +226,8 @@ void c2_default_options(c2_options* opt) {
   opt->d_sim_ptr = nullptr;
   opt->d_sim_items = nullptr;
   opt->d_sim_bits = nullptr;
+  opt->fn_offset = 0;
+  opt->cluster_base = 0;
 }
 
 const char* c2_status_string(c2_status s) {
@@ -291,6 +292,7 @@ c2_status c2_get_stats(const void* d_ws, c2_stream_t stream, c2_stats* out) {
   out->tc_macs = (int64_t)h.tc_macs;
   out->tc_clusters = h.tc_clusters;
   out->tc_tiles = h.tc_tiles;
+  out->select_general = h.select_general;
   return C2_OK;
 }
 

@@ -64,8 +64,8 @@ __global__ void __launch_bounds__(256) k_validate(const int32_t* __restrict__ pt
 // seed.  Stored item-major as uint16 [m][tp] so one 16-byte load serves 8
 // functions.
 __global__ void k_build_htab(uint16_t* __restrict__ htab, int32_t m, int32_t t, int32_t tp,
-                             int32_t b, uint64_t seed, const int32_t* __restrict__ explicit_h,
-                             DevHeader* hdr) {
+                             int32_t b, uint64_t seed, int32_t fn_offset,
+                             const int32_t* __restrict__ explicit_h, DevHeader* hdr) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (int64_t)m * tp) return;
   const int32_t x = (int32_t)(idx / tp), i = (int32_t)(idx % tp);
@@ -79,7 +79,9 @@ __global__ void k_build_htab(uint16_t* __restrict__ htab, int32_t m, int32_t t, 
       }
       hv = (uint32_t)v;
     } else {
-      const uint64_t key = sm64_mix(seed + (uint64_t)(i + 1) * 0x9E3779B97F4A7C15ull);
+      // the run's function fn_offset + i (a shard of the functions)
+      const uint64_t key =
+          sm64_mix(seed + (uint64_t)(fn_offset + i + 1) * 0x9E3779B97F4A7C15ull);
       const uint64_t z = sm64_mix(key ^ ((uint64_t)(uint32_t)x * 0xC2B2AE3D27D4EB4Full));
       hv = (uint32_t)(((z >> 32) * (uint64_t)(uint32_t)b) >> 32);
     }
@@ -428,7 +430,7 @@ c2_status run_frh_cluster(const int32_t* ptr, const int32_t* items, const Sizes&
   Prof p_hash(st, "hash_minhash_level0");
   if (s.m > 0)
     C2_LAUNCH(k_build_htab, div_up((int64_t)s.m * s.tp, T), T, 0, st, w.htab, s.m, s.t, s.tp, s.b, seed,
-                                                                 opt.d_hash_table, w.hdr);
+              opt.fn_offset, opt.d_hash_table, w.hdr);
   C2_CUDA_TRY(cudaMemsetAsync(w.hist, 0, (nbins + 1) * sizeof(int32_t), st));
   if (s.n > 0 && opt.d_keys)
     C2_LAUNCH(k_keys_given, div_up(S, T), T, 0, st, opt.d_keys, S, s.n, s.b, w.key, w.hist, w.hdr);

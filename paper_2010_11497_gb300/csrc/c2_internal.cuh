@@ -47,6 +47,8 @@ struct DevHeader {
   unsigned long long tc_macs;      // tensor-core multiply-adds issued for count matrices
   int32_t tc_clusters;             // count matrices computed on the tensor cores
   int32_t tc_tiles;                // their 128 x 256 tiles
+  int32_t select_general;          // brute-force rows the select kernel handed to the keyed path
+  int32_t pad2;
 };
 static_assert(sizeof(DevHeader) <= 256, "header must fit 256 bytes");
 

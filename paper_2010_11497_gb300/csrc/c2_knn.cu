@@ -947,30 +947,30 @@ static __device__ __noinline__ void row_topk_keyed(const RowTopkArgs& a, int w, 
 // estimate corrected by one step either way (every product below 2^32).
 __device__ __forceinline__ uint32_t jac_q16(uint32_t c, uint32_t u) {
   const uint32_t num = c << 16;
-  uint32_t q = (uint32_t)__float2uint_rz(__fmul_rn((float)num, __frcp_rn((float)u)));
+  // the float quotient is within 0.01 of num / u (relative error below 2^-21)
+  uint32_t q = (uint32_t)__float2uint_rz(__fdividef((float)num, (float)u));
   q = min(q, 65536u);
   if (q * u > num) --q;
   else if ((q + 1u) * u <= num) ++q;
   return min(q, 65535u);
 }
 
-// Brute-force rows by exact selection (keyed rows: unions below 2^16, rows of
-// at most kSelMaxM candidates): warp per member.  q = floor(65536 J) is exact
-// and monotone in J, so the k best candidates are among those whose q reaches
-// the k-th largest q.
-//  1. One pass over the count row computes q for every candidate into shared
-//     memory (0 for the member itself and for candidates with no common item)
-//     and each lane's largest q.  The k-th largest of the 32 lane maxima, T0,
-//     is at most the row's k-th largest q (k distinct candidates reach it).
-//  2. The candidates with q >= T0 -- few -- are histogrammed in 256 buckets
-//     over [T0, 65535] (a warp scan finds the bucket of the k-th largest),
-//     and if the buckets are wider than one value, the candidates of that
-//     bucket again by their low bits: the exact k-th largest q, qk.
-//  3. The candidates with q >= qk (at most 64) are staged as exact order keys
-//     and sorted (two warp sorts and a bitonic merge): the top k.
-// Rows with more than 64 candidates tied at qk, or longer than kSelMaxM, go
-// through the general keyed path.
-constexpr int kSelMaxM = 2048;
+// Brute-force rows by exact selection (keyed rows: unions below 2^16): warp
+// per member.  q = floor(65536 J) is exact and monotone in J, so the k best
+// candidates are among those whose q reaches the row's k-th largest q.
+//  1. One pass over the count row finds each lane's best candidate (exact
+//     cross-multiplication); T0 = the k-th largest of the 32 lanes' q is at
+//     most the row's k-th largest q (k distinct candidates reach it).
+//  2. A second pass stages every candidate with q >= T0 (tested exactly as
+//     c * 2^16 >= T0 * u) -- typically a few k of them, at most kSelStage.
+//  3. In shared memory: the staged q are histogrammed in 256 buckets over
+//     [T0, 65535] (and the bucket of the k-th largest again by its low bits
+//     when buckets are wider than one value), giving the exact k-th largest
+//     q, qk; the staged candidates with q >= qk (at most 64) get exact order
+//     keys and are sorted (one or two warp sorts and a bitonic merge).
+// Rows with more than kSelStage candidates above T0, or more than 64 at or
+// above qk, go through the general keyed path.
+constexpr int kSelStage = 256;
 
 // k-th largest (1-based) of the lanes' values (k <= 32): a warp bitonic sort.
 __device__ __forceinline__ uint32_t warp_kth_largest(uint32_t v, int k) {
@@ -1028,98 +1028,130 @@ __device__ __forceinline__ int hist_select(const uint32_t* hist, int need, uint3
   return __shfl_sync(0xffffffffu, b, L);
 }
 
-__global__ void __launch_bounds__(kNT, 4) k_gram_select(const __grid_constant__ RowTopkArgs a) {
-  __shared__ uint16_t s_q[kNT / 32][kSelMaxM];
+__global__ void __launch_bounds__(kNT, 6) k_gram_select(const __grid_constant__ RowTopkArgs a) {
+  __shared__ uint2 s_stage[kNT / 32][kSelStage];   // (pos | lid << 16, c | u << 16)
   __shared__ uint32_t s_hist[kNT / 32][256];
-  __shared__ uint64_t s_stage[kNT / 32][64];
-  __shared__ uint2 s_scu[kNT / 32][64];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (w >= *a.n_users_dev || dev_failed(a.hdr)) return;
+  uint2* stg = s_stage[warp];
+  uint32_t* hist = s_hist[warp];
   const int slot = a.u_slot[w];
   const int c = a.gcl[a.u_g[w]];
   const int cs = a.cptr[c], M = a.cptr[c + 1] - cs, Mp = (M + 7) & ~7;
-  if (M > kSelMaxM) {
-    row_topk_keyed(a, w, s_scu[warp]);
-    return;
-  }
-  uint16_t* Q = s_q[warp];
-  uint32_t* hist = s_hist[warp];
-  uint64_t* stg = s_stage[warp];
   const int P = a.ipos[slot];
   const uint16_t* row = a.gram + a.gofs[c] + (int64_t)P * Mp;
   const int2* info = a.iinfo + cs;
   const uint32_t my = (uint32_t)a.slen[slot];
   const int k = a.k;
-  // 1. every candidate's q into shared memory, the lanes' maxima
-  uint32_t qmax = 0u;
+  // 1. each lane's best candidate by J (ties need not be broken here)
+  uint32_t bc = 0u, bu = 1u;
 #pragma unroll 4
   for (int p = lane; p < M; p += 32) {
     const uint32_t cc = p != P ? (uint32_t)row[p] : 0u;
-    uint32_t q = 0u;
-    if (cc) q = jac_q16(cc, my + (uint32_t)info[p].y - cc) + 1u;   // 0 = not a candidate
-    Q[p] = (uint16_t)min(q, 65535u);
-    qmax = max(qmax, q);
+    if (cc == 0u) continue;
+    const uint32_t u = my + (uint32_t)info[p].y - cc;
+    if (cc * bu > bc * u) { bc = cc; bu = u; }
   }
-  const uint32_t T0 = max(warp_kth_largest(qmax, k), 1u);   // floor of the k-th largest
-  // 2. histogram of q >= T0 over [T0, 65535] in 256 buckets of width 2^sh
-  const int sh = max(0, 32 - __clz((int)(65535u - T0)) - 8);
-#pragma unroll
-  for (int i = 0; i < 8; ++i) hist[lane + 32 * i] = 0u;
-  __syncwarp();
-  for (int p = lane; p < M; p += 32) {
-    const uint32_t q = Q[p];
-    if (q >= T0) atomicAdd(&hist[(q - T0) >> sh], 1u);
-  }
-  __syncwarp();
-  uint32_t above = 0u;
-  const int b1 = hist_select(hist, k, &above);
-  uint32_t qk;    // the exact k-th largest q (T0 when fewer than k candidates reach T0)
-  bool ok = true;
-  if (b1 < 0) {
-    qk = T0;
-  } else if (sh == 0) {
-    qk = T0 + (uint32_t)b1;
-    ok = above + hist[b1] <= 64u;
-  } else {
-    const uint32_t lo = T0 + ((uint32_t)b1 << sh);
-    __syncwarp();
-#pragma unroll
-    for (int i = 0; i < 8; ++i) hist[lane + 32 * i] = 0u;
-    __syncwarp();
-    for (int p = lane; p < M; p += 32) {
-      const uint32_t q = Q[p];
-      if (q >= lo && q < lo + (1u << sh)) atomicAdd(&hist[q - lo], 1u);
-    }
-    __syncwarp();
-    uint32_t above2 = 0u;
-    const int b2 = hist_select(hist, k - (int)above, &above2);
-    qk = lo + (uint32_t)(b2 < 0 ? 0 : b2);
-    ok = b2 >= 0 && above + above2 + hist[b2] <= 64u;
-  }
-  if (!__all_sync(0xffffffffu, ok)) {
-    row_topk_keyed(a, w, s_scu[warp]);
-    return;
-  }
-  // 3. stage the candidates with q >= qk, sort their exact keys
+  const uint32_t qbest = bc ? jac_q16(bc, bu) : 0u;
+  const uint32_t T0 = warp_kth_largest(qbest, k);   // 0: fewer than k lanes have a candidate
+  // 2. stage the candidates with q >= T0 (every candidate when T0 = 0)
   int n = 0;
+  bool ok = true;
+#pragma unroll 2
   for (int p0 = 0; p0 < M; p0 += 32) {
     const int p = p0 + lane;
-    const bool pass = p < M && (uint32_t)Q[p] >= qk;
-    const unsigned m = __ballot_sync(0xffffffffu, pass);
-    if (pass) {
-      const uint32_t cc = (uint32_t)row[p];
-      const int2 in = info[p];
-      stg[n + __popc(m & lanemask_lt())] = nbr_key(cc, my + (uint32_t)in.y - cc, in.x, p);
+    bool pass = false;
+    uint32_t cc = 0u, u = 0u;
+    int2 in = make_int2(0, 0);
+    if (p < M && p != P) {
+      cc = (uint32_t)row[p];
+      if (cc) {
+        in = info[p];
+        u = my + (uint32_t)in.y - cc;
+        pass = (cc << 16) >= T0 * u;
+      }
     }
+    const unsigned m = __ballot_sync(0xffffffffu, pass);
+    if (n + __popc(m) > kSelStage) {
+      ok = false;
+      break;
+    }
+    if (pass)
+      stg[n + __popc(m & lanemask_lt())] =
+          make_uint2((uint32_t)p | ((uint32_t)in.x << 16), cc | (u << 16));
     n += __popc(m);
   }
+  if (!ok) {
+    if (lane == 0) atomicAdd(&a.hdr->select_general, 1);
+    row_topk_keyed(a, w, stg);
+    return;
+  }
   __syncwarp();
-  uint64_t x = lane < n ? stg[lane] : 0ull;
-  x = warp_sort32_keys(x);
+  // 3. the exact k-th largest q among the staged, when more than 64 are staged
+  uint32_t qk = 0u;
+  if (n > 64) {
+    auto q_at = [&](int i) -> uint32_t {   // staged entry i's q (0xFFFFFFFF past the end)
+      if (i >= n) return 0xFFFFFFFFu;
+      const uint32_t x = stg[i].y;
+      return jac_q16(x & 0xFFFFu, x >> 16);
+    };
+    const int sh = max(0, 32 - __clz((int)(65535u - T0)) - 8);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) hist[lane + 32 * e] = 0u;
+    __syncwarp();
+    for (int i = lane; i < n; i += 32) atomicAdd(&hist[(q_at(i) - T0) >> sh], 1u);
+    __syncwarp();
+    uint32_t above = 0u;
+    const int b1 = hist_select(hist, k, &above);   // n > 64 >= k: b1 >= 0
+    if (sh == 0) {
+      qk = T0 + (uint32_t)b1;
+      ok = above + hist[b1] <= 64u;
+    } else {
+      const uint32_t lo = T0 + ((uint32_t)b1 << sh);
+      __syncwarp();
+#pragma unroll
+      for (int e = 0; e < 8; ++e) hist[lane + 32 * e] = 0u;
+      __syncwarp();
+      for (int i = lane; i < n; i += 32) {
+        const uint32_t q = q_at(i);
+        if (q >= lo && q < lo + (1u << sh)) atomicAdd(&hist[q - lo], 1u);
+      }
+      __syncwarp();
+      uint32_t above2 = 0u;
+      const int b2 = hist_select(hist, k - (int)above, &above2);
+      qk = lo + (uint32_t)(b2 < 0 ? 0 : b2);
+      ok = b2 >= 0 && above + above2 + hist[b2] <= 64u;
+    }
+    if (!__all_sync(0xffffffffu, ok)) {
+      if (lane == 0) atomicAdd(&a.hdr->select_general, 1);
+      row_topk_keyed(a, w, stg);
+      return;
+    }
+    // compact the staged with q >= qk to the front, in place: chunk e is read
+    // before it is written, and writes never reach a later chunk
+    int m_n = 0;
+    for (int i0 = 0; i0 < n; i0 += 32) {
+      const int i = i0 + lane;
+      const uint2 x = i < n ? stg[i] : make_uint2(0u, 0u);
+      const bool pass = i < n && jac_q16(x.y & 0xFFFFu, x.y >> 16) >= qk;
+      __syncwarp();
+      const unsigned m = __ballot_sync(0xffffffffu, pass);
+      if (pass) stg[m_n + __popc(m & lanemask_lt())] = x;
+      m_n += __popc(m);
+      __syncwarp();
+    }
+    n = m_n;
+  }
+  // exact order keys of the (at most 64) selected, sorted
+  auto key_of = [&](int i) -> uint64_t {
+    if (i >= n) return 0ull;
+    const uint2 x = stg[i];
+    return nbr_key(x.y & 0xFFFFu, x.y >> 16, (int32_t)(x.x >> 16), (int32_t)(x.x & 0xFFFFu));
+  };
+  uint64_t x = warp_sort32_keys(key_of(lane));
   if (n > 32) {
-    uint64_t y = lane + 32 < n ? stg[lane + 32] : 0ull;
-    y = warp_sort32_keys(y);
+    const uint64_t y = warp_sort32_keys(key_of(lane + 32));
     const uint64_t r = __shfl_sync(0xffffffffu, y, 31 - lane);
     x = r > x ? r : x;
 #pragma unroll
@@ -1561,6 +1593,7 @@ struct GreedyArgs {
   unsigned* counter;
   int32_t k, round, n_random, mcap;
   int32_t max_draws;       // bound on the round-0 draws per member
+  uint32_t cluster_base;   // the run's number of cluster 0 (Philox counter word 0)
   uint2 key;               // Philox key = run seed
   const int32_t* ipos;     // slot -> internal position
   const int2* iinfo;       // internal slot -> (local index, profile length)
@@ -1610,7 +1643,8 @@ __global__ void __launch_bounds__(kNT) k_greedy_init(GreedyArgs a) {
         if (lane == 0) dev_fail(a.hdr, C2_ERR_TIMEOUT);
         break;
       }
-      const uint4 r = philox10(make_uint4((uint32_t)c, (uint32_t)l, 0u, (uint32_t)(j0 + lane)), a.key);
+      const uint4 r = philox10(
+          make_uint4((uint32_t)c + a.cluster_base, (uint32_t)l, 0u, (uint32_t)(j0 + lane)), a.key);
       const int v = draw_other(r.x, l, M);
       const unsigned peers = __match_any_sync(0xffffffffu, v);
       const bool first = (peers & lanemask_lt()) == 0;
@@ -1836,7 +1870,8 @@ __global__ void __launch_bounds__(kNT, 4) k_greedy_round(GreedyArgs a) {
       for (int d0 = 0; d0 < a.n_random; d0 += 32) {
         int v = -1;
         if (d0 + lane < a.n_random) {
-          const uint4 r = philox10(make_uint4((uint32_t)c, (uint32_t)lid_me, (uint32_t)a.round,
+          const uint4 r = philox10(make_uint4((uint32_t)c + a.cluster_base, (uint32_t)lid_me,
+                                              (uint32_t)a.round,
                                               (uint32_t)(d0 + lane)), a.key);
           v = a.ipos[cs + draw_other(r.x, lid_me, M)];
         }
@@ -2575,6 +2610,7 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
       ga.ipos = w.ipos; ga.iinfo = w.iinfo;
       ga.k = k; ga.n_random = opt.greedy_random; ga.key = key;
       ga.max_draws = opt.greedy_max_draws > 0 ? opt.greedy_max_draws : (1 << 24);
+      ga.cluster_base = (uint32_t)opt.cluster_base;
       ga.out_id = lid; ga.out_in = lin; ga.out_un = lun; ga.hdr = w.hdr;
       ga.mcap = (mmax + 31) & ~31;
       {

@@ -31,7 +31,7 @@ def test_status_strings(lib):
 def test_default_options(lib):
     o = c2.options()
     assert o.greedy_threshold == 0 and o.greedy_rounds == -1 and o.strategy == -1
-    assert list(o.reserved) == [0] * 2 and o.d_keys is None and o.greedy_max_draws == 0
+    assert o.fn_offset == 0 and o.cluster_base == 0 and o.d_keys is None and o.greedy_max_draws == 0
     assert o.d_sim_ptr is None and o.d_sim_bits is None and o.sim_n_items == 0
 
 
@@ -67,8 +67,8 @@ def test_host_argument_errors_need_no_gpu(lib):
     rc = lib.c2_build_knn_graph(fake, fake, 10, 10, 5, 2, 8, 4, 1, C.byref(o), fake, fake, fake,
                                 C.c_void_p(4096 + 8), 1 << 30, None)
     assert rc == 4
-    # non-zero reserved option fields
-    o.reserved[1] = 1
+    # negative shard offsets
+    o.fn_offset = -1
     rc = lib.c2_build_knn_graph(fake, fake, 10, 10, 5, 2, 8, 4, 1, C.byref(o), fake, fake, fake,
                                 C.c_void_p(4096), 1 << 30, None)
     assert rc == 1

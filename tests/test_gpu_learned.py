@@ -254,3 +254,39 @@ def test_learned_fallback_device_error_is_returned(c2):
         model.build_knn_graph(dptr, ditems, m_items, k, n, seed, opts=opts,
                               quality_threshold=2.0, n_probe=200)
     assert e.value.code == 6
+
+
+def test_trained_proposer_gains_over_frh_on_held_out_data(c2):
+    # The gain of the network over the method without it: trained on the
+    # plain-C^2 graphs of two seeds, evaluated on a third seed of the same
+    # world (profiles with community structure), at equal t, b and N the
+    # learned keys give a graph of higher quality (Eq. 2 against the exact
+    # graph) than FastRandomHash keys.
+    from paper_2010_11497_gb300.train_proposer import positive_pairs
+    n, m_items, k, t, b, N = 5000, 2000, 10, 4, 32, 400
+
+    def data(seed):
+        ptr, items = synth.random_profiles(n, m_items, 30, seed, mu=0.8, n_comm=16)
+        return dev(ptr), dev(items)
+
+    train = []
+    for s in (201, 202):
+        dptr, ditems = data(s)
+        nid, _, _ = c2.c2_build_knn_graph(dptr, ditems, m_items, k, t, b, N, s)
+        train.append((dptr, ditems, positive_pairs(nid)))
+    model = _model(c2, t=t, b=b, seed=16)
+    rng = np.random.default_rng(0)
+    for step in range(300):
+        tptr, titems, pairs = train[step % 2]
+        idx = torch.from_numpy(rng.integers(0, pairs.shape[0], 4096)).cuda()
+        model.train_step(tptr, titems, pairs[idx].contiguous(), lr=3e-3, lam=3.0)
+    dptr, ditems = data(203)
+    _, jin, jun = c2.c2_bruteforce_knn(dptr, ditems, m_items, k)
+    judge = c2.c2_avg_sim(jin, jun)
+    _, fin, fun = c2.c2_build_knn_graph(dptr, ditems, m_items, k, t, b, N, 203)
+    q_frh = c2.c2_avg_sim(fin, fun) / judge
+    keys = model.propose(dptr, ditems)
+    _, lin, lun = c2.c2_build_knn_graph(dptr, ditems, m_items, k, t, b, N, 203,
+                                        opts=c2.options(keys=keys))
+    q_learned = c2.c2_avg_sim(lin, lun) / judge
+    assert q_learned > q_frh + 0.02, (q_frh, q_learned)

@@ -536,3 +536,23 @@ def test_minhash_keys_and_build(c2):
     assert_same(gin, oin, "nbr_inter")
     assert_same(gun, oun, "nbr_union")
     assert st["pairs"] == pairs
+
+
+@pytest.mark.parametrize("G", [2, 4])
+def test_logical_shards_equal_one_call(c2, G):
+    # sharding by hash function: G shards of t/G functions each (fn_offset,
+    # cluster_base), their rows concatenated in function order and merged,
+    # equal one call with all t functions and the oracle; greedy clusters
+    # included (their random starts draw with the run's cluster numbers)
+    from paper_2010_11497_gb300.shard import build_knn_graph_sharded
+    ptr, items = synth.random_profiles(3000, 400, 20, 27, zipf_s=1.1)
+    m, k, t, b, N, seed, thr = 400, 10, 4, 8, 600, 17, 150
+    kw = dict(greedy_threshold=thr, greedy_rounds=3)
+    ref = c2.c2_build_knn_graph(to_dev(ptr), to_dev(items), m, k, t, b, N, seed,
+                                opts=c2.options(**kw))
+    got = build_knn_graph_sharded(to_dev(ptr), to_dev(items), m, k, t, b, N, seed, shards=G, **kw)
+    for a, r in zip(got, ref):
+        assert torch.equal(a, r)
+    oid, oin, oun, _ = oracle.build_graph(ptr, items, m, k, t, b, N, seed, thr, 3)
+    assert_same(got[0], oid, "nbr_id")
+    assert_same(got[2], oun, "nbr_union")
