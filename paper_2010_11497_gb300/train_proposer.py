@@ -58,7 +58,7 @@ def quality(ptr, items, n_items, k, nbr_inter, nbr_union, judge=None):
 
 
 def run(workload="learned_ml20m", train_seeds=(6, 7, 8, 9), steps=400, batch=8192, lr=2e-3,
-        lam=10.0, dim=64, hidden=256, rows_log2=18, model_seed=2010, mu=0.0, log=print,
+        lam=3.0, dim=64, hidden=256, rows_log2=18, model_seed=2010, mu=0.0, log=print,
         lams=None):
     """Trains one model per balance weight in `lams` (default: [lam]) on the
     same training graphs; returns the results and the model of the best
@@ -177,7 +177,9 @@ def main():
     ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--batch", type=int, default=8192)
     ap.add_argument("--lr", type=float, default=2e-3)
-    ap.add_argument("--lam", type=float, default=10.0)
+    ap.add_argument("--lam", type=float, default=3.0,
+                    help="balance weight (3: best quality on the workload's own profiles; 10 on "
+                         "profiles with community structure)")
     ap.add_argument("--lams", type=float, nargs="*", default=None)
     ap.add_argument("--mu", type=float, default=0.0)
     ap.add_argument("--save", default="")
