@@ -80,6 +80,9 @@ def parse():
     ap.add_argument("--strategy", type=int, default=-1,
                     help="count-matrix strategy: -1 autotuned (default), 0 merge, 1-2 table, "
                          "3 tensor cores")
+    ap.add_argument("--autotune-cache", default="",
+                    help="autotuner table file: loaded before the warm-ups when present, saved "
+                         "after them (a profiled run then repeats the decisions of a plain one)")
     ap.add_argument("--gram-budget-mb", type=int, default=0,
                     help="cap on count matrices held at once (0 = library default)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
@@ -499,11 +502,15 @@ def main():
         c2.c2_build_knn_graph(ptr, items, w.n_items, w.k, w.t, wb, wN, seed, opts=opts, ws=ws,
                               out=out, check=False)
 
+    if args.autotune_cache and os.path.exists(args.autotune_cache):
+        c2.c2_autotune_load(args.autotune_cache)
     for _ in range(max(3, args.warmup)):
         flush.zero_()
         step()
     torch.cuda.synchronize()
     assert c2.c2_get_status(ws) == 0, "build reported a device error"
+    if args.autotune_cache:
+        c2.c2_autotune_save(args.autotune_cache)
     stats = c2.c2_get_stats(ws)
 
     # timed region

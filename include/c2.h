@@ -430,6 +430,16 @@ int64_t c2_kernel_launches(void);
  * writes the process-wide table as a JSON array into buf (like
  * c2_profile_report) and returns the bytes the full report needs. */
 size_t c2_autotune_report(char* buf, size_t len);
+/* The autotuner's table on disk (a text file, one line per problem size):
+ * c2_autotune_save writes the process's table to `path` (0, or -1 when the
+ * file cannot be written); c2_autotune_load merges a saved table into the
+ * process's (entries of the same sizes are replaced; table shapes this
+ * library does not have are measured again) and returns the number of
+ * entries read, or -1 when `path` is missing or not such a table.  Loaded
+ * decisions are used as if measured in this process, so later builds repeat
+ * them (e.g. under a profiler, which changes the timings).  Host only. */
+int32_t c2_autotune_save(const char* path);
+int32_t c2_autotune_load(const char* path);
 void c2_profile_enable(int on);
 size_t c2_profile_report(char* buf, size_t len);
 

@@ -106,6 +106,8 @@ _SIGS = {
     "c2_merge_topk_noalloc_max_slots": (C.c_int64, []),
     "c2_kernel_launches": (C.c_int64, []),
     "c2_autotune_report": (C.c_size_t, [C.c_char_p, C.c_size_t]),
+    "c2_autotune_save": (C.c_int32, [C.c_char_p]),
+    "c2_autotune_load": (C.c_int32, [C.c_char_p]),
     "c2_profile_enable": (None, [C.c_int]),
     "c2_profile_report": (C.c_size_t, [C.c_char_p, C.c_size_t]),
 }
@@ -404,6 +406,14 @@ def c2_reset_status(ws, stream=None):
 
 def c2_status_string(code: int) -> str:
     return lib().c2_status_string(code).decode()
+
+
+def c2_autotune_save(path: str) -> int:
+    return int(lib().c2_autotune_save(str(path).encode()))
+
+
+def c2_autotune_load(path: str) -> int:
+    return int(lib().c2_autotune_load(str(path).encode()))
 
 
 def c2_autotune_report() -> list:

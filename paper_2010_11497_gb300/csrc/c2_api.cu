@@ -502,6 +502,8 @@ c2_status c2_avg_sim(const int32_t* d_nbr_inter, const int32_t* d_nbr_union, int
 }
 
 size_t c2_autotune_report(char* buf, size_t len) { return c2::autotune_report(buf, len); }
+int32_t c2_autotune_save(const char* path) { return path ? c2::autotune_save(path) : -1; }
+int32_t c2_autotune_load(const char* path) { return path ? c2::autotune_load(path) : -1; }
 
 size_t c2_goldfinger_workspace_size(int32_t n_users) {
   if (n_users < 0) return 0;

@@ -203,41 +203,59 @@ __global__ void k_mark_oversized(const int32_t* __restrict__ lsize, const int32_
 
 // For every slot of an oversized cluster with last key eta:
 //   next = min { h_i(x) : x in P_u, h_i(x) > eta }   (b when undefined)
-// and count the sub-groups.  One warp per slot, 8 slots per warp-group.
+// and count the sub-groups.  One warp per user: the user's oversized slots
+// of a group of 8 functions are served by one walk over its profile, each
+// item's 16-byte hash row giving all 8 functions' values.
 __global__ void k_split_keys(const int32_t* __restrict__ ptr, const int32_t* __restrict__ items,
-                             const uint16_t* __restrict__ htab, int32_t n, int64_t S, int32_t tp,
+                             const uint16_t* __restrict__ htab, int32_t n, int32_t t, int32_t tp,
                              int32_t b, const int32_t* __restrict__ lab,
                              const int32_t* __restrict__ ovscan, const int32_t* __restrict__ leta,
                              int32_t* __restrict__ nextkey, int32_t* __restrict__ subcnt,
                              const DevHeader* hdr) {
   if (dev_failed(hdr)) return;
   const int lane = threadIdx.x & 31;
-  const int64_t s0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) & ~int64_t(31);
-  const int64_t my = s0 + lane;
-  bool ov = false;
-  int32_t l = 0;
-  if (my < S) {
-    l = lab[my];
-    ov = ovscan[l + 1] != ovscan[l];
-  }
-  unsigned todo = __ballot_sync(0xffffffffu, ov);
-  while (todo) {
-    const int src = __ffs(todo) - 1;
-    todo &= todo - 1;
-    const int64_t s = s0 + src;
-    const int32_t ls = __shfl_sync(0xffffffffu, l, src);
-    const int64_t i = s / n, u = s % n;
-    const int32_t eta = leta[ls];
-    uint32_t best = (uint32_t)b;
-    for (int32_t j = ptr[u] + lane; j < ptr[u + 1]; j += 32) {
-      const uint32_t hv = htab[(int64_t)items[j] * tp + i];
-      if ((int32_t)hv > eta) best = min(best, hv);
+  const int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (u >= n) return;
+  const int32_t s0 = ptr[u], e0 = ptr[u + 1];
+  for (int c = 0; c < t; c += 8) {
+    // lane q < 8 looks up function c + q's slot: oversized?, its label and eta
+    int32_t l = 0, eta = 0;
+    bool ov = false;
+    if (lane < 8 && c + lane < t) {
+      l = lab[(int64_t)(c + lane) * n + u];
+      ov = ovscan[l + 1] != ovscan[l];
+      eta = leta[l];
+    }
+    const unsigned ovm = __ballot_sync(0xffffffffu, ov) & 0xFFu;
+    if (ovm == 0u) continue;
+    int32_t et[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) et[q] = __shfl_sync(0xffffffffu, eta, q);
+    uint32_t best[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) best[q] = (uint32_t)b;
+    for (int32_t j = s0 + lane; j < e0; j += 32) {
+      const uint4 hv = *reinterpret_cast<const uint4*>(htab + (int64_t)items[j] * tp + c);
+      const uint32_t w[4] = {hv.x, hv.y, hv.z, hv.w};
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const uint32_t v = (w[q >> 1] >> (16 * (q & 1))) & 0xFFFFu;
+        if (((ovm >> q) & 1u) && (int32_t)v > et[q]) best[q] = min(best[q], v);
+      }
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(0xffffffffu, best, o));
-    if (lane == 0) {
-      nextkey[s] = (int32_t)best;
-      atomicAdd(&subcnt[(int64_t)ovscan[ls] * (b + 1) + best], 1);
+    for (int q = 0; q < 8; ++q) {
+      if (!((ovm >> q) & 1u)) continue;   // warp-uniform
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) best[q] = min(best[q], __shfl_xor_sync(0xffffffffu, best[q], o));
+    }
+    if (lane < 8 && ov) {
+      uint32_t mine = best[0];
+#pragma unroll
+      for (int q = 1; q < 8; ++q)
+        if (lane == q) mine = best[q];
+      nextkey[(int64_t)(c + lane) * n + u] = (int32_t)mine;
+      atomicAdd(&subcnt[(int64_t)ovscan[l] * (b + 1) + mine], 1);
     }
   }
 }
@@ -465,8 +483,8 @@ c2_status run_frh_cluster(const int32_t* ptr, const int32_t* items, const Sizes&
     if (O > s.omax) { out = C2_ERR_UNSUPPORTED; break; }
     C2_LAUNCH(k_ovlist, div_up(S, T), T, 0, st, w.ovidx, S, w.ovlist);
     cudaMemsetAsync(w.subcnt, 0, O * (s.b + 1) * sizeof(int32_t), st);
-    C2_LAUNCH(k_split_keys, div_up(S, T), T, 0, st, ptr, items, w.htab, s.n, S, s.tp, s.b, w.lab, w.ovidx,
-                                             w.leta, w.key, w.subcnt, w.hdr);
+    C2_LAUNCH(k_split_keys, div_up((int64_t)s.n * 32, T), T, 0, st, ptr, items, w.htab, s.n, s.t,
+              s.tp, s.b, w.lab, w.ovidx, w.leta, w.key, w.subcnt, w.hdr);
     C2_LAUNCH(k_split_plan, (unsigned)O, 256, 0, st, w.ovlist, s.b, w.subcnt, w.subrank, w.sub_resid,
                                                w.nchild, w.hdr);
     if (scan_exclusive(w.nchild, w.nchild, S, w.scan_tmp, st) != cudaSuccess) { out = C2_ERR_CUDA; break; }

@@ -717,5 +717,7 @@ c2_status run_exact_counts(const int32_t* ptr, const int32_t* items, int32_t n, 
 
 int num_sms();
 size_t autotune_report(char* buf, size_t len);
+int autotune_save(const char* path);
+int autotune_load(const char* path);
 
 }  // namespace c2

@@ -2432,7 +2432,9 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
           if (rc) return rc;
           rc = timed([&]() { return run_tc(members[bk], false); }, &t_tc);
           if (rc) return rc;
-          tune.route[bk] = t_tc < t_tab ? 1 : 0;
+          // the tensor cores must win clearly: routing any bucket to them adds the
+          // density count of every candidate cluster to each later build
+          tune.route[bk] = t_tc < 0.8f * t_tab ? 1 : 0;
           tune.table_ms[bk] = t_tab;
           tune.tc_ms[bk] = t_tc;
         }
@@ -2795,6 +2797,79 @@ size_t autotune_report(char* buf, size_t len) {
     buf[n] = 0;
   }
   return out.size() + 1;
+}
+
+// Text form of the autotuner's table, one line per problem size:
+//   n m t b N k thr unified shapes_done tc_done  (W NT MB ms) x kBuckets
+//   (route table_ms tc_ms) x (kBuckets * kDensityBuckets)
+// after a first line "c2-autotune 1".
+int autotune_save(const char* path) {
+  FILE* f = fopen(path, "w");
+  if (!f) return -1;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  fprintf(f, "c2-autotune 1\n");
+  for (const auto& kv : g_tune) {
+    const TuneKey& k = kv.first;
+    const TuneEntry& e = kv.second;
+    fprintf(f, "%lld %lld %lld %lld %lld %lld %lld %d %d %d", (long long)k.n, (long long)k.m,
+            (long long)k.t, (long long)k.b, (long long)k.N, (long long)k.k, (long long)k.thr,
+            e.unified ? 1 : 0, e.shapes_done ? 1 : 0, e.tc_done ? 1 : 0);
+    for (int q = 0; q < kBuckets; ++q)
+      fprintf(f, " %d %d %d %.6g", e.cfg[q].W, e.cfg[q].NT, e.cfg[q].MB, e.ms[q]);
+    for (int i = 0; i < kBuckets * kDensityBuckets; ++i)
+      fprintf(f, " %d %.6g %.6g", (int)e.route[i], e.table_ms[i], e.tc_ms[i]);
+    fprintf(f, "\n");
+  }
+  const int rc = ferror(f) ? -1 : 0;
+  fclose(f);
+  return rc;
+}
+
+// Reads a table written by autotune_save and merges it into the process's
+// table (its entries replace those of the same sizes).  Returns the number
+// of entries read, or -1 when the file is missing or not such a table.
+int autotune_load(const char* path) {
+  FILE* f = fopen(path, "r");
+  if (!f) return -1;
+  char magic[32] = {0};
+  int version = 0;
+  if (fscanf(f, "%31s %d", magic, &version) != 2 || strcmp(magic, "c2-autotune") || version != 1) {
+    fclose(f);
+    return -1;
+  }
+  std::map<TuneKey, TuneEntry> got;
+  for (;;) {
+    long long v[7];
+    int uni = 0, sd = 0, td = 0;
+    if (fscanf(f, "%lld %lld %lld %lld %lld %lld %lld %d %d %d", &v[0], &v[1], &v[2], &v[3], &v[4],
+               &v[5], &v[6], &uni, &sd, &td) != 10)
+      break;
+    TuneEntry e;
+    e.unified = uni != 0;
+    e.shapes_done = sd != 0;
+    e.tc_done = td != 0;
+    bool ok = true;
+    for (int q = 0; q < kBuckets && ok; ++q)
+      ok = fscanf(f, "%d %d %d %f", &e.cfg[q].W, &e.cfg[q].NT, &e.cfg[q].MB, &e.ms[q]) == 4;
+    for (int i = 0; i < kBuckets * kDensityBuckets && ok; ++i) {
+      int r = -1;
+      ok = fscanf(f, "%d %f %f", &r, &e.table_ms[i], &e.tc_ms[i]) == 3;
+      e.route[i] = (int8_t)(r < -1 || r > 1 ? -1 : r);
+    }
+    if (!ok) break;
+    // only shapes this build has are kept; anything else is measured again
+    for (int q = 0; q < kBuckets; ++q) {
+      bool known = false;
+      for (const TableCfg& c : kGramShapes)
+        known = known || (c.W == e.cfg[q].W && c.NT == e.cfg[q].NT && c.MB == e.cfg[q].MB);
+      if (!known) e.shapes_done = false;
+    }
+    got[TuneKey{v[0], v[1], v[2], v[3], v[4], v[5], v[6]}] = e;
+  }
+  fclose(f);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  for (const auto& kv : got) g_tune[kv.first] = kv.second;
+  return (int)got.size();
 }
 
 }  // namespace c2

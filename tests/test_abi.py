@@ -116,3 +116,21 @@ def test_goldfinger_and_exact_counts_argument_errors_need_no_gpu(lib):
     rc = lib.c2_build_knn_graph(fake, fake, 10, 10, 5, 2, 8, 4, 1, C.byref(o), fake, fake, fake,
                                 C.c_void_p(4096), 1 << 30, None)
     assert rc == 1
+
+
+def test_autotune_table_round_trip_needs_no_gpu(lib, tmp_path):
+    # a saved table is read back into the process's table (host only)
+    p = tmp_path / "tune.txt"
+    routes = " ".join("%d 0.5 0.25" % (1 if i == 7 else -1) for i in range(20))
+    shapes = " ".join("1 256 4 1.5" for _ in range(4))
+    p.write_text("c2-autotune 1\n123 456 8 4096 2000 30 4500 1 1 1 " + shapes + " " + routes + "\n")
+    assert c2.c2_autotune_load(str(p)) == 1
+    rep = [e for e in c2.c2_autotune_report() if e.get("n") == 123]
+    assert rep and rep[0]["m"] == 456 and rep[0]["buckets"][0]["threads"] == 256
+    assert [s["use"] for s in rep[0]["strategy"]] == ["tensor"]
+    q = tmp_path / "again.txt"
+    assert c2.c2_autotune_save(str(q)) == 0
+    assert "123 456 8 4096 2000 30 4500" in q.read_text()
+    assert c2.c2_autotune_load(str(tmp_path / "missing.txt")) == -1
+    (tmp_path / "bad.txt").write_text("not a table\n")
+    assert c2.c2_autotune_load(str(tmp_path / "bad.txt")) == -1
