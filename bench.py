@@ -640,10 +640,10 @@ def main():
                            "l2": "flushed (512 MiB write) before each step",
                            "parallelism": f"replicas{world}" if world > 1 else "single"},
                 "pairs_per_step": pairs, "gram_pairs_per_step": stats["gram_pairs"],
-                "intersections_per_step": stats["brute_pairs"] + stats["gram_pairs"],
+                "intersections_per_step": stats["brute_pairs"] + stats["greedy_pairs"],
                 "pairs_split": {"brute_force": stats["brute_pairs"],
                                 "greedy_evaluations": pairs - stats["brute_pairs"],
-                                "greedy_count_matrix_entries": stats["gram_pairs"]},
+                                "greedy_count_matrix_pairs": stats["greedy_pairs"]},
                 "quality": quality, "e2e": e2e, "gpu_launches": launches,
                 "gpu_launches_per_step": launches / args.steps,
                 "wall_s_timed": wall, "step_ms": step_ms,
