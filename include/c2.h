@@ -163,7 +163,9 @@ typedef struct {
   int32_t tc_tiles;         /* their 128 x 256 tiles                                       */
   int32_t select_general;   /* brute-force rows with more than 64 candidates tied at their
                                k-th value, ranked by the general path                      */
-  int32_t reserved2;
+  int32_t direct_users;     /* members of greedy clusters refined without a count matrix
+                               (over 10,240 members, or a matrix beyond gram_budget_bytes):
+                               their counts come from the profiles, one warp per member    */
 } c2_stats;
 
 /* Fills *opt with the defaults described above.  Never fails. */
@@ -222,8 +224,13 @@ c2_status c2_minhash_keys(const int32_t* d_csr_ptr, const int32_t* d_csr_items, 
  * Greedy clusters start from a random k-graph drawn with Philox4x32-10
  * (key = seed, counter = (cluster number, member index, round, draw)) and
  * refine every member's list with its neighbours' neighbours for
- * greedy_rounds synchronous rounds.  Synchronises `stream` once to size the
- * greedy phase. */
+ * greedy_rounds synchronous rounds.  A greedy cluster of more than 10,240
+ * members, or whose M x round_up(M, 8) 16-bit count matrix exceeds
+ * gram_budget_bytes, counts its similarities from the profiles instead (one
+ * warp per member; needs k + k^2 + greedy_random <= 1536, else
+ * C2_ERR_UNSUPPORTED); the rows are the same.  The CSR is not validated
+ * again: it must be the one c2_frh_cluster validated.  Synchronises `stream`
+ * once to size the greedy phase. */
 c2_status c2_cluster_knn(const int32_t* d_csr_ptr, const int32_t* d_csr_items, int32_t n_users,
                          int32_t n_items, int32_t t, const int32_t* d_cptr,
                          const int32_t* d_cusers, const int32_t* d_n_clusters, int32_t k,

@@ -56,7 +56,7 @@ class Stats(C.Structure):
                 ("brute_gram_elems", C.c_int64), ("brute_rows", C.c_int32),
                 ("reserved", C.c_int32), ("brute_pairs", C.c_int64),
                 ("greedy_pairs", C.c_int64), ("tc_macs", C.c_int64), ("tc_clusters", C.c_int32),
-                ("tc_tiles", C.c_int32), ("select_general", C.c_int32), ("reserved2", C.c_int32)]
+                ("tc_tiles", C.c_int32), ("select_general", C.c_int32), ("direct_users", C.c_int32)]
 
 
 _lib = None
@@ -397,7 +397,8 @@ def c2_get_stats(ws, stream=None) -> dict:
                 item_visits_brute=s.item_visits_brute, item_visits_greedy=s.item_visits_greedy,
                 brute_gram_elems=s.brute_gram_elems, brute_rows=s.brute_rows,
                 brute_pairs=s.brute_pairs, greedy_pairs=s.greedy_pairs, tc_macs=s.tc_macs,
-                tc_clusters=s.tc_clusters, tc_tiles=s.tc_tiles, select_general=s.select_general)
+                tc_clusters=s.tc_clusters, tc_tiles=s.tc_tiles, select_general=s.select_general,
+                direct_users=s.direct_users)
 
 
 def c2_reset_status(ws, stream=None):

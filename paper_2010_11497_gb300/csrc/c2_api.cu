@@ -111,6 +111,9 @@ void bind_knn_ws(Ws& w, const Sizes& s, KnnWs& c) {
   c.gorder = w.take<int32_t>(S + 1);
   c.gt_list = w.take<int32_t>(S + 1);
   c.rl_len = w.take<int32_t>(S + 1);
+  c.bg_flag = w.take<int32_t>(S + 1);
+  c.bg_off = w.take<int32_t>(S + 1);
+  c.bg_slot = w.take<int32_t>(S + 1);
   // tiles of one batch: at most 6 M^2 / (128 * 256) per cluster of M >= 128
   // members, and the batch's sum of M^2 is at most gram_budget / 2
   c.gt_work_cap = s.tc ? std::min<int64_t>(S + 64, 3 * s.gram_budget / 32768 + 64) : 0;
@@ -293,6 +296,7 @@ c2_status c2_get_stats(const void* d_ws, c2_stream_t stream, c2_stats* out) {
   out->tc_clusters = h.tc_clusters;
   out->tc_tiles = h.tc_tiles;
   out->select_general = h.select_general;
+  out->direct_users = h.direct_users;
   return C2_OK;
 }
 

@@ -124,14 +124,18 @@ __global__ void __launch_bounds__(256) k_minhash(const int32_t* __restrict__ ptr
       uint32_t mn[8];
 #pragma unroll
       for (int q = 0; q < 8; ++q) mn[q] = (uint32_t)b;
-      for (int32_t j = s + lane; j < e; j += 32) {
-        const int32_t x = items[j];
-        const uint4 hv = *reinterpret_cast<const uint4*>(htab + (int64_t)x * tp + c);
-        const uint32_t w[4] = {hv.x, hv.y, hv.z, hv.w};
+      // two items per lane and step: both loads and both hash rows in flight
+      for (int32_t j = s + lane; j < e; j += 64) {
+        const bool two = j + 32 < e;
+        const int32_t x0 = items[j];
+        const int32_t x1 = two ? items[j + 32] : x0;
+        const uint4 h0 = *reinterpret_cast<const uint4*>(htab + (int64_t)x0 * tp + c);
+        const uint4 h1 = *reinterpret_cast<const uint4*>(htab + (int64_t)x1 * tp + c);
+        const uint32_t w[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          mn[2 * q] = min(mn[2 * q], w[q] & 0xFFFFu);
-          mn[2 * q + 1] = min(mn[2 * q + 1], w[q] >> 16);
+          mn[2 * q] = min(mn[2 * q], min(w[q] & 0xFFFFu, w[q + 4] & 0xFFFFu));
+          mn[2 * q + 1] = min(mn[2 * q + 1], min(w[q] >> 16, w[q + 4] >> 16));
         }
       }
 #pragma unroll
@@ -252,13 +256,22 @@ __device__ __forceinline__ void split_keys_user(
     uint32_t best[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) best[q] = (uint32_t)b;
-    for (int32_t j = s0 + lane; j < e0; j += 32) {
-      const uint4 hv = *reinterpret_cast<const uint4*>(htab + (int64_t)items[j] * tp + c);
-      const uint32_t w[4] = {hv.x, hv.y, hv.z, hv.w};
+    // two items per lane and step: both loads and both hash rows in flight
+    for (int32_t j = s0 + lane; j < e0; j += 64) {
+      const bool two = j + 32 < e0;
+      const int32_t x0 = items[j];
+      const int32_t x1 = two ? items[j + 32] : x0;
+      const uint4 h0 = *reinterpret_cast<const uint4*>(htab + (int64_t)x0 * tp + c);
+      const uint4 h1 = *reinterpret_cast<const uint4*>(htab + (int64_t)x1 * tp + c);
+      const uint32_t w[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
-        const uint32_t v = (w[q >> 1] >> (16 * (q & 1))) & 0xFFFFu;
-        if (((ovm >> q) & 1u) && (int32_t)v > et[q]) best[q] = min(best[q], v);
+        const uint32_t v0 = (w[q >> 1] >> (16 * (q & 1))) & 0xFFFFu;
+        const uint32_t v1 = (w[4 + (q >> 1)] >> (16 * (q & 1))) & 0xFFFFu;
+        if ((ovm >> q) & 1u) {
+          if ((int32_t)v0 > et[q]) best[q] = min(best[q], v0);
+          if ((int32_t)v1 > et[q]) best[q] = min(best[q], v1);
+        }
       }
     }
 #pragma unroll

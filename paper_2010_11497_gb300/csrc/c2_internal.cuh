@@ -48,7 +48,7 @@ struct DevHeader {
   int32_t tc_clusters;             // count matrices computed on the tensor cores
   int32_t tc_tiles;                // their 128 x 256 tiles
   int32_t select_general;          // brute-force rows the select kernel handed to the keyed path
-  int32_t pad2;
+  int32_t direct_users;            // members of greedy clusters without a count matrix
 };
 static_assert(sizeof(DevHeader) <= 256, "header must fit 256 bytes");
 
@@ -173,6 +173,7 @@ struct KnnWs {
   int32_t* gorder;         // [S+1] per batch position: cluster (batch-relative), cost order
   int32_t* gt_list;        // [S+1] tensor-core clusters (count-matrix indices)
   int32_t* rl_len;         // [S+1] per slot: entries of its remapped list
+  int32_t *bg_flag, *bg_off, *bg_slot;  // [S+1] greedy members without a count matrix
   int4* gt_work;           // [gt_work_cap] (cluster, row tile, column tile, stages)
   int64_t gt_work_cap;
   uint16_t* rl;            // [t][rl_pn] remapped lists (absent when unused)
@@ -706,6 +707,16 @@ c2_status gram_tc_run(const int4* work, int n_work, const int32_t* cptr, const i
 int gram_tc_tile_rows();
 int gram_tc_tile_cols();
 int gram_tc_stage_cols();
+
+// Greedy clusters without a count matrix (c2_greedy_big.cu).
+bool big_greedy_supported(int32_t k, int32_t n_random);
+c2_status run_big_greedy(const int32_t* ptr, const int32_t* items, int32_t m, const int32_t* cptr,
+                         const int32_t* cusers, const int32_t* slot2c, const int32_t* gkind_c,
+                         int64_t S, int64_t n_users, int32_t k, int32_t rounds, int32_t n_random,
+                         int32_t max_draws, uint32_t cluster_base, uint2 key, int32_t* flag,
+                         int32_t* off, int32_t* bslot, int32_t* scan_tmp, int32_t* wl0,
+                         int32_t* wl1, int32_t* out_id, int32_t* out_in, int32_t* out_un,
+                         DevHeader* hdr, cudaStream_t st);
 
 // GoldFinger fingerprints and exact rescoring (c2_goldfinger.cu).
 size_t goldfinger_ws_bytes(int32_t n);

@@ -1388,13 +1388,15 @@ __global__ void k_fill_small(const int32_t* __restrict__ flag, const int32_t* __
 }
 
 // ------------------------------------------------------------------ preparation
-// Per cluster: does it get a count matrix (every greedy cluster, and brute-
-// force clusters of at least small_cut members), is it greedy, pair count;
-// singletons get an empty row (nobody else is in their cluster).
+// Per cluster: does it get a count matrix (greedy clusters up to kMaxGreedyM
+// members whose matrix fits the budget of cap elements, and brute-force
+// clusters of at least small_cut members), is it greedy (1 with a count
+// matrix, 2 without), pair count; singletons get an empty row (nobody else is
+// in their cluster).
 __global__ void k_prep(const int32_t* __restrict__ cptr, const int32_t* __restrict__ n_clusters,
                        const int32_t* __restrict__ cusers, const int32_t* __restrict__ ptr,
                        int64_t S, int32_t thr, int32_t small_cut, int32_t small_items, int32_t k,
-                       int32_t* __restrict__ gflag, int32_t* __restrict__ gkind,
+                       int64_t cap, int32_t* __restrict__ gflag, int32_t* __restrict__ gkind,
                        int32_t* __restrict__ small_cnt,
                        int32_t* __restrict__ lid, int32_t* __restrict__ lin,
                        int32_t* __restrict__ lun, DevHeader* hdr) {
@@ -1404,6 +1406,8 @@ __global__ void k_prep(const int32_t* __restrict__ cptr, const int32_t* __restri
   if (c < S && c < L) M = cptr[c + 1] - cptr[c];
   const bool brute = M >= 2 && M < thr;
   const bool greedy = M >= 2 && M >= thr;
+  const bool direct =
+      greedy && (M > kMaxGreedyM || (int64_t)M * (((int64_t)M + 7) & ~int64_t(7)) > cap);
   // small brute-force clusters whose profiles fit the per-warp stage go to
   // the warp-per-cluster kernel
   bool small = false;
@@ -1418,8 +1422,14 @@ __global__ void k_prep(const int32_t* __restrict__ cptr, const int32_t* __restri
   // counts are 16-bit: profiles of more than 65535 items are unsupported
   if (c == 0 && hdr->knn_max_len > 65535) dev_fail(hdr, C2_ERR_UNSUPPORTED);
   if (c < S) {
-    gflag[c] = (greedy || (brute && !small)) ? 1 : 0;
-    gkind[c] = greedy ? 1 : 0;
+    gflag[c] = ((greedy && !direct) || (brute && !small)) ? 1 : 0;
+    gkind[c] = direct ? 2 : (greedy ? 1 : 0);
+    if (direct) {
+      atomicMax(&hdr->max_cluster, M);
+      atomicAdd(&hdr->greedy_users, M);
+      atomicAdd(&hdr->n_greedy, 1);
+      atomicAdd(&hdr->direct_users, M);
+    }
     small_cnt[c] = small ? 1 : 0;
     if (M == 1) {
       const int64_t s = cptr[c];
@@ -2177,8 +2187,10 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
   C2_LAUNCH(k_set_count, 1, 1, 0, st, &w.hdr->knn_max_len, 0);
   C2_LAUNCH(k_slot_info, div_up(S, T), T, 0, st, cptr, n_clusters, cusers, ptr, S, w.slot2c,
             w.slen, w.hdr);
+  const int64_t cap = s.gram_budget / (int64_t)sizeof(uint16_t);
+  C2_LAUNCH(k_set_count, 1, 1, 0, st, &w.hdr->direct_users, 0);
   C2_LAUNCH(k_prep, div_up(S, T), T, 0, st, cptr, n_clusters, cusers, ptr, S, thr, small_cut,
-            kSmallItems, k, w.gflag, w.gkind_c, w.small_cnt, lid, lin, lun, w.hdr);
+            kSmallItems, k, cap, w.gflag, w.gkind_c, w.small_cnt, lid, lin, lun, w.hdr);
   C2_CUDA_TRY(cudaGetLastError());
   // the hashed count-matrix kernel is the candidate when no item table fits
   const bool hash_ok = !tc.W && opt.strategy != C2_STRATEGY_MERGE &&
@@ -2218,14 +2230,30 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
   C2_CUDA_TRY(scan_exclusive(w.gflag, w.gidx, S, w.scan_tmp, st));
   C2_LAUNCH(k_greedy_list, div_up(S, T), T, 0, st, w.gflag, w.gidx, w.gkind_c, cptr, S, w.gcl,
             w.gsq, w.gsz, w.gkind, w.hdr);
-  int32_t ng = 0, max_len = 0, nnz32 = 0;
+  int32_t ng = 0, max_len = 0, nnz32 = 0, n_direct = 0;
   C2_CUDA_TRY(cudaMemcpyAsync(&ng, &w.hdr->n_work, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  C2_CUDA_TRY(cudaMemcpyAsync(&n_direct, &w.hdr->direct_users, sizeof(int32_t),
+                              cudaMemcpyDeviceToHost, st));
   C2_CUDA_TRY(cudaMemcpyAsync(&max_len, &w.hdr->knn_max_len, sizeof(int32_t),
                               cudaMemcpyDeviceToHost, st));
   if (tc_allowed)
     C2_CUDA_TRY(cudaMemcpyAsync(&nnz32, ptr + s.n, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   C2_CUDA_TRY(cudaStreamSynchronize(st));
+  // greedy clusters without a count matrix: counts from the profiles, one
+  // warp per member (the working lists are free again before the batches)
+  p_gsetup.end();
+  if (n_direct > 0) {
+    Prof p_direct(st, "greedy_direct");
+    const uint2 dkey = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+    c2_status rc = run_big_greedy(
+        ptr, items, s.m, cptr, cusers, w.slot2c, w.gkind_c, S, n_direct, k, rounds,
+        opt.greedy_random, opt.greedy_max_draws > 0 ? opt.greedy_max_draws : (1 << 24),
+        (uint32_t)opt.cluster_base, dkey, w.bg_flag, w.bg_off, w.bg_slot, w.scan_tmp, w.wl0,
+        w.wl1, lid, lin, lun, w.hdr, st);
+    if (rc) return rc;
+  }
   if (ng == 0) return C2_OK;
+  Prof p_gsetup2(st, "gram_setup");
   const TuneKey tkey{s.n, s.m, s.t, s.b, s.N, k, thr};
   TuneEntry tune;
   if (opt.strategy == C2_STRATEGY_AUTO) {
@@ -2276,13 +2304,12 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
     C2_CUDA_TRY(cudaMemcpyAsync(gclh.data(), w.gcl, ng * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   }
   C2_CUDA_TRY(cudaStreamSynchronize(st));
-  const int64_t cap = s.gram_budget / (int64_t)sizeof(uint16_t);
   // exact 64-bit order keys need unions below 2^16 and clusters below 2^14
   bool keyed = max_len <= 32767;
   // hashed count matrices when every profile fits one pass of the hash table
   const bool use_hash = hash_ok && max_len <= kHashCap;
   for (int g = 0; g < ng; ++g) {
-    if ((gkind[g] && gsz[g] > kMaxGreedyM) || goff[g + 1] - goff[g] > cap) return C2_ERR_UNSUPPORTED;
+    if (goff[g + 1] - goff[g] > cap) return C2_ERR_UNSUPPORTED;   // brute force only
     if (gsz[g] > 16383) keyed = false;
   }
   C2_LAUNCH(k_iota, div_up(ng, T), T, 0, st, w.gseq, (int64_t)ng);
@@ -2294,7 +2321,7 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
   auto tc_bucket = [&](int g) {
     return size_bucket(gsz[g]) * kDensityBuckets + density_bucket(gsum[g], gsz[g], gk2[g]);
   };
-  p_gsetup.end();
+  p_gsetup2.end();
 
   GramArgs ga0{};
   ga0.ptr = ptr; ga0.items = items; ga0.pptr = w.pptr; ga0.pitems = w.pitems;

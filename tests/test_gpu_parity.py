@@ -110,14 +110,15 @@ def test_frh_ml1m_full(c2):
 
 
 # ------------------------------------------------------------------ Step 2
-def check_local(c2, ptr, items, m, t, b, N, k, seed, thr, rounds=10, nrand=0, strategy=-1):
+def check_local(c2, ptr, items, m, t, b, N, k, seed, thr, rounds=10, nrand=0, strategy=-1,
+                budget=0):
     o = oracle.frh_cluster(ptr, items, m, t, b, N, seed)
     li, lc, lu, pairs = oracle.cluster_knn(ptr, items, o["cptr"], o["cusers"], k, seed, thr,
                                            rounds, nrand)
     dptr, ditems = to_dev(ptr), to_dev(items)
     g = c2.c2_frh_cluster(dptr, ditems, m, t, b, N, seed)
     opts = c2.options(greedy_threshold=thr, greedy_rounds=rounds, greedy_random=nrand,
-                      strategy=strategy)
+                      strategy=strategy, gram_budget_bytes=budget)
     n = ptr.size - 1
     ws = c2.workspace(c2.workspace_size(n, items.size, m, k, t, b, N, opts), DEV)
     c2.c2_reset_status(ws)
@@ -173,6 +174,35 @@ def test_local_greedy_with_merge_counts(c2):
     # forced merge strategy: greedy clusters get their count rows by merges
     ptr, items = synth.random_profiles(2000, 400, 20, 24, zipf_s=1.1)
     check_local(c2, ptr, items, 400, 3, 8, 600, 10, 22, 150, 3, 0, strategy=0)
+
+
+@pytest.mark.parametrize("rounds,nrand", [(0, 0), (3, 0), (2, 5)])
+def test_local_greedy_direct_counts(c2, rounds, nrand):
+    # a count-matrix budget that holds every brute-force cluster (below 150
+    # members) but no greedy one: the greedy clusters count from the profiles
+    ptr, items = synth.random_profiles(2500, 400, 20, 14, zipf_s=1.1)
+    budget = 2 * 149 * 152
+    _, _, st = check_local(c2, ptr, items, 400, 3, 8, 600, 12, 21, 150, rounds, nrand,
+                           budget=budget)
+    assert st["direct_users"] == st["greedy_users"] > 0
+
+
+def test_local_greedy_direct_wide_items(c2):
+    # 100k items: no profile bitmap fits shared memory, counts come from merges
+    ptr, items = synth.random_profiles(3000, 100000, 14, 31, zipf_s=1.05)
+    _, _, st = check_local(c2, ptr, items, 100000, 2, 4, 900, 10, 5, 200, 3, 2,
+                           budget=2 * 199 * 200)
+    assert st["direct_users"] > 0
+
+
+def test_greedy_over_member_cap(c2):
+    # b = 1 and no split: one cluster of about 11,000 members, above the
+    # 10,240-member bound of the count-matrix greedy path
+    n, m, k = 11000, 2000, 10
+    ptr, items = synth.random_profiles(n, m, 12, 77, zipf_s=1.1)
+    _, _, st = check_local(c2, ptr, items, m, 1, 1, 20000, k, 8, 500, 2, 2)
+    assert st["max_cluster"] > 10240
+    assert st["direct_users"] == st["max_cluster"]
 
 
 def test_build_wide_items_with_greedy(c2):
@@ -380,15 +410,19 @@ def test_workspace_too_small(c2):
     assert e.value.code == 4
 
 
-def test_greedy_draw_bound_reports_timeout(c2):
+@pytest.mark.parametrize("budget", [0, 2 * 49 * 56])
+def test_greedy_draw_bound_reports_timeout(c2, budget):
     # The greedy random start's bounded loop: a bound below one batch of 32
     # draws stops every member's start, C2_ERR_TIMEOUT reaches the status
     # word, and the kernels after it (rounds, emit, merge) leave the outputs
-    # untouched.  The default bound gives the oracle's graph.
+    # untouched.  The default bound gives the oracle's graph.  The small budget
+    # holds the brute-force clusters' count matrices (below 50 members) and no
+    # greedy one: those take the path without count matrices.
     ptr, items = synth.random_profiles(1200, 300, 20, 51, zipf_s=1.1)
     n, m, k, t, b, N, seed, thr = 1200, 300, 8, 2, 4, 1200, 3, 50
     dptr, ditems = to_dev(ptr), to_dev(items)
-    opts = c2.options(greedy_threshold=thr, greedy_rounds=2, greedy_max_draws=1)
+    opts = c2.options(greedy_threshold=thr, greedy_rounds=2, greedy_max_draws=1,
+                      gram_budget_bytes=budget)
     ws = c2.workspace(c2.workspace_size(n, items.size, m, k, t, b, N, opts), DEV)
     out = [torch.full((n, k), -7, dtype=torch.int32, device=DEV) for _ in range(3)]
     c2.c2_build_knn_graph(dptr, ditems, m, k, t, b, N, seed, opts=opts, ws=ws, out=out,
