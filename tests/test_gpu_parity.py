@@ -433,7 +433,8 @@ def test_greedy_draw_bound_reports_timeout(c2, budget):
         assert bool((o == -7).all())
     # the same workspace, cleared by the next build, with the default bound
     gid, gin, gun = c2.c2_build_knn_graph(dptr, ditems, m, k, t, b, N, seed, ws=ws,
-                                          opts=c2.options(greedy_threshold=thr, greedy_rounds=2))
+                                          opts=c2.options(greedy_threshold=thr, greedy_rounds=2,
+                                                          gram_budget_bytes=budget))
     oid, oin, oun, _ = oracle.build_graph(ptr, items, m, k, t, b, N, seed, thr, 2)
     assert_same(gid, oid, "nbr_id")
     assert_same(gin, oin, "nbr_inter")
