@@ -91,75 +91,45 @@ __global__ void k_build_htab(uint16_t* __restrict__ htab, int32_t m, int32_t t, 
 
 // ------------------------------------------------------------------ A2: FRH keys
 // key[i][u] = min over u's items of h_i (Eq. 3); b for an empty profile.
-// One warp per user (persistent warps striding over the users); each lane
-// loads a 16-byte row of 8 hashes per item.  Also counts the level-0
-// histogram of (function, key): keys of many users coincide (the least
-// hashes of popular items), so each block sums its keys in a small
-// shared-memory cache of (bin, count) pairs and adds every cached bin to the
-// global histogram once at exit; a key whose cache slot holds another bin
-// goes to the global histogram directly.
-constexpr int kHistCache = 1024;
-constexpr uint32_t kCacheEmpty = 0xFFFFFFFFu;
-
-__global__ void __launch_bounds__(256) k_minhash(const int32_t* __restrict__ ptr,
-                                                 const int32_t* __restrict__ items,
-                                                 const uint16_t* __restrict__ htab, int32_t n,
-                                                 int32_t t, int32_t tp, int32_t b,
-                                                 int32_t* __restrict__ key,
-                                                 int32_t* __restrict__ hist, DevHeader* hdr) {
-  __shared__ uint32_t c_bin[kHistCache];
-  __shared__ uint32_t c_cnt[kHistCache];
-  for (int i = threadIdx.x; i < kHistCache; i += blockDim.x) {
-    c_bin[i] = kCacheEmpty;
-    c_cnt[i] = 0u;
-  }
-  __syncthreads();
+// One warp per user; each lane loads a 16-byte row of 8 hashes per item.
+// Also counts the level-0 histogram of (function, key).
+__global__ void k_minhash(const int32_t* __restrict__ ptr, const int32_t* __restrict__ items,
+                          const uint16_t* __restrict__ htab, int32_t n, int32_t t, int32_t tp,
+                          int32_t b, int32_t* __restrict__ key, int32_t* __restrict__ hist,
+                          DevHeader* hdr) {
+  if (dev_failed(hdr)) return;
   const int lane = threadIdx.x & 31;
-  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  const bool failed = dev_failed(hdr);
-  for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n && !failed;
-       u += nwarps) {
-    const int32_t s = ptr[u], e = ptr[u + 1];
-    for (int c = 0; c < tp; c += 8) {
-      uint32_t mn[8];
+  const int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (u >= n) return;
+  const int32_t s = ptr[u], e = ptr[u + 1];
+  for (int c = 0; c < tp; c += 8) {
+    uint32_t mn[8];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) mn[q] = (uint32_t)b;
-      // two items per lane and step: both loads and both hash rows in flight
-      for (int32_t j = s + lane; j < e; j += 64) {
-        const bool two = j + 32 < e;
-        const int32_t x0 = items[j];
-        const int32_t x1 = two ? items[j + 32] : x0;
-        const uint4 h0 = *reinterpret_cast<const uint4*>(htab + (int64_t)x0 * tp + c);
-        const uint4 h1 = *reinterpret_cast<const uint4*>(htab + (int64_t)x1 * tp + c);
-        const uint32_t w[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
+    for (int q = 0; q < 8; ++q) mn[q] = (uint32_t)b;
+    for (int32_t j = s + lane; j < e; j += 32) {
+      const int32_t x = items[j];
+      const uint4 hv = *reinterpret_cast<const uint4*>(htab + (int64_t)x * tp + c);
+      const uint32_t w[4] = {hv.x, hv.y, hv.z, hv.w};
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          mn[2 * q] = min(mn[2 * q], min(w[q] & 0xFFFFu, w[q + 4] & 0xFFFFu));
-          mn[2 * q + 1] = min(mn[2 * q + 1], min(w[q] >> 16, w[q + 4] >> 16));
-        }
+      for (int q = 0; q < 4; ++q) {
+        mn[2 * q] = min(mn[2 * q], w[q] & 0xFFFFu);
+        mn[2 * q + 1] = min(mn[2 * q + 1], w[q] >> 16);
       }
+    }
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
+    for (int q = 0; q < 8; ++q) {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) mn[q] = min(mn[q], __shfl_xor_sync(0xffffffffu, mn[q], o));
-      }
+      for (int o = 16; o > 0; o >>= 1) mn[q] = min(mn[q], __shfl_xor_sync(0xffffffffu, mn[q], o));
+    }
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int i = c + q;
-        if (lane == q && i < t) {
-          key[(int64_t)i * n + u] = (int32_t)mn[q];
-          const uint32_t bin = (uint32_t)i * (uint32_t)(b + 1) + mn[q];
-          const uint32_t slot = (bin * 2654435761u) >> 22;   // 10 bits: kHistCache slots
-          const uint32_t prev = atomicCAS(&c_bin[slot], kCacheEmpty, bin);
-          if (prev == kCacheEmpty || prev == bin) atomicAdd(&c_cnt[slot], 1u);
-          else atomicAdd(&hist[bin], 1);
-        }
+    for (int q = 0; q < 8; ++q) {
+      const int i = c + q;
+      if (lane == q && i < t) {
+        key[(int64_t)i * n + u] = (int32_t)mn[q];
+        atomicAdd(&hist[(int64_t)i * (b + 1) + mn[q]], 1);
       }
     }
   }
-  __syncthreads();
-  for (int i = threadIdx.x; i < kHistCache; i += blockDim.x)
-    if (c_cnt[i]) atomicAdd(&hist[c_bin[i]], (int32_t)c_cnt[i]);
 }
 
 // First-level keys given by the caller (a learned proposer): copy, check the
@@ -231,13 +201,21 @@ __global__ void k_mark_oversized(const int32_t* __restrict__ lsize, const int32_
   nchild[l] = live ? 1 : 0;
 }
 
-// The split keys of user u's oversized slots (see k_split_keys).
-__device__ __forceinline__ void split_keys_user(
-    const int32_t* __restrict__ ptr, const int32_t* __restrict__ items,
-    const uint16_t* __restrict__ htab, int32_t n, int32_t t, int32_t tp, int32_t b,
-    const int32_t* __restrict__ lab, const int32_t* __restrict__ ovscan,
-    const int32_t* __restrict__ leta, int32_t* __restrict__ nextkey, int32_t* __restrict__ subcnt,
-    int64_t u, int lane, uint32_t* c_bin, uint32_t* c_cnt) {
+// For every slot of an oversized cluster with last key eta:
+//   next = min { h_i(x) : x in P_u, h_i(x) > eta }   (b when undefined)
+// and count the sub-groups.  One warp per user: the user's oversized slots
+// of a group of 8 functions are served by one walk over its profile, each
+// item's 16-byte hash row giving all 8 functions' values.
+__global__ void k_split_keys(const int32_t* __restrict__ ptr, const int32_t* __restrict__ items,
+                             const uint16_t* __restrict__ htab, int32_t n, int32_t t, int32_t tp,
+                             int32_t b, const int32_t* __restrict__ lab,
+                             const int32_t* __restrict__ ovscan, const int32_t* __restrict__ leta,
+                             int32_t* __restrict__ nextkey, int32_t* __restrict__ subcnt,
+                             const DevHeader* hdr) {
+  if (dev_failed(hdr)) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (u >= n) return;
   const int32_t s0 = ptr[u], e0 = ptr[u + 1];
   for (int c = 0; c < t; c += 8) {
     // lane q < 8 looks up function c + q's slot: oversized?, its label and eta
@@ -256,22 +234,13 @@ __device__ __forceinline__ void split_keys_user(
     uint32_t best[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) best[q] = (uint32_t)b;
-    // two items per lane and step: both loads and both hash rows in flight
-    for (int32_t j = s0 + lane; j < e0; j += 64) {
-      const bool two = j + 32 < e0;
-      const int32_t x0 = items[j];
-      const int32_t x1 = two ? items[j + 32] : x0;
-      const uint4 h0 = *reinterpret_cast<const uint4*>(htab + (int64_t)x0 * tp + c);
-      const uint4 h1 = *reinterpret_cast<const uint4*>(htab + (int64_t)x1 * tp + c);
-      const uint32_t w[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
+    for (int32_t j = s0 + lane; j < e0; j += 32) {
+      const uint4 hv = *reinterpret_cast<const uint4*>(htab + (int64_t)items[j] * tp + c);
+      const uint32_t w[4] = {hv.x, hv.y, hv.z, hv.w};
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
-        const uint32_t v0 = (w[q >> 1] >> (16 * (q & 1))) & 0xFFFFu;
-        const uint32_t v1 = (w[4 + (q >> 1)] >> (16 * (q & 1))) & 0xFFFFu;
-        if ((ovm >> q) & 1u) {
-          if ((int32_t)v0 > et[q]) best[q] = min(best[q], v0);
-          if ((int32_t)v1 > et[q]) best[q] = min(best[q], v1);
-        }
+        const uint32_t v = (w[q >> 1] >> (16 * (q & 1))) & 0xFFFFu;
+        if (((ovm >> q) & 1u) && (int32_t)v > et[q]) best[q] = min(best[q], v);
       }
     }
 #pragma unroll
@@ -286,45 +255,9 @@ __device__ __forceinline__ void split_keys_user(
       for (int q = 1; q < 8; ++q)
         if (lane == q) mine = best[q];
       nextkey[(int64_t)(c + lane) * n + u] = (int32_t)mine;
-      const uint32_t bin = (uint32_t)ovscan[l] * (uint32_t)(b + 1) + mine;
-      const uint32_t slot = (bin * 2654435761u) >> 22;
-      const uint32_t prev = atomicCAS(&c_bin[slot], kCacheEmpty, bin);
-      if (prev == kCacheEmpty || prev == bin) atomicAdd(&c_cnt[slot], 1u);
-      else atomicAdd(&subcnt[bin], 1);
+      atomicAdd(&subcnt[(int64_t)ovscan[l] * (b + 1) + mine], 1);
     }
   }
-}
-
-// For every slot of an oversized cluster with last key eta:
-//   next = min { h_i(x) : x in P_u, h_i(x) > eta }   (b when undefined)
-// and count the sub-groups.  One warp per user (persistent warps striding
-// over the users): the user's oversized slots of a group of 8 functions are
-// served by one walk over its profile, each item's 16-byte hash row giving
-// all 8 functions' values.  Sub-group counts go through the block's cache of
-// (bin, count) pairs, as the level-0 histogram does.
-__global__ void __launch_bounds__(256) k_split_keys(
-    const int32_t* __restrict__ ptr, const int32_t* __restrict__ items,
-    const uint16_t* __restrict__ htab, int32_t n, int32_t t, int32_t tp, int32_t b,
-    const int32_t* __restrict__ lab, const int32_t* __restrict__ ovscan,
-    const int32_t* __restrict__ leta, int32_t* __restrict__ nextkey, int32_t* __restrict__ subcnt,
-    const DevHeader* hdr) {
-  __shared__ uint32_t c_bin[kHistCache];
-  __shared__ uint32_t c_cnt[kHistCache];
-  for (int i = threadIdx.x; i < kHistCache; i += blockDim.x) {
-    c_bin[i] = kCacheEmpty;
-    c_cnt[i] = 0u;
-  }
-  __syncthreads();
-  const int lane = threadIdx.x & 31;
-  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  const bool failed = dev_failed(hdr);
-  for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n && !failed;
-       u += nwarps)
-    split_keys_user(ptr, items, htab, n, t, tp, b, lab, ovscan, leta, nextkey, subcnt, u, lane,
-                    c_bin, c_cnt);
-  __syncthreads();
-  for (int i = threadIdx.x; i < kHistCache; i += blockDim.x)
-    if (c_cnt[i]) atomicAdd(&subcnt[c_bin[i]], (int32_t)c_cnt[i]);
 }
 
 // Per oversized cluster (one block): rank the sub-groups with >= 2 users in
@@ -520,8 +453,8 @@ c2_status run_frh_cluster(const int32_t* ptr, const int32_t* items, const Sizes&
   if (s.n > 0 && opt.d_keys)
     C2_LAUNCH(k_keys_given, div_up(S, T), T, 0, st, opt.d_keys, S, s.n, s.b, w.key, w.hist, w.hdr);
   else if (s.n > 0)
-    C2_LAUNCH(k_minhash, (int)std::min<int64_t>(div_up((int64_t)s.n * 32, 256), (int64_t)num_sms() * 8),
-              256, 0, st, ptr, items, w.htab, s.n, s.t, s.tp, s.b, w.key, w.hist, w.hdr);
+    C2_LAUNCH(k_minhash, div_up((int64_t)s.n * 32, T), T, 0, st, ptr, items, w.htab, s.n, s.t,
+              s.tp, s.b, w.key, w.hist, w.hdr);
   C2_LAUNCH(k_flag_nonzero, div_up(nbins, T), T, 0, st, w.hist, w.binlab, nbins);
   C2_CUDA_TRY(scan_exclusive(w.binlab, w.binlab, nbins, w.scan_tmp, st));
   C2_CUDA_TRY(cudaMemsetAsync(w.lsize, 0, (S + 1) * sizeof(int32_t), st));
@@ -550,10 +483,8 @@ c2_status run_frh_cluster(const int32_t* ptr, const int32_t* items, const Sizes&
     if (O > s.omax) { out = C2_ERR_UNSUPPORTED; break; }
     C2_LAUNCH(k_ovlist, div_up(S, T), T, 0, st, w.ovidx, S, w.ovlist);
     cudaMemsetAsync(w.subcnt, 0, O * (s.b + 1) * sizeof(int32_t), st);
-    C2_LAUNCH(k_split_keys,
-              (int)std::min<int64_t>(div_up((int64_t)s.n * 32, 256), (int64_t)num_sms() * 8), 256,
-              0, st, ptr, items, w.htab, s.n, s.t, s.tp, s.b, w.lab, w.ovidx, w.leta, w.key,
-              w.subcnt, w.hdr);
+    C2_LAUNCH(k_split_keys, div_up((int64_t)s.n * 32, T), T, 0, st, ptr, items, w.htab, s.n, s.t,
+              s.tp, s.b, w.lab, w.ovidx, w.leta, w.key, w.subcnt, w.hdr);
     C2_LAUNCH(k_split_plan, (unsigned)O, 256, 0, st, w.ovlist, s.b, w.subcnt, w.subrank, w.sub_resid,
                                                w.nchild, w.hdr);
     if (scan_exclusive(w.nchild, w.nchild, S, w.scan_tmp, st) != cudaSuccess) { out = C2_ERR_CUDA; break; }
