@@ -322,9 +322,8 @@ c2_status c2_exact_counts(const int32_t* d_csr_ptr, const int32_t* d_csr_items, 
                           int32_t* d_nbr_union, c2_stream_t stream);
 
 /* Step 3 without a workspace, for callers that cannot allocate device memory
- * when they merge (inside a stream capture without a memory pool, plug-ins
- * whose host owns every allocation, loops that forbid allocation after
- * start-up).  The paper has no counterpart: this is a deployment variant of
+ * when they merge (plug-ins whose host application owns every allocation,
+ * real-time loops that forbid allocation after start-up).  The paper has no counterpart: this is a deployment variant of
  * c2_merge_topk with the same arguments and results, minus the workspace.
  * Its scratch (a status word and one index per (function, user) pair) lives
  * in an 8 MiB array inside the library that every GPU loading the library

@@ -1,8 +1,7 @@
 // Step 3 (the per-user merge) for callers that cannot allocate device memory.
 //
-// Some callers cannot call cudaMalloc at the point where they merge: code
-// running inside a stream capture without a memory pool, plug-ins whose host
-// application owns every allocation, or real-time loops that forbid
+// Some callers cannot call cudaMalloc at the point where they merge: plug-ins
+// whose host application owns every allocation, or real-time loops that forbid
 // allocation after start-up.  They cannot provide the workspace the other
 // entry points need.  c2_merge_topk_noalloc runs the same merge kernels with
 // their scratch (the device status word and the slot index of every

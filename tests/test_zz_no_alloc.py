@@ -1,8 +1,8 @@
 """The workspace-free merge entry point (c2_merge_topk_noalloc).
 
 It exists for callers that cannot allocate device memory when they merge
-(inside a stream capture without a memory pool, plug-ins whose host owns every
-allocation); its scratch is a fixed array inside the library.  The local rows
+(plug-ins whose host application owns every allocation, loops that forbid
+allocation after start-up); its scratch is a fixed array inside the library.  The local rows
 it merges come from the CPU oracle, and its results are checked against the
 oracle's merge (Algorithm 3) and against the workspace entry point
 c2_merge_topk, on calls in a row.  This file is named so that pytest collects
