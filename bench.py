@@ -337,6 +337,7 @@ KERNEL_SOURCES = {
     "k_greedy_round": ["c2_knn.cu", "c2_internal.cuh"],
     "k_gram": ["c2_knn.cu", "c2_internal.cuh"],
     "k_gram_topk": ["c2_knn.cu", "c2_internal.cuh"],
+    "k_gram_select": ["c2_knn.cu", "c2_internal.cuh"],
     "k_merge": ["c2_merge.cu", "c2_internal.cuh"],
     "k_minhash": ["c2_cluster.cu", "c2_internal.cuh"],
 }
@@ -420,7 +421,10 @@ def phase_model(dom, phase_ms, phase_calls, stats, w, nnz, pk, W, steps):
                          f"{pk['bf16_tflops']:.0f} TFLOP/s"}
     if dom == "brute_rows" and stats.get("brute_rows"):
         bytes_ = 2 * stats["brute_gram_elems"] + 12 * k * stats["brute_rows"]
-        return hbm("k_gram_topk", bytes_ / per_build,
+        # exact selection serves keyed rows (every union below 2^16, clusters
+        # below 2^14 members); the general top-k kernel the others
+        keyed = 2 * stats.get("max_profile", 0) < 65536 and stats.get("max_cluster", 0) < 16384
+        return hbm("k_gram_select" if keyed else "k_gram_topk", bytes_ / per_build,
                    f"count rows read once (2 B x {stats['brute_gram_elems']:.3e} elements) + "
                    f"12 k B of list per row ({stats['brute_rows']} rows)")
     if dom == "merge":

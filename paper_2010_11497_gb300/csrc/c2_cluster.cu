@@ -90,44 +90,103 @@ __global__ void k_build_htab(uint16_t* __restrict__ htab, int32_t m, int32_t t, 
 }
 
 // ------------------------------------------------------------------ A2: FRH keys
+// The hash rows of one user's items, walked by a warp: lane l takes the
+// 16-byte chunks l, l + 32, ... of the row's items (one vector load for four
+// items; the chunk holding the array's last item is read item by item), then
+// loads the four items' rows of 8 hashes (16 bytes each) together, so a row
+// of up to 128 items costs two dependent loads per lane.  fn(hv) sees the
+// 8 hashes of functions c .. c + 7 of every item of [s, e) exactly once.
+// `vec` is false when the items array is not 16-byte aligned.
+template <class Fn>
+__device__ __forceinline__ void walk_hash_rows(const int32_t* __restrict__ items, int64_t nnz,
+                                               int32_t s, int32_t e, bool vec,
+                                               const uint16_t* __restrict__ htab, int32_t tp,
+                                               int32_t c, Fn&& fn) {
+  const int lane = threadIdx.x & 31;
+  if (!vec) {
+#pragma unroll 4
+    for (int32_t j = s + lane; j < e; j += 32)
+      fn(__ldg(reinterpret_cast<const uint4*>(htab + (int64_t)items[j] * tp + c)));
+    return;
+  }
+  for (int64_t j4 = (s >> 2) + lane; 4 * j4 < e; j4 += 32) {
+    int32_t xs[4];
+    if (4 * j4 + 4 <= nnz) {
+      const int4 v = __ldg(reinterpret_cast<const int4*>(items) + j4);
+      xs[0] = v.x; xs[1] = v.y; xs[2] = v.z; xs[3] = v.w;
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) xs[q] = 4 * j4 + q < nnz ? items[4 * j4 + q] : 0;
+    }
+    uint4 hv[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int64_t j = 4 * j4 + q;
+      if (j >= s && j < e) hv[q] = __ldg(reinterpret_cast<const uint4*>(htab + (int64_t)xs[q] * tp + c));
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int64_t j = 4 * j4 + q;
+      if (j >= s && j < e) fn(hv[q]);
+    }
+  }
+}
+
+// Minimum over the warp of each of the lanes' 8 values v[0..7], by halving
+// exchanges (4 + 2 + 1 shuffles, then 2 more): value q's minimum ends in the
+// four lanes with (lane >> 2) == q.
+__device__ __forceinline__ uint32_t warp_min8(const uint32_t v[8]) {
+  const int lane = threadIdx.x & 31;
+  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+  uint32_t r4[4], r2[2];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {   // keep values 4*b4 + q
+    const uint32_t keep = b4 ? v[q + 4] : v[q], send = b4 ? v[q] : v[q + 4];
+    r4[q] = min(keep, __shfl_xor_sync(0xffffffffu, send, 16));
+  }
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {   // keep values 4*b4 + 2*b3 + q
+    const uint32_t keep = b3 ? r4[q + 2] : r4[q], send = b3 ? r4[q] : r4[q + 2];
+    r2[q] = min(keep, __shfl_xor_sync(0xffffffffu, send, 8));
+  }
+  const uint32_t keep = b2 ? r2[1] : r2[0], send = b2 ? r2[0] : r2[1];
+  uint32_t r = min(keep, __shfl_xor_sync(0xffffffffu, send, 4));   // value lane >> 2
+  r = min(r, __shfl_xor_sync(0xffffffffu, r, 2));
+  return min(r, __shfl_xor_sync(0xffffffffu, r, 1));
+}
+
 // key[i][u] = min over u's items of h_i (Eq. 3); b for an empty profile.
-// One warp per user; each lane loads a 16-byte row of 8 hashes per item.
-// Also counts the level-0 histogram of (function, key).
-__global__ void k_minhash(const int32_t* __restrict__ ptr, const int32_t* __restrict__ items,
-                          const uint16_t* __restrict__ htab, int32_t n, int32_t t, int32_t tp,
-                          int32_t b, int32_t* __restrict__ key, int32_t* __restrict__ hist,
-                          DevHeader* hdr) {
+// One warp per user (hash rows walked by walk_hash_rows).  Also counts the
+// level-0 histogram of (function, key).
+__global__ void __launch_bounds__(256) k_minhash(const int32_t* __restrict__ ptr,
+                                                 const int32_t* __restrict__ items, int32_t vec,
+                                                 const uint16_t* __restrict__ htab,
+                                                 int32_t n, int32_t t, int32_t tp, int32_t b,
+                                                 int32_t* __restrict__ key,
+                                                 int32_t* __restrict__ hist, DevHeader* hdr) {
   if (dev_failed(hdr)) return;
   const int lane = threadIdx.x & 31;
   const int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (u >= n) return;
   const int32_t s = ptr[u], e = ptr[u + 1];
+  const int64_t nnz = ptr[n];   // validated: the items array holds ptr[n] entries
   for (int c = 0; c < tp; c += 8) {
     uint32_t mn[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) mn[q] = (uint32_t)b;
-    for (int32_t j = s + lane; j < e; j += 32) {
-      const int32_t x = items[j];
-      const uint4 hv = *reinterpret_cast<const uint4*>(htab + (int64_t)x * tp + c);
+    walk_hash_rows(items, nnz, s, e, vec != 0, htab, tp, c, [&](const uint4& hv) {
       const uint32_t w[4] = {hv.x, hv.y, hv.z, hv.w};
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         mn[2 * q] = min(mn[2 * q], w[q] & 0xFFFFu);
         mn[2 * q + 1] = min(mn[2 * q + 1], w[q] >> 16);
       }
-    }
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) mn[q] = min(mn[q], __shfl_xor_sync(0xffffffffu, mn[q], o));
-    }
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int i = c + q;
-      if (lane == q && i < t) {
-        key[(int64_t)i * n + u] = (int32_t)mn[q];
-        atomicAdd(&hist[(int64_t)i * (b + 1) + mn[q]], 1);
-      }
+    });
+    const uint32_t r = warp_min8(mn);
+    const int i = c + (lane >> 2);
+    if ((lane & 3) == 0 && i < t) {
+      key[(int64_t)i * n + u] = (int32_t)r;
+      atomicAdd(&hist[(int64_t)i * (b + 1) + r], 1);
     }
   }
 }
@@ -206,17 +265,18 @@ __global__ void k_mark_oversized(const int32_t* __restrict__ lsize, const int32_
 // and count the sub-groups.  One warp per user: the user's oversized slots
 // of a group of 8 functions are served by one walk over its profile, each
 // item's 16-byte hash row giving all 8 functions' values.
-__global__ void k_split_keys(const int32_t* __restrict__ ptr, const int32_t* __restrict__ items,
-                             const uint16_t* __restrict__ htab, int32_t n, int32_t t, int32_t tp,
-                             int32_t b, const int32_t* __restrict__ lab,
-                             const int32_t* __restrict__ ovscan, const int32_t* __restrict__ leta,
-                             int32_t* __restrict__ nextkey, int32_t* __restrict__ subcnt,
-                             const DevHeader* hdr) {
+__global__ void __launch_bounds__(256) k_split_keys(
+    const int32_t* __restrict__ ptr, const int32_t* __restrict__ items, int32_t vec,
+    const uint16_t* __restrict__ htab, int32_t n, int32_t t, int32_t tp, int32_t b,
+    const int32_t* __restrict__ lab, const int32_t* __restrict__ ovscan,
+    const int32_t* __restrict__ leta, int32_t* __restrict__ nextkey, int32_t* __restrict__ subcnt,
+    const DevHeader* hdr) {
   if (dev_failed(hdr)) return;
   const int lane = threadIdx.x & 31;
   const int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (u >= n) return;
   const int32_t s0 = ptr[u], e0 = ptr[u + 1];
+  const int64_t nnz = ptr[n];   // validated: the items array holds ptr[n] entries
   for (int c = 0; c < t; c += 8) {
     // lane q < 8 looks up function c + q's slot: oversized?, its label and eta
     int32_t l = 0, eta = 0;
@@ -234,26 +294,19 @@ __global__ void k_split_keys(const int32_t* __restrict__ ptr, const int32_t* __r
     uint32_t best[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) best[q] = (uint32_t)b;
-    for (int32_t j = s0 + lane; j < e0; j += 32) {
-      const uint4 hv = *reinterpret_cast<const uint4*>(htab + (int64_t)items[j] * tp + c);
+    walk_hash_rows(items, nnz, s0, e0, vec != 0, htab, tp, c, [&](const uint4& hv) {
       const uint32_t w[4] = {hv.x, hv.y, hv.z, hv.w};
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         const uint32_t v = (w[q >> 1] >> (16 * (q & 1))) & 0xFFFFu;
         if (((ovm >> q) & 1u) && (int32_t)v > et[q]) best[q] = min(best[q], v);
       }
-    }
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      if (!((ovm >> q) & 1u)) continue;   // warp-uniform
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) best[q] = min(best[q], __shfl_xor_sync(0xffffffffu, best[q], o));
-    }
+    });
+    const uint32_t r = warp_min8(best);
+    // function c + q's result sits in lanes 4q .. 4q + 3; lane q < 8 holds
+    // that slot's label
+    const uint32_t mine = __shfl_sync(0xffffffffu, r, 4 * (lane & 7));
     if (lane < 8 && ov) {
-      uint32_t mine = best[0];
-#pragma unroll
-      for (int q = 1; q < 8; ++q)
-        if (lane == q) mine = best[q];
       nextkey[(int64_t)(c + lane) * n + u] = (int32_t)mine;
       atomicAdd(&subcnt[(int64_t)ovscan[l] * (b + 1) + mine], 1);
     }
@@ -439,6 +492,8 @@ c2_status run_frh_cluster(const int32_t* ptr, const int32_t* items, const Sizes&
   const int64_t S = s.S;
   const int64_t nbins = (int64_t)s.t * (s.b + 1);
   const int T = 256;
+  // 16-byte item loads need a 16-byte aligned items array
+  const int32_t vec16 = ((uintptr_t)items & 15u) == 0 ? 1 : 0;
   c2_status rc;
   {
     Prof p(st, "validate");
@@ -453,8 +508,8 @@ c2_status run_frh_cluster(const int32_t* ptr, const int32_t* items, const Sizes&
   if (s.n > 0 && opt.d_keys)
     C2_LAUNCH(k_keys_given, div_up(S, T), T, 0, st, opt.d_keys, S, s.n, s.b, w.key, w.hist, w.hdr);
   else if (s.n > 0)
-    C2_LAUNCH(k_minhash, div_up((int64_t)s.n * 32, T), T, 0, st, ptr, items, w.htab, s.n, s.t,
-              s.tp, s.b, w.key, w.hist, w.hdr);
+    C2_LAUNCH(k_minhash, div_up((int64_t)s.n * 32, T), T, 0, st, ptr, items, vec16, w.htab,
+              s.n, s.t, s.tp, s.b, w.key, w.hist, w.hdr);
   C2_LAUNCH(k_flag_nonzero, div_up(nbins, T), T, 0, st, w.hist, w.binlab, nbins);
   C2_CUDA_TRY(scan_exclusive(w.binlab, w.binlab, nbins, w.scan_tmp, st));
   C2_CUDA_TRY(cudaMemsetAsync(w.lsize, 0, (S + 1) * sizeof(int32_t), st));
@@ -483,8 +538,8 @@ c2_status run_frh_cluster(const int32_t* ptr, const int32_t* items, const Sizes&
     if (O > s.omax) { out = C2_ERR_UNSUPPORTED; break; }
     C2_LAUNCH(k_ovlist, div_up(S, T), T, 0, st, w.ovidx, S, w.ovlist);
     cudaMemsetAsync(w.subcnt, 0, O * (s.b + 1) * sizeof(int32_t), st);
-    C2_LAUNCH(k_split_keys, div_up((int64_t)s.n * 32, T), T, 0, st, ptr, items, w.htab, s.n, s.t,
-              s.tp, s.b, w.lab, w.ovidx, w.leta, w.key, w.subcnt, w.hdr);
+    C2_LAUNCH(k_split_keys, div_up((int64_t)s.n * 32, T), T, 0, st, ptr, items, vec16,
+              w.htab, s.n, s.t, s.tp, s.b, w.lab, w.ovidx, w.leta, w.key, w.subcnt, w.hdr);
     C2_LAUNCH(k_split_plan, (unsigned)O, 256, 0, st, w.ovlist, s.b, w.subcnt, w.subrank, w.sub_resid,
                                                w.nchild, w.hdr);
     if (scan_exclusive(w.nchild, w.nchild, S, w.scan_tmp, st) != cudaSuccess) { out = C2_ERR_CUDA; break; }

@@ -958,16 +958,19 @@ __device__ __forceinline__ uint32_t jac_q16(uint32_t c, uint32_t u) {
 // Brute-force rows by exact selection (keyed rows: unions below 2^16): warp
 // per member.  q = floor(65536 J) is exact and monotone in J, so the k best
 // candidates are among those whose q reaches the row's k-th largest q.
-//  1. One pass over the count row finds each lane's best candidate (exact
-//     cross-multiplication); T0 = the k-th largest of the 32 lanes' q is at
-//     most the row's k-th largest q (k distinct candidates reach it).
+//  1. One pass over the count row (four candidates per lane and step, one
+//     8-byte load of counts) keeps each lane's two largest estimates of q (a
+//     float quotient, at most one above the exact q).  T0 = the k-th largest
+//     of these 64 estimates, minus one, is at most the row's k-th largest q
+//     (k distinct candidates reach it).
 //  2. A second pass stages every candidate with q >= T0 (tested exactly as
-//     c * 2^16 >= T0 * u) -- typically a few k of them, at most kSelStage.
-//  3. In shared memory: the staged q are histogrammed in 256 buckets over
-//     [T0, 65535] (and the bucket of the k-th largest again by its low bits
-//     when buckets are wider than one value), giving the exact k-th largest
-//     q, qk; the staged candidates with q >= qk (at most 64) get exact order
-//     keys and are sorted (one or two warp sorts and a bitonic merge).
+//     c * 2^16 >= T0 * u) -- typically a few more than k, at most kSelStage.
+//  3. In shared memory, when more than 64 are staged: the staged q are
+//     histogrammed in 256 buckets over [T0, 65535] (and the bucket of the k-th
+//     largest again by its low bits when buckets are wider than one value),
+//     giving the exact k-th largest q, qk; the staged candidates with q >= qk
+//     are kept.  The (at most 64) remaining get exact order keys and are
+//     sorted (one or two warp sorts and a bitonic merge).
 // Rows with more than kSelStage candidates above T0, or more than 64 at or
 // above qk, go through the general keyed path.
 constexpr int kSelStage = 256;
@@ -985,6 +988,37 @@ __device__ __forceinline__ uint32_t warp_kth_largest(uint32_t v, int k) {
       const bool take = (lower == best_first) ? (o > v) : (v > o);
       v = take ? o : v;
     }
+  }
+  return __shfl_sync(0xffffffffu, v, k - 1);
+}
+
+// Bitonic sort of one value per lane, largest first.
+__device__ __forceinline__ uint32_t warp_sort32_desc(uint32_t v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int size = 2; size <= 32; size <<= 1) {
+#pragma unroll
+    for (int j = size >> 1; j > 0; j >>= 1) {
+      const uint32_t o = __shfl_xor_sync(0xffffffffu, v, j);
+      const bool best_first = size == 32 || (lane & size) == 0;
+      const bool lower = (lane & j) == 0;
+      v = (lower == best_first) ? max(o, v) : min(o, v);
+    }
+  }
+  return v;
+}
+
+// k-th largest (1-based, k <= 32) of the 64 values a, b held by the lanes:
+// both sorted, the largest 32 of the two are a bitonic sequence, cleaned.
+__device__ __forceinline__ uint32_t warp_kth_largest64(uint32_t a, uint32_t b, int k) {
+  const int lane = threadIdx.x & 31;
+  a = warp_sort32_desc(a);
+  b = warp_sort32_desc(b);
+  uint32_t v = max(a, __shfl_sync(0xffffffffu, b, 31 - lane));
+#pragma unroll
+  for (int j = 16; j > 0; j >>= 1) {
+    const uint32_t o = __shfl_xor_sync(0xffffffffu, v, j);
+    v = (lane & j) == 0 ? max(o, v) : min(o, v);
   }
   return __shfl_sync(0xffffffffu, v, k - 1);
 }
@@ -1041,46 +1075,61 @@ __global__ void __launch_bounds__(kNT, 6) k_gram_select(const __grid_constant__ 
   const int cs = a.cptr[c], M = a.cptr[c + 1] - cs, Mp = (M + 7) & ~7;
   const int P = a.ipos[slot];
   const uint16_t* row = a.gram + a.gofs[c] + (int64_t)P * Mp;
+  // rows start on 16 bytes (matrices of M x Mp entries, Mp a multiple of 8)
+  const uint2* row4 = reinterpret_cast<const uint2*>(row);
+  const int M4 = (M + 3) >> 2;
   const int2* info = a.iinfo + cs;
   const uint32_t my = (uint32_t)a.slen[slot];
   const int k = a.k;
-  // 1. each lane's best candidate by J (ties need not be broken here)
-  uint32_t bc = 0u, bu = 1u;
-#pragma unroll 4
-  for (int p = lane; p < M; p += 32) {
-    const uint32_t cc = p != P ? (uint32_t)row[p] : 0u;
-    if (cc == 0u) continue;
-    const uint32_t u = my + (uint32_t)info[p].y - cc;
-    if (cc * bu > bc * u) { bc = cc; bu = u; }
+  // 1. each lane's two largest estimates of q
+  uint32_t q1 = 0u, q2 = 0u;
+#pragma unroll 2
+  for (int g = lane; g < M4; g += 32) {
+    const uint2 cw = row4[g];
+    const uint32_t cq[4] = {cw.x & 0xFFFFu, cw.x >> 16, cw.y & 0xFFFFu, cw.y >> 16};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int p = 4 * g + q;
+      if (p < M && p != P && cq[q]) {
+        const uint32_t u = my + (uint32_t)info[p].y - cq[q];
+        // within one of the exact quotient (relative error below 2^-21)
+        const uint32_t qe = __float2uint_rz(__fdividef((float)(cq[q] << 16), (float)u));
+        q2 = max(q2, min(q1, qe));
+        q1 = max(q1, qe);
+      }
+    }
   }
-  const uint32_t qbest = bc ? jac_q16(bc, bu) : 0u;
-  const uint32_t T0 = warp_kth_largest(qbest, k);   // 0: fewer than k lanes have a candidate
+  const uint32_t kth = warp_kth_largest64(q1, q2, k);   // 0: fewer than k candidates seen
+  const uint32_t T0 = kth ? kth - 1u : 0u;
   // 2. stage the candidates with q >= T0 (every candidate when T0 = 0)
   int n = 0;
   bool ok = true;
-#pragma unroll 2
-  for (int p0 = 0; p0 < M; p0 += 32) {
-    const int p = p0 + lane;
-    bool pass = false;
-    uint32_t cc = 0u, u = 0u;
-    int2 in = make_int2(0, 0);
-    if (p < M && p != P) {
-      cc = (uint32_t)row[p];
-      if (cc) {
+  for (int g0 = 0; g0 < M4 && ok; g0 += 32) {
+    const int g = g0 + lane;
+    uint2 cw = make_uint2(0u, 0u);
+    if (g < M4) cw = row4[g];
+    const uint32_t cq[4] = {cw.x & 0xFFFFu, cw.x >> 16, cw.y & 0xFFFFu, cw.y >> 16};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int p = 4 * g + q;
+      bool pass = false;
+      uint32_t u = 0u;
+      int2 in = make_int2(0, 0);
+      if (p < M && p != P && cq[q]) {
         in = info[p];
-        u = my + (uint32_t)in.y - cc;
-        pass = (cc << 16) >= T0 * u;
+        u = my + (uint32_t)in.y - cq[q];
+        pass = (cq[q] << 16) >= T0 * u;
       }
+      const unsigned m = __ballot_sync(0xffffffffu, pass);
+      if (n + __popc(m) > kSelStage) {
+        ok = false;
+        break;
+      }
+      if (pass)
+        stg[n + __popc(m & lanemask_lt())] =
+            make_uint2((uint32_t)p | ((uint32_t)in.x << 16), cq[q] | (u << 16));
+      n += __popc(m);
     }
-    const unsigned m = __ballot_sync(0xffffffffu, pass);
-    if (n + __popc(m) > kSelStage) {
-      ok = false;
-      break;
-    }
-    if (pass)
-      stg[n + __popc(m & lanemask_lt())] =
-          make_uint2((uint32_t)p | ((uint32_t)in.x << 16), cc | (u << 16));
-    n += __popc(m);
   }
   if (!ok) {
     if (lane == 0) atomicAdd(&a.hdr->select_general, 1);
