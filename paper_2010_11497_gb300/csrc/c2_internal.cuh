@@ -680,6 +680,12 @@ c2_status run_validate(const int32_t* ptr, const int32_t* items, const Sizes& s,
 // of slice s; A [M][K] and Bt [N][K] row-major BF16.  Timeouts of its bounded
 // waits are recorded in *status.
 bool tc_logits_ok(int K, int N, int b);
+// C[M][N] (FP32, row stride ldc) = A[M][K] . B[N][K]^T (+ bias[N]) on the tensor
+// cores (tcgen05), BF16 row-major operands, K a multiple of 64; 16-byte aligned
+// pointers.  Device-side timeouts go to *status.
+bool tc_gemm_ok(int M, int N, int K);
+c2_status tc_gemm(const __nv_bfloat16* A, const __nv_bfloat16* B, int M, int N, int K,
+                  const float* bias, float* C, int ldc, int32_t* status, cudaStream_t st);
 int tc_slice_width();
 c2_status tc_transpose_bf16(const __nv_bfloat16* B, int K, int N, __nv_bfloat16* Bt,
                             cudaStream_t st);

@@ -386,7 +386,7 @@ __global__ void __launch_bounds__(NT, MB > 0 ? MB : 1) k_gram(GramArgs a) {
               const uint32_t hi = (C[creg(j1)] >> (16 * chalf(j1))) & 0xFFFFu;
               wv[h] = lo | (hi << 16);
             }
-            dst[g8] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+            __stcs(dst + g8, make_uint4(wv[0], wv[1], wv[2], wv[3]));
           }
         }
         // column p of the tile's rows (the tile's own block is computed whole)
@@ -394,7 +394,9 @@ __global__ void __launch_bounds__(NT, MB > 0 ? MB : 1) k_gram(GramArgs a) {
           uint16_t* col = G0 + (int64_t)(tq * Q) * Mp + p;
 #pragma unroll
           for (int j = 0; j < Q; ++j)
-            if (j < nq) col[(int64_t)j * Mp] = (uint16_t)((C[creg(j)] >> (16 * chalf(j))) & 0xFFFFu);
+            if (j < nq)
+              __stcs(reinterpret_cast<unsigned short*>(col + (int64_t)j * Mp),
+                     (unsigned short)((C[creg(j)] >> (16 * chalf(j))) & 0xFFFFu));
         }
       }
     }

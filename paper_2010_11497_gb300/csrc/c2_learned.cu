@@ -85,8 +85,15 @@ struct ModelScratch {
   float* loss;           // [4]
   int32_t* rowlist;      // [rows] user of each row
   float2* part;          // [rows][T / slice] (max, argmax) per column slice (proposals)
-  __nv_bfloat16* w2t;    // [T][H] transposed W2 for the tcgen05 logits GEMM (proposals)
+  __nv_bfloat16* w2t;    // [T][H] transposed W2 for the tcgen05 logits GEMMs
+  __nv_bfloat16* hT;     // [H][rows] training: transposed operands of dW2 = h^T dz on the
+  __nv_bfloat16* dzT;    // [T][rows]   tensor cores (both K-major)
 };
+
+// Training GEMMs on the tensor cores (tcgen05): logits z = h W2 + b2,
+// dh = dz W2^T and dW2 = h^T dz need H and T multiples of 64 (and, per call,
+// a multiple of 64 rows); the small GEMMs (K or N = D) stay on mma.sync.
+bool tc_train_dims(const ModelDims& d) { return d.H % 64 == 0 && d.T % 64 == 0 && d.H <= 65536; }
 
 // How a proposal computes the per-head argmax:
 //   2: tcgen05 logits GEMM with the argmax of 256-column slices in its epilogue
@@ -115,6 +122,11 @@ size_t bind_scratch(char* base, const ModelDims& d, int rows, bool train, ModelS
   if (kind == 1) q.part = w.take<float2>((size_t)rows * (d.T / 128));
   q.rowlist = w.take<int32_t>(rows);
   q.loss = w.take<float>(4);
+  if (train && tc_train_dims(d)) {
+    q.w2t = w.take<__nv_bfloat16>((size_t)d.T * d.H);
+    q.hT = w.take<__nv_bfloat16>((size_t)d.H * rows);
+    q.dzT = w.take<__nv_bfloat16>((size_t)d.T * rows);
+  }
   if (train) {
     q.dz16 = w.take<__nv_bfloat16>((size_t)rows * d.T);
     q.dh = w.take<float>((size_t)rows * d.H);
@@ -765,9 +777,31 @@ bool fast_ok(int N, int K) { return N % FBN == 0 && K % FBK == 0; }
 // per-slice (max, argmax) partials instead of the logits.
 c2_status model_forward(const ModelDims& d, const ModelParams& p, const ModelScratch& s,
                         const int32_t* ptr, const int32_t* items, int nrows, cudaStream_t st,
-                        float2* part = nullptr) {
+                        float2* part = nullptr, int32_t* tc_status = nullptr) {
   c2_status rc0 = embbag_fwd(ptr, items, s.rowlist, nrows, p.E16, d.D, d.rows, d.seed, s.e, s.e16, st);
   if (rc0) return rc0;
+  if (tc_status) {
+    // hidden layer on mma.sync (K = D), logits on the tensor cores
+    c2_status rc;
+    if (fast_ok(d.H, d.D)) {
+      FastGemmArgs f1{};
+      f1.A = s.e16; f1.lda = d.D; f1.B = p.W1_16; f1.ldb = d.H;
+      f1.C = s.hpre; f1.C16 = s.h16; f1.ldc = d.H; f1.bias = p.b1; f1.relu = 1;
+      f1.M = nrows; f1.N = d.H; f1.K = d.D;
+      rc = gemm_fast(f1, st);
+    } else {
+      GemmArgs g1{};
+      g1.A = s.e16; g1.sam = d.D; g1.sak = 1;
+      g1.B = p.W1_16; g1.sbk = d.H; g1.sbn = 1;
+      g1.C = s.hpre; g1.C16 = s.h16; g1.ldc = d.H; g1.bias = p.b1; g1.relu = 1;
+      g1.M = nrows; g1.N = d.H; g1.K = d.D;
+      rc = gemm(g1, st);
+    }
+    if (rc) return rc;
+    rc = tc_transpose_bf16(p.W2_16, d.H, d.T, s.w2t, st);
+    if (rc) return rc;
+    return tc_gemm(s.h16, s.w2t, nrows, d.T, d.H, p.b2, s.z, d.T, tc_status, st);
+  }
   if (fast_ok(d.H, d.D) && fast_ok(d.T, d.H)) {
     FastGemmArgs f1{};
     f1.A = s.e16; f1.lda = d.D; f1.B = p.W1_16; f1.ldb = d.H;
@@ -842,8 +876,9 @@ c2_status model_grads(const ModelDims& d, const ModelParams& p, const ModelScrat
                       const int32_t* ptr, const int32_t* items, int n, const int32_t* pairs, int P,
                       float lambda, float* dz_debug, DevHeader* hdr, cudaStream_t st) {
   const int rows = 2 * P;
+  const bool tc = tc_train_dims(d) && rows % 64 == 0 && s.w2t;
   C2_LAUNCH(k_rowlist_pairs, div_up(P, 256), 256, 0, st, pairs, P, n, s.rowlist, hdr);
-  c2_status rc = model_forward(d, p, s, ptr, items, rows, st);
+  c2_status rc = model_forward(d, p, s, ptr, items, rows, st, nullptr, tc ? &hdr->status : nullptr);
   if (rc) return rc;
   C2_LAUNCH(k_softmax, div_up((int64_t)rows * d.t * 32, 256), 256, 0, st, s.z, rows, d.t, d.b, d.T);
   C2_LAUNCH(k_colmean, div_up(d.T, 256), 256, 0, st, s.z, rows, d.T, s.colmean);
@@ -851,21 +886,35 @@ c2_status model_grads(const ModelDims& d, const ModelParams& p, const ModelScrat
   C2_LAUNCH(k_pair_loss, div_up((int64_t)P * d.t * 32, 256), 256, 0, st, s.z, P, d.t, d.b, d.T,
             s.colmean, lambda, 1e-9f, s.dz16, dz_debug, s.loss);
   C2_LAUNCH(k_balance_loss, 1, 256, 0, st, s.colmean, d.T, d.t, d.b, lambda, s.loss);
-  // dW2 = h^T dz  [H][T];  db2 = sum_r dz
-  GemmArgs a{};
-  a.A = s.h16; a.sam = 1; a.sak = d.H;        // A(m=h, k=r) = h16[r][h]
-  a.B = s.dz16; a.sbk = d.T; a.sbn = 1;       // B(k=r, n=c) = dz[r][c]
-  a.C = s.gW2; a.ldc = d.T; a.M = d.H; a.N = d.T; a.K = rows;
-  rc = gemm(a, st);
-  if (rc) return rc;
+  if (tc) {
+    // dW2 = h^T dz [H][T] with both operands transposed (K = rows contiguous)
+    rc = tc_transpose_bf16(s.h16, rows, d.H, s.hT, st);
+    if (rc) return rc;
+    rc = tc_transpose_bf16(s.dz16, rows, d.T, s.dzT, st);
+    if (rc) return rc;
+    rc = tc_gemm(s.hT, s.dzT, d.H, d.T, rows, nullptr, s.gW2, d.T, &hdr->status, st);
+    if (rc) return rc;
+    // dh = dz W2^T [rows][H]: W2 [H][T] is already K-major
+    rc = tc_gemm(s.dz16, p.W2_16, rows, d.H, d.T, nullptr, s.dh, d.H, &hdr->status, st);
+    if (rc) return rc;
+  } else {
+    // dW2 = h^T dz  [H][T]
+    GemmArgs a{};
+    a.A = s.h16; a.sam = 1; a.sak = d.H;        // A(m=h, k=r) = h16[r][h]
+    a.B = s.dz16; a.sbk = d.T; a.sbn = 1;       // B(k=r, n=c) = dz[r][c]
+    a.C = s.gW2; a.ldc = d.T; a.M = d.H; a.N = d.T; a.K = rows;
+    rc = gemm(a, st);
+    if (rc) return rc;
+    // dh = dz W2^T  [rows][H]
+    GemmArgs b{};
+    b.A = s.dz16; b.sam = d.T; b.sak = 1;       // A(m=r, k=c) = dz[r][c]
+    b.B = p.W2_16; b.sbk = 1; b.sbn = d.T;      // B(k=c, n=h) = W2[h][c]
+    b.C = s.dh; b.ldc = d.H; b.M = rows; b.N = d.H; b.K = d.T;
+    rc = gemm(b, st);
+    if (rc) return rc;
+  }
+  // db2 = sum_r dz; dh is then masked by the ReLU
   C2_LAUNCH(k_colsum_bf16, div_up(d.T, 256), 256, 0, st, s.dz16, rows, d.T, s.gb2);
-  // dh = dz W2^T  [rows][H], masked by ReLU
-  GemmArgs b{};
-  b.A = s.dz16; b.sam = d.T; b.sak = 1;       // A(m=r, k=c) = dz[r][c]
-  b.B = p.W2_16; b.sbk = 1; b.sbn = d.T;      // B(k=c, n=h) = W2[h][c]
-  b.C = s.dh; b.ldc = d.H; b.M = rows; b.N = d.H; b.K = d.T;
-  rc = gemm(b, st);
-  if (rc) return rc;
   C2_LAUNCH(k_relu_bwd, div_up((int64_t)rows * d.H, 256), 256, 0, st, s.dh, s.hpre,
             (size_t)rows * d.H, s.dh16);
   // dW1 = e^T dh  [D][H];  db1 = sum_r dh

@@ -280,6 +280,224 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   }
 }
 
+// ---------------------------------------------------------------- general GEMM
+// C[M][N] (FP32, row stride ldc) = A[M][K] . B[N][K]^T (+ bias[N]), BF16
+// operands, FP32 accumulation: the training GEMMs of the learned proposer
+// (logits z = h W2, hidden gradient dh = dz W2^T, weight gradient
+// dW2 = h^T dz with both operands transposed first, so that every operand is
+// K-major).  Work item = (row tile of 128, column tile of 256, K chunk of
+// kc_per blocks of 64); CTAs (one per SM, persistent) walk contiguous ranges
+// of items.  A warp issues TMA loads of both operands (128-byte swizzle) into
+// a ring of stages; one thread issues tcgen05.mma (M = 128, N = 256, K = 16)
+// into one of two TMEM accumulators; eight epilogue warps read their rows
+// with tcgen05.ld and store them (16-byte stores), or add them with FP32
+// atomics when K is split over several items (C then starts at zero; the
+// bias is added by the first K chunk).  Bounded waits as in k_logits_tc.
+constexpr int GC_STAGES = 4;
+constexpr int GC_A_STAGE = TC_BM * TC_BK * 2;          // 16 KiB
+constexpr int GC_B_STAGE = TC_BN * TC_BK * 2;          // 32 KiB
+constexpr int GC_STAGE = GC_A_STAGE + GC_B_STAGE;
+constexpr int GC_NBARS = 2 * GC_STAGES + 2 + 2 + 1;
+constexpr size_t GC_SMEM = 1024 + (size_t)GC_STAGES * GC_STAGE + GC_NBARS * 8;
+
+struct GcArgs {
+  float* C;
+  const float* bias;   // [N] or null
+  int32_t* status;
+  int M, N, K, ldc;
+  int MT, NT, KS, kc_per;   // row tiles, column tiles, K chunks, 64-blocks per chunk
+  long long total;          // MT * NT * KS
+  int atomic;               // K split: add into C
+};
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+              GcArgs g) {
+  extern __shared__ uint8_t gc_smem_raw[];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_sh;
+  uint8_t* sm = (uint8_t*)(((uintptr_t)gc_smem_raw + 1023) & ~(uintptr_t)1023);
+  const int KB = g.K / TC_BK;   // 64-blocks of K
+  const uint32_t sbase = su32(sm);
+  const uint32_t bars = sbase + (uint32_t)GC_STAGES * GC_STAGE;
+  auto sfull = [&](int i) { return bars + 8u * i; };
+  auto sempty = [&](int i) { return bars + 8u * (GC_STAGES + i); };
+  auto accfull = [&](int i) { return bars + 8u * (2 * GC_STAGES + i); };
+  auto accempty = [&](int i) { return bars + 8u * (2 * GC_STAGES + 2 + i); };
+  const uint32_t bdone = bars + 8u * (2 * GC_STAGES + 4);
+  volatile int* abort_flag = &abort_sh;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long lo = g.total * blockIdx.x / gridDim.x;
+  const long long hi = g.total * (blockIdx.x + 1) / gridDim.x;
+  // item -> (row tile, column tile, K chunk), K chunk fastest
+  auto decode = [&](long long idx, int& mt, int& nt, int& ks) {
+    ks = (int)(idx % g.KS);
+    const long long r = idx / g.KS;
+    nt = (int)(r % g.NT);
+    mt = (int)(r / g.NT);
+  };
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < GC_STAGES; ++i) {
+      mbar_init(sfull(i), 1);
+      mbar_init(sempty(i), 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(accfull(i), 1);
+      mbar_init(accempty(i), TC_EPI_WARPS);
+    }
+    mbar_init(bdone, 1);
+    abort_sh = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    prefetch_map(&tmA);
+    prefetch_map(&tmB);
+  }
+  if (warp == 1) tmem_alloc(su32(&tmem_slot), TC_TMEM_COLS);
+  __syncwarp();
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer
+    int stage = 0;
+    uint32_t phase = 0;
+    int issued[GC_STAGES];
+    uint32_t last_par[GC_STAGES];
+    for (int i = 0; i < GC_STAGES; ++i) issued[i] = 0, last_par[i] = 0;
+    bool ok = true;
+    for (long long idx = lo; idx < hi && ok; ++idx) {
+      int mt, nt, ks;
+      decode(idx, mt, nt, ks);
+      const int kb0 = ks * g.kc_per, kb1 = min(KB, kb0 + g.kc_per);
+      for (int kb = kb0; kb < kb1; ++kb) {
+        if (!tc_wait(sempty(stage), phase ^ 1u, abort_flag, true)) {
+          ok = false;
+          break;
+        }
+        const uint32_t sa = sbase + (uint32_t)stage * GC_STAGE;
+        mbar_expect_tx(sfull(stage), (uint32_t)GC_STAGE);
+        tma_load_2d(sa, &tmA, kb * TC_BK, mt * TC_BM, sfull(stage));
+        tma_load_2d(sa + GC_A_STAGE, &tmB, kb * TC_BK, nt * TC_BN, sfull(stage));
+        issued[stage] = 1;
+        last_par[stage] = phase;
+        if (++stage == GC_STAGES) stage = 0, phase ^= 1u;
+      }
+    }
+    if (!ok) {
+      tc_abort(abort_flag, g.status);
+      for (int i = 0; i < GC_STAGES; ++i)
+        if (issued[i]) tc_wait(sfull(i), last_par[i], abort_flag, false);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer
+    int stage = 0;
+    uint32_t phase = 0;
+    long long t = 0;
+    bool ok = true;
+    for (long long idx = lo; idx < hi && ok; ++idx, ++t) {
+      int mt, nt, ks;
+      decode(idx, mt, nt, ks);
+      const int kb0 = ks * g.kc_per, kb1 = min(KB, kb0 + g.kc_per);
+      const int a = (int)(t & 1);
+      const uint32_t use = (uint32_t)(t >> 1);
+      if (!tc_wait(accempty(a), (use & 1u) ^ 1u, abort_flag, true)) {
+        ok = false;
+        break;
+      }
+      fence_after();
+      const uint32_t d = tmem + (uint32_t)(a * TC_BN);
+      for (int kb = kb0; kb < kb1; ++kb) {
+        if (!tc_wait(sfull(stage), phase, abort_flag, true)) {
+          ok = false;
+          break;
+        }
+        fence_after();
+        const uint32_t abase = sbase + (uint32_t)stage * GC_STAGE;
+        const uint32_t bbase = abase + GC_A_STAGE;
+#pragma unroll
+        for (int kk = 0; kk < TC_BK / 16; ++kk)
+          umma_f16(d, sw128_desc(abase + kk * 32), sw128_desc(bbase + kk * 32), TC_IDESC,
+                   (kb > kb0 || kk > 0) ? 1u : 0u);
+        umma_commit(sempty(stage));
+        if (++stage == GC_STAGES) stage = 0, phase ^= 1u;
+      }
+      if (!ok) break;
+      umma_commit(accfull(a));
+    }
+    if (!ok) tc_abort(abort_flag, g.status);
+    umma_commit(bdone);
+    tc_wait(bdone, 0, abort_flag, false);
+  } else if (warp >= 2) {
+    // ---------------- epilogue: rows 32q .. 32q + 31, columns h*128 .. h*128 + 127
+    const int q = warp & 3, h = (warp - 2) >> 2;
+    long long t = 0;
+    for (long long idx = lo; idx < hi; ++idx, ++t) {
+      int mt, nt, ks;
+      decode(idx, mt, nt, ks);
+      const int a = (int)(t & 1);
+      const uint32_t use = (uint32_t)(t >> 1);
+      const bool ready = __all_sync(0xffffffffu, tc_wait(accfull(a), use & 1u, abort_flag, true));
+      if (!ready) {
+        if (lane == 0) tc_abort(abort_flag, g.status);
+        break;
+      }
+      fence_after();
+      const int row = mt * TC_BM + 32 * q + lane;
+      const int col0 = nt * TC_BN + h * TC_EPI_COLS;
+      const uint32_t tbase =
+          tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(a * TC_BN + h * TC_EPI_COLS);
+      const bool add_bias = g.bias && ks == 0;
+      float* crow = g.C + (int64_t)row * g.ldc;
+      const bool vec = !g.atomic && (g.ldc & 3) == 0;
+#pragma unroll 1
+      for (int c32 = 0; c32 < TC_EPI_COLS; c32 += 32) {
+        uint32_t r[32];
+        tmem_ld32_async(tbase + c32, r);
+        tmem_wait(r);
+        const int cb = col0 + c32;
+        if (row < g.M) {
+          if (vec && cb + 32 <= g.N) {
+#pragma unroll
+            for (int j4 = 0; j4 < 8; ++j4) {
+              float4 v = make_float4(__uint_as_float(r[4 * j4]), __uint_as_float(r[4 * j4 + 1]),
+                                     __uint_as_float(r[4 * j4 + 2]), __uint_as_float(r[4 * j4 + 3]));
+              if (add_bias) {
+                const float4 bb = __ldg(reinterpret_cast<const float4*>(g.bias + cb) + j4);
+                v.x += bb.x; v.y += bb.y; v.z += bb.z; v.w += bb.w;
+              }
+              reinterpret_cast<float4*>(crow + cb)[j4] = v;
+            }
+          } else {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              const int col = cb + j;
+              if (col < g.N) {
+                float v = __uint_as_float(r[j]);
+                if (add_bias) v += g.bias[col];
+                if (g.atomic) atomicAdd(crow + col, v);
+                else crow[col] = v;
+              }
+            }
+          }
+        }
+      }
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(accempty(a));
+    }
+  }
+  __syncwarp();
+  fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    fence_after();
+    tmem_dealloc(tmem, TC_TMEM_COLS);
+  }
+}
+
 // Bt[j][k] = B[k][j] (BF16), 32 x 32 tiles through shared memory.
 __global__ void k_transpose_bf16(const __nv_bfloat16* __restrict__ B, int K, int N,
                                  __nv_bfloat16* __restrict__ Bt) {
@@ -359,6 +577,45 @@ c2_status tc_logits_argmax(const __nv_bfloat16* A, int M, int K, const __nv_bflo
                                    (int)TC_SMEM));
   const int grid = (int)std::min<long long>(num_sms(), g.total);
   C2_LAUNCH(k_logits_tc, grid, TC_THREADS, TC_SMEM, st, tmA, tmB, g);
+  C2_CUDA_TRY(cudaGetLastError());
+  return C2_OK;
+}
+
+bool tc_gemm_ok(int M, int N, int K) { return M > 0 && N > 0 && K >= TC_BK && K % TC_BK == 0; }
+
+c2_status tc_gemm(const __nv_bfloat16* A, const __nv_bfloat16* B, int M, int N, int K,
+                  const float* bias, float* C, int ldc, int32_t* status, cudaStream_t st) {
+  if (M <= 0 || N <= 0) return C2_OK;
+  if (!tc_gemm_ok(M, N, K) || ldc < N) return C2_ERR_UNSUPPORTED;
+  if (((uintptr_t)A & 15u) || ((uintptr_t)B & 15u) || ((uintptr_t)C & 15u) ||
+      (bias && ((uintptr_t)bias & 15u)))
+    return C2_ERR_INVALID_ARG;
+  CUtensorMap tmA, tmB;
+  if (!make_map(&tmA, A, K, M, TC_BM) || !make_map(&tmB, B, K, N, TC_BN)) return C2_ERR_CUDA;
+  GcArgs g;
+  g.C = C;
+  g.bias = bias;
+  g.status = status;
+  g.M = M;
+  g.N = N;
+  g.K = K;
+  g.ldc = ldc;
+  g.MT = div_up(M, TC_BM);
+  g.NT = div_up(N, TC_BN);
+  const int KB = K / TC_BK;
+  // split K when the output tiles leave SMs idle and each chunk keeps at
+  // least 16 blocks of 64
+  int KS = 1;
+  while ((long long)g.MT * g.NT * KS * 2 <= num_sms() && KB / (KS * 2) >= 16) KS *= 2;
+  g.kc_per = div_up(KB, KS);
+  g.KS = div_up(KB, g.kc_per);
+  g.atomic = g.KS > 1;
+  g.total = (long long)g.MT * g.NT * g.KS;
+  if (g.atomic) C2_CUDA_TRY(cudaMemset2DAsync(C, (size_t)ldc * 4, 0, (size_t)N * 4, M, st));
+  C2_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)GC_SMEM));
+  const int grid = (int)std::min<long long>(num_sms(), g.total);
+  C2_LAUNCH(k_gemm_tc, grid, TC_THREADS, GC_SMEM, st, tmA, tmB, g);
   C2_CUDA_TRY(cudaGetLastError());
   return C2_OK;
 }

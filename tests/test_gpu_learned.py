@@ -80,11 +80,16 @@ def test_model_keys_match_oracle(c2):
     assert len(diff) <= 0.01 * keys.size
 
 
-def test_model_gradients_match_oracle(c2):
-    m = _model(c2)
+@pytest.mark.parametrize("t,b,hidden,n_pairs", [
+    (4, 32, 64, 256),      # 512 rows: logits, dh and dW2 on the tensor cores (tcgen05)
+    (4, 32, 64, 250),      # 500 rows (not a multiple of 64): the mma.sync GEMMs
+    (2, 512, 256, 2048),   # 4,096 rows, 1,024 logits: several tiles, dW2 with K split
+])
+def test_model_gradients_match_oracle(c2, t, b, hidden, n_pairs):
+    m = _model(c2, t=t, b=b, hidden=hidden)
     ptr, items = synth.random_profiles(600, 400, 20, 43)
     rng = np.random.default_rng(4)
-    pairs = rng.integers(0, 600, (256, 2)).astype(np.int32)
+    pairs = rng.integers(0, 600, (n_pairs, 2)).astype(np.int32)
     lam = 0.1
     loss, grads = m.gradients(dev(ptr), dev(items), dev(pairs), lam)
     params = [x.cpu().numpy() for x in m.params()]
