@@ -957,6 +957,27 @@ __device__ __forceinline__ uint32_t jac_q16(uint32_t c, uint32_t u) {
   return min(q, 65535u);
 }
 
+// floor(a / u) for a <= 0xFFFF0000 and 0 < u < 2^16 without an integer
+// division: the float quotient is within one of a / u (relative error below
+// 2^-21 on a quotient below 2^17), corrected by one step either way (every
+// product stays below 2^32).
+__device__ __forceinline__ uint32_t udiv16(uint32_t a, uint32_t u) {
+  uint32_t q = __float2uint_rz(__fdividef((float)a, (float)u));
+  if (q * u > a) --q;
+  else if ((q + 1u) * u <= a) ++q;
+  return q;
+}
+
+// nbr_key for 0 < c <= u < 2^16 (keyed rows), its two 16-bit quotient steps
+// by udiv16: the same key.
+__device__ __forceinline__ uint64_t nbr_key16(uint32_t c, uint32_t u, int32_t lid, int32_t pos) {
+  const uint32_t a = c << 16;
+  const uint32_t q1 = udiv16(a, u);
+  const uint32_t q2 = udiv16((a - q1 * u) << 16, u);
+  const uint64_t K = ((uint64_t)q1 << 16) | q2;
+  return (K << 31) | ((uint64_t)(16383u - (uint32_t)lid) << 17) | ((uint64_t)(uint32_t)pos << 1);
+}
+
 // Brute-force rows by exact selection (keyed rows: unions below 2^16): warp
 // per member.  q = floor(65536 J) is exact and monotone in J, so the k best
 // candidates are among those whose q reaches the row's k-th largest q.
@@ -1194,14 +1215,16 @@ __global__ void __launch_bounds__(kNT, 6) k_gram_select(const __grid_constant__ 
     }
     n = m_n;
   }
-  // exact order keys of the (at most 64) selected, sorted
+  // exact order keys of the (at most 64) selected, sorted: one warp sort of
+  // the first 32; up to 16 more are inserted one at a time, more than that
+  // are sorted too and merged
   auto key_of = [&](int i) -> uint64_t {
     if (i >= n) return 0ull;
     const uint2 x = stg[i];
-    return nbr_key(x.y & 0xFFFFu, x.y >> 16, (int32_t)(x.x >> 16), (int32_t)(x.x & 0xFFFFu));
+    return nbr_key16(x.y & 0xFFFFu, x.y >> 16, (int32_t)(x.x >> 16), (int32_t)(x.x & 0xFFFFu));
   };
   uint64_t x = warp_sort32_keys(key_of(lane));
-  if (n > 32) {
+  if (n > 48) {
     const uint64_t y = warp_sort32_keys(key_of(lane + 32));
     const uint64_t r = __shfl_sync(0xffffffffu, y, 31 - lane);
     x = r > x ? r : x;
@@ -1211,6 +1234,9 @@ __global__ void __launch_bounds__(kNT, 6) k_gram_select(const __grid_constant__ 
       const bool lower = (lane & j) == 0;
       x = lower ? (o > x ? o : x) : (o < x ? o : x);
     }
+  } else if (n > 32) {
+    const uint64_t y = key_of(lane + 32);
+    for (int i = 0; i < n - 32; ++i) key_list_insert(x, k, __shfl_sync(0xffffffffu, y, i));
   }
   if (lane < k) {
     const int64_t o = (int64_t)slot * k + lane;

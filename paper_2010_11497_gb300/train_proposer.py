@@ -166,10 +166,43 @@ def time_propose(workload="learned_ml20m", chunk=65536, reps=10, dim=64, hidden=
     return r
 
 
+def time_train(workload="learned_ml20m", batch=8192, reps=20, dim=64, hidden=256, rows_log2=18,
+               model_seed=2010, lam=3.0, log=print):
+    """Times c2_model_train_step on the workload's target data with seeded
+    random pairs (the GEMM shapes of training; the pairs' content does not
+    change the work): 3 warm-up steps, then the mean of `reps` steps (CUDA
+    events).  With batch a multiple of 32 the three large GEMMs of a step run
+    on the tensor cores (tcgen05), otherwise on mma.sync."""
+    w = synth.WORKLOADS[workload]
+    ptr, items, _ = synth.load(workload, w.seed)
+    dptr, ditems = dev(ptr), dev(items)
+    model = c2.Model(w.t, w.b, dim, hidden, rows_log2, model_seed).init()
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(model_seed)
+    pairs = torch.randint(0, w.n_users, (batch, 2), device="cuda", generator=gen,
+                          dtype=torch.int32)
+    for _ in range(3):
+        model.train_step(dptr, ditems, pairs, lam=lam)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        model.train_step(dptr, ditems, pairs, lam=lam)
+    e1.record()
+    torch.cuda.synchronize()
+    r = dict(workload=workload, t=w.t, b=w.b, dim=dim, hidden=hidden, batch_pairs=batch,
+             rows=2 * batch, reps=reps, train_step_ms=e0.elapsed_time(e1) / reps,
+             gemm_flop_per_step=3 * 2 * (2 * batch) * hidden * w.t * w.b)
+    log(json.dumps(r))
+    return r
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--time-propose", action="store_true",
                     help="time proposals of an untrained network on the target data and exit")
+    ap.add_argument("--time-train", action="store_true",
+                    help="time training steps on random pairs of the target data and exit")
     ap.add_argument("--chunk", type=int, default=65536, help="users per proposal chunk")
     ap.add_argument("--reps", type=int, default=10)
     ap.add_argument("--workload", default="learned_ml20m")
@@ -186,6 +219,9 @@ def main():
     a = ap.parse_args()
     if a.time_propose:
         time_propose(a.workload, a.chunk, a.reps)
+        return
+    if a.time_train:
+        time_train(a.workload, a.batch, a.reps, lam=a.lam)
         return
     _, model = run(a.workload, tuple(a.train_seeds), a.steps, a.batch, a.lr, a.lam, mu=a.mu,
                    lams=a.lams)
