@@ -19,8 +19,9 @@ Sizes make_sizes(int32_t n, int64_t nnz, int32_t m, int32_t k, int32_t t, int32_
   s.tp = (t + 7) / 8 * 8;
   s.omax = s.S / ((int64_t)N + 1) + 1;
   int64_t budget = (opt && opt->gram_budget_bytes > 0) ? opt->gram_budget_bytes : (int64_t(2) << 30);
-  // sum over clusters of M * round_up(M, 8) <= S * (n + 7), two bytes each
-  const int64_t worst = 2 * s.S * ((int64_t)std::max<int32_t>(n, 1) + 8);
+  // sum over clusters of (M + 1) * round_up(M, 8) (the count rows and the row
+  // of member lengths) <= S * (n + 15), two bytes each
+  const int64_t worst = 2 * s.S * ((int64_t)std::max<int32_t>(n, 1) + 16);
   s.gram_budget = std::max<int64_t>(std::min(budget, worst), 2);
   // tensor-core count matrices, when the item universe and the strategy allow
   // that path; their remapped lists (one padded profile area per function)

@@ -49,6 +49,7 @@ struct DevHeader {
   int32_t tc_tiles;                // their 128 x 256 tiles
   int32_t select_general;          // brute-force rows the select kernel handed to the keyed path
   int32_t direct_users;            // members of greedy clusters without a count matrix
+  unsigned long long gram_len_elems;  // elements of the count matrices' length rows
 };
 static_assert(sizeof(DevHeader) <= 256, "header must fit 256 bytes");
 

@@ -768,13 +768,18 @@ __global__ void __launch_bounds__(256) k_order(const int32_t* __restrict__ gcl, 
                                                const int32_t* __restrict__ cptr,
                                                const int32_t* __restrict__ slen,
                                                int32_t* __restrict__ ipos,
-                                               int2* __restrict__ iinfo) {
+                                               int2* __restrict__ iinfo,
+                                               const int64_t* __restrict__ gofs,
+                                               uint16_t* __restrict__ gram) {
   __shared__ int32_t start[64];
   __shared__ int32_t wcnt[8][64];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int c = gcl[g0 + blockIdx.x];
-  const int cbase = cptr[c], M = cptr[c + 1] - cbase;
+  const int cbase = cptr[c], M = cptr[c + 1] - cbase, Mp = (M + 7) & ~7;
+  // the row after the M count rows: profile lengths in internal order
+  uint16_t* lenrow = gram + gofs[c] + (int64_t)M * Mp;
   if (tid < 64) start[tid] = 0;
+  if (tid < Mp - M) lenrow[M + tid] = 0;
   __syncthreads();
   for (int i = tid; i < M; i += 256) atomicAdd(&start[63 - len_bucket(slen[cbase + i])], 1);
   __syncthreads();
@@ -803,6 +808,7 @@ __global__ void __launch_bounds__(256) k_order(const int32_t* __restrict__ gcl, 
       for (int w2 = 0; w2 < warp; ++w2) off += wcnt[w2][bk];
       ipos[cbase + i] = off;
       iinfo[cbase + off] = make_int2(i, len);
+      lenrow[off] = (uint16_t)len;
     }
     __syncthreads();
     if (tid < 64) {
@@ -1102,19 +1108,22 @@ __global__ void __launch_bounds__(kNT, 6) k_gram_select(const __grid_constant__ 
   const uint2* row4 = reinterpret_cast<const uint2*>(row);
   const int M4 = (M + 3) >> 2;
   const int2* info = a.iinfo + cs;
+  // the row after the count rows holds the members' lengths (same positions)
+  const uint2* len4 = reinterpret_cast<const uint2*>(a.gram + a.gofs[c] + (int64_t)M * Mp);
   const uint32_t my = (uint32_t)a.slen[slot];
   const int k = a.k;
   // 1. each lane's two largest estimates of q
   uint32_t q1 = 0u, q2 = 0u;
 #pragma unroll 2
   for (int g = lane; g < M4; g += 32) {
-    const uint2 cw = row4[g];
+    const uint2 cw = row4[g], lw = len4[g];
     const uint32_t cq[4] = {cw.x & 0xFFFFu, cw.x >> 16, cw.y & 0xFFFFu, cw.y >> 16};
+    const uint32_t lq[4] = {lw.x & 0xFFFFu, lw.x >> 16, lw.y & 0xFFFFu, lw.y >> 16};
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int p = 4 * g + q;
       if (p < M && p != P && cq[q]) {
-        const uint32_t u = my + (uint32_t)info[p].y - cq[q];
+        const uint32_t u = my + lq[q] - cq[q];
         // within one of the exact quotient (relative error below 2^-21)
         const uint32_t qe = __float2uint_rz(__fdividef((float)(cq[q] << 16), (float)u));
         q2 = max(q2, min(q1, qe));
@@ -1129,18 +1138,20 @@ __global__ void __launch_bounds__(kNT, 6) k_gram_select(const __grid_constant__ 
   bool ok = true;
   for (int g0 = 0; g0 < M4 && ok; g0 += 32) {
     const int g = g0 + lane;
-    uint2 cw = make_uint2(0u, 0u);
-    if (g < M4) cw = row4[g];
+    uint2 cw = make_uint2(0u, 0u), lw = make_uint2(0u, 0u);
+    if (g < M4) {
+      cw = row4[g];
+      lw = len4[g];
+    }
     const uint32_t cq[4] = {cw.x & 0xFFFFu, cw.x >> 16, cw.y & 0xFFFFu, cw.y >> 16};
+    const uint32_t lq[4] = {lw.x & 0xFFFFu, lw.x >> 16, lw.y & 0xFFFFu, lw.y >> 16};
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int p = 4 * g + q;
       bool pass = false;
       uint32_t u = 0u;
-      int2 in = make_int2(0, 0);
       if (p < M && p != P && cq[q]) {
-        in = info[p];
-        u = my + (uint32_t)in.y - cq[q];
+        u = my + lq[q] - cq[q];
         pass = (cq[q] << 16) >= T0 * u;
       }
       const unsigned m = __ballot_sync(0xffffffffu, pass);
@@ -1148,9 +1159,9 @@ __global__ void __launch_bounds__(kNT, 6) k_gram_select(const __grid_constant__ 
         ok = false;
         break;
       }
-      if (pass)
+      if (pass)   // the local index of a staged candidate only
         stg[n + __popc(m & lanemask_lt())] =
-            make_uint2((uint32_t)p | ((uint32_t)in.x << 16), cq[q] | (u << 16));
+            make_uint2((uint32_t)p | ((uint32_t)info[p].x << 16), cq[q] | (u << 16));
       n += __popc(m);
     }
   }
@@ -1245,7 +1256,7 @@ __global__ void __launch_bounds__(kNT, 6) k_gram_select(const __grid_constant__ 
     if (id >= 0) {
       const int pos = key_pos(x);
       oc = (uint32_t)row[pos];
-      ou = my + (uint32_t)info[pos].y - oc;
+      ou = my + (uint32_t)reinterpret_cast<const uint16_t*>(len4)[pos] - oc;
     }
     a.out_id[o] = id >= 0 ? a.cusers[cs + id] : -1;
     a.out_in[o] = (int32_t)oc;
@@ -1484,7 +1495,7 @@ __global__ void k_prep(const int32_t* __restrict__ cptr, const int32_t* __restri
   const bool brute = M >= 2 && M < thr;
   const bool greedy = M >= 2 && M >= thr;
   const bool direct =
-      greedy && (M > kMaxGreedyM || (int64_t)M * (((int64_t)M + 7) & ~int64_t(7)) > cap);
+      greedy && (M > kMaxGreedyM || ((int64_t)M + 1) * (((int64_t)M + 7) & ~int64_t(7)) > cap);
   // small brute-force clusters whose profiles fit the per-warp stage go to
   // the warp-per-cluster kernel
   bool small = false;
@@ -1583,15 +1594,19 @@ __global__ void k_greedy_list(const int32_t* __restrict__ gflag, const int32_t* 
   const int g = gidx[c];
   const int32_t M = cptr[c + 1] - cptr[c];
   gcl[g] = (int32_t)c;
-  gsq[g] = (int64_t)M * ((M + 7) & ~7);   // rows padded to 16 bytes
+  // M rows of counts, then one row of the members' profile lengths (uint16,
+  // internal order); rows padded to 16 bytes
+  const int64_t Mp = (M + 7) & ~7;
+  gsq[g] = ((int64_t)M + 1) * Mp;
   gsz[g] = M;
   gkind[g] = gkind_c[c];
+  atomicAdd(&hdr->gram_len_elems, (unsigned long long)Mp);
   if (gkind_c[c]) {
     atomicMax(&hdr->max_cluster, M);
     atomicAdd(&hdr->greedy_users, M);
     atomicAdd(&hdr->n_greedy, 1);
   } else {
-    atomicAdd(&hdr->brute_gram_elems, (unsigned long long)gsq[g]);
+    atomicAdd(&hdr->brute_gram_elems, (unsigned long long)(M * Mp));
     atomicAdd(&hdr->brute_rows, M);
   }
 }
@@ -2027,8 +2042,10 @@ __global__ void __launch_bounds__(kNT) k_greedy_emit(GreedyArgs a) {
 }
 
 __global__ void k_gram_stats(const int64_t* __restrict__ goff, int32_t ng, DevHeader* hdr) {
-  hdr->greedy_gram_elems = (unsigned long long)goff[ng];
-  hdr->gram_pairs += (unsigned long long)goff[ng];
+  // count elements, without the length rows
+  const unsigned long long e = (unsigned long long)goff[ng] - hdr->gram_len_elems;
+  hdr->greedy_gram_elems = e;
+  hdr->gram_pairs += e;
 }
 
 // ------------------------------------------------------------------ launch helpers
@@ -2506,7 +2523,7 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
                 w.gofs, w.bu_cnt, w.bb_cnt, w.bw_cnt);
       // internal order (members by decreasing profile length) of every
       // count-matrix cluster of the batch
-      C2_LAUNCH(k_order, nb, 256, 0, st, w.gcl, g0, cptr, w.slen, w.ipos, w.iinfo);
+      C2_LAUNCH(k_order, nb, 256, 0, st, w.gcl, g0, cptr, w.slen, w.ipos, w.iinfo, w.gofs, w.gram);
       // strategy of each cluster of the batch: 0 table, 1 tensor cores
       std::vector<int32_t> route(nb, 0);
       if (tc_possible && (tc.W || use_hash) && opt.strategy == C2_STRATEGY_AUTO) {

@@ -179,9 +179,10 @@ def test_local_greedy_with_merge_counts(c2):
 @pytest.mark.parametrize("rounds,nrand", [(0, 0), (3, 0), (2, 5)])
 def test_local_greedy_direct_counts(c2, rounds, nrand):
     # a count-matrix budget that holds every brute-force cluster (below 150
-    # members) but no greedy one: the greedy clusters count from the profiles
+    # members: 149 count rows and the row of lengths, 152 entries each) but no
+    # greedy one: the greedy clusters count from the profiles
     ptr, items = synth.random_profiles(2500, 400, 20, 14, zipf_s=1.1)
-    budget = 2 * 149 * 152
+    budget = 2 * 150 * 152
     _, _, st = check_local(c2, ptr, items, 400, 3, 8, 600, 12, 21, 150, rounds, nrand,
                            budget=budget)
     assert st["direct_users"] == st["greedy_users"] > 0
@@ -191,7 +192,7 @@ def test_local_greedy_direct_wide_items(c2):
     # 100k items: no profile bitmap fits shared memory, counts come from merges
     ptr, items = synth.random_profiles(3000, 100000, 14, 31, zipf_s=1.05)
     _, _, st = check_local(c2, ptr, items, 100000, 2, 4, 900, 10, 5, 200, 3, 2,
-                           budget=2 * 199 * 200)
+                           budget=2 * 200 * 200)
     assert st["direct_users"] > 0
 
 
@@ -224,8 +225,9 @@ def test_local_greedy_small_budget_batches(c2):
     ptr, items = synth.random_profiles(3000, 300, 15, 15, zipf_s=1.2)
     o = oracle.frh_cluster(ptr, items, 300, 2, 8, 500, 4)
     sizes = np.diff(o["cptr"])
-    # count matrices keep rows padded to 8 entries (16 bytes)
-    big = int((sizes.astype(np.int64) * ((sizes + 7) // 8 * 8)).max()) * 2
+    # count matrices: M count rows and one row of lengths, padded to 8 entries
+    # (16 bytes)
+    big = int(((sizes.astype(np.int64) + 1) * ((sizes + 7) // 8 * 8)).max()) * 2
     k, thr = 8, 100
     li, lc, lu, pairs = oracle.cluster_knn(ptr, items, o["cptr"], o["cusers"], k, 4, thr, 3)
     dptr, ditems = to_dev(ptr), to_dev(items)
@@ -241,9 +243,12 @@ def test_local_greedy_small_budget_batches(c2):
 
 
 # ------------------------------------------------------------------ Step 3 + whole build
-def test_merge_parity(c2):
+# t*k <= 256: the ids seen so far are kept in a shared-memory set; (12, 30):
+# rows compared with the list by shuffles
+@pytest.mark.parametrize("t,k", [(5, 9), (8, 32), (12, 30)])
+def test_merge_parity(c2, t, k):
     ptr, items = synth.random_profiles(2000, 300, 20, 16)
-    m, t, b, N, k, seed = 300, 5, 16, 300, 9, 3
+    m, b, N, seed = 300, 16, 300, 3
     o = oracle.frh_cluster(ptr, items, m, t, b, N, seed)
     li, lc, lu, _ = oracle.cluster_knn(ptr, items, o["cptr"], o["cusers"], k, seed, 10 ** 9)
     rid, rin, run = oracle.merge_topk(o["cptr"], o["cusers"], 2000, k, li, lc, lu)
@@ -410,7 +415,7 @@ def test_workspace_too_small(c2):
     assert e.value.code == 4
 
 
-@pytest.mark.parametrize("budget", [0, 2 * 49 * 56])
+@pytest.mark.parametrize("budget", [0, 2 * 50 * 56])
 def test_greedy_draw_bound_reports_timeout(c2, budget):
     # The greedy random start's bounded loop: a bound below one batch of 32
     # draws stops every member's start, C2_ERR_TIMEOUT reaches the status
