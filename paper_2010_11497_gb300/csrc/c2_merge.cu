@@ -18,8 +18,29 @@ __global__ void k_pos_of(const int32_t* __restrict__ cusers, int64_t S, int32_t 
 
 // One warp per user; rows are folded 4 at a time (their slot and entry loads
 // issued together).  The first row is the list; every later row drops the
-// ids the list already holds (equal ids carry equal counts), is compacted
-// (it stays sorted) and is merged with the list by one bitonic merge.
+// ids seen in an earlier row and is merged with the list by one bitonic merge
+// (after compaction it stays sorted).  An id seen before carries the same
+// counts (the similarity is exact), so it is in the list already or ranks
+// below the list's k-th, which only improves: dropping it changes nothing.
+// The ids seen so far sit in a per-warp open-addressing set in shared memory
+// (one probe sequence per lane and row) when t * k <= 256, at most half of its
+// 512 slots; larger products compare each row with the list by shuffles.
+constexpr int kMergeSetLog = 9;
+constexpr int kMergeSet = 1 << kMergeSetLog;
+
+// Inserts id into the set; false when it was there already.  Ends within
+// kMergeSet probes (the set never fills).
+__device__ __forceinline__ bool merge_set_insert(int32_t* set, int32_t id) {
+  uint32_t slot = ((uint32_t)id * 0x9E3779B1u) >> (32 - kMergeSetLog);
+  for (int probe = 0; probe < kMergeSet; ++probe) {
+    const int32_t old = atomicCAS(&set[slot], -1, id);
+    if (old == -1) return true;
+    if (old == id) return false;
+    slot = (slot + 1) & (kMergeSet - 1);
+  }
+  return false;
+}
+
 __global__ void __launch_bounds__(256) k_merge(const int32_t* __restrict__ pos_of, int32_t n,
                                                int32_t t, int32_t k,
                                                const int32_t* __restrict__ lid,
@@ -30,9 +51,17 @@ __global__ void __launch_bounds__(256) k_merge(const int32_t* __restrict__ pos_o
                                                int32_t* __restrict__ nun, const DevHeader* hdr) {
   __shared__ int32_t s_id[8][32];
   __shared__ uint2 s_cu[8][32];
+  __shared__ int32_t s_set[8][kMergeSet];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (u >= n || dev_failed(hdr)) return;
+  int32_t* set = s_set[warp];
+  // rows beyond the set's half-full bound fall back to the shuffle scan
+  const bool use_set = t * k <= kMergeSet / 2;
+  if (use_set) {
+    for (int i = lane; i < kMergeSet; i += 32) set[i] = -1;
+    __syncwarp();
+  }
   WarpList L;
   L.id = -1; L.c = 0; L.u = 0;
   for (int i0 = 0; i0 < t; i0 += 4) {
@@ -50,13 +79,16 @@ __global__ void __launch_bounds__(256) k_merge(const int32_t* __restrict__ pos_o
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
       if (i0 + r >= t) break;
-      if (i0 + r == 0) { L = R[0]; continue; }
-      // drop ids already in the list
       bool dup = false;
-      for (int j = 0; j < k; ++j) {
-        const int32_t lj = __shfl_sync(0xffffffffu, L.id, j);   // every lane takes part
-        dup |= R[r].id >= 0 && R[r].id == lj;
+      if (use_set) {
+        if (R[r].id >= 0) dup = !merge_set_insert(set, R[r].id);
+      } else if (i0 + r > 0) {
+        for (int j = 0; j < k; ++j) {
+          const int32_t lj = __shfl_sync(0xffffffffu, L.id, j);   // every lane takes part
+          dup |= R[r].id >= 0 && R[r].id == lj;
+        }
       }
+      if (i0 + r == 0) { L = R[0]; continue; }
       const unsigned keep = __ballot_sync(0xffffffffu, R[r].id >= 0 && !dup);
       if (keep == 0u) continue;
       // compact the survivors (still sorted) to the front
