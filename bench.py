@@ -431,8 +431,9 @@ def phase_model(dom, phase_ms, phase_calls, stats, w, nnz, pk, W, steps):
         return hbm("k_merge", 4 * S + 12 * S * k + 12 * n * k,
                    "t rows of k (id, inter, union) read per user, one row written, slot map read")
     if dom == "hash_minhash_level0":
-        return hbm("k_minhash", 4 * (n + 1) + 4 * nnz + 4 * S,
-                   "CSR read once plus one key per (function, user) slot")
+        return hbm("k_minhash", 4 * (n + 1) + 4 * nnz + 12 * S,
+                   "CSR read once plus three keys per (function, user) slot (the minimum and "
+                   "the next two distinct values)")
     return None
 
 

@@ -40,6 +40,7 @@ void bind_cluster_ws(Ws& w, const Sizes& s, ClusterWs& c) {
   c.htab = w.take<uint16_t>((size_t)std::max<int64_t>(s.m, 1) * s.tp);
   c.key = w.take<int32_t>(S + 1);
   c.key2 = w.take<int32_t>(S + 1);
+  c.key3 = w.take<int32_t>(S + 1);
   c.lab = w.take<int32_t>(S + 1);
   c.lab2 = w.take<int32_t>(S + 1);
   c.hist = w.take<int32_t>(nbins + 1);

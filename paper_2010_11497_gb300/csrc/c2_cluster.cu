@@ -157,16 +157,18 @@ __device__ __forceinline__ uint32_t warp_min8(const uint32_t v[8]) {
 
 // key[i][u] = min over u's items of h_i (Eq. 3); b for an empty profile.
 // One warp per user (hash rows walked by walk_hash_rows).  Also counts the
-// level-0 histogram of (function, key), and keeps key2[i][u], the second
-// smallest distinct value of h_i over u's items (b when there is none): the
-// key of the first split of an oversized cluster (the smallest value above
-// the cluster's key), so that level needs no second walk of the profiles.
-__global__ void __launch_bounds__(256) k_minhash(const int32_t* __restrict__ ptr,
+// level-0 histogram of (function, key), and keeps key2[i][u] and key3[i][u],
+// the second and third smallest distinct values of h_i over u's items (b when
+// there is none): the keys of the first two splits of an oversized cluster
+// (each split key is the smallest value above the cluster's key), so those
+// levels need no second walk of the profiles.
+__global__ void __launch_bounds__(256, 4) k_minhash(const int32_t* __restrict__ ptr,
                                                  const int32_t* __restrict__ items, int32_t vec,
                                                  const uint16_t* __restrict__ htab,
                                                  int32_t n, int32_t t, int32_t tp, int32_t b,
                                                  int32_t* __restrict__ key,
                                                  int32_t* __restrict__ key2,
+                                                 int32_t* __restrict__ key3,
                                                  int32_t* __restrict__ hist, DevHeader* hdr) {
   if (dev_failed(hdr)) return;
   const int lane = threadIdx.x & 31;
@@ -175,33 +177,44 @@ __global__ void __launch_bounds__(256) k_minhash(const int32_t* __restrict__ ptr
   const int32_t s = ptr[u], e = ptr[u + 1];
   const int64_t nnz = ptr[n];   // validated: the items array holds ptr[n] entries
   for (int c = 0; c < tp; c += 8) {
-    uint32_t mn[8], m2[8];   // the lane's smallest and second smallest distinct values
+    // the lane's three smallest distinct values per function, ascending
+    uint32_t v0[8], v1[8], v2[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) mn[q] = m2[q] = (uint32_t)b;
+    for (int q = 0; q < 8; ++q) v0[q] = v1[q] = v2[q] = (uint32_t)b;
     walk_hash_rows(items, nnz, s, e, vec != 0, htab, tp, c, [&](const uint4& hv) {
       const uint32_t w[4] = {hv.x, hv.y, hv.z, hv.w};
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         const uint32_t h = (w[q >> 1] >> (16 * (q & 1))) & 0xFFFFu;
-        const uint32_t lo = min(mn[q], h), hi = max(mn[q], h);
-        m2[q] = h == mn[q] ? m2[q] : min(m2[q], hi);
-        mn[q] = lo;
+        // insertion into the sorted three (a value already held changes nothing)
+        const bool seen = h == v0[q] || h == v1[q];
+        const uint32_t x = max(v0[q], h), y = max(v1[q], x);
+        if (!seen) {
+          v0[q] = min(v0[q], h);
+          v1[q] = min(v1[q], x);
+          v2[q] = min(v2[q], y);
+        }
       }
     });
-    const uint32_t r = warp_min8(mn);
-    // the lane's smallest value above each function's minimum, then its minimum
+    const uint32_t r0 = warp_min8(v0);
+    // each lane's smallest value above the warp's minimum, then above the
+    // warp's second value
     uint32_t above[8];
 #pragma unroll
+    for (int q = 0; q < 8; ++q) above[q] = v0[q] > __shfl_sync(0xffffffffu, r0, 4 * q) ? v0[q] : v1[q];
+    const uint32_t r1 = warp_min8(above);
+#pragma unroll
     for (int q = 0; q < 8; ++q) {
-      const uint32_t v0 = __shfl_sync(0xffffffffu, r, 4 * q);
-      above[q] = mn[q] > v0 ? mn[q] : m2[q];
+      const uint32_t m1 = __shfl_sync(0xffffffffu, r1, 4 * q);
+      above[q] = v0[q] > m1 ? v0[q] : (v1[q] > m1 ? v1[q] : v2[q]);
     }
     const uint32_t r2 = warp_min8(above);
     const int i = c + (lane >> 2);
     if ((lane & 3) == 0 && i < t) {
-      key[(int64_t)i * n + u] = (int32_t)r;
-      key2[(int64_t)i * n + u] = (int32_t)r2;
-      atomicAdd(&hist[(int64_t)i * (b + 1) + r], 1);
+      key[(int64_t)i * n + u] = (int32_t)r0;
+      key2[(int64_t)i * n + u] = (int32_t)r1;
+      key3[(int64_t)i * n + u] = (int32_t)r2;
+      atomicAdd(&hist[(int64_t)i * (b + 1) + r0], 1);
     }
   }
 }
@@ -275,11 +288,13 @@ __global__ void k_mark_oversized(const int32_t* __restrict__ lsize, const int32_
   nchild[l] = live ? 1 : 0;
 }
 
-// The first split level of FastRandomHash clusters: every slot of an
-// oversized cluster holds the cluster's key eta = its own minimum, so its next
-// key (the smallest value above eta) is the second smallest distinct value
-// k_minhash kept.  One thread per slot.
-__global__ void k_split_keys_first(const int32_t* __restrict__ key2, int64_t S, int32_t b,
+// The first two split levels of FastRandomHash clusters: at level L every slot
+// of an oversized cluster holds the cluster's key eta = its own (L+1)-th
+// smallest distinct value (level 0: the minimum; the sub-clusters of a split
+// carry their members' next value, and residuals never split again), so its
+// next key (the smallest value above eta) is the (L+2)-th, which k_minhash
+// kept (`next` = key2 or key3).  One thread per slot.
+__global__ void k_split_keys_first(const int32_t* __restrict__ next, int64_t S, int32_t b,
                                    const int32_t* __restrict__ lab,
                                    const int32_t* __restrict__ ovscan,
                                    int32_t* __restrict__ nextkey, int32_t* __restrict__ subcnt,
@@ -288,7 +303,7 @@ __global__ void k_split_keys_first(const int32_t* __restrict__ key2, int64_t S, 
   if (s >= S || dev_failed(hdr)) return;
   const int32_t l = lab[s];
   if (ovscan[l + 1] == ovscan[l]) return;
-  const int32_t nk = key2[s];
+  const int32_t nk = next[s];
   nextkey[s] = nk;
   atomicAdd(&subcnt[(int64_t)ovscan[l] * (b + 1) + nk], 1);
 }
@@ -542,7 +557,7 @@ c2_status run_frh_cluster(const int32_t* ptr, const int32_t* items, const Sizes&
     C2_LAUNCH(k_keys_given, div_up(S, T), T, 0, st, opt.d_keys, S, s.n, s.b, w.key, w.hist, w.hdr);
   else if (s.n > 0)
     C2_LAUNCH(k_minhash, div_up((int64_t)s.n * 32, T), T, 0, st, ptr, items, vec16, w.htab,
-              s.n, s.t, s.tp, s.b, w.key, w.key2, w.hist, w.hdr);
+              s.n, s.t, s.tp, s.b, w.key, w.key2, w.key3, w.hist, w.hdr);
   C2_LAUNCH(k_flag_nonzero, div_up(nbins, T), T, 0, st, w.hist, w.binlab, nbins);
   C2_CUDA_TRY(scan_exclusive(w.binlab, w.binlab, nbins, w.scan_tmp, st));
   C2_CUDA_TRY(cudaMemsetAsync(w.lsize, 0, (S + 1) * sizeof(int32_t), st));
@@ -571,9 +586,9 @@ c2_status run_frh_cluster(const int32_t* ptr, const int32_t* items, const Sizes&
     if (O > s.omax) { out = C2_ERR_UNSUPPORTED; break; }
     C2_LAUNCH(k_ovlist, div_up(S, T), T, 0, st, w.ovidx, S, w.ovlist);
     cudaMemsetAsync(w.subcnt, 0, O * (s.b + 1) * sizeof(int32_t), st);
-    if (level == 0 && !opt.d_keys)   // first split of FastRandomHash keys: no walk
-      C2_LAUNCH(k_split_keys_first, div_up(S, T), T, 0, st, w.key2, S, s.b, w.lab, w.ovidx, w.key,
-                w.subcnt, w.hdr);
+    if (level < 2 && !opt.d_keys)   // first two splits of FastRandomHash keys: no walk
+      C2_LAUNCH(k_split_keys_first, div_up(S, T), T, 0, st, level == 0 ? w.key2 : w.key3, S, s.b,
+                w.lab, w.ovidx, w.key, w.subcnt, w.hdr);
     else
       C2_LAUNCH(k_split_keys, div_up((int64_t)s.n * 32, T), T, 0, st, ptr, items, vec16,
                 w.htab, s.n, s.t, s.tp, s.b, w.lab, w.ovidx, w.leta, w.key, w.subcnt, w.hdr);

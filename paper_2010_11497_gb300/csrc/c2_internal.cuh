@@ -114,6 +114,7 @@ struct ClusterWs {
   uint16_t* htab;          // [m][tp]
   int32_t* key;            // [S] level-0 keys, then next keys
   int32_t* key2;           // [S] second smallest distinct hash value (b: none)
+  int32_t* key3;           // [S] third smallest distinct hash value (b: none)
   int32_t *lab, *lab2;     // [S] per-slot labels
   int32_t* hist;           // [t*(b+1)+1]
   int32_t* binlab;         // [t*(b+1)+1]
