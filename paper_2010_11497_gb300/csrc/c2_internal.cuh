@@ -447,6 +447,17 @@ struct WarpTopk {
   }
 };
 
+// floor(a / u) for a <= 0xFFFF0000 and 0 < u < 2^16 with a quotient below
+// 2^17, without an integer division (estimate and correct): the float
+// quotient is within one of a / u (relative error below 2^-21), corrected by
+// one integer step either way (every product stays below 2^32).
+__device__ __forceinline__ uint32_t udiv16(uint32_t a, uint32_t u) {
+  uint32_t q = __float2uint_rz(__fdividef((float)a, (float)u));
+  if (q * u > a) --q;
+  else if ((q + 1u) * u <= a) ++q;
+  return q;
+}
+
 // ------------------------------------------------------------ keyed lists
 // Exact order key of a neighbour (c common items, u union, local index `lid`
 // in the cluster's user-id order, position `pos` in the cluster's internal
@@ -456,14 +467,14 @@ struct WarpTopk {
 // different ones (they differ by at least 1/(u u') > 2^-32); 16383 - lid
 // ranks the lower id first among equal values; pos and the one-bit mark only
 // ride along (lid already differs between candidates).  Larger key = better
-// neighbour; 0 = empty.  K comes from two 32-bit divisions: c*2^16 = q1*u +
-// r1, then r1*2^16 / u, both exact because c, r1 < 2^16.
+// neighbour; 0 = empty.  K comes from two exact 16-bit quotient steps:
+// c*2^16 = q1*u + r1, then r1*2^16 / u (c, r1 < 2^16), by udiv16.
 __device__ __forceinline__ uint64_t nbr_key(uint32_t c, uint32_t u, int32_t lid, int32_t pos,
                                             uint32_t mark = 0u) {
   const uint32_t ud = u ? u : 1u;            // c = u = 0 only for two empty profiles
   const uint32_t a = c << 16;
-  const uint32_t q1 = a / ud, r1 = a - q1 * ud;
-  const uint32_t q2 = (r1 << 16) / ud;
+  const uint32_t q1 = udiv16(a, ud), r1 = a - q1 * ud;
+  const uint32_t q2 = udiv16(r1 << 16, ud);
   const uint64_t K = c ? (((uint64_t)q1 << 16) | q2) : 0ull;
   return (K << 31) | ((uint64_t)(16383u - (uint32_t)lid) << 17) |
          ((uint64_t)(uint32_t)pos << 1) | (uint64_t)(mark & 1u);
