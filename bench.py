@@ -85,6 +85,8 @@ def parse():
                          "after them (a profiled run then repeats the decisions of a plain one)")
     ap.add_argument("--gram-budget-mb", type=int, default=0,
                     help="cap on count matrices held at once (0 = library default)")
+    ap.add_argument("--cpu-full", action="store_true",
+                    help="cpu_baseline: time the oracle's whole build once instead of a sample")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="target CPU seconds of the oracle sample")
     return ap.parse_args()
@@ -292,6 +294,18 @@ def oracle_sample(ptr, items, w, seed, budget_s, rng_seed=2010, clustering=None,
             f"scaled to every cluster by estimated work: {p_est:.4g} pair evaluations in an "
             f"estimated {t_total:.1f} s for the whole build; single thread")
     return p_est / t_total, desc, cl
+
+
+def oracle_full(ptr, items, w, seed):
+    """Times the oracle's whole build once (Steps 1-3, single thread).
+    Returns (pairs/s, description)."""
+    import oracle
+    t0 = time.perf_counter()
+    _, _, _, pairs = oracle.build_graph(ptr, items, w.n_items, w.k, w.t, w.b, w.N, seed,
+                                        w.greedy_threshold, w.greedy_rounds)
+    dt = time.perf_counter() - t0
+    return pairs / dt, (f"oracle whole build (Steps 1-3) of all {w.n_users} users: {pairs:.4g} "
+                        f"pair evaluations in {dt:.1f} s; single thread")
 
 
 # ------------------------------------------------------------------ reference arm
@@ -626,7 +640,10 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
-        v, desc, _ = oracle_sample(ptr_np, items_np, w, seed, args.cpu_seconds)
+        if args.cpu_full:
+            v, desc = oracle_full(ptr_np, items_np, w, seed)
+        else:
+            v, desc, _ = oracle_sample(ptr_np, items_np, w, seed, args.cpu_seconds)
         cpu = {"value": v, "unit": "pairs/s", "cores": 1, "kind": "oracle", "sample": desc,
                "host": host_cpu()}
 
