@@ -74,6 +74,11 @@ WORKLOADS = {
     "sparse_wide_1m": Workload(
         "sparse_wide_1m", 1_000_000, 1_300_000, ("lognormal", 60.0, 1.0, 20, 10000), 0.8, 4,
         k=20, t=8, b=8192, N=4000, greedy_threshold=5 * 20 * 20),
+    # sparse_wide_1m's shape at a fifth of its users: small enough for a full
+    # profiler capture of the hashed count-matrix kernel (a few GB on the device)
+    "sparse_wide_200k": Workload(
+        "sparse_wide_200k", 200_000, 1_300_000, ("lognormal", 60.0, 1.0, 20, 10000), 0.8, 4,
+        k=20, t=8, b=8192, N=4000, greedy_threshold=5 * 20 * 20),
     "learned_ml20m": Workload(
         "learned_ml20m", 138493, 26744, ("powerlaw", 1.8, None, 20, None, 20_000_000), 1.0, 5,
         k=30, t=8, b=1024, N=2000, greedy_threshold=5 * 30 * 30),
