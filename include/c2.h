@@ -430,9 +430,10 @@ int64_t c2_kernel_launches(void);
 /* Autotuner (batching of uneven clusters; no counterpart in the paper).  With
  * strategy C2_STRATEGY_AUTO, the first c2_cluster_knn / c2_build_knn_graph
  * call for given sizes (n_users, n_items, t, b, N, k, threshold) times every
- * shared-memory table shape (item words 1-2 x 128-512 threads per block) on
- * each cluster-size bucket (32-127, 128-511, 512-2047, 2048+ users) and keeps
- * the fastest for later calls; results never depend on the choice.  This
+ * shared-memory table shape (item words 1-2 x 128-512 threads per block, and
+ * for item universes below 2^16 whether the profiles are walked as a 16-bit
+ * copy) on each cluster-size bucket (32-127, 128-511, 512-2047, 2048+ users)
+ * and keeps the fastest for later calls; results never depend on the choice.  This
  * writes the process-wide table as a JSON array into buf (like
  * c2_profile_report) and returns the bytes the full report needs. */
 size_t c2_autotune_report(char* buf, size_t len);

@@ -67,6 +67,7 @@ void bind_cluster_ws(Ws& w, const Sizes& s, ClusterWs& c) {
 
 void bind_knn_ws(Ws& w, const Sizes& s, KnnWs& c) {
   const int64_t S = s.S;
+  c.pptr16 = w.take<int32_t>((size_t)s.n + 1);
   c.slot2c = w.take<int32_t>(S + 1);
   c.slen = w.take<int32_t>(S + 1);
   c.small_cnt = w.take<int32_t>(S + 1);
@@ -173,8 +174,9 @@ size_t layout(char* base, size_t ws_bytes, const Sizes& s, DevHeader** hdr, Buil
   return fixed;
 }
 
-// Bytes of the padded-profile tail for nnz entries over n rows.
-size_t tail_bytes(int64_t nnz, int32_t n) { return (size_t)(nnz + 3 * (int64_t)n + 64) * 4; }
+// Bytes of the tail before the remapped lists: the padded profiles (nnz
+// entries over n rows) and their 16-bit copy.
+size_t tail_bytes(int64_t nnz, int32_t n) { return rl_offset(nnz, n); }
 
 bool sizes_ok(int32_t n, int32_t m, int32_t k, int32_t t, int32_t b, int32_t N) {
   return n >= 0 && m >= 0 && k >= 1 && k <= kMaxK && t >= 1 && t <= kMaxT && b >= 1 &&

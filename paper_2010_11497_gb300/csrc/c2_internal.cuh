@@ -93,16 +93,22 @@ struct Sizes {
   bool tc;             // the tensor-core count matrices are allowed (strategy, item universe)
 };
 
-// The remapped lists of the tensor-core count matrices sit in the workspace
-// tail after the padded profiles (which take tail_bytes()): one area of
-// rl_stride() uint16 entries per function.
-inline int64_t rl_stride(int64_t nnz, int32_t n) { return (nnz + 3 * (int64_t)n + 4) & ~int64_t(3); }
-inline size_t rl_offset(int64_t nnz, int32_t n) {
+// The workspace tail holds, from its start: the padded profiles (int32, rows
+// padded to 4 items: (nnz + 3n + 64) entries), then, 256-byte aligned, a
+// 16-bit copy of the profiles for item universes below 2^16 (rows padded to
+// 8 items: (nnz + 7n + 64) entries), then the remapped lists of the
+// tensor-core count matrices: one area of rl_stride() uint16 entries per
+// function.
+inline size_t p16_offset(int64_t nnz, int32_t n) {
   return ((size_t)(nnz + 3 * (int64_t)n + 64) * 4 + 255) & ~size_t(255);
 }
+inline size_t p16_bytes(int64_t nnz, int32_t n) {
+  return ((size_t)(nnz + 7 * (int64_t)n + 64) * 2 + 255) & ~size_t(255);
+}
+inline int64_t rl_stride(int64_t nnz, int32_t n) { return (nnz + 3 * (int64_t)n + 4) & ~int64_t(3); }
+inline size_t rl_offset(int64_t nnz, int32_t n) { return p16_offset(nnz, n) + p16_bytes(nnz, n); }
 inline size_t rl_tail_bytes(int64_t nnz, int32_t n, int32_t t) {
-  return rl_offset(nnz, n) - (size_t)(nnz + 3 * (int64_t)n + 64) * 4 +
-         (size_t)t * rl_stride(nnz, n) * 2 + 256;
+  return (size_t)t * rl_stride(nnz, n) * 2 + 256;
 }
 
 // Item universes up to this size can use the tensor-core count matrices (the
@@ -135,6 +141,8 @@ struct ClusterWs {
 
 struct KnnWs {
   DevHeader* hdr;
+  int32_t* pptr16;         // [n+1] row offsets of the 16-bit profile copy (rows padded to 8)
+  uint16_t* pitems16;      // the 16-bit profile copy in the tail (null: not built)
   int32_t* slot2c;         // [S] slot -> cluster
   int32_t* slen;           // [S] profile length of the slot's user
   int32_t* small_cnt;      // [S+1] members of clusters for the merge kernel, per cluster

@@ -143,6 +143,51 @@ __device__ __forceinline__ void count_row4(const int4* __restrict__ r4, int n4,
   }
 }
 
+// Walks one 16-bit padded profile (n8 loads of 8 items) in steps of 24 items
+// (three 16-byte loads, the next step's loads issued before the current step
+// is counted), flushing the 4-bit lanes every 12 items.
+template <int W>
+__device__ __forceinline__ void count_row16(const uint4* __restrict__ r8, int n8,
+                                            const uint32_t* __restrict__ T, int sentinel,
+                                            uint32_t* C) {
+  const uint32_t s2 = (uint32_t)sentinel * 0x10001u;
+  const uint4 pad = make_uint4(s2, s2, s2, s2);
+  uint4 cur[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) cur[j] = j < n8 ? __ldg(r8 + j) : pad;
+  uint32_t acc[4 * W];
+#pragma unroll
+  for (int i = 0; i < 4 * W; ++i) acc[i] = 0;
+  for (int i = 0; i < n8; i += 3) {
+    uint4 nxt[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) nxt[j] = (i + 3 + j < n8) ? __ldg(r8 + i + 3 + j) : pad;
+    const uint32_t ws[12] = {cur[0].x, cur[0].y, cur[0].z, cur[0].w, cur[1].x, cur[1].y,
+                             cur[1].z, cur[1].w, cur[2].x, cur[2].y, cur[2].z, cur[2].w};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+#pragma unroll
+      for (int q = 0; q < 6; ++q) {
+        const uint32_t xs[2] = {ws[6 * h + q] & 0xFFFFu, ws[6 * h + q] >> 16};
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          if (W == 1) {
+            add_mask(acc, T[xs[e]]);
+          } else {
+            const uint2 mm = reinterpret_cast<const uint2*>(T)[xs[e]];
+            add_mask(acc, mm.x);
+            add_mask(acc + 4, mm.y);
+          }
+        }
+      }
+#pragma unroll
+      for (int w = 0; w < W; ++w) flush(acc + 4 * w, C + 16 * w);
+    }
+#pragma unroll
+    for (int j = 0; j < 3; ++j) cur[j] = nxt[j];
+  }
+}
+
 template <int W, int NT>
 __host__ __device__ constexpr int table_static_words() {
   return 16 * W * NT + 2 * NT;
@@ -327,8 +372,11 @@ struct GramArgs {
   unsigned* counter;
 };
 
-template <int W, int NT, int MB>
-__global__ void __launch_bounds__(NT, MB > 0 ? MB : 1) k_gram(GramArgs a) {
+// P16: the candidates' profiles are walked in the 16-bit copy (pptr16,
+// pitems16; item ids below 2^16), eight items per 16-byte load.
+template <int W, int NT, int MB, bool P16>
+__global__ void __launch_bounds__(NT, MB > 0 ? MB : 1)
+    k_gram(GramArgs a, const int32_t* __restrict__ pptr16, const uint16_t* __restrict__ pitems16) {
   constexpr int Q = 32 * W, NWARP = NT / 32;
   extern __shared__ __align__(16) uint32_t T[];
   __shared__ int32_t q_id[Q];
@@ -370,8 +418,12 @@ __global__ void __launch_bounds__(NT, MB > 0 ? MB : 1) k_gram(GramArgs a) {
         uint32_t C[16 * W];
 #pragma unroll
         for (int r = 0; r < 16 * W; ++r) C[r] = 0;
-        count_row4<W>(reinterpret_cast<const int4*>(a.pitems + a.pptr[v]), (len + 3) >> 2, T,
-                      a.n_items, C);
+        if constexpr (P16)
+          count_row16<W>(reinterpret_cast<const uint4*>(pitems16 + pptr16[v]), (len + 7) >> 3, T,
+                         a.n_items, C);
+        else
+          count_row4<W>(reinterpret_cast<const int4*>(a.pitems + a.pptr[v]), (len + 3) >> 2, T,
+                        a.n_items, C);
         visits += (unsigned)len;
         // row p, columns tq*Q .. tq*Q + nq (16-byte stores, padding columns allowed)
         uint4* dst = reinterpret_cast<uint4*>(Gc + (int64_t)p * Mp);
@@ -1322,6 +1374,27 @@ __device__ __forceinline__ void merge_knn_row(const MergeArgs& a, int64_t row) {
 }
 
 // Judge mode: one warp per query against every user.
+// The 16-bit copy of the profiles for item universes below 2^16: rows padded
+// to a multiple of 8 items (one 16-byte load) with the sentinel item m.
+__global__ void k_pad_len8(const int32_t* __restrict__ ptr, int32_t n, int32_t* __restrict__ plen) {
+  const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (u < n) plen[u] = ((ptr[u + 1] - ptr[u]) + 7) & ~7;
+}
+__global__ void k_pad_copy16(const int32_t* __restrict__ ptr, const int32_t* __restrict__ items,
+                             const int32_t* __restrict__ pptr16, int32_t n, int32_t m,
+                             int64_t capacity, uint16_t* __restrict__ p16, DevHeader* hdr) {
+  const int lane = threadIdx.x & 31;
+  const int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (u >= n || dev_failed(hdr)) return;
+  if ((int64_t)pptr16[n] > capacity || pptr16[n] < 0) {
+    if (lane == 0) dev_fail(hdr, C2_ERR_WORKSPACE);
+    return;
+  }
+  const int32_t s = ptr[u], len = ptr[u + 1] - s, ps = pptr16[u], plen = pptr16[u + 1] - ps;
+#pragma unroll 4
+  for (int j = lane; j < plen; j += 32) p16[ps + j] = (uint16_t)(j < len ? items[s + j] : m);
+}
+
 __global__ void __launch_bounds__(kNT) k_merge_knn(MergeArgs a) {
   const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (w >= a.n_rows || dev_failed(a.hdr)) return;
@@ -2031,6 +2104,7 @@ __global__ void k_gram_stats(const int64_t* __restrict__ goff, int32_t ng, DevHe
 struct TableCfg {
   int W, NT;
   int MB;   // k_gram: minimum resident blocks per SM (register cap), 0 = none
+  int P16;  // k_gram: walk the 16-bit copy of the profiles (item ids below 2^16)
 };
 
 int smem_optin() {
@@ -2091,15 +2165,17 @@ TableCfg pick_table(int strategy, int m) {
 
 int gram_smem_bytes(TableCfg c, int m) { return 4 * table_T_words(c.W, m); }
 
-template <int W, int NT, int MB>
-c2_status launch_gram_t(const GramArgs& a, cudaStream_t st) {
+template <int W, int NT, int MB, bool P16>
+c2_status launch_gram_t(const GramArgs& a, const int32_t* pptr16, const uint16_t* pitems16,
+                        cudaStream_t st) {
   const int smem = gram_smem_bytes(TableCfg{W, NT, MB}, a.n_items);
-  C2_CUDA_TRY(cudaFuncSetAttribute(k_gram<W, NT, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  auto kern = k_gram<W, NT, MB, P16>;
+  C2_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   int per_sm = 0;
-  C2_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gram<W, NT, MB>, NT, smem));
+  C2_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem));
   if (per_sm < 1) return C2_ERR_UNSUPPORTED;
   C2_CUDA_TRY(cudaMemsetAsync(a.counter, 0, sizeof(unsigned), st));
-  C2_LAUNCH(k_gram<W COMMA NT COMMA MB>, num_sms() * per_sm, NT, smem, st, a);
+  C2_LAUNCH(kern, num_sms() * per_sm, NT, smem, st, a, pptr16, pitems16);
   C2_CUDA_TRY(cudaGetLastError());
   return C2_OK;
 }
@@ -2117,18 +2193,30 @@ c2_status launch_gram_hash(const GramArgs& a, cudaStream_t st) {
   return C2_OK;
 }
 
-c2_status launch_gram(TableCfg c, const GramArgs& a, cudaStream_t st) {
-  if (c.W == 1 && c.NT == 128 && c.MB == 0) return launch_gram_t<1, 128, 0>(a, st);
-  if (c.W == 1 && c.NT == 128 && c.MB == 5) return launch_gram_t<1, 128, 5>(a, st);
-  if (c.W == 1 && c.NT == 256 && c.MB == 0) return launch_gram_t<1, 256, 0>(a, st);
-  if (c.W == 1 && c.NT == 256 && c.MB == 3) return launch_gram_t<1, 256, 3>(a, st);
-  if (c.W == 1 && c.NT == 256 && c.MB == 4) return launch_gram_t<1, 256, 4>(a, st);
-  if (c.W == 1 && c.NT == 256 && c.MB == 5) return launch_gram_t<1, 256, 5>(a, st);
-  if (c.W == 1 && c.NT == 512 && c.MB == 0) return launch_gram_t<1, 512, 0>(a, st);
-  if (c.W == 1 && c.NT == 512 && c.MB == 2) return launch_gram_t<1, 512, 2>(a, st);
-  if (c.W == 2 && c.NT == 128 && c.MB == 0) return launch_gram_t<2, 128, 0>(a, st);
-  if (c.W == 2 && c.NT == 256 && c.MB == 0) return launch_gram_t<2, 256, 0>(a, st);
-  if (c.W == 2 && c.NT == 512 && c.MB == 0) return launch_gram_t<2, 512, 0>(a, st);
+// pptr16 / pitems16: the 16-bit profile copy (null when not built); the
+// shapes with P16 walk it when it is there.
+c2_status launch_gram(TableCfg c, const GramArgs& a, const int32_t* pptr16,
+                      const uint16_t* pitems16, cudaStream_t st) {
+  if (c.P16 && !pitems16) c.P16 = 0;   // no copy (workspace too small): the int32 rows
+  if (c.P16) {
+    if (c.W == 1 && c.NT == 512 && c.MB == 2) return launch_gram_t<1, 512, 2, true>(a, pptr16, pitems16, st);
+    if (c.W == 1 && c.NT == 512 && c.MB == 0) return launch_gram_t<1, 512, 0, true>(a, pptr16, pitems16, st);
+    if (c.W == 1 && c.NT == 256 && c.MB == 3) return launch_gram_t<1, 256, 3, true>(a, pptr16, pitems16, st);
+    if (c.W == 1 && c.NT == 256 && c.MB == 4) return launch_gram_t<1, 256, 4, true>(a, pptr16, pitems16, st);
+    if (c.W == 1 && c.NT == 256 && c.MB == 5) return launch_gram_t<1, 256, 5, true>(a, pptr16, pitems16, st);
+    return C2_ERR_UNSUPPORTED;
+  }
+  if (c.W == 1 && c.NT == 128 && c.MB == 0) return launch_gram_t<1, 128, 0, false>(a, nullptr, nullptr, st);
+  if (c.W == 1 && c.NT == 128 && c.MB == 5) return launch_gram_t<1, 128, 5, false>(a, nullptr, nullptr, st);
+  if (c.W == 1 && c.NT == 256 && c.MB == 0) return launch_gram_t<1, 256, 0, false>(a, nullptr, nullptr, st);
+  if (c.W == 1 && c.NT == 256 && c.MB == 3) return launch_gram_t<1, 256, 3, false>(a, nullptr, nullptr, st);
+  if (c.W == 1 && c.NT == 256 && c.MB == 4) return launch_gram_t<1, 256, 4, false>(a, nullptr, nullptr, st);
+  if (c.W == 1 && c.NT == 256 && c.MB == 5) return launch_gram_t<1, 256, 5, false>(a, nullptr, nullptr, st);
+  if (c.W == 1 && c.NT == 512 && c.MB == 0) return launch_gram_t<1, 512, 0, false>(a, nullptr, nullptr, st);
+  if (c.W == 1 && c.NT == 512 && c.MB == 2) return launch_gram_t<1, 512, 2, false>(a, nullptr, nullptr, st);
+  if (c.W == 2 && c.NT == 128 && c.MB == 0) return launch_gram_t<2, 128, 0, false>(a, nullptr, nullptr, st);
+  if (c.W == 2 && c.NT == 256 && c.MB == 0) return launch_gram_t<2, 256, 0, false>(a, nullptr, nullptr, st);
+  if (c.W == 2 && c.NT == 512 && c.MB == 0) return launch_gram_t<2, 512, 0, false>(a, nullptr, nullptr, st);
   return C2_ERR_UNSUPPORTED;
 }
 
@@ -2162,9 +2250,10 @@ struct TuneEntry {
 std::mutex g_tune_mu;
 std::map<TuneKey, TuneEntry> g_tune;
 
-const TableCfg kGramShapes[] = {{2, 256, 0}, {2, 512, 0}, {2, 128, 0}, {1, 512, 0}, {1, 256, 0},
-                                 {1, 128, 0}, {1, 256, 3}, {1, 256, 4}, {1, 256, 5}, {1, 512, 2},
-                                 {1, 128, 5}};
+const TableCfg kGramShapes[] = {{2, 256, 0},    {2, 512, 0},    {2, 128, 0},    {1, 512, 0},
+                                 {1, 256, 0},    {1, 128, 0},    {1, 256, 3},    {1, 256, 4},
+                                 {1, 256, 5},    {1, 512, 2},    {1, 128, 5},    {1, 512, 2, 1},
+                                 {1, 256, 3, 1}, {1, 256, 4, 1}, {1, 256, 5, 1}, {1, 512, 0, 1}};
 
 bool gram_fits(TableCfg c, int m) { return gram_smem_bytes(c, m) + 1024 <= smem_optin(); }
 
@@ -2309,8 +2398,7 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
                               cudaMemcpyDeviceToHost, st));
   C2_CUDA_TRY(cudaMemcpyAsync(&max_len, &w.hdr->knn_max_len, sizeof(int32_t),
                               cudaMemcpyDeviceToHost, st));
-  if (tc_allowed)
-    C2_CUDA_TRY(cudaMemcpyAsync(&nnz32, ptr + s.n, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  C2_CUDA_TRY(cudaMemcpyAsync(&nnz32, ptr + s.n, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   C2_CUDA_TRY(cudaStreamSynchronize(st));
   // greedy clusters without a count matrix: counts from the profiles, one
   // warp per member (the working lists are free again before the batches)
@@ -2397,6 +2485,22 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
   p_gsetup2.end();
 
   GramArgs ga0{};
+  // the table kernel walks a 16-bit copy of the profiles when item ids fit
+  // 16 bits (half the load instructions of the int32 rows)
+  w.pitems16 = nullptr;
+  // needed by the autotuner's trials, or when a tuned shape walks it
+  bool want16 = opt.strategy == C2_STRATEGY_AUTO && !tune.shapes_done;
+  for (int q = 0; q < kBuckets; ++q)
+    want16 = want16 || (opt.strategy == C2_STRATEGY_AUTO && tune.shapes_done && tune.cfg[q].P16);
+  if (want16 && tc.W > 0 && s.m <= 65535 && nnz32 > 0 &&
+      (int64_t)(p16_offset(nnz32, s.n) + p16_bytes(nnz32, s.n)) <= w.tail_bytes) {
+    w.pitems16 = reinterpret_cast<uint16_t*>(reinterpret_cast<char*>(w.pitems) +
+                                             p16_offset(nnz32, s.n));
+    C2_LAUNCH(k_pad_len8, div_up(s.n, T), T, 0, st, ptr, s.n, w.pptr16);
+    C2_CUDA_TRY(scan_exclusive(w.pptr16, w.pptr16, s.n, w.scan_tmp, st));
+    C2_LAUNCH(k_pad_copy16, div_up((int64_t)s.n * 32, T), T, 0, st, ptr, items, w.pptr16, s.n,
+              s.m, (int64_t)(p16_bytes(nnz32, s.n) / 2), w.pitems16, w.hdr);
+  }
   ga0.ptr = ptr; ga0.items = items; ga0.pptr = w.pptr; ga0.pitems = w.pitems;
   ga0.n_items = s.m; ga0.work_c = w.work_c; ga0.work_t = w.work_t;
   ga0.cptr = cptr; ga0.cusers = cusers; ga0.iinfo = w.iinfo; ga0.gofs = w.gofs; ga0.gram = w.gram;
@@ -2535,7 +2639,7 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
             GramArgs ga = ga0;
             ga.work_begin = w.bt_off;
             ga.work_end = w.bt_off + nb;
-            return tc.W ? launch_gram(tc, ga, st) : launch_gram_hash(ga, st);
+            return tc.W ? launch_gram(tc, ga, w.pptr16, w.pitems16, st) : launch_gram_hash(ga, st);
           }, &t_tab);
           if (rc) return rc;
           rc = timed([&]() { return run_tc(members[bk], false); }, &t_tc);
@@ -2580,7 +2684,7 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
           GramArgs ga = ga0;
           ga.work_begin = w.bt_off;
           ga.work_end = w.bt_off + nb;
-          return launch_gram(shape, ga, st);
+          return launch_gram(shape, ga, w.pptr16, w.pitems16, st);
         };
         if (opt.strategy == C2_STRATEGY_AUTO && !tune.shapes_done) {
           // first call for these sizes: time every shape that fits, on each
@@ -2594,7 +2698,7 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
             if (!present[q]) continue;
             float best = 1e30f;
             for (const TableCfg& shape : kGramShapes) {
-              if (!gram_fits(shape, s.m)) continue;
+              if (!gram_fits(shape, s.m) || (shape.P16 && !w.pitems16)) continue;
               float ms = 0.f;
               c2_status rc = timed([&]() { return run_bucket(q, shape); }, &ms);
               if (rc) return rc;
@@ -2605,7 +2709,7 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
           float uni_best = 1e30f;
           TableCfg uni_cfg = tc;
           for (const TableCfg& shape : kGramShapes) {
-            if (!gram_fits(shape, s.m)) continue;
+            if (!gram_fits(shape, s.m) || (shape.P16 && !w.pitems16)) continue;
             float ms = 0.f;
             c2_status rc = timed([&]() { return run_bucket(-1, shape); }, &ms);
             if (rc) return rc;
@@ -2874,9 +2978,9 @@ size_t autotune_report(char* buf, size_t len) {
     for (int q = 0; q < kBuckets; ++q) {
       snprintf(tmp, sizeof tmp,
                "%s{\"sizes\": \"%s\", \"words\": %d, \"threads\": %d, \"min_blocks\": %d, "
-               "\"ms\": %.4f}",
+               "\"items16\": %s, \"ms\": %.4f}",
                q ? ", " : "", names[q], kv.second.cfg[q].W, kv.second.cfg[q].NT, kv.second.cfg[q].MB,
-               kv.second.ms[q]);
+               kv.second.cfg[q].P16 ? "true" : "false", kv.second.ms[q]);
       out += tmp;
     }
     out += "], \"strategy\": [";
@@ -2908,14 +3012,14 @@ size_t autotune_report(char* buf, size_t len) {
 }
 
 // Text form of the autotuner's table, one line per problem size:
-//   n m t b N k thr unified shapes_done tc_done  (W NT MB ms) x kBuckets
+//   n m t b N k thr unified shapes_done tc_done  (W NT MB P16 ms) x kBuckets
 //   (route table_ms tc_ms) x (kBuckets * kDensityBuckets)
-// after a first line "c2-autotune 1".
+// after a first line "c2-autotune 2".
 int autotune_save(const char* path) {
   FILE* f = fopen(path, "w");
   if (!f) return -1;
   std::lock_guard<std::mutex> lk(g_tune_mu);
-  fprintf(f, "c2-autotune 1\n");
+  fprintf(f, "c2-autotune 2\n");
   for (const auto& kv : g_tune) {
     const TuneKey& k = kv.first;
     const TuneEntry& e = kv.second;
@@ -2923,7 +3027,7 @@ int autotune_save(const char* path) {
             (long long)k.t, (long long)k.b, (long long)k.N, (long long)k.k, (long long)k.thr,
             e.unified ? 1 : 0, e.shapes_done ? 1 : 0, e.tc_done ? 1 : 0);
     for (int q = 0; q < kBuckets; ++q)
-      fprintf(f, " %d %d %d %.6g", e.cfg[q].W, e.cfg[q].NT, e.cfg[q].MB, e.ms[q]);
+      fprintf(f, " %d %d %d %d %.6g", e.cfg[q].W, e.cfg[q].NT, e.cfg[q].MB, e.cfg[q].P16, e.ms[q]);
     for (int i = 0; i < kBuckets * kDensityBuckets; ++i)
       fprintf(f, " %d %.6g %.6g", (int)e.route[i], e.table_ms[i], e.tc_ms[i]);
     fprintf(f, "\n");
@@ -2941,7 +3045,7 @@ int autotune_load(const char* path) {
   if (!f) return -1;
   char magic[32] = {0};
   int version = 0;
-  if (fscanf(f, "%31s %d", magic, &version) != 2 || strcmp(magic, "c2-autotune") || version != 1) {
+  if (fscanf(f, "%31s %d", magic, &version) != 2 || strcmp(magic, "c2-autotune") || version != 2) {
     fclose(f);
     return -1;
   }
@@ -2958,7 +3062,8 @@ int autotune_load(const char* path) {
     e.tc_done = td != 0;
     bool ok = true;
     for (int q = 0; q < kBuckets && ok; ++q)
-      ok = fscanf(f, "%d %d %d %f", &e.cfg[q].W, &e.cfg[q].NT, &e.cfg[q].MB, &e.ms[q]) == 4;
+      ok = fscanf(f, "%d %d %d %d %f", &e.cfg[q].W, &e.cfg[q].NT, &e.cfg[q].MB, &e.cfg[q].P16,
+                  &e.ms[q]) == 5;
     for (int i = 0; i < kBuckets * kDensityBuckets && ok; ++i) {
       int r = -1;
       ok = fscanf(f, "%d %f %f", &r, &e.table_ms[i], &e.tc_ms[i]) == 3;
@@ -2969,7 +3074,8 @@ int autotune_load(const char* path) {
     for (int q = 0; q < kBuckets; ++q) {
       bool known = false;
       for (const TableCfg& c : kGramShapes)
-        known = known || (c.W == e.cfg[q].W && c.NT == e.cfg[q].NT && c.MB == e.cfg[q].MB);
+        known = known || (c.W == e.cfg[q].W && c.NT == e.cfg[q].NT && c.MB == e.cfg[q].MB &&
+                          c.P16 == e.cfg[q].P16);
       if (!known) e.shapes_done = false;
     }
     got[TuneKey{v[0], v[1], v[2], v[3], v[4], v[5], v[6]}] = e;

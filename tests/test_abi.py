@@ -122,11 +122,12 @@ def test_autotune_table_round_trip_needs_no_gpu(lib, tmp_path):
     # a saved table is read back into the process's table (host only)
     p = tmp_path / "tune.txt"
     routes = " ".join("%d 0.5 0.25" % (1 if i == 7 else -1) for i in range(20))
-    shapes = " ".join("1 256 4 1.5" for _ in range(4))
-    p.write_text("c2-autotune 1\n123 456 8 4096 2000 30 4500 1 1 1 " + shapes + " " + routes + "\n")
+    shapes = " ".join("1 256 4 1 1.5" for _ in range(4))
+    p.write_text("c2-autotune 2\n123 456 8 4096 2000 30 4500 1 1 1 " + shapes + " " + routes + "\n")
     assert c2.c2_autotune_load(str(p)) == 1
     rep = [e for e in c2.c2_autotune_report() if e.get("n") == 123]
     assert rep and rep[0]["m"] == 456 and rep[0]["buckets"][0]["threads"] == 256
+    assert rep[0]["buckets"][0]["items16"] is True
     assert [s["use"] for s in rep[0]["strategy"]] == ["tensor"]
     q = tmp_path / "again.txt"
     assert c2.c2_autotune_save(str(q)) == 0
