@@ -188,6 +188,140 @@ __device__ __forceinline__ void count_row16(const uint4* __restrict__ r8, int n8
   }
 }
 
+// ---- bit-sliced counts (tables of one word: 32 queries)
+// Each thread keeps its candidate's 32 counts as 16 bit planes: bit b of
+// plane i is bit i of the count of the query marked with bit b.  Query j of a
+// tile is marked with bit qbit(j), which puts queries 2h and 2h+1 at bits h
+// and 16+h, so that transposing the planes as two 16 x 16 bit matrices (one
+// per half word) leaves word h = count(2h) | count(2h+1) << 16: the row
+// segment as it is stored.
+__device__ __forceinline__ uint32_t qbit(int j) { return (uint32_t)((j >> 1) + 16 * (j & 1)); }
+
+// Full adder on 32 one-bit lanes: a <- a ^ b ^ c, carry <- majority(a, b, c).
+__device__ __forceinline__ void csa(uint32_t& a, uint32_t b, uint32_t c, uint32_t& carry) {
+  carry = (a & b) | (a & c) | (b & c);
+  a ^= b ^ c;
+}
+
+// Adds 16 masks to the planes A[0..B-1]: a carry-save tree (15 full adders)
+// into the planes of weight 1, 2, 4 and 8, then the one carry of weight 16
+// rippled through the planes above.  The counts stay below 2^B (B = 8 when
+// every walked profile is shorter than 256 items).
+template <int B>
+__device__ __forceinline__ void add16(uint32_t* A, const uint32_t* m) {
+  uint32_t t8[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    uint32_t t4[2];
+#pragma unroll
+    for (int g = 0; g < 2; ++g) {
+      uint32_t t2[2];
+#pragma unroll
+      for (int e = 0; e < 2; ++e) csa(A[0], m[8 * h + 4 * g + 2 * e], m[8 * h + 4 * g + 2 * e + 1], t2[e]);
+      csa(A[1], t2[0], t2[1], t4[g]);
+    }
+    csa(A[2], t4[0], t4[1], t8[h]);
+  }
+  uint32_t t;
+  csa(A[3], t8[0], t8[1], t);
+#pragma unroll
+  for (int b = 4; b < B; ++b) {
+    const uint32_t c = A[b] & t;
+    A[b] ^= t;
+    t = c;
+  }
+}
+
+// Two 16 x 16 bit transposes at once (one per half word) of the planes
+// z[0..15]: z[h] bit i <-> z[i] bit h, and likewise bits 16+i / 16+h.
+// Block swaps of 8 (byte permutes), 4, 2 and 1 rows.
+__device__ __forceinline__ void transpose_halves16(uint32_t* z) {
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const uint32_t a = z[k], b = z[k + 8];
+    z[k] = __byte_perm(a, b, 0x6240);
+    z[k + 8] = __byte_perm(a, b, 0x7351);
+  }
+#pragma unroll
+  for (int k = 0; k < 16; ++k)
+    if (!(k & 4)) {
+      const uint32_t t = ((z[k] >> 4) ^ z[k + 4]) & 0x0F0F0F0Fu;
+      z[k + 4] ^= t;
+      z[k] ^= t << 4;
+    }
+#pragma unroll
+  for (int k = 0; k < 16; ++k)
+    if (!(k & 2)) {
+      const uint32_t t = ((z[k] >> 2) ^ z[k + 2]) & 0x33333333u;
+      z[k + 2] ^= t;
+      z[k] ^= t << 2;
+    }
+#pragma unroll
+  for (int k = 0; k < 16; ++k)
+    if (!(k & 1)) {
+      const uint32_t t = ((z[k] >> 1) ^ z[k + 1]) & 0x55555555u;
+      z[k + 1] ^= t;
+      z[k] ^= t << 1;
+    }
+}
+
+// Walks one 16-bit padded profile (n8 loads of 8 items) 16 items at a time
+// into the planes A, the next two loads issued before the current 16 items
+// are counted.
+template <int B>
+__device__ __forceinline__ void count_row16_bs(const uint4* __restrict__ r8, int n8,
+                                               const uint32_t* __restrict__ T, int sentinel,
+                                               uint32_t* A) {
+  const uint32_t s2 = (uint32_t)sentinel * 0x10001u;
+  const uint4 pad = make_uint4(s2, s2, s2, s2);
+  uint4 cur[2];
+#pragma unroll
+  for (int j = 0; j < 2; ++j) cur[j] = j < n8 ? __ldg(r8 + j) : pad;
+  for (int i = 0; i < n8; i += 2) {
+    uint4 nxt[2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) nxt[j] = (i + 2 + j < n8) ? __ldg(r8 + i + 2 + j) : pad;
+    const uint32_t ws[8] = {cur[0].x, cur[0].y, cur[0].z, cur[0].w,
+                            cur[1].x, cur[1].y, cur[1].z, cur[1].w};
+    uint32_t m[16];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      m[2 * q] = T[ws[q] & 0xFFFFu];
+      m[2 * q + 1] = T[ws[q] >> 16];
+    }
+    add16<B>(A, m);
+#pragma unroll
+    for (int j = 0; j < 2; ++j) cur[j] = nxt[j];
+  }
+}
+
+// The same over the int32 padded profile (n4 loads of 4 items).
+template <int B>
+__device__ __forceinline__ void count_row4_bs(const int4* __restrict__ r4, int n4,
+                                              const uint32_t* __restrict__ T, int sentinel,
+                                              uint32_t* A) {
+  const int4 pad = make_int4(sentinel, sentinel, sentinel, sentinel);
+  int4 cur[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) cur[j] = j < n4 ? __ldg(r4 + j) : pad;
+  for (int i = 0; i < n4; i += 4) {
+    int4 nxt[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) nxt[j] = (i + 4 + j < n4) ? __ldg(r4 + i + 4 + j) : pad;
+    uint32_t m[16];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      m[4 * j] = T[cur[j].x];
+      m[4 * j + 1] = T[cur[j].y];
+      m[4 * j + 2] = T[cur[j].z];
+      m[4 * j + 3] = T[cur[j].w];
+    }
+    add16<B>(A, m);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) cur[j] = nxt[j];
+  }
+}
+
 template <int W, int NT>
 __host__ __device__ constexpr int table_static_words() {
   return 16 * W * NT + 2 * NT;
@@ -399,8 +533,9 @@ __global__ void __launch_bounds__(NT, MB > 0 ? MB : 1)
     __syncthreads();
     for (int j = warp; j < nq; j += NWARP) {
       const int u = q_id[j];
+      const uint32_t bit = W == 1 ? 1u << qbit(j) : 1u << (j & 31);
       for (int e = a.ptr[u] + lane; e < a.ptr[u + 1]; e += 32)
-        atomicOr(&T[a.items[e] * W + (j >> 5)], 1u << (j & 31));
+        atomicOr(&T[a.items[e] * W + (j >> 5)], bit);
     }
     __syncthreads();
     uint16_t* G0 = a.gram + a.gofs[c];
@@ -411,6 +546,44 @@ __global__ void __launch_bounds__(NT, MB > 0 ? MB : 1)
       p0 = tq * Q + __shfl_sync(0xffffffffu, p0, 0);
       if (p0 >= M) break;
       const int p = p0 + lane;
+      if constexpr (W == 1) {
+        const unsigned act = __ballot_sync(0xffffffffu, p < M);
+        if (p < M) {
+          const int2 info = a.iinfo[cbase + p];
+          const int v = a.cusers[cbase + info.x];
+          const int len = info.y;
+          uint32_t A[16];
+#pragma unroll
+          for (int r = 0; r < 16; ++r) A[r] = 0;
+          // eight planes while every profile of the warp is shorter than 256
+          const bool wide = __any_sync(act, len > 255);
+          if constexpr (P16) {
+            const uint4* r8 = reinterpret_cast<const uint4*>(pitems16 + pptr16[v]);
+            if (wide) count_row16_bs<16>(r8, (len + 7) >> 3, T, a.n_items, A);
+            else count_row16_bs<8>(r8, (len + 7) >> 3, T, a.n_items, A);
+          } else {
+            const int4* r4 = reinterpret_cast<const int4*>(a.pitems + a.pptr[v]);
+            if (wide) count_row4_bs<16>(r4, (len + 3) >> 2, T, a.n_items, A);
+            else count_row4_bs<8>(r4, (len + 3) >> 2, T, a.n_items, A);
+          }
+          visits += (unsigned)len;
+          transpose_halves16(A);   // A[h] = count(2h) | count(2h + 1) << 16
+          uint4* dst = reinterpret_cast<uint4*>(Gc + (int64_t)p * Mp);
+#pragma unroll
+          for (int g8 = 0; g8 < 4; ++g8)
+            if (g8 * 8 < nq)
+              __stcs(dst + g8, make_uint4(A[4 * g8], A[4 * g8 + 1], A[4 * g8 + 2], A[4 * g8 + 3]));
+          if (p >= (tq + 1) * Q) {
+            uint16_t* col = G0 + (int64_t)(tq * Q) * Mp + p;
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+              if (j < nq)
+                __stcs(reinterpret_cast<unsigned short*>(col + (int64_t)j * Mp),
+                       (unsigned short)(A[j >> 1] >> (16 * (j & 1))));
+          }
+        }
+        continue;
+      }
       if (p < M) {
         const int2 info = a.iinfo[cbase + p];
         const int v = a.cusers[cbase + info.x];

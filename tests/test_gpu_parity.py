@@ -141,6 +141,43 @@ def test_local_brute_force_strategies(c2, strategy):
         assert st["tc_clusters"] >= 1 and st["tc_macs"] > 0
 
 
+def _shape_test_profiles():
+    # log-normal lengths around 150 (up to 1,200 items: walks with eight and
+    # with sixteen bit planes, and warps mixing both), plus identical pairs of
+    # 255-, 256- and 900-item profiles, whose counts reach 255 (the largest
+    # count of eight planes), 256 and 900
+    ptr, items = synth.random_profiles(1800, 1500, 150, 31, zipf_s=0.9, lmax=1200)
+    rows = [items[ptr[u]:ptr[u + 1]].tolist() for u in range(ptr.size - 1)]
+    rng = np.random.default_rng(77)
+    for length, copies in ((255, 3), (256, 2), (900, 2)):
+        r = sorted(rng.choice(1500, size=length, replace=False).tolist())
+        rows.extend([r] * copies)
+    return csr_from_sets(rows)
+
+
+@pytest.mark.parametrize("shape", [(1, 512, 2, 1), (1, 256, 5, 1), (1, 512, 0, 1),
+                                   (1, 512, 2, 0), (1, 256, 4, 0), (2, 256, 0, 0)])
+def test_local_table_shapes(c2, tmp_path, shape):
+    # each table shape the autotuner can choose (words of queries, threads,
+    # resident blocks, 16-bit or int32 profile walk), forced by a loaded
+    # table; 98 clusters of up to 500 members (many 32-query tiles, ragged
+    # last tiles, mirrored columns): local rows and pair counts equal the
+    # oracle's
+    ptr, items = _shape_test_profiles()
+    n, m, t, b, N, k, thr, seed = ptr.size - 1, 1500, 2, 64, 500, 10, 10 ** 9, 13
+    W, NT, MB, P16 = shape
+    cfg = " ".join(f"{W} {NT} {MB} {P16} 1" for _ in range(4))
+    routes = " ".join("0 1 2" for _ in range(20))
+    path = tmp_path / "tune.txt"
+    path.write_text(f"c2-autotune 2\n{n} {m} {t} {b} {N} {k} {thr} 1 1 1 {cfg} {routes}\n")
+    assert c2.c2_autotune_load(str(path)) == 1
+    check_local(c2, ptr, items, m, t, b, N, k, seed, thr)
+    rep = [e for e in c2.c2_autotune_report()
+           if (e.get("n"), e.get("m"), e.get("t"), e.get("b"), e.get("N")) == (n, m, t, b, N)]
+    assert rep and rep[0]["buckets"][0]["threads"] == NT
+    assert rep[0]["buckets"][0]["items16"] is bool(P16)
+
+
 def test_local_brute_force_tensor_cores_many_tiles(c2):
     # clusters of up to 1,771 members (14 row tiles, 7 column tiles, ragged
     # edges; two residuals above N) over 3,000 items: operands of many
