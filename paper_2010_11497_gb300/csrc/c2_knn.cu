@@ -506,6 +506,44 @@ struct GramArgs {
   unsigned* counter;
 };
 
+// Marks (bit) or clears (Clear) the table entries of query u's items, read
+// from the padded copy the walk reads (eight 16-bit or four int32 items per
+// 16-byte load, one load per lane and step): a query of up to 256 items is
+// one step.  Padding positions are skipped, so the sentinel's entry stays 0.
+template <int W, bool P16, bool Clear>
+__device__ __forceinline__ void mark_query(uint32_t* T, int word, uint32_t bit, int u, int lane,
+                                           const GramArgs& a, const int32_t* __restrict__ pptr16,
+                                           const uint16_t* __restrict__ pitems16) {
+  const int len = a.ptr[u + 1] - a.ptr[u];
+  if constexpr (P16) {
+    const uint4* r8 = reinterpret_cast<const uint4*>(pitems16 + pptr16[u]);
+    for (int g = lane; g < (len + 7) >> 3; g += 32) {
+      const uint4 q = __ldg(r8 + g);
+      const uint32_t ws[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const uint32_t x = (e & 1) ? ws[e >> 1] >> 16 : ws[e >> 1] & 0xFFFFu;
+        if (8 * g + e < len) {
+          if constexpr (Clear) T[x * W + word] = 0u;
+          else atomicOr(&T[x * W + word], bit);
+        }
+      }
+    }
+  } else {
+    const int4* r4 = reinterpret_cast<const int4*>(a.pitems + a.pptr[u]);
+    for (int g = lane; g < (len + 3) >> 2; g += 32) {
+      const int4 q = __ldg(r4 + g);
+      const int xs[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        if (4 * g + e < len) {
+          if constexpr (Clear) T[xs[e] * W + word] = 0u;
+          else atomicOr(&T[xs[e] * W + word], bit);
+        }
+    }
+  }
+}
+
 // P16: the candidates' profiles are walked in the 16-bit copy (pptr16,
 // pitems16; item ids below 2^16), eight items per 16-byte load.
 template <int W, int NT, int MB, bool P16>
@@ -531,12 +569,9 @@ __global__ void __launch_bounds__(NT, MB > 0 ? MB : 1)
     const int nq = min(Q, M - tq * Q);
     if (tid < Q) q_id[tid] = tid < nq ? a.cusers[cbase + a.iinfo[cbase + tq * Q + tid].x] : -1;
     __syncthreads();
-    for (int j = warp; j < nq; j += NWARP) {
-      const int u = q_id[j];
-      const uint32_t bit = W == 1 ? 1u << qbit(j) : 1u << (j & 31);
-      for (int e = a.ptr[u] + lane; e < a.ptr[u + 1]; e += 32)
-        atomicOr(&T[a.items[e] * W + (j >> 5)], bit);
-    }
+    for (int j = warp; j < nq; j += NWARP)
+      mark_query<W, P16, false>(T, j >> 5, W == 1 ? 1u << qbit(j) : 1u << (j & 31), q_id[j], lane,
+                                a, pptr16, pitems16);
     __syncthreads();
     uint16_t* G0 = a.gram + a.gofs[c];
     uint16_t* Gc = G0 + tq * Q;
@@ -626,10 +661,8 @@ __global__ void __launch_bounds__(NT, MB > 0 ? MB : 1)
       }
     }
     __syncthreads();
-    for (int j = warp; j < nq; j += NWARP) {
-      const int u = q_id[j];
-      for (int e = a.ptr[u] + lane; e < a.ptr[u + 1]; e += 32) T[a.items[e] * W + (j >> 5)] = 0;
-    }
+    for (int j = warp; j < nq; j += NWARP)
+      mark_query<W, P16, true>(T, j >> 5, 0u, q_id[j], lane, a, pptr16, pitems16);
     if (tid == 0) s_next = 0;
     __syncthreads();
   }
