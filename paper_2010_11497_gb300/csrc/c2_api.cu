@@ -101,6 +101,7 @@ void bind_knn_ws(Ws& w, const Sizes& s, KnnWs& c) {
   c.ub_g = w.take<int32_t>(S + 1);
   c.ipos = w.take<int32_t>(S + 1);
   c.iinfo = w.take<int2>(S + 1);
+  c.islot = w.take<int4>(S + 1);
   c.chg0 = w.take<int32_t>(S + 1);
   c.chg1 = w.take<int32_t>(S + 1);
   c.gfresh = w.take<int32_t>(S + 1);

@@ -168,6 +168,8 @@ struct KnnWs {
   int32_t *ub_slot, *ub_g; // [S+1] brute-force users of a batch
   int32_t* ipos;           // [S+1] slot -> internal position in its cluster
   int2* iinfo;             // [S+1] internal slot -> (local index, profile length)
+  int4* islot;             // [S+1] internal slot -> (int32 padded offset, 16-bit padded
+                           //        offset, profile length, user)
   int32_t *chg0, *chg1;    // [S+1] greedy: list changed in the last round
   int32_t* gfresh;         // [S+1] greedy: evaluations of the last computed round
   int32_t* pptr;           // [n+1] padded CSR offsets

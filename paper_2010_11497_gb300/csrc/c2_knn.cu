@@ -500,26 +500,28 @@ struct GramArgs {
   const int32_t* cptr;
   const int32_t* cusers;
   const int2* iinfo;       // internal slot -> (local index, profile length)
+  const int4* islot;       // internal slot -> (int32 offset, 16-bit offset, length, user)
   const int64_t* gofs;
   uint16_t* gram;
   DevHeader* hdr;
   unsigned* counter;
 };
 
-// Marks (bit) or clears (Clear) the table entries of query u's items, read
+// Marks (bit) or clears (Clear) the table entries of the items of query q
+// (its slot record: padded offsets and length), read
 // from the padded copy the walk reads (eight 16-bit or four int32 items per
 // 16-byte load, one load per lane and step): a query of up to 256 items is
 // one step.  Padding positions are skipped, so the sentinel's entry stays 0.
 template <int W, bool P16, bool Clear>
-__device__ __forceinline__ void mark_query(uint32_t* T, int word, uint32_t bit, int u, int lane,
-                                           const GramArgs& a, const int32_t* __restrict__ pptr16,
+__device__ __forceinline__ void mark_query(uint32_t* T, int word, uint32_t bit, int4 q, int lane,
+                                           const GramArgs& a,
                                            const uint16_t* __restrict__ pitems16) {
-  const int len = a.ptr[u + 1] - a.ptr[u];
+  const int len = q.z;
   if constexpr (P16) {
-    const uint4* r8 = reinterpret_cast<const uint4*>(pitems16 + pptr16[u]);
+    const uint4* r8 = reinterpret_cast<const uint4*>(pitems16 + q.y);
     for (int g = lane; g < (len + 7) >> 3; g += 32) {
-      const uint4 q = __ldg(r8 + g);
-      const uint32_t ws[4] = {q.x, q.y, q.z, q.w};
+      const uint4 x8 = __ldg(r8 + g);
+      const uint32_t ws[4] = {x8.x, x8.y, x8.z, x8.w};
 #pragma unroll
       for (int e = 0; e < 8; ++e) {
         const uint32_t x = (e & 1) ? ws[e >> 1] >> 16 : ws[e >> 1] & 0xFFFFu;
@@ -530,10 +532,10 @@ __device__ __forceinline__ void mark_query(uint32_t* T, int word, uint32_t bit, 
       }
     }
   } else {
-    const int4* r4 = reinterpret_cast<const int4*>(a.pitems + a.pptr[u]);
+    const int4* r4 = reinterpret_cast<const int4*>(a.pitems + q.x);
     for (int g = lane; g < (len + 3) >> 2; g += 32) {
-      const int4 q = __ldg(r4 + g);
-      const int xs[4] = {q.x, q.y, q.z, q.w};
+      const int4 x4 = __ldg(r4 + g);
+      const int xs[4] = {x4.x, x4.y, x4.z, x4.w};
 #pragma unroll
       for (int e = 0; e < 4; ++e)
         if (4 * g + e < len) {
@@ -551,7 +553,7 @@ __global__ void __launch_bounds__(NT, MB > 0 ? MB : 1)
     k_gram(GramArgs a, const int32_t* __restrict__ pptr16, const uint16_t* __restrict__ pitems16) {
   constexpr int Q = 32 * W, NWARP = NT / 32;
   extern __shared__ __align__(16) uint32_t T[];
-  __shared__ int32_t q_id[Q];
+  __shared__ int4 q_slot[Q];
   __shared__ int s_work, s_next;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int i = tid; i < (a.n_items + 1) * W; i += NT) T[i] = 0;
@@ -567,11 +569,11 @@ __global__ void __launch_bounds__(NT, MB > 0 ? MB : 1)
     const int c = a.work_c[wi], tq = a.work_t[wi];
     const int cbase = a.cptr[c], M = a.cptr[c + 1] - cbase, Mp = (M + 7) & ~7;
     const int nq = min(Q, M - tq * Q);
-    if (tid < Q) q_id[tid] = tid < nq ? a.cusers[cbase + a.iinfo[cbase + tq * Q + tid].x] : -1;
+    if (tid < Q) q_slot[tid] = tid < nq ? a.islot[cbase + tq * Q + tid] : make_int4(0, 0, 0, -1);
     __syncthreads();
     for (int j = warp; j < nq; j += NWARP)
-      mark_query<W, P16, false>(T, j >> 5, W == 1 ? 1u << qbit(j) : 1u << (j & 31), q_id[j], lane,
-                                a, pptr16, pitems16);
+      mark_query<W, P16, false>(T, j >> 5, W == 1 ? 1u << qbit(j) : 1u << (j & 31), q_slot[j],
+                                lane, a, pitems16);
     __syncthreads();
     uint16_t* G0 = a.gram + a.gofs[c];
     uint16_t* Gc = G0 + tq * Q;
@@ -584,20 +586,19 @@ __global__ void __launch_bounds__(NT, MB > 0 ? MB : 1)
       if constexpr (W == 1) {
         const unsigned act = __ballot_sync(0xffffffffu, p < M);
         if (p < M) {
-          const int2 info = a.iinfo[cbase + p];
-          const int v = a.cusers[cbase + info.x];
-          const int len = info.y;
+          const int4 sl = a.islot[cbase + p];
+          const int len = sl.z;
           uint32_t A[16];
 #pragma unroll
           for (int r = 0; r < 16; ++r) A[r] = 0;
           // eight planes while every profile of the warp is shorter than 256
           const bool wide = __any_sync(act, len > 255);
           if constexpr (P16) {
-            const uint4* r8 = reinterpret_cast<const uint4*>(pitems16 + pptr16[v]);
+            const uint4* r8 = reinterpret_cast<const uint4*>(pitems16 + sl.y);
             if (wide) count_row16_bs<16>(r8, (len + 7) >> 3, T, a.n_items, A);
             else count_row16_bs<8>(r8, (len + 7) >> 3, T, a.n_items, A);
           } else {
-            const int4* r4 = reinterpret_cast<const int4*>(a.pitems + a.pptr[v]);
+            const int4* r4 = reinterpret_cast<const int4*>(a.pitems + sl.x);
             if (wide) count_row4_bs<16>(r4, (len + 3) >> 2, T, a.n_items, A);
             else count_row4_bs<8>(r4, (len + 3) >> 2, T, a.n_items, A);
           }
@@ -620,17 +621,16 @@ __global__ void __launch_bounds__(NT, MB > 0 ? MB : 1)
         continue;
       }
       if (p < M) {
-        const int2 info = a.iinfo[cbase + p];
-        const int v = a.cusers[cbase + info.x];
-        const int len = info.y;
+        const int4 sl = a.islot[cbase + p];
+        const int len = sl.z;
         uint32_t C[16 * W];
 #pragma unroll
         for (int r = 0; r < 16 * W; ++r) C[r] = 0;
         if constexpr (P16)
-          count_row16<W>(reinterpret_cast<const uint4*>(pitems16 + pptr16[v]), (len + 7) >> 3, T,
+          count_row16<W>(reinterpret_cast<const uint4*>(pitems16 + sl.y), (len + 7) >> 3, T,
                          a.n_items, C);
         else
-          count_row4<W>(reinterpret_cast<const int4*>(a.pitems + a.pptr[v]), (len + 3) >> 2, T,
+          count_row4<W>(reinterpret_cast<const int4*>(a.pitems + sl.x), (len + 3) >> 2, T,
                         a.n_items, C);
         visits += (unsigned)len;
         // row p, columns tq*Q .. tq*Q + nq (16-byte stores, padding columns allowed)
@@ -662,7 +662,7 @@ __global__ void __launch_bounds__(NT, MB > 0 ? MB : 1)
     }
     __syncthreads();
     for (int j = warp; j < nq; j += NWARP)
-      mark_query<W, P16, true>(T, j >> 5, 0u, q_id[j], lane, a, pptr16, pitems16);
+      mark_query<W, P16, true>(T, j >> 5, 0u, q_slot[j], lane, a, pitems16);
     if (tid == 0) s_next = 0;
     __syncthreads();
   }
@@ -1028,7 +1028,11 @@ __global__ void __launch_bounds__(256) k_order(const int32_t* __restrict__ gcl, 
                                                int32_t* __restrict__ ipos,
                                                int2* __restrict__ iinfo,
                                                const int64_t* __restrict__ gofs,
-                                               uint16_t* __restrict__ gram) {
+                                               uint16_t* __restrict__ gram,
+                                               const int32_t* __restrict__ cusers,
+                                               const int32_t* __restrict__ pptr,
+                                               const int32_t* __restrict__ pptr16,
+                                               int4* __restrict__ islot) {
   __shared__ int32_t start[64];
   __shared__ int32_t wcnt[8][64];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1066,6 +1070,8 @@ __global__ void __launch_bounds__(256) k_order(const int32_t* __restrict__ gcl, 
       for (int w2 = 0; w2 < warp; ++w2) off += wcnt[w2][bk];
       ipos[cbase + i] = off;
       iinfo[cbase + off] = make_int2(i, len);
+      const int v = cusers[cbase + i];
+      islot[cbase + off] = make_int4(pptr[v], pptr16 ? pptr16[v] : 0, len, v);
       lenrow[off] = (uint16_t)len;
     }
     __syncthreads();
@@ -2709,7 +2715,8 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
   }
   ga0.ptr = ptr; ga0.items = items; ga0.pptr = w.pptr; ga0.pitems = w.pitems;
   ga0.n_items = s.m; ga0.work_c = w.work_c; ga0.work_t = w.work_t;
-  ga0.cptr = cptr; ga0.cusers = cusers; ga0.iinfo = w.iinfo; ga0.gofs = w.gofs; ga0.gram = w.gram;
+  ga0.cptr = cptr; ga0.cusers = cusers; ga0.iinfo = w.iinfo; ga0.islot = w.islot;
+  ga0.gofs = w.gofs; ga0.gram = w.gram;
   ga0.hdr = w.hdr; ga0.counter = &w.hdr->work_counter[1];
 
   // host -> device copy of small per-batch tables; the host buffer is reused
@@ -2820,7 +2827,8 @@ c2_status run_cluster_knn(const int32_t* ptr, const int32_t* items, const Sizes&
                 w.gofs, w.bu_cnt, w.bb_cnt, w.bw_cnt);
       // internal order (members by decreasing profile length) of every
       // count-matrix cluster of the batch
-      C2_LAUNCH(k_order, nb, 256, 0, st, w.gcl, g0, cptr, w.slen, w.ipos, w.iinfo, w.gofs, w.gram);
+      C2_LAUNCH(k_order, nb, 256, 0, st, w.gcl, g0, cptr, w.slen, w.ipos, w.iinfo, w.gofs, w.gram,
+                cusers, w.pptr, w.pitems16 ? w.pptr16 : nullptr, w.islot);
       // strategy of each cluster of the batch: 0 table, 1 tensor cores
       std::vector<int32_t> route(nb, 0);
       if (tc_possible && (tc.W || use_hash) && opt.strategy == C2_STRATEGY_AUTO) {
