@@ -1224,10 +1224,11 @@ __device__ __forceinline__ uint32_t jac_q16(uint32_t c, uint32_t u) {
 // per member.  q = floor(65536 J) is exact and monotone in J, so the k best
 // candidates are among those whose q reaches the row's k-th largest q.
 //  1. One pass over the count row (four candidates per lane and step, one
-//     8-byte load of counts) keeps each lane's two largest estimates of q (a
-//     float quotient, at most one above the exact q).  T0 = the k-th largest
-//     of these 64 estimates, minus one, is at most the row's k-th largest q
-//     (k distinct candidates reach it).
+//     8-byte load of counts; the member itself and the padding are zeroed
+//     per load) keeps each lane's two largest estimates of q (a float
+//     quotient, at most one above the exact q).  T0 = the k-th largest of
+//     these 64 estimates (a bitwise search, one warp sum per bit), minus one,
+//     is at most the row's k-th largest q (k distinct candidates reach it).
 //  2. A second pass stages every candidate with q >= T0 (tested exactly as
 //     c * 2^16 >= T0 * u) -- typically a few more than k, at most kSelStage.
 //  3. In shared memory, when more than 64 are staged: the staged q are
@@ -1239,54 +1240,6 @@ __device__ __forceinline__ uint32_t jac_q16(uint32_t c, uint32_t u) {
 // Rows with more than kSelStage candidates above T0, or more than 64 at or
 // above qk, go through the general keyed path.
 constexpr int kSelStage = 256;
-
-// k-th largest (1-based) of the lanes' values (k <= 32): a warp bitonic sort.
-__device__ __forceinline__ uint32_t warp_kth_largest(uint32_t v, int k) {
-  const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int size = 2; size <= 32; size <<= 1) {
-#pragma unroll
-    for (int j = size >> 1; j > 0; j >>= 1) {
-      const uint32_t o = __shfl_xor_sync(0xffffffffu, v, j);
-      const bool best_first = size == 32 || (lane & size) == 0;
-      const bool lower = (lane & j) == 0;
-      const bool take = (lower == best_first) ? (o > v) : (v > o);
-      v = take ? o : v;
-    }
-  }
-  return __shfl_sync(0xffffffffu, v, k - 1);
-}
-
-// Bitonic sort of one value per lane, largest first.
-__device__ __forceinline__ uint32_t warp_sort32_desc(uint32_t v) {
-  const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int size = 2; size <= 32; size <<= 1) {
-#pragma unroll
-    for (int j = size >> 1; j > 0; j >>= 1) {
-      const uint32_t o = __shfl_xor_sync(0xffffffffu, v, j);
-      const bool best_first = size == 32 || (lane & size) == 0;
-      const bool lower = (lane & j) == 0;
-      v = (lower == best_first) ? max(o, v) : min(o, v);
-    }
-  }
-  return v;
-}
-
-// k-th largest (1-based, k <= 32) of the 64 values a, b held by the lanes:
-// both sorted, the largest 32 of the two are a bitonic sequence, cleaned.
-__device__ __forceinline__ uint32_t warp_kth_largest64(uint32_t a, uint32_t b, int k) {
-  const int lane = threadIdx.x & 31;
-  a = warp_sort32_desc(a);
-  b = warp_sort32_desc(b);
-  uint32_t v = max(a, __shfl_sync(0xffffffffu, b, 31 - lane));
-#pragma unroll
-  for (int j = 16; j > 0; j >>= 1) {
-    const uint32_t o = __shfl_xor_sync(0xffffffffu, v, j);
-    v = (lane & j) == 0 ? max(o, v) : min(o, v);
-  }
-  return __shfl_sync(0xffffffffu, v, k - 1);
-}
 
 // Bucket (largest first) holding the need-th largest of a 256-bucket
 // histogram: lane l holds buckets 255 - 8l .. 248 - 8l.  Returns -1 when the
@@ -1348,57 +1301,84 @@ __global__ void __launch_bounds__(kNT, 6) k_gram_select(const __grid_constant__ 
   const uint2* len4 = reinterpret_cast<const uint2*>(a.gram + a.gofs[c] + (int64_t)M * Mp);
   const uint32_t my = (uint32_t)a.slen[slot];
   const int k = a.k;
-  // 1. each lane's two largest estimates of q
+  // 1. each lane's two largest estimates of q.  Counts of the member itself
+  // (position P) and of the padding past M are cleared per 8-byte load, so
+  // that every position can be treated alike (a zero count estimates 0).
+  const int gP = P >> 2, gL = M4 - 1;
+  const uint32_t maskP = (P & 1) ? 0x0000FFFFu : 0xFFFF0000u;   // clears position P in its word
+  const int rL = M - 4 * gL;                                     // positions of the last load
+  const uint32_t tailx = rL >= 2 ? 0xFFFFFFFFu : 0x0000FFFFu;
+  const uint32_t taily = rL >= 4 ? 0xFFFFFFFFu : (rL == 3 ? 0x0000FFFFu : 0u);
+  auto load_counts = [&](int g) -> uint2 {
+    uint2 cw = row4[g];
+    if (g == gP) {
+      if (P & 2) cw.y &= maskP;
+      else cw.x &= maskP;
+    }
+    if (g == gL) {
+      cw.x &= tailx;
+      cw.y &= taily;
+    }
+    return cw;
+  };
   uint32_t q1 = 0u, q2 = 0u;
 #pragma unroll 2
   for (int g = lane; g < M4; g += 32) {
-    const uint2 cw = row4[g], lw = len4[g];
+    const uint2 cw = load_counts(g), lw = len4[g];
     const uint32_t cq[4] = {cw.x & 0xFFFFu, cw.x >> 16, cw.y & 0xFFFFu, cw.y >> 16};
     const uint32_t lq[4] = {lw.x & 0xFFFFu, lw.x >> 16, lw.y & 0xFFFFu, lw.y >> 16};
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const int p = 4 * g + q;
-      if (p < M && p != P && cq[q]) {
-        const uint32_t u = my + lq[q] - cq[q];
-        // within one of the exact quotient (relative error below 2^-21)
-        const uint32_t qe = __float2uint_rz(__fdividef((float)(cq[q] << 16), (float)u));
-        q2 = max(q2, min(q1, qe));
-        q1 = max(q1, qe);
-      }
+      const uint32_t u = my + lq[q] - cq[q];
+      // within one of the exact quotient (relative error below 2^-21); 0
+      // for a zero count (0 / 0 converts to 0 as well)
+      const uint32_t qe = __float2uint_rz(__fdividef((float)(cq[q] << 16), (float)u));
+      q2 = max(q2, min(q1, qe));
+      q1 = max(q1, qe);
     }
   }
-  const uint32_t kth = warp_kth_largest64(q1, q2, k);   // 0: fewer than k candidates seen
+  // the k-th largest of the 64 estimates (0: fewer than k reach 1), bit by bit
+  uint32_t kth = 0u;
+#pragma unroll
+  for (int bit = 16; bit >= 0; --bit) {
+    const uint32_t c = kth | (1u << bit);
+    if (__reduce_add_sync(0xffffffffu, (uint32_t)(q1 >= c) + (uint32_t)(q2 >= c)) >= (uint32_t)k)
+      kth = c;
+  }
   const uint32_t T0 = kth ? kth - 1u : 0u;
   // 2. stage the candidates with q >= T0 (every candidate when T0 = 0)
   int n = 0;
   bool ok = true;
-  for (int g0 = 0; g0 < M4 && ok; g0 += 32) {
+  for (int g0 = 0; g0 < M4; g0 += 32) {
     const int g = g0 + lane;
     uint2 cw = make_uint2(0u, 0u), lw = make_uint2(0u, 0u);
     if (g < M4) {
-      cw = row4[g];
+      cw = load_counts(g);
       lw = len4[g];
     }
     const uint32_t cq[4] = {cw.x & 0xFFFFu, cw.x >> 16, cw.y & 0xFFFFu, cw.y >> 16};
     const uint32_t lq[4] = {lw.x & 0xFFFFu, lw.x >> 16, lw.y & 0xFFFFu, lw.y >> 16};
+    uint32_t uu[4];
+    unsigned m[4];
+    int tot = 0;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const int p = 4 * g + q;
-      bool pass = false;
-      uint32_t u = 0u;
-      if (p < M && p != P && cq[q]) {
-        u = my + lq[q] - cq[q];
-        pass = (cq[q] << 16) >= T0 * u;
+      uu[q] = my + lq[q] - cq[q];
+      m[q] = __ballot_sync(0xffffffffu, cq[q] != 0u && (cq[q] << 16) >= T0 * uu[q]);
+      tot += __popc(m[q]);
+    }
+    if (n + tot > kSelStage) {
+      ok = false;
+      break;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if ((m[q] >> lane) & 1u) {   // the local index of a staged candidate only
+        const int p = 4 * g + q;
+        stg[n + __popc(m[q] & lanemask_lt())] =
+            make_uint2((uint32_t)p | ((uint32_t)info[p].x << 16), cq[q] | (uu[q] << 16));
       }
-      const unsigned m = __ballot_sync(0xffffffffu, pass);
-      if (n + __popc(m) > kSelStage) {
-        ok = false;
-        break;
-      }
-      if (pass)   // the local index of a staged candidate only
-        stg[n + __popc(m & lanemask_lt())] =
-            make_uint2((uint32_t)p | ((uint32_t)info[p].x << 16), cq[q] | (u << 16));
-      n += __popc(m);
+      n += __popc(m[q]);
     }
   }
   if (!ok) {
