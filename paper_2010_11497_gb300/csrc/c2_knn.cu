@@ -553,28 +553,62 @@ __global__ void __launch_bounds__(NT, MB > 0 ? MB : 1)
     k_gram(GramArgs a, const int32_t* __restrict__ pptr16, const uint16_t* __restrict__ pitems16) {
   constexpr int Q = 32 * W, NWARP = NT / 32;
   extern __shared__ __align__(16) uint32_t T[];
-  __shared__ int4 q_slot[Q];
-  __shared__ int s_work, s_next;
+  // Blocks of 16 warps or more keep two work-item buffers: the next tile
+  // (work counter, cluster, its queries' slot records) is fetched by one warp
+  // while the current tile is walked.  Smaller blocks, where that warp would
+  // be missed in the walk and other resident blocks hide the latency, fetch
+  // each tile when the previous one is done.
+  constexpr bool kAhead = NWARP >= 16;
+  __shared__ int4 q_slot[2][Q];
+  __shared__ int s_wi[2], s_c[2], s_tq[2], s_cbase[2], s_M[2];
+  __shared__ int s_next;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int i = tid; i < (a.n_items + 1) * W; i += NT) T[i] = 0;
   if (tid == 0) s_next = 0;
   const int wbeg = *a.work_begin, nwork = *a.work_end;
   unsigned long long visits = 0;
-  __syncthreads();
-  for (;;) {
-    if (tid == 0) s_work = dev_failed(a.hdr) ? nwork : wbeg + (int)atomicAdd(a.counter, 1u);
-    __syncthreads();
-    const int wi = s_work;
-    if (wi >= nwork) break;
-    const int c = a.work_c[wi], tq = a.work_t[wi];
-    const int cbase = a.cptr[c], M = a.cptr[c + 1] - cbase, Mp = (M + 7) & ~7;
+  auto fetch = [&](int buf) {   // one whole warp
+    int wi = 0;
+    if (lane == 0) wi = dev_failed(a.hdr) ? nwork : wbeg + (int)atomicAdd(a.counter, 1u);
+    wi = __shfl_sync(0xffffffffu, wi, 0);
+    int c = 0, tq = 0, cbase = 0, M = 0;
+    if (wi < nwork) {
+      c = a.work_c[wi];
+      tq = a.work_t[wi];
+      cbase = a.cptr[c];
+      M = a.cptr[c + 1] - cbase;
+    }
     const int nq = min(Q, M - tq * Q);
-    if (tid < Q) q_slot[tid] = tid < nq ? a.islot[cbase + tq * Q + tid] : make_int4(0, 0, 0, -1);
+    for (int j = lane; j < Q; j += 32)
+      q_slot[buf][j] = j < nq ? a.islot[cbase + tq * Q + j] : make_int4(0, 0, 0, -1);
+    if (lane == 0) {
+      s_wi[buf] = wi;
+      s_c[buf] = c;
+      s_tq[buf] = tq;
+      s_cbase[buf] = cbase;
+      s_M[buf] = M;
+    }
+  };
+  if (kAhead) {
+    if (warp == 0) fetch(0);
     __syncthreads();
+  }
+  for (int buf = 0;; buf ^= kAhead ? 1 : 0) {
+    if (!kAhead) {
+      if (warp == 0) fetch(0);
+      __syncthreads();
+    }
+    const int wi = s_wi[buf];
+    if (wi >= nwork) break;
+    const int c = s_c[buf], tq = s_tq[buf];
+    const int cbase = s_cbase[buf], M = s_M[buf], Mp = (M + 7) & ~7;
+    const int nq = min(Q, M - tq * Q);
     for (int j = warp; j < nq; j += NWARP)
-      mark_query<W, P16, false>(T, j >> 5, W == 1 ? 1u << qbit(j) : 1u << (j & 31), q_slot[j],
-                                lane, a, pitems16);
+      mark_query<W, P16, false>(T, j >> 5, W == 1 ? 1u << qbit(j) : 1u << (j & 31),
+                                q_slot[buf][j], lane, a, pitems16);
     __syncthreads();
+    // the other buffer was last read before the previous tile's final barrier
+    if (kAhead && warp == NWARP - 1) fetch(buf ^ 1);
     uint16_t* G0 = a.gram + a.gofs[c];
     uint16_t* Gc = G0 + tq * Q;
     for (;;) {
@@ -662,7 +696,7 @@ __global__ void __launch_bounds__(NT, MB > 0 ? MB : 1)
     }
     __syncthreads();
     for (int j = warp; j < nq; j += NWARP)
-      mark_query<W, P16, true>(T, j >> 5, 0u, q_slot[j], lane, a, pitems16);
+      mark_query<W, P16, true>(T, j >> 5, 0u, q_slot[buf][j], lane, a, pitems16);
     if (tid == 0) s_next = 0;
     __syncthreads();
   }
