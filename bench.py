@@ -413,7 +413,15 @@ def phase_model(dom, phase_ms, phase_calls, stats, w, nnz, pk, W, steps):
                          f"{stats.get('greedy_evaluated', 0)} candidates looked up); {peak_note}"}
     if dom == "gram":
         visits = stats["item_visits_brute"] + stats["item_visits_greedy"]
-        ops_per_visit = 1 + W + 12 * W + 48 * W / 12.0
+        if W == 1:
+            # bit-sliced counts: table load (1), item unpack (1), a carry-save
+            # tree of 15 full adders of 2 logic ops per 16 items (1.875), the
+            # weight-16 carry rippled through at most 12 planes (24 / 16 = 1.5)
+            ops_per_visit = 1 + 1 + 30 / 16.0 + 24 / 16.0
+        else:
+            # 4-bit SWAR counters: table load (1), W words (W), spreading and
+            # adding each word (12 W), flushing every 12 items (48 W / 12)
+            ops_per_visit = 1 + W + 12 * W + 48 * W / 12.0
         achieved = visits / per_build * ops_per_visit / (ms * 1e-3) / 1e12
         return {"kernel": "k_gram<%d>" % W, "phase": dom, "bound": "alu", "achieved": achieved,
                 "peak": alu_peak, "unit": "Tlane-op/s", "frac": achieved / alu_peak,
