@@ -60,19 +60,33 @@ constexpr int kScanFlat = 8192;
 
 template <class T>
 __global__ void __launch_bounds__(256) k_scan_add_flat(T* out, int64_t n, const T* bsum, int nb) {
-  __shared__ T red[256];
+  __shared__ T red[8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   T acc = 0;
   for (int j = threadIdx.x; j < (int)blockIdx.x; j += 256) acc += bsum[j];
-  red[threadIdx.x] = acc;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) red[warp] = acc;
   __syncthreads();
-  for (int o = 128; o > 0; o >>= 1) {
-    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-    __syncthreads();
-  }
-  const T add = red[0];
+  T add = 0;
+#pragma unroll
+  for (int w = 0; w < 8; ++w) add += red[w];
   const int64_t base = (int64_t)blockIdx.x * kScanTile;
-  for (int i = threadIdx.x; i < kScanTile; i += 256)
-    if (base + i < n) out[base + i] += add;
+  constexpr int V = 16 / sizeof(T);   // elements per 16-byte access
+  if (base + kScanTile <= n && (reinterpret_cast<uintptr_t>(out + base) & 15) == 0) {
+    // a whole, aligned tile: 16-byte loads and stores
+    uint4* o4 = reinterpret_cast<uint4*>(out + base);
+    for (int i = threadIdx.x; i < kScanTile / V; i += 256) {
+      uint4 q = o4[i];
+      T* e = reinterpret_cast<T*>(&q);
+#pragma unroll
+      for (int v = 0; v < V; ++v) e[v] += add;
+      o4[i] = q;
+    }
+  } else {
+    for (int i = threadIdx.x; i < kScanTile; i += 256)
+      if (base + i < n) out[base + i] += add;
+  }
   if ((int)blockIdx.x == nb - 1 && threadIdx.x == 0) out[n] = add + bsum[nb - 1];
 }
 
