@@ -51,3 +51,15 @@ def test_models_match_hand_computation():
     # shares add up to one and the dominant phase comes first
     assert abs(sum(r["share"] for r in rows) - 1.0) < 1e-9
     assert rows[0]["phase"] == "greedy_rounds"
+
+
+def test_two_word_table_model():
+    # two-word tables keep 4-bit SWAR counters: 1 + W + 12 W + 48 W / 12 = 35
+    # lane-ops per item visit at W = 2
+    ms = dict(PER_BUILD_MS)
+    calls = {k: 1 for k in ms}
+    _, rows = bench.roofline(ms, calls, STATS, W10, 10_034_432, PEAKS, "measured", 2, 1)
+    by = {r["phase"]: r for r in rows}
+    ach = STATS["item_visits_greedy"] * 35 / (PER_BUILD_MS["gram"] * 1e-3) / 1e12
+    assert abs(by["gram"]["achieved"] - ach) < 1e-9 * ach
+    assert by["gram"]["kernel"] == "k_gram<2>"
